@@ -1,0 +1,330 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself: each check is a hand-worked
+example, a closed form, an independent brute force, a theorem's bound or an
+eigen-decomposition identity.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _tiles(n, nb):
+    return (n + nb - 1) // nb
+
+
+def _np_leaf_norms_int(A, nb):
+    """Tile norms for integer-valued inputs (every sum is exact, so the order does not matter)."""
+    n = A.shape[0]
+    m = _tiles(n, nb)
+    P = np.zeros((m * nb, m * nb))
+    P[:n, :n] = A
+    return (P.reshape(m, nb, m, nb) ** 2).sum(axis=(1, 3))
+
+
+def _decaying_int(n, seed, length=4.0, amp=6):
+    """Integer matrix with an exponentially decaying envelope: tile norms spread over orders of magnitude,
+    and every FP64 sum of products is exact."""
+    rng = np.random.default_rng(seed)
+    i = np.arange(n)
+    env = np.floor(amp * np.exp(-np.abs(i[:, None] - i[None, :]) / length) + 0.5)
+    return env * rng.integers(-2, 3, size=(n, n))
+
+
+# --------------------------------------------------------------------------- hand-worked example
+
+
+def test_worked_example_4x4():
+    g = json.load(open(os.path.join(GOLD, "spamm_worked_4x4.json")))
+    A = np.array(g["A"], dtype=np.float64)
+    for case in g["cases"]:
+        C, cnt = oracle.spamm(A, A, g["nb"], case["tau"])
+        np.testing.assert_array_equal(C, np.array(case["C"], dtype=np.float64))
+        tasks, _ = oracle.cull(A, A, g["nb"], case["tau"])
+        want = sorted((i, j, k) for i, j, k in case["tasks_ikj"])
+        assert sorted(map(tuple, tasks.tolist())) == want
+        assert cnt == len(want)
+        # the list is ordered by output tile (i, k), then j ascending
+        assert [tuple(t) for t in tasks.tolist()] == sorted(want, key=lambda t: (t[0], t[2], t[1]))
+
+
+# --------------------------------------------------------------------------- P1: tau = 0 is the dense product
+
+
+@pytest.mark.parametrize("n,nb", [(16, 4), (37, 8), (64, 16), (100, 32), (5, 8)])
+def test_tau_zero_is_dense_product_bitwise(n, nb):
+    A = synth.integer_matrix(n, seed=1)
+    B = synth.integer_matrix(n, seed=2)
+    C, cnt = oracle.spamm(A, B, nb, 0.0)
+    exact = (A.astype(np.int64) @ B.astype(np.int64)).astype(np.float64)
+    np.testing.assert_array_equal(C, exact)
+    assert cnt == _tiles(n, nb) ** 3
+
+
+# --------------------------------------------------------------------------- P2: tile-level closed form of the lemma
+
+
+@pytest.mark.parametrize("n,nb,tau", [(64, 8, 1e-2), (64, 8, 5e-2), (96, 16, 2e-2), (70, 8, 3e-2), (128, 16, 1e-3)])
+def test_tile_closed_form(n, nb, tau):
+    """C_ik = sum_j A_ij B_jk [nu_A(i,j) nu_B(j,k) >= tau^2 nu_A nu_B] (the lemma of the Proposition at tile
+    granularity; the recursion is equivalent to this flat test because parent norms dominate their children)."""
+    A = _decaying_int(n, 3)
+    B = _decaying_int(n, 4, length=6.0)
+    m = _tiles(n, nb)
+    na, nbm = _np_leaf_norms_int(A, nb), _np_leaf_norms_int(B, nb)
+    thr = ((tau * tau) * na.sum()) * nbm.sum()
+    P = m * nb
+    Ap = np.zeros((P, P), dtype=np.int64)
+    Bp = np.zeros((P, P), dtype=np.int64)
+    Ap[:n, :n] = A
+    Bp[:n, :n] = B
+    want = np.zeros((P, P), dtype=np.int64)
+    kept = 0
+    for i in range(m):
+        for k in range(m):
+            for j in range(m):
+                if not (na[i, j] * nbm[j, k] < thr):
+                    kept += 1
+                    want[i * nb:(i + 1) * nb, k * nb:(k + 1) * nb] += \
+                        Ap[i * nb:(i + 1) * nb, j * nb:(j + 1) * nb] @ Bp[j * nb:(j + 1) * nb, k * nb:(k + 1) * nb]
+    C, cnt = oracle.spamm(A, B, nb, tau)
+    assert 0 < cnt < m ** 3, "choose tau so that the cull is not trivial"
+    assert cnt == kept
+    np.testing.assert_array_equal(C, want[:n, :n].astype(np.float64))
+
+
+def test_elementwise_lemma_nb1():
+    """At N_b = 1 every culled term satisfies |a_il||b_lj| < tau ||a|| ||b|| and every kept one does not."""
+    n = 24
+    A = _decaying_int(n, 5, length=3.0)
+    B = _decaying_int(n, 6, length=3.0)
+    tau = 0.02
+    C, _ = oracle.spamm(A, B, 1, tau)
+    tab2 = (tau * tau) * (A * A).sum() * (B * B).sum()
+    keep = (A[:, :, None] ** 2) * (B[None, :, :] ** 2) >= tab2          # [i, l, j]
+    want = np.einsum("il,lj,ilj->ij", A, B, keep.astype(np.float64))
+    np.testing.assert_array_equal(C, want)
+
+
+# --------------------------------------------------------------------------- P3: recursion == brute force
+
+
+@pytest.mark.parametrize("n,nb,tau", [(64, 4, 1e-2), (100, 8, 1e-3), (128, 8, 5e-2), (33, 4, 0.0), (200, 16, 1e-3)])
+def test_recursive_cull_equals_flat(n, nb, tau):
+    A = synth.decay_matrix(n, seed=7, length=5.0)
+    B = synth.decay_matrix(n, seed=8, length=9.0)
+    rec, thr = oracle.cull(A, B, nb, tau)
+    flat = oracle.cull_flat(A, B, nb, tau)
+    np.testing.assert_array_equal(rec, flat)
+    # independent numpy brute force with the oracle's own leaf norms and threshold
+    la, lb = oracle.leaf_norms(A, nb), oracle.leaf_norms(B, nb)
+    keep = ~((la[:, :, None] * lb[None, :, :]) < thr)           # [i, j, k]
+    ii, jj, kk = np.nonzero(keep)
+    brute = np.stack([ii, jj, kk], 1)
+    brute = brute[np.lexsort((brute[:, 1], brute[:, 2], brute[:, 0]))]
+    np.testing.assert_array_equal(rec, brute)
+
+
+def test_norm_tree_levels():
+    """Each level is the sum of its existing children; the root is ||A||_F^2; ragged grids have no phantom nodes."""
+    n, nb = 77, 8
+    A = synth.integer_matrix(n, seed=9)
+    levels = oracle.norm_tree(A, nb)
+    m = _tiles(n, nb)
+    assert levels[-1].shape == (m, m)
+    np.testing.assert_array_equal(levels[-1], _np_leaf_norms_int(A, nb))
+    assert levels[0].shape == (1, 1) and levels[0][0, 0] == (A * A).sum()
+    for l in range(len(levels) - 1):
+        child = levels[l + 1]
+        d = levels[l].shape[0]
+        pad = np.zeros((2 * d, 2 * d))
+        pad[:child.shape[0], :child.shape[1]] = child
+        np.testing.assert_array_equal(levels[l], pad.reshape(d, 2, d, 2).sum(axis=(1, 3)))
+
+
+# --------------------------------------------------------------------------- P4: the Proposition's bounds
+
+
+@pytest.mark.parametrize("tau", [1e-1, 3e-2, 1e-2, 1e-3])
+@pytest.mark.parametrize("nb", [1, 4, 16])
+def test_proposition_bounds(tau, nb):
+    n = 64
+    A = synth.decay_matrix(n, seed=11, length=4.0)
+    B = synth.decay_matrix(n, seed=12, length=6.0)
+    C, _ = oracle.spamm(A, B, nb, tau)
+    D = C - A @ B
+    tab = tau * np.linalg.norm(A) * np.linalg.norm(B)
+    slack = 1e-12 * np.abs(A) .sum() * np.abs(B).sum()     # rounding of the two products
+    assert np.abs(D).max() <= n * tab + slack
+    assert np.linalg.norm(D) <= n * n * tab + slack
+    # sharper: the error is at most the sum over culled tile pairs of ||A_ij|| ||B_jk||
+    tasks, _ = oracle.cull(A, B, nb, tau)
+    la, lb = oracle.leaf_norms(A, nb), oracle.leaf_norms(B, nb)
+    m = la.shape[0]
+    kept = np.zeros((m, m, m), dtype=bool)
+    kept[tasks[:, 0], tasks[:, 1], tasks[:, 2]] = True
+    cullsum = (np.sqrt(la[:, :, None] * lb[None, :, :]) * (~kept)).sum()
+    assert np.linalg.norm(D) <= cullsum * (1 + 1e-12) + slack
+
+
+def test_normwise_tau_bound_is_not_a_theorem():
+    """||A(x)B - AB|| <= tau ||A|| ||B|| without the n^2 factor fails on the all-ones matrix (reading of the bound)."""
+    n = 16
+    A = np.ones((n, n))
+    tau = 1.01 / (n * n)        # every leaf |a||b| = 1 < tau * n^2 at N_b = 1
+    C, cnt = oracle.spamm(A, A, 1, tau)
+    assert cnt == 0 and not C.any()
+    err = np.linalg.norm(C - A @ A)
+    tab = tau * np.linalg.norm(A) ** 2
+    assert err > 10 * tab
+    assert err <= n * n * tab
+
+
+# --------------------------------------------------------------------------- P5: NS iterates in the eigenbasis
+
+
+def _scalar_ns(lam, iters, order=0):
+    y = lam.copy()
+    z = np.ones_like(lam)
+    x = lam.copy()
+    for _ in range(iters):
+        t = 1.5 - 0.5 * x
+        if order == 0:
+            y = t * y
+            z = z * t
+        else:
+            y = y * t
+            z = t * z
+        x = y * z
+    return y, z
+
+
+@pytest.mark.parametrize("iters", [1, 2, 5, 12])
+def test_ns_iterates_match_eigen_recursion(iters):
+    n, nb = 40, 8
+    S = synth.gaussian_lattice(n, sigma=0.7, seed=0)
+    c = np.abs(S).sum(1).max()
+    lam, Q = np.linalg.eigh(S / c)
+    y, z = _scalar_ns(lam, iters)
+    r = oracle.sqrt_invsqrt(S, nb, 0.0, iters)
+    Yk = (Q * (y * math.sqrt(c))) @ Q.T
+    Zk = (Q * (z / math.sqrt(c))) @ Q.T
+    assert r["iters"] == iters
+    assert np.linalg.norm(r["Y"] - Yk) <= 1e-12 * np.linalg.norm(Yk)
+    assert np.linalg.norm(r["Z"] - Zk) <= 1e-11 * np.linalg.norm(Zk)
+
+
+def test_ns_diagonal_is_scalar_recursion_bitwise():
+    d = np.array([0.9, 0.05, 0.3, 1.7, 0.011, 0.6, 2.0, 0.25, 0.125, 1.0, 0.75, 0.4])
+    S = np.diag(d)
+    c = d.max()
+    for order in (0, 1):
+        r = oracle.sqrt_invsqrt(S, 4, 0.0, 9, order=order)
+        y, z = _scalar_ns(d / c, 9, order)
+        np.testing.assert_array_equal(np.diag(r["Y"]), y * math.sqrt(c))
+        np.testing.assert_array_equal(np.diag(r["Z"]), z / math.sqrt(c))
+        assert not (r["Y"] - np.diag(np.diag(r["Y"]))).any()
+
+
+# --------------------------------------------------------------------------- P6/P7: convergence, KMS
+
+
+def test_sqrt_2x2_closed_form():
+    g = json.load(open(os.path.join(GOLD, "sqrt_2x2.json")))
+    S = np.array(g["S"], dtype=np.float64)
+    ev = {"sqrt": math.sqrt}
+    Yw = np.array([[eval(e, {"__builtins__": {}}, ev) for e in row] for row in g["sqrt_expr"]])
+    Zw = np.array([[eval(e, {"__builtins__": {}}, ev) for e in row] for row in g["invsqrt_expr"]])
+    r = oracle.sqrt_invsqrt(S, 1, 0.0, 40)
+    np.testing.assert_allclose(r["Y"], Yw, rtol=0, atol=4e-16 * 4)
+    np.testing.assert_allclose(r["Z"], Zw, rtol=0, atol=4e-16 * 4)
+
+
+@pytest.mark.parametrize("kind", ["gauss", "kms"])
+def test_ns_converges_to_square_roots(kind):
+    n, nb = 96, 16
+    S = synth.gaussian_lattice(n, 0.6, seed=0) if kind == "gauss" else synth.kms(n, 0.9)
+    r = oracle.sqrt_invsqrt(S, nb, 0.0, 30)
+    lam, Q = np.linalg.eigh(S)
+    Sh = (Q * np.sqrt(lam)) @ Q.T
+    Smh = (Q / np.sqrt(lam)) @ Q.T
+    Y, Z = r["Y"], r["Z"]
+    kappa = lam.max() / lam.min()
+    tol = 1e-13 * kappa
+    assert np.linalg.norm(Y - Sh) <= tol * np.linalg.norm(Sh)
+    assert np.linalg.norm(Z - Smh) <= tol * np.linalg.norm(Smh)
+    assert np.linalg.norm(Y @ Z - np.eye(n)) <= tol * math.sqrt(n)
+    assert oracle.residual(S, Z) <= tol * math.sqrt(n)
+    assert np.linalg.norm(Y @ Y - S) <= tol * np.linalg.norm(S)
+    assert abs(r["t_hist"][-1]) <= 1e-14
+
+
+def test_kms_inverse_closed_form():
+    n, rho = 64, 0.9
+    S = synth.kms(n, rho)
+    Sinv = synth.kms_inverse(n, rho)
+    # the closed form itself: S * Sinv = I
+    np.testing.assert_allclose(S @ Sinv, np.eye(n), atol=1e-12)
+    r = oracle.sqrt_invsqrt(S, 16, 0.0, 30)
+    Z = r["Z"]
+    assert np.linalg.norm(Z @ Z - Sinv) <= 1e-11 * np.linalg.norm(Sinv)
+    # spectrum of KMS lies in [(1-rho)/(1+rho), (1+rho)/(1-rho)]
+    lam = np.linalg.eigvalsh(S)
+    assert lam.min() >= (1 - rho) / (1 + rho) - 1e-12 and lam.max() <= (1 + rho) / (1 - rho) + 1e-12
+
+
+# --------------------------------------------------------------------------- P8: padding invariance, order
+
+
+@pytest.mark.parametrize("tau", [0.0, 1e-3])
+def test_zero_padding_invariance(tau):
+    n, nb = 50, 16
+    A = synth.decay_matrix(n, seed=21)
+    B = synth.decay_matrix(n, seed=22)
+    C, _ = oracle.spamm(A, B, nb, tau)
+    P = 64
+    Ap = np.zeros((P, P)); Ap[:n, :n] = A
+    Bp = np.zeros((P, P)); Bp[:n, :n] = B
+    Cp, _ = oracle.spamm(Ap, Bp, nb, tau)
+    np.testing.assert_array_equal(Cp[:n, :n], C)
+    assert not Cp[n:, :].any() and not Cp[:, n:].any()
+
+
+def test_transpose_consistency_integer():
+    n, nb, tau = 72, 8, 2e-2
+    A = _decaying_int(n, 31)
+    B = _decaying_int(n, 32, length=7.0)
+    C, c1 = oracle.spamm(A, B, nb, tau)
+    Ct, c2 = oracle.spamm(B.T.copy(), A.T.copy(), nb, tau)
+    assert c1 == c2
+    np.testing.assert_array_equal(C.T, Ct)
+
+
+def test_order_variants_agree():
+    n, nb = 64, 8
+    S = synth.gaussian_lattice(n, 0.7, seed=2)
+    a = oracle.sqrt_invsqrt(S, nb, 0.0, 25, order=0)
+    b = oracle.sqrt_invsqrt(S, nb, 0.0, 25, order=1)
+    assert np.linalg.norm(a["Z"] - b["Z"]) <= 1e-12 * np.linalg.norm(a["Z"])
+
+
+def test_tol_stop_and_regularisation():
+    n, nb = 64, 16
+    S = synth.kms(n, 0.8)
+    r = oracle.sqrt_invsqrt(S, nb, 0.0, 50, tol_t=1e-12)
+    assert r["iters"] < 50 and abs(r["t_hist"][-1]) <= 1e-12
+    mu_rel = 1e-3
+    c0 = oracle.gershgorin(S)
+    r2 = oracle.sqrt_invsqrt(S, nb, 0.0, 40, mu_rel=mu_rel)
+    Smu = S + mu_rel * c0 * np.eye(n)
+    lam, Q = np.linalg.eigh(Smu)
+    assert np.linalg.norm(r2["Z"] - (Q / np.sqrt(lam)) @ Q.T) <= 1e-12 * np.linalg.norm(r2["Z"]) * 10
+    assert r2["scale_c"] == pytest.approx(c0 + mu_rel * c0, rel=1e-15)
