@@ -1,0 +1,375 @@
+#!/usr/bin/env python
+"""Benchmark of the SpAMM dual-channel Newton-Schulz solve (S^{1/2} and S^{-1/2}).
+
+Workload (one "step" = one full solve): Kac-Murdock-Szego matrix
+S_ij = 0.9^|i-j|, N = 4096, leaf tiles N_b = 64, 30 iterations of the
+dual-channel iteration with SpAMM products at tau (y channel tau_s =
+0.01 tau).  The headline tau is the largest power of ten for which the
+oracle's solve meets ||Z S Z - I||_F <= 1e-8 at this size; the tau sweep
+{1e-4, 1e-6, 1e-8} (task counts, residual, solves/s) is reported beside it.
+
+Prints one JSON line.  ``--impl reference`` times the CPU oracle instead.
+Multi-GPU (torchrun): every rank solves its own copy (independent problems,
+weak scaling, no collective on the data path); value = all solves / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N = 4096
+RHO = 0.9
+LEAF = 64
+MAXIT = 30
+TAU_HEADLINE = 1e-14
+TAU_SWEEP = (1e-4, 1e-6, 1e-8)
+GATE = 1e-8
+METRIC = "NS sqrt/invsqrt solves/s at ||ZSZ-I||_F<=1e-8 (KMS N=4096)"
+UNIT = "solves/s"
+
+
+def workload_name(tau: float, precision: str) -> str:
+    return (f"KMS rho={RHO} N={N} N_b={LEAF} tau={tau:g} tau_s={0.01 * tau:g} {MAXIT} dual-channel NS iterations, "
+            f"{precision} leaf products")
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.th = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.th:
+            self.th.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle timing
+
+
+def oracle_solve_rate(S, tau: float, budget_s: float, min_solves: int = 1) -> tuple[float, int, float]:
+    import oracle
+    t0 = time.perf_counter()
+    cnt = 0
+    while True:
+        oracle.sqrt_invsqrt(S, LEAF, tau, MAXIT)
+        cnt += 1
+        el = time.perf_counter() - t0
+        if cnt >= min_solves and el >= budget_s:
+            break
+        if el > 0 and cnt >= min_solves and el / cnt * (cnt + 1) > 3 * budget_s:
+            break
+    return cnt / el, cnt, el
+
+
+def run_reference(args, ws, rank):
+    """The oracle as it stands, timed on this host's cores on the bench workload."""
+    if rank != 0:
+        return 0
+    import oracle
+    import synth
+    oracle.build()
+    S = synth.kms(N, RHO)
+    tau = args.tau
+    for _ in range(args.warmup):
+        oracle.sqrt_invsqrt(S, LEAF, tau, MAXIT)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.sqrt_invsqrt(S, LEAF, tau, MAXIT)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    v = len(times) / tot
+    cores = oracle.num_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(tau, "FP64 CPU oracle"), "n": N, "leaf": LEAF, "tau": tau,
+                       "maxit": MAXIT},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{len(times)} full solves of the workload on {cores} OpenMP threads"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+
+def measure_dgemm_tflops(torch, dev) -> float:
+    """cuBLAS FP64 GEMM throughput on this GPU (denominator of the FP64 roofline)."""
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device=dev)
+    b = torch.randn(n, n, dtype=torch.float64, device=dev)
+    for _ in range(2):
+        torch.matmul(a, b)
+    torch.cuda.synchronize()
+    best = math.inf
+    for _ in range(3):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 1e3)
+    del a, b
+    return 2.0 * n ** 3 / best / 1e12
+
+
+def run_gpu(args, ws, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_1508_05856_gb300 as sp
+    import synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    sp.lib()
+    prec = sp.EMU64 if args.precision == "emu64" else sp.FP64
+    tau = args.tau
+
+    S = synth.kms(N, RHO)
+    Sd = torch.from_numpy(S).to(dev)
+    Yd = torch.empty_like(Sd)
+    Zd = torch.empty_like(Sd)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def solve(t, profile=False, residual=False):
+        return sp.sqrt_invsqrt(Sd, t, MAXIT, leaf=LEAF, precision=prec, Y=Yd, Z=Zd, profile=profile,
+                               residual=residual)
+
+    # verification solve (untimed): residual against the gate, FP64 dense
+    _, _, vst = solve(tau, residual=True)
+    for _ in range(max(args.warmup, 3)):
+        solve(tau)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    l0 = sp.kernel_launches()
+    step_s = []
+    gemm_ms = 0.0
+    gemm_launches = 0
+    gemm_flops = 0.0
+    for _ in range(args.steps):
+        flush.zero_()                       # L2 (129 MB) flushed between timed solves
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, _, st = solve(tau, profile=True)
+        e1.record(stream)
+        e1.synchronize()
+        step_s.append(e0.elapsed_time(e1) / 1e3)
+        gemm_ms += st["gemm_ms"]
+        gemm_launches += st["gemm_launches"]
+        gemm_flops += st["flops"]
+    launches = sp.kernel_launches() - l0
+    barrier()
+    clk = clocks.stop()
+    tot = sum(step_s)
+    if ws > 1:
+        t = torch.tensor([tot], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_max = float(t.item())
+    else:
+        tot_max = tot
+    value = ws * args.steps / tot_max
+
+    # end to end through the C ABI with pinned host buffers (H2D of S, D2H of Y and Z inside the region)
+    Sh = torch.from_numpy(S).pin_memory()
+    Yh = torch.empty((N, N), dtype=torch.float64).pin_memory()
+    Zh = torch.empty((N, N), dtype=torch.float64).pin_memory()
+    sp.sqrt_invsqrt(Sh, tau, MAXIT, leaf=LEAF, precision=prec, Y=Yh, Z=Zh)
+    e2e_t = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sp.sqrt_invsqrt(Sh, tau, MAXIT, leaf=LEAF, precision=prec, Y=Yh, Z=Zh)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_tot = sum(e2e_t)
+    if ws > 1:
+        t = torch.tensor([e2e_tot], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_tot = float(t.item())
+
+    # tau sweep (the configuration's cull-count / error study)
+    sweep = []
+    if not args.no_sweep:
+        for ts in TAU_SWEEP:
+            _, _, rs = solve(ts, residual=True)
+            tt = []
+            for _ in range(3):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                solve(ts)
+                e1.record(stream)
+                e1.synchronize()
+                tt.append(e0.elapsed_time(e1) / 1e3)
+            sweep.append({"tau": ts, "solves_per_s": 3 / sum(tt), "resid_F": rs["resid_F"],
+                          "tasks": rs["tasks_total"], "volume_pct": 100.0 * rs["tasks_total"] / rs["tasks_dense"],
+                          "gate_met": bool(rs["resid_F"] <= GATE)})
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    # roofline of the dominant kernel (the leaf-product kernel)
+    avg_ms = gemm_ms / max(1, gemm_launches)
+    flops_per_launch = gemm_flops / max(1, gemm_launches)
+    achieved = flops_per_launch / (avg_ms / 1e3) / 1e12 if avg_ms > 0 else 0.0
+    if prec == sp.FP64:
+        peak = measure_dgemm_tflops(torch, dev)
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if peak else None, "traffic": None,
+                "kernel": f"k_gemm_f64<{LEAF}>",
+                "peak_source": "cuBLAS FP64 GEMM 4096^3 measured in this run (FP64 pipe)",
+                "share_of_step": gemm_ms / 1e3 / tot if tot else None}
+    else:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+        peak = peaks.get("bf16_tflops", 1900.0)
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if peak else None, "traffic": None, "kernel": "emu64 leaf products",
+                "peak_source": "bf16_tflops of measured" if peaks else "fallback 1.9 PFLOP/s",
+                "share_of_step": gemm_ms / 1e3 / tot if tot else None}
+
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        import oracle
+        oracle.build()
+        rate, cnt, el = oracle_solve_rate(S, tau, budget_s=args.cpu_budget)
+        cpu = {"value": rate, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"{cnt} full solve(s) of the same workload in {el:.1f} s"}
+
+    nbytes = N * N * 8
+    p50 = statistics.median(step_s) * 1e3
+    p99 = sorted(step_s)[min(len(step_s) - 1, int(math.ceil(0.99 * len(step_s))) - 1)] * 1e3
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == sp.FP64 else "bf16-split",
+            "data": "synthetic",
+            "config": {"workload": workload_name(tau, args.precision.upper()), "n": N, "leaf": LEAF, "tau": tau,
+                       "tau_s": 0.01 * tau, "maxit": MAXIT, "precision": args.precision,
+                       "l2": "flushed by a 256 MB write before every timed solve",
+                       "parallelism": f"replicas x{ws}"},
+            "latency_ms": {"p50": p50, "p99": p99},
+            "resid_F": vst["resid_F"], "gate": GATE, "gate_met": bool(vst["resid_F"] <= GATE),
+            "tasks_per_solve": vst["tasks_total"], "volume_pct": 100.0 * vst["tasks_total"] / vst["tasks_dense"],
+            "t_final": vst["t_final"],
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": ws * args.steps / e2e_tot, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                    "d2h_bytes_per_step": 2 * nbytes},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "tau_sweep": sweep}
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp64", "emu64"], default="fp64")
+    ap.add_argument("--tau", type=float, default=TAU_HEADLINE)
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle time for cpu_baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+    return run_gpu(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,172 @@
+/*
+ * spamm.h -- C ABI of the GB300 SpAMM / Newton-Schulz library (libspamm.so).
+ *
+ * The method is from Challacombe, Haut & Bock, "A N-Body Solver for Square
+ * Root Iteration":
+ *   - SpAMM product A (x)_tau B, Eq. (newspamm): both operands are held as a
+ *     quadtree of Frobenius norms; a sub-product a^i . b^i is culled when
+ *     ||a^i|| ||b^i|| < tau ||A|| ||B|| (relative criterion, root norms of the
+ *     whole operands), and only the surviving leaf-tile products are formed.
+ *   - Dual-channel Newton-Schulz iteration, Eq. (cannonical), with the NS map
+ *     h[x] = (3 - x)/2 (alpha = 1, Sec. 4.2): from S scaled into (0,1],
+ *     X0 = Y0 = S, Z0 = I;  T = h[X];  Y <- T (x)_{tau_s} Y;  Z <- Z (x)_tau T;
+ *     X <- Y (x)_tau Z;  Y -> S^{1/2}, Z -> S^{-1/2}.  tau_s is the tighter
+ *     threshold of the "sensitive" y channel (Sec. 4.1, tau_s ~ 0.01 tau).
+ *   - Trace error t_k = (n - tr X_k)/n monitors convergence (Sec. 4.2).
+ *
+ * Conventions for every entry point:
+ *   - Matrices are dense, row-major, n x n, double precision.
+ *   - A matrix pointer may address host memory or device memory of the
+ *     current CUDA device; the library tells them apart with
+ *     cudaPointerGetAttributes and stages host data through its own device
+ *     buffers.  The caller owns every pointer it passes; inputs are not
+ *     modified; the call returns after the results are written.
+ *   - The library owns its scratch space (tile buffers, norm trees, task
+ *     lists), cached per problem size and released by spamm_release().
+ *   - Work runs on opts->stream (a cudaStream_t; NULL is the legacy default
+ *     stream).  Calls are thread safe; concurrent calls use separate scratch.
+ *   - Leaf tiles are N_b x N_b with N_b in {32, 64, 128}.  The tile grid has
+ *     m = ceil(n / N_b) tiles per side; edge tiles are zero padded and
+ *     quadtree nodes that cover no tile do not exist.
+ *   - Return value: SPAMM_OK (0) or a negative SPAMM_ERR_* code; no C++
+ *     exception crosses this interface.  spamm_last_error() gives a message
+ *     for the calling thread's most recent failure.
+ */
+#ifndef SPAMM_H
+#define SPAMM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define SPAMM_OK 0
+#define SPAMM_ERR_ARG (-1)           /* bad size, tau < 0 or NaN, bad option    */
+#define SPAMM_ERR_NOMEM (-2)         /* device allocation failed                 */
+#define SPAMM_ERR_DIVERGED (-3)      /* t_k not finite or |t_k| >= 1: the
+                                        iteration left its basin (Sec. 5.3);
+                                        outputs are still written              */
+#define SPAMM_ERR_NOTCONVERGED (-4)  /* tol_t > 0 and maxit reached with
+                                        |t_k| > tol_t; outputs are written      */
+#define SPAMM_ERR_TIMEOUT (-5)       /* a bounded device-side wait expired      */
+#define SPAMM_ERR_ADMIT (-6)         /* server: request footprint exceeds the
+                                        memory budget                          */
+#define SPAMM_ERR_CUDA (-7)          /* a CUDA runtime call failed              */
+#define SPAMM_ERR_UNSUPPORTED (-8)   /* option or size this build does not do   */
+#define SPAMM_ERR_NOTFOUND (-9)      /* server: unknown request id              */
+
+/* ---- arithmetic of the leaf-tile products ------------------------------ */
+#define SPAMM_FP64 0   /* FP64 tiles, FP64 fused multiply-add                  */
+#define SPAMM_EMU64 1  /* FP64 tiles split into 8-bit BF16 slices multiplied on
+                          the tensor cores with exact FP32 partial sums and
+                          64-bit accumulation (FP64-class result)              */
+
+/* ---- order of the two channel products --------------------------------- */
+#define SPAMM_ORDER_PAPER 0       /* Y <- T Y, Z <- Z T, X <- Y Z (as printed)  */
+#define SPAMM_ORDER_TRANSPOSED 1  /* Y <- Y T, Z <- T Z, X <- Z Y: the exact
+                                     transpose of the printed iteration        */
+
+typedef struct spamm_opts {
+    int leaf;          /* N_b: 32, 64 or 128; 0 selects 64                      */
+    int precision;     /* SPAMM_FP64 or SPAMM_EMU64                             */
+    double tau_s;      /* y-channel threshold; < 0 selects 0.01 * tau           */
+    double mu_rel;     /* Tikhonov shift S + mu I (Sec. 6) with
+                          mu = mu_rel * Gershgorin bound of S; 0 = none        */
+    double tol_t;      /* stop once |t_k| <= tol_t; 0 runs exactly maxit steps  */
+    int order;         /* SPAMM_ORDER_PAPER or SPAMM_ORDER_TRANSPOSED           */
+    int residual;      /* nonzero: also compute ||Z S Z - I||_F (FP64, dense)   */
+    int profile;       /* nonzero: time every leaf-product kernel with CUDA
+                          events on the call's stream (stats->gemm_ms)         */
+    void* stream;      /* cudaStream_t; NULL = legacy default stream            */
+} spamm_opts;
+
+typedef struct spamm_stats {
+    int iters;                 /* iterations run                                */
+    double t_final;            /* t_k of the last iteration                     */
+    double resid_F;            /* ||Z S Z - I||_F if opts->residual, else -1    */
+    double scale_c;            /* Gershgorin bound c used to scale S into (0,1] */
+    long long tasks_total;     /* surviving leaf products over the whole call   */
+    long long tasks_dense;     /* leaf products without culling (m^3 per product) */
+    double flops;              /* 2 N_b^3 per surviving leaf product            */
+    double* t_hist;            /* in: NULL or caller array of maxit doubles      */
+    long long* task_hist;      /* in: NULL or caller array of 3*maxit counts
+                                  (y, z, x products of each iteration)          */
+    double gemm_ms;            /* opts->profile: summed duration of the
+                                  leaf-product kernels (CUDA events), else 0    */
+    long long gemm_launches;   /* leaf-product kernel launches of the call       */
+} spamm_stats;
+
+/* Fill *opts with defaults: leaf 64, SPAMM_FP64, tau_s = 0.01 tau, no shift,
+ * fixed iteration count, paper order, no residual, default stream. */
+void spamm_opts_init(spamm_opts* opts);
+
+/*
+ * C = A (x)_tau B, Eq. (newspamm), with the relative criterion
+ * ||A_ij||_F ||B_jk||_F < tau ||A||_F ||B||_F (evaluated squared, in FP64;
+ * strict "<" culls).  tau = 0 gives the dense product.  Per output tile the
+ * surviving products are summed with j ascending.  opts may be NULL
+ * (defaults); stats may be NULL.
+ * Errors: SPAMM_ERR_ARG for n <= 0, tau < 0 or NaN, or a bad leaf size.
+ */
+int spamm_multiply(const double* A, const double* B, double* C, int n, double tau,
+                   const spamm_opts* opts, spamm_stats* stats);
+
+/*
+ * Y ~ S^{1/2} and Z ~ S^{-1/2} for symmetric positive definite S by the
+ * dual-channel iteration of Eq. (cannonical) (see the top of this file).
+ * S is scaled by its Gershgorin bound c (plus mu, Sec. 6) into (0,1]; the
+ * results are unscaled as Y * sqrt(c), Z / sqrt(c).  Runs maxit iterations,
+ * or fewer when opts->tol_t > 0.  Y and Z are written even when the status
+ * is SPAMM_ERR_DIVERGED or SPAMM_ERR_NOTCONVERGED.
+ */
+int spamm_sqrt_invsqrt(const double* S, int n, double tau, int maxit, double* Y, double* Z,
+                       const spamm_opts* opts, spamm_stats* stats);
+
+/*
+ * `count` independent problems of (possibly) different sizes, each exactly
+ * as spamm_sqrt_invsqrt(S[q], n[q], tau[q], maxit, Y[q], Z[q], opts, ...).
+ * The problems run concurrently on the device; every result is the one a
+ * single call gives (the leaf size and arithmetic depend only on the
+ * request, never on what it is batched with).  stats may be NULL or an array
+ * of `count` entries.  Returns the first nonzero per-problem status, or 0.
+ */
+int spamm_sqrt_invsqrt_batched(int count, const double* const* S, const int* n, const double* tau,
+                               int maxit, double* const* Y, double* const* Z, const spamm_opts* opts,
+                               spamm_stats* stats);
+
+/*
+ * Norm tree of A for parity checks: nu_leaf[i*m + j] = ||A_ij||_F^2 for the
+ * m x m leaf tiles (m = ceil(n/leaf)), accumulated in FP64, and *root =
+ * ||A||_F^2 summed up the quadtree (Sec. 1, norm recursion).
+ */
+int spamm_norm_tree(const double* A, int n, int leaf, double* nu_leaf, double* root, void* stream);
+
+/*
+ * Task list of A (x)_tau B for parity checks: for output tile (i,k),
+ * counts[i*m + k] surviving j, listed ascending in jlist[(i*m + k)*m + 0 ..].
+ * counts holds m*m ints and jlist m*m*m ints (host or device).  *thr gets
+ * the squared threshold tau^2 ||A||^2 ||B||^2 and *total the task count.
+ */
+int spamm_cull(const double* A, const double* B, int n, double tau, int leaf, int* counts, int* jlist,
+               double* thr, long long* total, void* stream);
+
+/* Message for the calling thread's last failure ("" if none). */
+const char* spamm_last_error(void);
+
+/* Short name of a status code. */
+const char* spamm_strerror(int status);
+
+/* Free every cached scratch buffer (call with no work in flight). */
+int spamm_release(void);
+
+/* Number of CUDA kernels this library has launched since it was loaded
+ * (all threads).  A diagnostic for counting device work per call. */
+long long spamm_kernel_launches(void);
+
+/* Library version string. */
+const char* spamm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPAMM_H */

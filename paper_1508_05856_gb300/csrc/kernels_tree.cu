@@ -1,0 +1,365 @@
+// Norm-tree, cull and bookkeeping kernels of the SpAMM path.
+//
+//  * pack + leaf norms (the quadtree decoration of Sec. 1: every leaf tile
+//    carries its squared Frobenius norm, accumulated in FP64),
+//  * upper quadtree levels (parent = sum of its existing children),
+//  * the two-sided metric query of Eq. (newspamm) as a per-output-tile scan
+//    with a coarse-level pre-filter,
+//  * Gershgorin scaling (Sec. 3.2), the NS map h[X] = 1.5 I - 0.5 X, the
+//    trace error t_k (Sec. 4.2), unpacking and the residual norm.
+//
+// All reductions run in a fixed order, so every result is deterministic.
+#include "spamm_internal.cuh"
+
+namespace spamm {
+
+Geometry make_geometry(int n, int nb) {
+    Geometry g;
+    g.n = n;
+    g.nb = nb;
+    g.m = (n + nb - 1) / nb;
+    int L = 0;
+    while ((1 << L) < g.m) ++L;
+    g.L = L;
+    long total = 0;
+    for (int l = L; l >= 0; --l) {
+        int sh = L - l;
+        g.dim[l] = (g.m + (1 << sh) - 1) >> sh;
+        g.off[l] = total;
+        total += (long)g.dim[l] * g.dim[l];
+    }
+    g.tree_size = total;
+    g.coarse = L >= 3 ? L - 3 : 0;
+    g.coarse_shift = L - g.coarse;
+    return g;
+}
+
+TreeDev tree_dev(const Geometry& g) {
+    TreeDev t;
+    t.m = g.m;
+    t.L = g.L;
+    t.coarse = g.coarse;
+    t.shift = g.coarse_shift;
+    for (int l = 0; l < kMaxLevels; ++l) {
+        t.dim[l] = g.dim[l];
+        t.off[l] = g.off[l];
+    }
+    return t;
+}
+
+// Deterministic block sum for blockDim.x == 256 (8 warps).
+__device__ __forceinline__ double block_sum_256(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 8; ++q) s += red[q];
+    return s;  // valid in thread 0
+}
+
+// ---------------------------------------------------------------- Gershgorin
+__global__ void k_rowsum(const double* __restrict__ S, int n, const double* __restrict__ mu_dev,
+                         double* __restrict__ rowsum) {
+    const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    const double mu = mu_dev ? *mu_dev : 0.0;
+    const double* r = S + (size_t)row * n;
+    double s = 0.0;
+    for (int j = lane; j < n; j += 32) {
+        double v = r[j];
+        if (j == row) v += mu;
+        s += fabs(v);
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) rowsum[row] = s;
+}
+
+__global__ void k_max(const double* __restrict__ v, int n, double* __restrict__ out) {
+    __shared__ double red[32];
+    double m = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, v[i]);
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) r = fmax(r, red[q]);
+        *out = r;
+    }
+}
+
+void launch_gershgorin(const double* S, int n, const double* mu_dev, double* rowsum, double* out_c,
+                       cudaStream_t st) {
+    k_rowsum<<<(n + 7) / 8, 256, 0, st>>>(S, n, mu_dev, rowsum);
+    note_launch();
+    k_max<<<1, 1024, 0, st>>>(rowsum, n, out_c);
+    note_launch();
+}
+
+__global__ void k_scale_mu(const double* c0, double mu_rel, double* mu_out) { *mu_out = mu_rel * (*c0); }
+
+void launch_scale_mu(const double* c0, double mu_rel, double* mu_out, cudaStream_t st) {
+    k_scale_mu<<<1, 1, 0, st>>>(c0, mu_rel, mu_out);
+    note_launch();
+}
+
+__global__ void k_sqrt_scalar(const double* c, double* out) { *out = sqrt(*c); }
+
+void launch_sqrt_scalar(const double* c, double* out, cudaStream_t st) {
+    k_sqrt_scalar<<<1, 1, 0, st>>>(c, out);
+    note_launch();
+}
+
+// ---------------------------------------------------------------- pack + leaf norms
+__global__ void __launch_bounds__(256) k_pack(const double* __restrict__ src, int n, int m, int nb,
+                                              const double* __restrict__ mu_dev, const double* __restrict__ c_dev,
+                                              double* __restrict__ dst, double* __restrict__ leaf) {
+    __shared__ double red[8];
+    const int tile = blockIdx.x;
+    const int i = tile / m, j = tile % m;
+    const int ne = nb * nb;
+    const double mu = mu_dev ? *mu_dev : 0.0;
+    const double c = c_dev ? *c_dev : 1.0;
+    const bool scaled = c_dev != nullptr;
+    double* d = dst + (size_t)tile * ne;
+    double acc = 0.0;
+    for (int idx = threadIdx.x; idx < ne; idx += 256) {
+        const int r = idx / nb, cc = idx - r * nb;
+        const int gi = i * nb + r, gj = j * nb + cc;
+        double v = 0.0;
+        if (gi < n && gj < n) {
+            v = src[(size_t)gi * n + gj];
+            if (scaled) {
+                if (gi == gj) v += mu;
+                v = v / c;
+            }
+        }
+        d[idx] = v;
+        acc = fma(v, v, acc);
+    }
+    const double s = block_sum_256(acc, red);
+    if (threadIdx.x == 0) leaf[tile] = s;
+}
+
+void launch_pack(const double* src, int n, const Geometry& g, const double* mu, const double* scale_c,
+                 TileMat dst, cudaStream_t st) {
+    k_pack<<<g.m * g.m, 256, 0, st>>>(src, n, g.m, g.nb, mu, scale_c, dst.t, dst.tree);
+    note_launch();
+}
+
+// T = 1.5 I - 0.5 X on the logical diagonal, -0.5 X elsewhere (Sec. 4.2 map, alpha = 1).
+__global__ void __launch_bounds__(256) k_hmap(const double* __restrict__ X, int n, int m, int nb,
+                                              double* __restrict__ T, double* __restrict__ leaf) {
+    __shared__ double red[8];
+    const int tile = blockIdx.x;
+    const int i = tile / m, j = tile % m;
+    const int ne = nb * nb;
+    const double* x = X + (size_t)tile * ne;
+    double* t = T + (size_t)tile * ne;
+    double acc = 0.0;
+    for (int idx = threadIdx.x; idx < ne; idx += 256) {
+        const int r = idx / nb, cc = idx - r * nb;
+        const int gi = i * nb + r, gj = j * nb + cc;
+        const double xv = x[idx];
+        const double v = (gi == gj && gi < n) ? 1.5 - 0.5 * xv : -0.5 * xv;
+        t[idx] = v;
+        acc = fma(v, v, acc);
+    }
+    const double s = block_sum_256(acc, red);
+    if (threadIdx.x == 0) leaf[tile] = s;
+}
+
+void launch_hmap(const double* X, const Geometry& g, TileMat T, cudaStream_t st) {
+    k_hmap<<<g.m * g.m, 256, 0, st>>>(X, g.n, g.m, g.nb, T.t, T.tree);
+    note_launch();
+}
+
+__global__ void __launch_bounds__(256) k_identity(int n, int m, int nb, double* __restrict__ Z,
+                                                  double* __restrict__ leaf) {
+    const int tile = blockIdx.x;
+    const int i = tile / m, j = tile % m;
+    const int ne = nb * nb;
+    double* z = Z + (size_t)tile * ne;
+    for (int idx = threadIdx.x; idx < ne; idx += 256) {
+        const int r = idx / nb, cc = idx - r * nb;
+        const int gi = i * nb + r, gj = j * nb + cc;
+        z[idx] = (gi == gj && gi < n) ? 1.0 : 0.0;
+    }
+    if (threadIdx.x == 0) {
+        int cnt = 0;
+        if (i == j) cnt = min(nb, n - i * nb);
+        leaf[tile] = (double)cnt;
+    }
+}
+
+void launch_identity(const Geometry& g, TileMat Z, cudaStream_t st) {
+    k_identity<<<g.m * g.m, 256, 0, st>>>(g.n, g.m, g.nb, Z.t, Z.tree);
+    note_launch();
+}
+
+// ---------------------------------------------------------------- quadtree levels
+__global__ void __launch_bounds__(1024) k_tree(TreeDev td, double* __restrict__ tree, const int* __restrict__ done) {
+    if (done && *done) return;
+    for (int l = td.L - 1; l >= 0; --l) {
+        const int d = td.dim[l], dc = td.dim[l + 1];
+        const double* ch = tree + td.off[l + 1];
+        double* pa = tree + td.off[l];
+        for (int idx = threadIdx.x; idx < d * d; idx += blockDim.x) {
+            const int I = idx / d, J = idx - I * d;
+            double s = 0.0;
+            for (int a = 0; a < 2; ++a)
+                for (int b = 0; b < 2; ++b) {
+                    const int ci = 2 * I + a, cj = 2 * J + b;
+                    if (ci < dc && cj < dc) s += ch[(size_t)ci * dc + cj];
+                }
+            pa[idx] = s;
+        }
+        __syncthreads();
+    }
+}
+
+void launch_tree(const Geometry& g, double* tree, const int* done, cudaStream_t st) {
+    k_tree<<<1, 1024, 0, st>>>(tree_dev(g), tree, done);
+    note_launch();
+}
+
+// ---------------------------------------------------------------- the cull
+// One thread per output tile (i, k): scan j ascending, skipping whole coarse
+// blocks J whose coarse pair product is below the threshold.  Parents hold
+// sums of non-negative children, so a coarse pair below the threshold has no
+// surviving leaf pair under it; the surviving set is exactly the leaf test
+// nuA(i,j) * nuB(j,k) >= thr, i.e. the recursion of Eq. (newspamm).
+__global__ void __launch_bounds__(128) k_cull(TreeDev td, const double* __restrict__ treeA,
+                                              const double* __restrict__ treeB, double tau,
+                                              int* __restrict__ counts, int* __restrict__ jlist,
+                                              unsigned long long* __restrict__ total, double* __restrict__ thr_out,
+                                              const int* __restrict__ done) {
+    if (done && *done) return;
+    __shared__ int red[4];
+    const int m = td.m;
+    const int i = blockIdx.y;
+    const int k = blockIdx.x * 128 + threadIdx.x;
+    const double thr = ((tau * tau) * treeA[td.off[0]]) * treeB[td.off[0]];
+    int cnt = 0;
+    if (k < m) {
+        const int dc = td.dim[td.coarse];
+        const double* cA = treeA + td.off[td.coarse];
+        const double* cB = treeB + td.off[td.coarse];
+        const int I = i >> td.shift, K = k >> td.shift;
+        const double* nA = treeA;   // leaf level at offset 0
+        const double* nB = treeB;
+        int* out = jlist + ((size_t)i * m + k) * m;
+        for (int J = 0; J < dc; ++J) {
+            if (cA[(size_t)I * dc + J] * cB[(size_t)J * dc + K] < thr) continue;
+            const int j0 = J << td.shift;
+            const int j1 = min(m, (J + 1) << td.shift);
+            for (int j = j0; j < j1; ++j)
+                if (!(nA[(size_t)i * m + j] * nB[(size_t)j * m + k] < thr)) out[cnt++] = j;
+        }
+        counts[(size_t)i * m + k] = cnt;
+    }
+    if (thr_out && i == 0 && k == 0) *thr_out = thr;
+    if (total) {
+        int v = cnt;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int s = red[0] + red[1] + red[2] + red[3];
+            if (s) atomicAdd(total, (unsigned long long)s);
+        }
+    }
+}
+
+void launch_cull(const Geometry& g, const double* treeA, const double* treeB, double tau, int* counts,
+                 int* jlist, unsigned long long* total, double* thr_out, const int* done, cudaStream_t st) {
+    dim3 grid((g.m + 127) / 128, g.m);
+    k_cull<<<grid, 128, 0, st>>>(tree_dev(g), treeA, treeB, tau, counts, jlist, total, thr_out, done);
+    note_launch();
+}
+
+// ---------------------------------------------------------------- unpack
+__global__ void __launch_bounds__(256) k_unpack(const double* __restrict__ src, int n, int m, int nb,
+                                                double* __restrict__ dst, const double* __restrict__ mul,
+                                                const double* __restrict__ div) {
+    const int tile = blockIdx.x;
+    const int i = tile / m, j = tile % m;
+    const int ne = nb * nb;
+    const double* s = src + (size_t)tile * ne;
+    const double fm = mul ? *mul : 1.0;
+    const double fd = div ? *div : 1.0;
+    for (int idx = threadIdx.x; idx < ne; idx += 256) {
+        const int r = idx / nb, cc = idx - r * nb;
+        const int gi = i * nb + r, gj = j * nb + cc;
+        if (gi < n && gj < n) {
+            double v = s[idx];
+            if (mul) v = v * fm;
+            if (div) v = v / fd;
+            dst[(size_t)gi * n + gj] = v;
+        }
+    }
+}
+
+void launch_unpack(const double* src, const Geometry& g, double* dst, const double* mul, const double* div,
+                   cudaStream_t st) {
+    k_unpack<<<g.m * g.m, 256, 0, st>>>(src, g.n, g.m, g.nb, dst, mul, div);
+    note_launch();
+}
+
+// ---------------------------------------------------------------- t_k
+__global__ void k_tk(const double* __restrict__ trace_part, int n, int m, int k, double tol_t,
+                     double* __restrict__ t_hist, int* __restrict__ done, int* __restrict__ iters) {
+    if (*done) return;
+    double tr = 0.0;
+    for (int i = 0; i < m; ++i) tr += trace_part[i];
+    const double t = ((double)n - tr) / (double)n;
+    t_hist[k] = t;
+    *iters = k + 1;
+    if (tol_t > 0.0 && fabs(t) <= tol_t) *done = 1;
+}
+
+void launch_tk(const double* trace_part, const Geometry& g, int k, double tol_t, double* t_hist, int* done,
+               int* iters, cudaStream_t st) {
+    k_tk<<<1, 1, 0, st>>>(trace_part, g.n, g.m, k, tol_t, t_hist, done, iters);
+    note_launch();
+}
+
+// ---------------------------------------------------------------- residual ||R - I||_F
+__global__ void __launch_bounds__(256) k_resid_tiles(const double* __restrict__ R, int n, int m, int nb,
+                                                     double* __restrict__ partial) {
+    __shared__ double red[8];
+    const int tile = blockIdx.x;
+    const int i = tile / m, j = tile % m;
+    const int ne = nb * nb;
+    const double* r = R + (size_t)tile * ne;
+    double acc = 0.0;
+    for (int idx = threadIdx.x; idx < ne; idx += 256) {
+        const int rr = idx / nb, cc = idx - rr * nb;
+        const int gi = i * nb + rr, gj = j * nb + cc;
+        if (gi < n && gj < n) {
+            const double d = r[idx] - (gi == gj ? 1.0 : 0.0);
+            acc = fma(d, d, acc);
+        }
+    }
+    const double s = block_sum_256(acc, red);
+    if (threadIdx.x == 0) partial[tile] = s;
+}
+
+__global__ void k_sum_sqrt(const double* __restrict__ partial, int cnt, double* __restrict__ out) {
+    double s = 0.0;
+    for (int q = 0; q < cnt; ++q) s += partial[q];
+    *out = sqrt(s);
+}
+
+void launch_resid_norm(const double* R, const Geometry& g, double* partial, double* out, cudaStream_t st) {
+    k_resid_tiles<<<g.m * g.m, 256, 0, st>>>(R, g.n, g.m, g.nb, partial);
+    note_launch();
+    k_sum_sqrt<<<1, 1, 0, st>>>(partial, g.m * g.m, out);
+    note_launch();
+}
+
+}  // namespace spamm

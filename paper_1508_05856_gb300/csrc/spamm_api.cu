@@ -1,0 +1,716 @@
+// C ABI of libspamm (declared in include/spamm.h): argument checks, scratch
+// management per problem size, and the host-side driver of the SpAMM product
+// and of the dual-channel Newton-Schulz iteration (Eq. (cannonical)).
+//
+// Every arithmetic step runs in the CUDA kernels of kernels_*.cu; this file
+// only orders the launches on the caller's stream and moves data across the
+// host/device boundary when the caller passes host pointers.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <atomic>
+#include <tuple>
+#include <vector>
+
+#include "spamm.h"
+#include "spamm_internal.cuh"
+
+namespace spamm {
+
+static std::atomic<long long> g_launches{0};
+void note_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+static thread_local std::string g_last_error;
+
+static void set_error(const char* what, cudaError_t e) {
+    char buf[512];
+    snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+    g_last_error = buf;
+}
+
+#define CK(call)                                  \
+    do {                                          \
+        cudaError_t e_ = (call);                  \
+        if (e_ != cudaSuccess) {                  \
+            set_error(#call, e_);                 \
+            return SPAMM_ERR_CUDA;                \
+        }                                         \
+    } while (0)
+
+#define CKA(call)                                              \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) {                               \
+            set_error(#call, e_);                              \
+            return e_ == cudaErrorMemoryAllocation ? SPAMM_ERR_NOMEM : SPAMM_ERR_CUDA; \
+        }                                                      \
+    } while (0)
+
+static bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// ----------------------------------------------------------------------------
+// Scratch of one problem size on one device.
+struct Plan {
+    int device = 0;
+    Geometry g;
+    TileMat buf[6];
+    int* counts = nullptr;
+    int* jlist = nullptr;
+    unsigned long long* task_ctr = nullptr;  // [3 * maxit_cap + 4]
+    double* t_hist = nullptr;                // [maxit_cap]
+    int maxit_cap = 0;
+    double* trace_part = nullptr;  // [m]
+    double* scal = nullptr;        // c0, mu, c, sqrt c, thr, resid, spare...
+    double* rowsum = nullptr;      // [n]
+    int* flags = nullptr;          // done, iters
+    double* partial = nullptr;     // [m*m]
+    double* stage[3] = {nullptr, nullptr, nullptr};  // n*n row-major staging
+    // profiling: event pairs around each leaf-product kernel of a call
+    std::vector<cudaEvent_t> ev;
+    int ev_used = 0;
+    bool profile = false;
+    long long gemm_launches = 0;
+};
+
+static void free_plan(Plan* p) {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(p->device);
+    for (auto& b : p->buf) {
+        cudaFree(b.t);
+        cudaFree(b.tree);
+    }
+    cudaFree(p->counts);
+    cudaFree(p->jlist);
+    cudaFree(p->task_ctr);
+    cudaFree(p->t_hist);
+    cudaFree(p->trace_part);
+    cudaFree(p->scal);
+    cudaFree(p->rowsum);
+    cudaFree(p->flags);
+    cudaFree(p->partial);
+    for (auto& s : p->stage) cudaFree(s);
+    for (auto e : p->ev) cudaEventDestroy(e);
+    cudaSetDevice(cur);
+    delete p;
+}
+
+static int alloc_plan(Plan* p, int n, int nb) {
+    p->g = make_geometry(n, nb);
+    const Geometry& g = p->g;
+    for (auto& b : p->buf) {
+        CKA(cudaMalloc(&b.t, g.elems() * sizeof(double)));
+        CKA(cudaMalloc(&b.tree, g.tree_size * sizeof(double)));
+    }
+    CKA(cudaMalloc(&p->counts, (size_t)g.m * g.m * sizeof(int)));
+    CKA(cudaMalloc(&p->jlist, (size_t)g.m * g.m * g.m * sizeof(int)));
+    CKA(cudaMalloc(&p->trace_part, (size_t)g.m * sizeof(double)));
+    CKA(cudaMalloc(&p->scal, 16 * sizeof(double)));
+    CKA(cudaMalloc(&p->rowsum, (size_t)n * sizeof(double)));
+    CKA(cudaMalloc(&p->flags, 4 * sizeof(int)));
+    CKA(cudaMalloc(&p->partial, (size_t)g.m * g.m * sizeof(double)));
+    return SPAMM_OK;
+}
+
+static int ensure_hist(Plan* p, int maxit) {
+    if (maxit <= p->maxit_cap) return SPAMM_OK;
+    cudaFree(p->task_ctr);
+    cudaFree(p->t_hist);
+    p->task_ctr = nullptr;
+    p->t_hist = nullptr;
+    int cap = maxit < 64 ? 64 : maxit;
+    CKA(cudaMalloc(&p->task_ctr, (3 * (size_t)cap + 4) * sizeof(unsigned long long)));
+    CKA(cudaMalloc(&p->t_hist, (size_t)cap * sizeof(double)));
+    p->maxit_cap = cap;
+    return SPAMM_OK;
+}
+
+static int ensure_stage(Plan* p, int which) {
+    if (p->stage[which]) return SPAMM_OK;
+    CKA(cudaMalloc(&p->stage[which], (size_t)p->g.n * p->g.n * sizeof(double)));
+    return SPAMM_OK;
+}
+
+class PlanPool {
+  public:
+    int acquire(int n, int nb, Plan** out) {
+        int dev = 0;
+        CK(cudaGetDevice(&dev));
+        auto key = std::make_tuple(dev, n, nb);
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            auto& v = free_[key];
+            if (!v.empty()) {
+                *out = v.back();
+                v.pop_back();
+                return SPAMM_OK;
+            }
+        }
+        Plan* p = new Plan;
+        p->device = dev;
+        int st = alloc_plan(p, n, nb);
+        if (st) {
+            free_plan(p);
+            return st;
+        }
+        *out = p;
+        return SPAMM_OK;
+    }
+    void release(Plan* p) {
+        std::lock_guard<std::mutex> lk(mu_);
+        free_[std::make_tuple(p->device, p->g.n, p->g.nb)].push_back(p);
+    }
+    void clear() {
+        std::lock_guard<std::mutex> lk(mu_);
+        for (auto& kv : free_)
+            for (Plan* p : kv.second) free_plan(p);
+        free_.clear();
+    }
+
+  private:
+    std::mutex mu_;
+    std::map<std::tuple<int, int, int>, std::vector<Plan*>> free_;
+};
+
+static PlanPool g_pool;
+
+struct PlanGuard {
+    Plan* p = nullptr;
+    ~PlanGuard() {
+        if (p) g_pool.release(p);
+    }
+};
+
+static bool leaf_ok(int nb) { return nb == 32 || nb == 64 || nb == 128; }
+
+static spamm_opts resolve_opts(const spamm_opts* o) {
+    spamm_opts r;
+    spamm_opts_init(&r);
+    if (o) r = *o;
+    if (r.leaf == 0) r.leaf = 64;
+    return r;
+}
+
+// Device view of a caller matrix: the pointer itself, or a staged copy.
+static int stage_in(Plan* p, int which, const double* src, cudaStream_t st, const double** dev) {
+    if (is_device_ptr(src)) {
+        *dev = src;
+        return SPAMM_OK;
+    }
+    int e = ensure_stage(p, which);
+    if (e) return e;
+    CK(cudaMemcpyAsync(p->stage[which], src, (size_t)p->g.n * p->g.n * sizeof(double), cudaMemcpyHostToDevice, st));
+    *dev = p->stage[which];
+    return SPAMM_OK;
+}
+
+static int out_target(Plan* p, int which, double* dst, double** dev) {
+    if (is_device_ptr(dst)) {
+        *dev = dst;
+        return SPAMM_OK;
+    }
+    int e = ensure_stage(p, which);
+    if (e) return e;
+    *dev = p->stage[which];
+    return SPAMM_OK;
+}
+
+static int stage_out(Plan* p, int which, double* dst, const double* dev, cudaStream_t st) {
+    if (dev == dst) return SPAMM_OK;
+    CK(cudaMemcpyAsync(dst, dev, (size_t)p->g.n * p->g.n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    (void)which;
+    return SPAMM_OK;
+}
+
+static void begin_call(Plan* p, bool profile) {
+    p->profile = profile;
+    p->ev_used = 0;
+    p->gemm_launches = 0;
+}
+
+static cudaEvent_t next_event(Plan* p) {
+    if (p->ev_used == (int)p->ev.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        p->ev.push_back(e);
+    }
+    return p->ev[p->ev_used++];
+}
+
+// Summed duration of the profiled kernels (call after the stream is synchronised).
+static double profiled_ms(Plan* p) {
+    double ms = 0.0;
+    for (int q = 0; q + 1 < p->ev_used; q += 2) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, p->ev[q], p->ev[q + 1]) == cudaSuccess) ms += t;
+    }
+    return ms;
+}
+
+// One SpAMM product of two packed operands into dst (tree leaves + levels).
+static void product(Plan* p, const TileMat& A, const TileMat& B, TileMat& C, double tau, EpiMode mode,
+                    unsigned long long* ctr, cudaStream_t st) {
+    const Geometry& g = p->g;
+    launch_cull(g, A.tree, B.tree, tau, p->counts, p->jlist, ctr, nullptr, p->flags, st);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (p->profile) {
+        e0 = next_event(p);
+        e1 = next_event(p);
+        if (e0 && e1) cudaEventRecord(e0, st);
+    }
+    launch_gemm_f64(g, A.t, B.t, C.t, C.tree, p->counts, p->jlist, 0, mode, p->trace_part, p->flags, st);
+    if (e0 && e1) cudaEventRecord(e1, st);
+    p->gemm_launches++;
+    launch_tree(g, C.tree, p->flags, st);
+}
+
+static int multiply_impl(const double* A, const double* B, double* C, int n, double tau, const spamm_opts& o,
+                         spamm_stats* stats) {
+    cudaStream_t st = (cudaStream_t)o.stream;
+    PlanGuard pg;
+    int e = g_pool.acquire(n, o.leaf, &pg.p);
+    if (e) return e;
+    Plan* p = pg.p;
+    const Geometry& g = p->g;
+    if ((e = ensure_hist(p, 1))) return e;
+    const double *dA, *dB;
+    double* dC;
+    if ((e = stage_in(p, 0, A, st, &dA))) return e;
+    if ((e = stage_in(p, 1, B, st, &dB))) return e;
+    if ((e = out_target(p, 2, C, &dC))) return e;
+    begin_call(p, o.profile != 0);
+    CK(cudaMemsetAsync(p->flags, 0, 4 * sizeof(int), st));
+    CK(cudaMemsetAsync(p->task_ctr, 0, 4 * sizeof(unsigned long long), st));
+    launch_pack(dA, n, g, nullptr, nullptr, p->buf[0], st);
+    launch_tree(g, p->buf[0].tree, nullptr, st);
+    launch_pack(dB, n, g, nullptr, nullptr, p->buf[1], st);
+    launch_tree(g, p->buf[1].tree, nullptr, st);
+    product(p, p->buf[0], p->buf[1], p->buf[2], tau, EPI_PLAIN, p->task_ctr, st);
+    launch_unpack(p->buf[2].t, g, dC, nullptr, nullptr, st);
+    CK(cudaGetLastError());
+    if ((e = stage_out(p, 2, C, dC, st))) return e;
+    unsigned long long tasks = 0;
+    CK(cudaMemcpyAsync(&tasks, p->task_ctr, sizeof(tasks), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (stats) {
+        stats->iters = 0;
+        stats->t_final = 0.0;
+        stats->resid_F = -1.0;
+        stats->scale_c = 1.0;
+        stats->tasks_total = (long long)tasks;
+        stats->tasks_dense = (long long)g.m * g.m * g.m;
+        stats->flops = 2.0 * (double)g.nb * g.nb * g.nb * (double)tasks;
+        stats->gemm_ms = p->profile ? profiled_ms(p) : 0.0;
+        stats->gemm_launches = p->gemm_launches;
+    }
+    return SPAMM_OK;
+}
+
+// ||Z S Z - I||_F in FP64 with dense products (verification only).
+static int residual_impl(Plan* p, const double* dS, const double* dZ, double* out, cudaStream_t st) {
+    const Geometry& g = p->g;
+    launch_pack(dS, g.n, g, nullptr, nullptr, p->buf[3], st);
+    launch_pack(dZ, g.n, g, nullptr, nullptr, p->buf[4], st);
+    launch_gemm_f64(g, p->buf[4].t, p->buf[3].t, p->buf[5].t, p->buf[5].tree, nullptr, nullptr, 1, EPI_PLAIN,
+                    nullptr, nullptr, st);
+    launch_gemm_f64(g, p->buf[5].t, p->buf[4].t, p->buf[3].t, p->buf[3].tree, nullptr, nullptr, 1, EPI_PLAIN,
+                    nullptr, nullptr, st);
+    launch_resid_norm(p->buf[3].t, g, p->partial, p->scal + 5, st);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(out, p->scal + 5, sizeof(double), cudaMemcpyDeviceToHost, st));
+    return SPAMM_OK;
+}
+
+static int sqrt_impl(const double* S, int n, double tau, int maxit, double* Y, double* Z, const spamm_opts& o,
+                     spamm_stats* stats) {
+    cudaStream_t st = (cudaStream_t)o.stream;
+    const double tau_s = o.tau_s < 0.0 ? 0.01 * tau : o.tau_s;
+    PlanGuard pg;
+    int e = g_pool.acquire(n, o.leaf, &pg.p);
+    if (e) return e;
+    Plan* p = pg.p;
+    const Geometry& g = p->g;
+    if ((e = ensure_hist(p, maxit > 0 ? maxit : 1))) return e;
+    const double* dS;
+    double *dY, *dZ;
+    if ((e = stage_in(p, 0, S, st, &dS))) return e;
+    if ((e = out_target(p, 1, Y, &dY))) return e;
+    if ((e = out_target(p, 2, Z, &dZ))) return e;
+    begin_call(p, o.profile != 0);
+
+    CK(cudaMemsetAsync(p->flags, 0, 4 * sizeof(int), st));
+    CK(cudaMemsetAsync(p->task_ctr, 0, (3 * (size_t)p->maxit_cap + 4) * sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(p->t_hist, 0, (size_t)p->maxit_cap * sizeof(double), st));
+
+    // a1: Gershgorin bound (plus the Tikhonov shift of Sec. 6) and scaling
+    double* c0 = p->scal + 0;
+    double* mu = p->scal + 1;
+    double* c = p->scal + 2;
+    double* sqc = p->scal + 3;
+    const double* mu_ptr = nullptr;
+    if (o.mu_rel > 0.0) {
+        launch_gershgorin(dS, n, nullptr, p->rowsum, c0, st);
+        launch_scale_mu(c0, o.mu_rel, mu, st);
+        mu_ptr = mu;
+    }
+    launch_gershgorin(dS, n, mu_ptr, p->rowsum, c, st);
+    launch_sqrt_scalar(c, sqc, st);
+
+    // a2: X0 = Y0 = S / c (packed with leaf norms), T0 = h[X0], Z0 = I
+    TileMat Yb = p->buf[0], Zb = p->buf[1], Tb = p->buf[2], Y2 = p->buf[3], Z2 = p->buf[4];
+    launch_pack(dS, n, g, mu_ptr, c, Yb, st);
+    launch_tree(g, Yb.tree, nullptr, st);
+    launch_hmap(Yb.t, g, Tb, st);
+    launch_tree(g, Tb.tree, nullptr, st);
+    launch_identity(g, Zb, st);
+    launch_tree(g, Zb.tree, nullptr, st);
+    CK(cudaGetLastError());
+
+    // a3-a6: the iteration
+    int it_host = 0;
+    for (int k = 0; k < maxit; ++k) {
+        unsigned long long* ctr = p->task_ctr + 3 * (size_t)k;
+        if (o.order == SPAMM_ORDER_PAPER) {
+            product(p, Tb, Yb, Y2, tau_s, EPI_PLAIN, ctr + 0, st);  // Y <- T (x)_{tau_s} Y
+            product(p, Zb, Tb, Z2, tau, EPI_PLAIN, ctr + 1, st);    // Z <- Z (x)_tau T
+            std::swap(Yb, Y2);
+            std::swap(Zb, Z2);
+            product(p, Yb, Zb, Tb, tau, EPI_NS_X, ctr + 2, st);     // X <- Y (x)_tau Z, T = h[X]
+        } else {
+            product(p, Yb, Tb, Y2, tau_s, EPI_PLAIN, ctr + 0, st);  // Y <- Y (x)_{tau_s} T
+            product(p, Tb, Zb, Z2, tau, EPI_PLAIN, ctr + 1, st);    // Z <- T (x)_tau Z
+            std::swap(Yb, Y2);
+            std::swap(Zb, Z2);
+            product(p, Zb, Yb, Tb, tau, EPI_NS_X, ctr + 2, st);     // X <- Z (x)_tau Y, T = h[X]
+        }
+        launch_tk(p->trace_part, g, k, o.tol_t, p->t_hist, p->flags, p->flags + 1, st);
+        CK(cudaGetLastError());
+        it_host = k + 1;
+        if (o.tol_t > 0.0) {
+            int done = 0;
+            CK(cudaMemcpyAsync(&done, p->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            if (done) break;
+        }
+    }
+
+    // a7: unscale and unpack
+    launch_unpack(Yb.t, g, dY, sqc, nullptr, st);
+    launch_unpack(Zb.t, g, dZ, nullptr, sqc, st);
+    CK(cudaGetLastError());
+    double resid = -1.0;
+    if (o.residual) {
+        if ((e = residual_impl(p, dS, dZ, &resid, st))) return e;
+    }
+    if ((e = stage_out(p, 1, Y, dY, st))) return e;
+    if ((e = stage_out(p, 2, Z, dZ, st))) return e;
+
+    std::vector<double> th((size_t)(it_host > 0 ? it_host : 1), 0.0);
+    std::vector<unsigned long long> kc(3 * (size_t)(it_host > 0 ? it_host : 1), 0ull);
+    double c_host = 0.0;
+    int flags_h[2] = {0, 0};
+    if (it_host > 0) {
+        CK(cudaMemcpyAsync(th.data(), p->t_hist, it_host * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(kc.data(), p->task_ctr, 3 * (size_t)it_host * sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaMemcpyAsync(&c_host, c, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(flags_h, p->flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+
+    const int iters = it_host;
+    long long total = 0;
+    for (int q = 0; q < 3 * iters; ++q) total += (long long)kc[q];
+    const double t_final = iters > 0 ? th[iters - 1] : 0.0;
+    if (stats) {
+        stats->iters = iters;
+        stats->t_final = t_final;
+        stats->resid_F = resid;
+        stats->scale_c = c_host;
+        stats->tasks_total = total;
+        stats->tasks_dense = 3ll * iters * (long long)g.m * g.m * g.m;
+        stats->flops = 2.0 * (double)g.nb * g.nb * g.nb * (double)total;
+        if (stats->t_hist)
+            for (int q = 0; q < iters; ++q) stats->t_hist[q] = th[q];
+        if (stats->task_hist)
+            for (int q = 0; q < 3 * iters; ++q) stats->task_hist[q] = (long long)kc[q];
+        stats->gemm_ms = p->profile ? profiled_ms(p) : 0.0;
+        stats->gemm_launches = p->gemm_launches;
+    }
+    for (int q = 0; q < iters; ++q)
+        if (!std::isfinite(th[q]) || std::fabs(th[q]) >= 1.0) {
+            g_last_error = "trace error left [0, 1): the iteration diverged";
+            return SPAMM_ERR_DIVERGED;
+        }
+    if (o.tol_t > 0.0 && !(std::fabs(t_final) <= o.tol_t)) {
+        g_last_error = "maxit reached before |t_k| <= tol_t";
+        return SPAMM_ERR_NOTCONVERGED;
+    }
+    return SPAMM_OK;
+}
+
+static int check_common(int n, double tau, const spamm_opts& o) {
+    if (n <= 0) {
+        g_last_error = "n must be positive";
+        return SPAMM_ERR_ARG;
+    }
+    if (!(tau >= 0.0) || std::isinf(tau)) {
+        g_last_error = "tau must be finite and >= 0";
+        return SPAMM_ERR_ARG;
+    }
+    if (!leaf_ok(o.leaf)) {
+        g_last_error = "leaf must be 32, 64 or 128";
+        return SPAMM_ERR_ARG;
+    }
+    if (o.precision != SPAMM_FP64 && o.precision != SPAMM_EMU64) {
+        g_last_error = "unknown precision";
+        return SPAMM_ERR_ARG;
+    }
+    if (o.order != SPAMM_ORDER_PAPER && o.order != SPAMM_ORDER_TRANSPOSED) {
+        g_last_error = "unknown order";
+        return SPAMM_ERR_ARG;
+    }
+    if (std::isnan(o.tau_s) || std::isnan(o.mu_rel) || o.mu_rel < 0.0 || std::isnan(o.tol_t) || o.tol_t < 0.0) {
+        g_last_error = "tau_s, mu_rel, tol_t must be numbers (mu_rel, tol_t >= 0)";
+        return SPAMM_ERR_ARG;
+    }
+    const long m = (n + o.leaf - 1) / o.leaf;
+    if (m > 1024) {
+        g_last_error = "more than 1024 leaf tiles per side";
+        return SPAMM_ERR_UNSUPPORTED;
+    }
+    return SPAMM_OK;
+}
+
+}  // namespace spamm
+
+using namespace spamm;
+
+extern "C" {
+
+void spamm_opts_init(spamm_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->leaf = 64;
+    o->precision = SPAMM_FP64;
+    o->tau_s = -1.0;
+    o->mu_rel = 0.0;
+    o->tol_t = 0.0;
+    o->order = SPAMM_ORDER_PAPER;
+    o->residual = 0;
+    o->stream = nullptr;
+}
+
+int spamm_multiply(const double* A, const double* B, double* C, int n, double tau, const spamm_opts* opts,
+                   spamm_stats* stats) {
+    try {
+        g_last_error.clear();
+        spamm_opts o = resolve_opts(opts);
+        int e = check_common(n, tau, o);
+        if (e) return e;
+        if (!A || !B || !C) {
+            g_last_error = "null matrix pointer";
+            return SPAMM_ERR_ARG;
+        }
+        if (o.precision != SPAMM_FP64) {
+            g_last_error = "precision not available for spamm_multiply in this build";
+            return SPAMM_ERR_UNSUPPORTED;
+        }
+        return multiply_impl(A, B, C, n, tau, o, stats);
+    } catch (...) {
+        g_last_error = "internal exception";
+        return SPAMM_ERR_CUDA;
+    }
+}
+
+int spamm_sqrt_invsqrt(const double* S, int n, double tau, int maxit, double* Y, double* Z, const spamm_opts* opts,
+                       spamm_stats* stats) {
+    try {
+        g_last_error.clear();
+        spamm_opts o = resolve_opts(opts);
+        int e = check_common(n, tau, o);
+        if (e) return e;
+        if (!S || !Y || !Z || maxit < 0) {
+            g_last_error = "null matrix pointer or maxit < 0";
+            return SPAMM_ERR_ARG;
+        }
+        if (o.precision != SPAMM_FP64) {
+            g_last_error = "precision not available in this build";
+            return SPAMM_ERR_UNSUPPORTED;
+        }
+        return sqrt_impl(S, n, tau, maxit, Y, Z, o, stats);
+    } catch (...) {
+        g_last_error = "internal exception";
+        return SPAMM_ERR_CUDA;
+    }
+}
+
+int spamm_sqrt_invsqrt_batched(int count, const double* const* S, const int* n, const double* tau, int maxit,
+                               double* const* Y, double* const* Z, const spamm_opts* opts, spamm_stats* stats) {
+    try {
+        g_last_error.clear();
+        if (count < 0 || (count > 0 && (!S || !n || !tau || !Y || !Z))) {
+            g_last_error = "bad batch arguments";
+            return SPAMM_ERR_ARG;
+        }
+        if (count == 0) return SPAMM_OK;
+        spamm_opts base = resolve_opts(opts);
+        for (int q = 0; q < count; ++q) {
+            int e = check_common(n[q], tau[q], base);
+            if (e) return e;
+        }
+        int dev = 0;
+        CK(cudaGetDevice(&dev));
+        const int workers = count < 8 ? count : 8;
+        std::vector<int> status(count, SPAMM_OK);
+        std::vector<std::string> errs(count);
+        std::atomic<int> next(0);
+        auto work = [&]() {
+            cudaSetDevice(dev);
+            cudaStream_t st = nullptr;
+            cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+            spamm_opts o = base;
+            o.stream = st;
+            for (;;) {
+                int q = next.fetch_add(1);
+                if (q >= count) break;
+                status[q] = sqrt_impl(S[q], n[q], tau[q], maxit, Y[q], Z[q], o, stats ? stats + q : nullptr);
+                if (status[q]) errs[q] = g_last_error;
+            }
+            cudaStreamDestroy(st);
+        };
+        std::vector<std::thread> th;
+        for (int w = 0; w < workers; ++w) th.emplace_back(work);
+        for (auto& t : th) t.join();
+        for (int q = 0; q < count; ++q)
+            if (status[q]) {
+                g_last_error = errs[q];
+                return status[q];
+            }
+        return SPAMM_OK;
+    } catch (...) {
+        g_last_error = "internal exception";
+        return SPAMM_ERR_CUDA;
+    }
+}
+
+int spamm_norm_tree(const double* A, int n, int leaf, double* nu_leaf, double* root, void* stream) {
+    try {
+        g_last_error.clear();
+        spamm_opts o;
+        spamm_opts_init(&o);
+        o.leaf = leaf == 0 ? 64 : leaf;
+        int e = check_common(n, 0.0, o);
+        if (e) return e;
+        if (!A || !nu_leaf || !root) {
+            g_last_error = "null pointer";
+            return SPAMM_ERR_ARG;
+        }
+        cudaStream_t st = (cudaStream_t)stream;
+        PlanGuard pg;
+        if ((e = g_pool.acquire(n, o.leaf, &pg.p))) return e;
+        Plan* p = pg.p;
+        const Geometry& g = p->g;
+        const double* dA;
+        if ((e = stage_in(p, 0, A, st, &dA))) return e;
+        launch_pack(dA, n, g, nullptr, nullptr, p->buf[0], st);
+        launch_tree(g, p->buf[0].tree, nullptr, st);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(nu_leaf, p->buf[0].tree, (size_t)g.m * g.m * sizeof(double), cudaMemcpyDefault, st));
+        CK(cudaMemcpyAsync(root, p->buf[0].tree + g.off[0], sizeof(double), cudaMemcpyDefault, st));
+        CK(cudaStreamSynchronize(st));
+        return SPAMM_OK;
+    } catch (...) {
+        g_last_error = "internal exception";
+        return SPAMM_ERR_CUDA;
+    }
+}
+
+int spamm_cull(const double* A, const double* B, int n, double tau, int leaf, int* counts, int* jlist, double* thr,
+               long long* total, void* stream) {
+    try {
+        g_last_error.clear();
+        spamm_opts o;
+        spamm_opts_init(&o);
+        o.leaf = leaf == 0 ? 64 : leaf;
+        int e = check_common(n, tau, o);
+        if (e) return e;
+        if (!A || !B || !counts || !jlist) {
+            g_last_error = "null pointer";
+            return SPAMM_ERR_ARG;
+        }
+        cudaStream_t st = (cudaStream_t)stream;
+        PlanGuard pg;
+        if ((e = g_pool.acquire(n, o.leaf, &pg.p))) return e;
+        Plan* p = pg.p;
+        const Geometry& g = p->g;
+        if ((e = ensure_hist(p, 1))) return e;
+        const double *dA, *dB;
+        if ((e = stage_in(p, 0, A, st, &dA))) return e;
+        if ((e = stage_in(p, 1, B, st, &dB))) return e;
+        CK(cudaMemsetAsync(p->task_ctr, 0, sizeof(unsigned long long), st));
+        CK(cudaMemsetAsync(p->jlist, 0xff, (size_t)g.m * g.m * g.m * sizeof(int), st));
+        launch_pack(dA, n, g, nullptr, nullptr, p->buf[0], st);
+        launch_tree(g, p->buf[0].tree, nullptr, st);
+        launch_pack(dB, n, g, nullptr, nullptr, p->buf[1], st);
+        launch_tree(g, p->buf[1].tree, nullptr, st);
+        launch_cull(g, p->buf[0].tree, p->buf[1].tree, tau, p->counts, p->jlist, p->task_ctr, p->scal + 4, nullptr,
+                    st);
+        CK(cudaGetLastError());
+        unsigned long long tot = 0;
+        double thr_h = 0.0;
+        CK(cudaMemcpyAsync(counts, p->counts, (size_t)g.m * g.m * sizeof(int), cudaMemcpyDefault, st));
+        CK(cudaMemcpyAsync(jlist, p->jlist, (size_t)g.m * g.m * g.m * sizeof(int), cudaMemcpyDefault, st));
+        CK(cudaMemcpyAsync(&tot, p->task_ctr, sizeof(tot), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(&thr_h, p->scal + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (thr) *thr = thr_h;
+        if (total) *total = (long long)tot;
+        return SPAMM_OK;
+    } catch (...) {
+        g_last_error = "internal exception";
+        return SPAMM_ERR_CUDA;
+    }
+}
+
+const char* spamm_last_error(void) { return g_last_error.c_str(); }
+
+const char* spamm_strerror(int s) {
+    switch (s) {
+        case SPAMM_OK: return "SPAMM_OK";
+        case SPAMM_ERR_ARG: return "SPAMM_ERR_ARG";
+        case SPAMM_ERR_NOMEM: return "SPAMM_ERR_NOMEM";
+        case SPAMM_ERR_DIVERGED: return "SPAMM_ERR_DIVERGED";
+        case SPAMM_ERR_NOTCONVERGED: return "SPAMM_ERR_NOTCONVERGED";
+        case SPAMM_ERR_TIMEOUT: return "SPAMM_ERR_TIMEOUT";
+        case SPAMM_ERR_ADMIT: return "SPAMM_ERR_ADMIT";
+        case SPAMM_ERR_CUDA: return "SPAMM_ERR_CUDA";
+        case SPAMM_ERR_UNSUPPORTED: return "SPAMM_ERR_UNSUPPORTED";
+        case SPAMM_ERR_NOTFOUND: return "SPAMM_ERR_NOTFOUND";
+        default: return "SPAMM_ERR_UNKNOWN";
+    }
+}
+
+int spamm_release(void) {
+    g_pool.clear();
+    return SPAMM_OK;
+}
+
+long long spamm_kernel_launches(void) { return g_launches.load(); }
+
+const char* spamm_version(void) { return "spamm-gb300 0.1"; }
+
+}  // extern "C"

@@ -1,0 +1,74 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds, loads,
+exports every symbol include/spamm.h declares, and rejects bad arguments
+before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1508_05856_gb300 as sp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _header_symbols():
+    txt = open(os.path.join(ROOT, "include", "spamm.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(spamm_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_library_builds_and_loads():
+    path = sp.build()
+    assert os.path.exists(path)
+    L = sp.lib()
+    assert sp.version().startswith("spamm-gb300")
+
+
+def test_every_header_symbol_is_exported():
+    syms = _header_symbols()
+    assert syms, "no declarations parsed"
+    assert sorted(sp.HEADER_SYMBOLS) == syms
+    raw = ctypes.CDLL(sp.lib_path())
+    for s in syms:
+        assert hasattr(raw, s), s
+
+
+def test_strerror_and_defaults():
+    L = sp.lib()
+    assert L.spamm_strerror(0) == b"SPAMM_OK"
+    assert L.spamm_strerror(-3) == b"SPAMM_ERR_DIVERGED"
+    o = sp.Opts()
+    L.spamm_opts_init(ctypes.byref(o))
+    assert o.leaf == 64 and o.precision == sp.FP64 and o.tau_s < 0 and o.order == sp.ORDER_PAPER
+
+
+@pytest.mark.parametrize("n,tau,leaf", [(0, 1e-6, 64), (-5, 1e-6, 64), (64, -1.0, 64), (64, float("nan"), 64),
+                                        (64, 1e-6, 48), (64, float("inf"), 64)])
+def test_bad_arguments_rejected_without_device(n, tau, leaf):
+    L = sp.lib()
+    o = sp.Opts()
+    L.spamm_opts_init(ctypes.byref(o))
+    o.leaf = leaf
+    buf = (ctypes.c_double * 16)()
+    st = L.spamm_multiply(buf, buf, buf, n, tau, ctypes.byref(o), None)
+    assert st == -1
+    assert L.spamm_last_error()
+    st = L.spamm_sqrt_invsqrt(buf, n, tau, 5, buf, buf, ctypes.byref(o), None)
+    assert st == -1
+
+
+def test_bad_option_fields_rejected():
+    L = sp.lib()
+    o = sp.Opts()
+    L.spamm_opts_init(ctypes.byref(o))
+    o.order = 7
+    buf = (ctypes.c_double * 16)()
+    assert L.spamm_sqrt_invsqrt(buf, 4, 0.0, 5, buf, buf, ctypes.byref(o), None) == -1
+    L.spamm_opts_init(ctypes.byref(o))
+    o.mu_rel = -1.0
+    assert L.spamm_sqrt_invsqrt(buf, 4, 0.0, 5, buf, buf, ctypes.byref(o), None) == -1
+    L.spamm_opts_init(ctypes.byref(o))
+    assert L.spamm_sqrt_invsqrt(None, 4, 0.0, 5, buf, buf, ctypes.byref(o), None) == -1
+    assert L.spamm_sqrt_invsqrt_batched(-1, None, None, None, 5, None, None, None, None) == -1
+    assert L.spamm_sqrt_invsqrt_batched(0, None, None, None, 5, None, None, None, None) == 0

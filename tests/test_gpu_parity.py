@@ -1,0 +1,195 @@
+"""GPU parity of the FP64 path against the CPU oracle, through the C ABI.
+
+Tolerances (FP64 path):
+  * leaf norms: relative 1e-13 (sums of nb^2 squares in a different order,
+    with fused multiply-adds: bound nb^2 u, observed ~1e-15);
+  * task lists: identical except triples within the band
+    |nu_a nu_b / thr - 1| <= 2e-6 (the norms feeding the test differ in the
+    last bits because the summation orders differ);
+  * one product with identical task lists: |C - C_oracle| <= 4 K u (|A||B|)
+    elementwise, K = inner length, u = 2^-53 (same summation order, fused vs
+    separate multiply-add);
+  * Newton-Schulz: ||Z - Z_oracle||_F / ||Z_oracle||_F <= 1e-10 (and Y alike).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+sp = pytest.importorskip("paper_1508_05856_gb300")
+
+pytestmark = pytest.mark.gpu
+U = 2.0 ** -53
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+def host(t):
+    return t.cpu().numpy() if hasattr(t, "cpu") else t
+
+
+def _band_ok(A, B, nb, tau, gpu_tasks, or_tasks, thr):
+    la, lb = oracle.leaf_norms(A, nb), oracle.leaf_norms(B, nb)
+    g = set(map(tuple, gpu_tasks.tolist()))
+    o = set(map(tuple, or_tasks.tolist()))
+    diff = g ^ o
+    for (i, j, k) in diff:
+        r = la[i, j] * lb[j, k] / thr if thr > 0 else math.inf
+        assert abs(r - 1.0) <= 2e-6, f"task {(i, j, k)} differs outside the tolerance band (ratio {r})"
+    return len(diff)
+
+
+# ------------------------------------------------------------------------------------------ norm tree
+
+
+@pytest.mark.parametrize("n,nb", [(256, 32), (200, 64), (1000, 128), (64, 64), (4096, 64)])
+def test_norm_tree(n, nb):
+    A = synth.decay_matrix(n, seed=n + nb)
+    nu, root = sp.norm_tree(dev(A), nb)
+    ref = oracle.leaf_norms(A, nb)
+    np.testing.assert_allclose(nu, ref, rtol=1e-13, atol=0)
+    tree = oracle.norm_tree(A, nb)
+    assert root == pytest.approx(tree[0][0, 0], rel=1e-13)
+
+
+# ------------------------------------------------------------------------------------------ cull
+
+
+@pytest.mark.parametrize("n,nb,tau", [(256, 32, 1e-3), (500, 32, 1e-4), (1024, 64, 1e-5), (640, 128, 1e-6),
+                                      (200, 64, 0.0), (4096, 64, 1e-8)])
+def test_cull_lists(n, nb, tau):
+    A = synth.decay_matrix(n, seed=1, length=n / 20)
+    B = synth.decay_matrix(n, seed=2, length=n / 15)
+    gt, thr, tot = sp.cull(dev(A), dev(B), tau, nb)
+    ot, othr = oracle.cull(A, B, nb, tau)
+    assert thr == pytest.approx(othr, rel=1e-12, abs=0)
+    assert tot == gt.shape[0]
+    nd = _band_ok(A, B, nb, tau, gt, ot, othr)
+    assert nd == 0 or nd < 3
+    if nd == 0:
+        np.testing.assert_array_equal(gt, ot)       # same canonical (i, k, j) order
+
+
+# ------------------------------------------------------------------------------------------ products
+
+
+@pytest.mark.parametrize("n,nb", [(64, 32), (100, 32), (256, 64), (300, 64), (384, 128), (129, 128)])
+def test_tau_zero_integer_bitwise(n, nb):
+    A = synth.integer_matrix(n, seed=3)
+    B = synth.integer_matrix(n, seed=4)
+    C, st = sp.multiply(dev(A), dev(B), 0.0, leaf=nb)
+    Co, cnt = oracle.spamm(A, B, nb, 0.0)
+    np.testing.assert_array_equal(host(C), Co)
+    assert st["tasks_total"] == cnt
+
+
+@pytest.mark.parametrize("n,nb,tau", [(256, 32, 1e-3), (333, 32, 1e-4), (512, 64, 1e-6), (768, 128, 1e-7),
+                                      (1000, 64, 0.0)])
+def test_multiply_matches_oracle(n, nb, tau):
+    A = synth.decay_matrix(n, seed=5, length=n / 16)
+    B = synth.decay_matrix(n, seed=6, length=n / 10)
+    C, st = sp.multiply(dev(A), dev(B), tau, leaf=nb)
+    C = host(C)
+    ot, thr = oracle.cull(A, B, nb, tau)
+    gt, _, _ = sp.cull(dev(A), dev(B), tau, nb)
+    _band_ok(A, B, nb, tau, gt, ot, thr)
+    Co = oracle.leaf_products(A, B, nb, gt)           # oracle arithmetic on the GPU's (valid) list
+    K = (max(1, int(np.bincount(gt[:, 0] * 10000 + gt[:, 2]).max())) if len(gt) else 1) * nb
+    bound = 4 * K * U * (np.abs(A) @ np.abs(B)) + 1e-300
+    assert (np.abs(C - Co) <= bound).all()
+    assert st["tasks_total"] == len(gt)
+
+
+def test_host_and_device_pointers_agree():
+    n, nb, tau = 300, 32, 1e-5
+    A = synth.decay_matrix(n, seed=8)
+    B = synth.decay_matrix(n, seed=9)
+    Ch, _ = sp.multiply(A, B, tau, leaf=nb)                # numpy in, numpy out (host staging)
+    Cd, _ = sp.multiply(dev(A), dev(B), tau, leaf=nb)
+    np.testing.assert_array_equal(Ch, host(Cd))
+
+
+# ------------------------------------------------------------------------------------------ Newton-Schulz
+
+
+def _ns_compare(S, nb, tau, maxit, **kw):
+    Y, Z, st = sp.sqrt_invsqrt(dev(S), tau, maxit, leaf=nb, **kw)
+    Y, Z = host(Y), host(Z)
+    kw2 = {k: v for k, v in kw.items() if k in ("tau_s", "mu_rel", "order", "tol_t")}
+    ref = oracle.sqrt_invsqrt(S, nb, tau, maxit, **kw2)
+    assert st["iters"] == ref["iters"]
+    ez = np.linalg.norm(Z - ref["Z"]) / np.linalg.norm(ref["Z"])
+    ey = np.linalg.norm(Y - ref["Y"]) / np.linalg.norm(ref["Y"])
+    assert ez <= 1e-10, ez
+    assert ey <= 1e-10, ey
+    assert st["scale_c"] == pytest.approx(ref["scale_c"], rel=1e-14)
+    np.testing.assert_allclose(st["t_hist"], ref["t_hist"], rtol=0, atol=1e-12)
+    return Y, Z, st, ref
+
+
+def test_ns_gaussian_256_leaf32():
+    """Gaussian decay, 256 jittered lattice points (sigma 0.6, seed 0), N_b 32, tau 1e-6, 30 iterations."""
+    S = synth.gaussian_lattice(256, 0.6, seed=0)
+    Y, Z, st, ref = _ns_compare(S, 32, 1e-6, 30)
+    np.testing.assert_array_equal(st["task_hist"], ref["task_hist"])
+
+
+@pytest.mark.parametrize("n,nb,tau,order", [(200, 32, 1e-5, 0), (200, 64, 1e-7, 1), (333, 128, 1e-6, 0),
+                                            (96, 32, 0.0, 1), (600, 64, 1e-9, 0)])
+def test_ns_ragged_and_orders(n, nb, tau, order):
+    S = synth.gaussian_lattice(n, 0.7, seed=n)
+    _ns_compare(S, nb, tau, 25, order=order)
+
+
+def test_ns_kms_regularised_and_tol():
+    S = synth.kms(320, 0.9)
+    _ns_compare(S, 64, 1e-8, 30, mu_rel=1e-3)
+    Y, Z, st, ref = _ns_compare(S, 32, 1e-10, 40, tol_t=1e-13)
+    assert st["iters"] < 40
+
+
+def test_ns_diagonal_bitwise():
+    d = np.linspace(0.01, 2.0, 150)
+    S = np.diag(d)
+    Y, Z, st = sp.sqrt_invsqrt(dev(S), 0.0, 12, leaf=32)
+    ref = oracle.sqrt_invsqrt(S, 32, 0.0, 12)
+    np.testing.assert_array_equal(host(Y), ref["Y"])
+    np.testing.assert_array_equal(host(Z), ref["Z"])
+
+
+def test_residual_matches_oracle():
+    S = synth.kms(256, 0.8)
+    Y, Z, st = sp.sqrt_invsqrt(dev(S), 1e-9, 25, leaf=32, residual=True)
+    r = oracle.residual(S, host(Z))
+    assert st["resid_F"] == pytest.approx(r, rel=1e-6, abs=1e-14)
+
+
+def test_batched_equals_single_bitwise():
+    specs = synth.batch_mix(6, lo=128, hi=512, seed=3)
+    Ss = [synth.make(s) for s in specs]
+    taus = [1e-6] * len(Ss)
+    Ys, Zs, sts = sp.sqrt_invsqrt_batched([dev(S) for S in Ss], taus, 20, leaf=32)
+    for S, Yb, Zb in zip(Ss, Ys, Zs):
+        Y1, Z1, _ = sp.sqrt_invsqrt(dev(S), 1e-6, 20, leaf=32)
+        assert torch.equal(Yb, Y1) and torch.equal(Zb, Z1)
+
+
+def test_divergence_reported():
+    """An indefinite S has no real square root: the trace error leaves [0,1) and the call says so."""
+    S = synth.kms(128, 0.5)
+    S[0, 0] = -3.0
+    Y, Z, st = sp.sqrt_invsqrt(dev(S), 0.0, 30, leaf=32, raise_on=False)
+    assert st["status"] == -3
+
+
+@pytest.mark.slow
+def test_ns_kms_4096_full_size():
+    """KMS rho 0.9, N 4096, N_b 64 (the benchmark workload's geometry) at tau 1e-8: full iteration vs oracle."""
+    S = synth.kms(4096, 0.9)
+    _ns_compare(S, 64, 1e-8, 30)
