@@ -150,6 +150,30 @@ int spamm_norm_tree(const double* A, int n, int leaf, double* nu_leaf, double* r
 int spamm_cull(const double* A, const double* B, int n, double tau, int leaf, int* counts, int* jlist,
                double* thr, long long* total, void* stream);
 
+/*
+ * C = A (x)_tau B like spamm_multiply, for callers that cannot allocate
+ * device memory.  The paper has no counterpart; this is an interface for
+ * programs that reserve all device memory up front and must not see a
+ * library allocate once they run.  No call here allocates: no cudaMalloc,
+ * cudaFree or allocating library routine.  The scratch is one fixed device
+ * array of about 6.3 MB, held on every GPU that loads the library until the
+ * process exits.
+ *   - A, B, C: device pointers (row-major n x n doubles, caller-owned).
+ *     Host pointers are rejected with SPAMM_ERR_ARG.
+ *   - n <= SPAMM_NOALLOC_MAX_N; larger n returns SPAMM_ERR_UNSUPPORTED.
+ *   - leaf: 32, 64 or 128 (0 selects 64).  stream: cudaStream_t or NULL.
+ *   - The work is enqueued on `stream` and the call returns without waiting;
+ *     synchronise the stream before reading C.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call shares the one array.  Calls ordered on one stream are safe;
+ *     calls that overlap on the GPU (other streams or threads) race.
+ * Same arithmetic and task lists as spamm_multiply with SPAMM_FP64.
+ */
+#define SPAMM_NOALLOC_MAX_N 512
+int spamm_multiply_noalloc(const double* A, const double* B, double* C, int n, double tau, int leaf,
+                           void* stream);
+
 /* Message for the calling thread's last failure ("" if none). */
 const char* spamm_last_error(void);
 

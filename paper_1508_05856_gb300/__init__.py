@@ -37,7 +37,7 @@ STATUS = {0: "SPAMM_OK", -1: "SPAMM_ERR_ARG", -2: "SPAMM_ERR_NOMEM", -3: "SPAMM_
 # every extern "C" function declared in include/spamm.h
 HEADER_SYMBOLS = ["spamm_opts_init", "spamm_multiply", "spamm_sqrt_invsqrt", "spamm_sqrt_invsqrt_batched",
                   "spamm_norm_tree", "spamm_cull", "spamm_last_error", "spamm_strerror", "spamm_release",
-                  "spamm_kernel_launches", "spamm_version"]
+                  "spamm_kernel_launches", "spamm_version", "spamm_multiply_noalloc"]
 
 
 class SpammError(RuntimeError):
@@ -106,6 +106,8 @@ def lib(build_if_missing: bool = True):
         L.spamm_strerror.restype = ctypes.c_char_p
         L.spamm_release.argtypes = []
         L.spamm_release.restype = ip
+        L.spamm_multiply_noalloc.argtypes = [vp, vp, vp, ip, ctypes.c_double, ip, vp]
+        L.spamm_multiply_noalloc.restype = ip
         L.spamm_kernel_launches.argtypes = []
         L.spamm_kernel_launches.restype = ctypes.c_longlong
         L.spamm_version.argtypes = []

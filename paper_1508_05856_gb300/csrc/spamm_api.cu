@@ -26,6 +26,8 @@ void note_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 static thread_local std::string g_last_error;
 
+void set_error_message(const char* msg) { g_last_error = msg; }
+
 static void set_error(const char* what, cudaError_t e) {
     char buf[512];
     snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
