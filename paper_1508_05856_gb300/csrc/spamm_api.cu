@@ -85,6 +85,8 @@ struct Plan {
     int ev_used = 0;
     bool profile = false;
     long long gemm_launches = 0;
+    bool emu = false;        // this call uses the tensor-core (SPAMM_EMU64) leaf products
+    bool emu_ready = false;  // slice buffers allocated
 };
 
 static void free_plan(Plan* p) {
@@ -94,6 +96,9 @@ static void free_plan(Plan* p) {
     for (auto& b : p->buf) {
         cudaFree(b.t);
         cudaFree(b.tree);
+        cudaFree(b.sliceA);
+        cudaFree(b.sliceB);
+        cudaFree(b.rmax);
     }
     cudaFree(p->counts);
     cudaFree(p->jlist);
@@ -137,6 +142,20 @@ static int ensure_hist(Plan* p, int maxit) {
     CKA(cudaMalloc(&p->task_ctr, (3 * (size_t)cap + 4) * sizeof(unsigned long long)));
     CKA(cudaMalloc(&p->t_hist, (size_t)cap * sizeof(double)));
     p->maxit_cap = cap;
+    return SPAMM_OK;
+}
+
+static int ensure_emu(Plan* p) {
+    if (p->emu_ready) return SPAMM_OK;
+    const Geometry& g = p->g;
+    const size_t per = emu_slice_bytes_per_tile() * (size_t)g.m * g.m;
+    for (auto& b : p->buf) {
+        CKA(cudaMalloc(&b.sliceA, per));
+        CKA(cudaMalloc(&b.sliceB, per));
+        CKA(cudaMalloc(&b.rmax, 2 * (size_t)g.m * g.nb * sizeof(unsigned long long)));
+        b.cmax = b.rmax + (size_t)g.m * g.nb;
+    }
+    p->emu_ready = true;
     return SPAMM_OK;
 }
 
@@ -237,8 +256,9 @@ static int stage_out(Plan* p, int which, double* dst, const double* dev, cudaStr
     return SPAMM_OK;
 }
 
-static void begin_call(Plan* p, bool profile) {
+static void begin_call(Plan* p, bool profile, bool emu) {
     p->profile = profile;
+    p->emu = emu;
     p->ev_used = 0;
     p->gemm_launches = 0;
 }
@@ -267,16 +287,30 @@ static void product(Plan* p, const TileMat& A, const TileMat& B, TileMat& C, dou
                     unsigned long long* ctr, cudaStream_t st) {
     const Geometry& g = p->g;
     launch_cull(g, A.tree, B.tree, tau, p->counts, p->jlist, ctr, nullptr, p->flags, st);
+    if (p->emu) cudaMemsetAsync(C.rmax, 0, 2 * (size_t)g.m * g.nb * sizeof(unsigned long long), st);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (p->profile) {
         e0 = next_event(p);
         e1 = next_event(p);
         if (e0 && e1) cudaEventRecord(e0, st);
     }
-    launch_gemm_f64(g, A.t, B.t, C.t, C.tree, p->counts, p->jlist, 0, mode, p->trace_part, p->flags, st);
+    if (p->emu) {
+        launch_gemm_emu(g, A, B, C, p->counts, p->jlist, mode, p->trace_part, p->flags, p->flags + 2, st);
+    } else {
+        launch_gemm_f64(g, A.t, B.t, C.t, C.tree, p->counts, p->jlist, 0, mode, p->trace_part, p->flags, st);
+    }
     if (e0 && e1) cudaEventRecord(e1, st);
     p->gemm_launches++;
     launch_tree(g, C.tree, p->flags, st);
+    if (p->emu) launch_slice(C.t, C.tree, C.rmax, C.cmax, C.sliceA, C.sliceB, g, p->flags, st);
+}
+
+// Row/column maxima and slices of a freshly packed matrix (tensor-core path).
+static void prepare_emu(Plan* p, const TileMat& M, cudaStream_t st) {
+    const Geometry& g = p->g;
+    cudaMemsetAsync(M.rmax, 0, 2 * (size_t)g.m * g.nb * sizeof(unsigned long long), st);
+    launch_rowcol_max(M.t, g, M.rmax, M.cmax, st);
+    launch_slice(M.t, M.tree, M.rmax, M.cmax, M.sliceA, M.sliceB, g, nullptr, st);
 }
 
 static int multiply_impl(const double* A, const double* B, double* C, int n, double tau, const spamm_opts& o,
@@ -293,20 +327,31 @@ static int multiply_impl(const double* A, const double* B, double* C, int n, dou
     if ((e = stage_in(p, 0, A, st, &dA))) return e;
     if ((e = stage_in(p, 1, B, st, &dB))) return e;
     if ((e = out_target(p, 2, C, &dC))) return e;
-    begin_call(p, o.profile != 0);
+    begin_call(p, o.profile != 0, o.precision == SPAMM_EMU64);
+    if (p->emu && (e = ensure_emu(p))) return e;
     CK(cudaMemsetAsync(p->flags, 0, 4 * sizeof(int), st));
     CK(cudaMemsetAsync(p->task_ctr, 0, 4 * sizeof(unsigned long long), st));
     launch_pack(dA, n, g, nullptr, nullptr, p->buf[0], st);
     launch_tree(g, p->buf[0].tree, nullptr, st);
     launch_pack(dB, n, g, nullptr, nullptr, p->buf[1], st);
     launch_tree(g, p->buf[1].tree, nullptr, st);
+    if (p->emu) {
+        prepare_emu(p, p->buf[0], st);
+        prepare_emu(p, p->buf[1], st);
+    }
     product(p, p->buf[0], p->buf[1], p->buf[2], tau, EPI_PLAIN, p->task_ctr, st);
     launch_unpack(p->buf[2].t, g, dC, nullptr, nullptr, st);
     CK(cudaGetLastError());
     if ((e = stage_out(p, 2, C, dC, st))) return e;
     unsigned long long tasks = 0;
+    int flags_h[4] = {0, 0, 0, 0};
     CK(cudaMemcpyAsync(&tasks, p->task_ctr, sizeof(tasks), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(flags_h, p->flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    if (flags_h[2]) {
+        g_last_error = "a bounded device-side wait of the tensor-core kernel expired";
+        return SPAMM_ERR_TIMEOUT;
+    }
     if (stats) {
         stats->iters = 0;
         stats->t_final = 0.0;
@@ -351,7 +396,8 @@ static int sqrt_impl(const double* S, int n, double tau, int maxit, double* Y, d
     if ((e = stage_in(p, 0, S, st, &dS))) return e;
     if ((e = out_target(p, 1, Y, &dY))) return e;
     if ((e = out_target(p, 2, Z, &dZ))) return e;
-    begin_call(p, o.profile != 0);
+    begin_call(p, o.profile != 0, o.precision == SPAMM_EMU64);
+    if (p->emu && (e = ensure_emu(p))) return e;
 
     CK(cudaMemsetAsync(p->flags, 0, 4 * sizeof(int), st));
     CK(cudaMemsetAsync(p->task_ctr, 0, (3 * (size_t)p->maxit_cap + 4) * sizeof(unsigned long long), st));
@@ -379,6 +425,11 @@ static int sqrt_impl(const double* S, int n, double tau, int maxit, double* Y, d
     launch_tree(g, Tb.tree, nullptr, st);
     launch_identity(g, Zb, st);
     launch_tree(g, Zb.tree, nullptr, st);
+    if (p->emu) {
+        prepare_emu(p, Yb, st);
+        prepare_emu(p, Tb, st);
+        prepare_emu(p, Zb, st);
+    }
     CK(cudaGetLastError());
 
     // a3-a6: the iteration
@@ -423,15 +474,19 @@ static int sqrt_impl(const double* S, int n, double tau, int maxit, double* Y, d
     std::vector<double> th((size_t)(it_host > 0 ? it_host : 1), 0.0);
     std::vector<unsigned long long> kc(3 * (size_t)(it_host > 0 ? it_host : 1), 0ull);
     double c_host = 0.0;
-    int flags_h[2] = {0, 0};
+    int flags_h[4] = {0, 0, 0, 0};
     if (it_host > 0) {
         CK(cudaMemcpyAsync(th.data(), p->t_hist, it_host * sizeof(double), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(kc.data(), p->task_ctr, 3 * (size_t)it_host * sizeof(unsigned long long),
                            cudaMemcpyDeviceToHost, st));
     }
     CK(cudaMemcpyAsync(&c_host, c, sizeof(double), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(flags_h, p->flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(flags_h, p->flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    if (flags_h[2]) {
+        g_last_error = "a bounded device-side wait of the tensor-core kernel expired";
+        return SPAMM_ERR_TIMEOUT;
+    }
 
     const int iters = it_host;
     long long total = 0;
@@ -490,6 +545,10 @@ static int check_common(int n, double tau, const spamm_opts& o) {
         return SPAMM_ERR_ARG;
     }
     const long m = (n + o.leaf - 1) / o.leaf;
+    if (o.precision == SPAMM_EMU64 && (o.leaf != 64 || m > 512)) {
+        g_last_error = "SPAMM_EMU64 needs leaf 64 and n <= 32768";
+        return SPAMM_ERR_UNSUPPORTED;
+    }
     if (m > 1024) {
         g_last_error = "more than 1024 leaf tiles per side";
         return SPAMM_ERR_UNSUPPORTED;
@@ -527,10 +586,6 @@ int spamm_multiply(const double* A, const double* B, double* C, int n, double ta
             g_last_error = "null matrix pointer";
             return SPAMM_ERR_ARG;
         }
-        if (o.precision != SPAMM_FP64) {
-            g_last_error = "precision not available for spamm_multiply in this build";
-            return SPAMM_ERR_UNSUPPORTED;
-        }
         return multiply_impl(A, B, C, n, tau, o, stats);
     } catch (...) {
         g_last_error = "internal exception";
@@ -548,10 +603,6 @@ int spamm_sqrt_invsqrt(const double* S, int n, double tau, int maxit, double* Y,
         if (!S || !Y || !Z || maxit < 0) {
             g_last_error = "null matrix pointer or maxit < 0";
             return SPAMM_ERR_ARG;
-        }
-        if (o.precision != SPAMM_FP64) {
-            g_last_error = "precision not available in this build";
-            return SPAMM_ERR_UNSUPPORTED;
         }
         return sqrt_impl(S, n, tau, maxit, Y, Z, o, stats);
     } catch (...) {

@@ -29,9 +29,16 @@ Geometry make_geometry(int n, int nb);
 // Tile-major FP64 matrix: tile (i,j) is nb*nb row-major doubles at
 // t + (i*m + j)*nb*nb.  tree holds the squared Frobenius norms of every
 // quadtree node.
+// With the tensor-core (SPAMM_EMU64) arithmetic a matrix also carries its
+// BF16 slices in the operand-A and operand-B layouts and the magnitude
+// maxima (IEEE bits) of its rows and columns.
 struct TileMat {
     double* t = nullptr;
     double* tree = nullptr;
+    uint8_t* sliceA = nullptr;
+    uint8_t* sliceB = nullptr;
+    unsigned long long* rmax = nullptr;  // [m*nb], followed by
+    unsigned long long* cmax = nullptr;  // [m*nb]
 };
 
 // Geometry passed by value to kernels.
@@ -85,5 +92,19 @@ void launch_resid_norm(const double* R, const Geometry& g, double* partial, doub
 void launch_gemm_f64(const Geometry& g, const double* A, const double* B, double* C, double* treeC,
                      const int* counts, const int* jlist, int dense, EpiMode mode, double* trace_part,
                      const int* done, cudaStream_t st);
+
+// ---- kernels_emu.cu (leaf tile 64 only) -----------------------------------
+size_t emu_slice_bytes_per_tile();  // bytes of one tile's slices in one operand role
+// Row/column magnitude maxima of a packed matrix (arrays must be zeroed first).
+void launch_rowcol_max(const double* X, const Geometry& g, unsigned long long* rmax, unsigned long long* cmax,
+                       cudaStream_t st);
+// BF16 slices of both operand roles from FP64 tiles and row/column maxima.
+void launch_slice(const double* X, const double* leaf, const unsigned long long* rmax, const unsigned long long* cmax,
+                  uint8_t* sA, uint8_t* sB, const Geometry& g, const int* done, cudaStream_t st);
+// Leaf products on the tensor cores; writes C's FP64 tiles, leaf norms and
+// row/column maxima (pre-zeroed), trace partials for EPI_NS_X; *err set on a
+// timed-out internal wait.
+void launch_gemm_emu(const Geometry& g, const TileMat& A, const TileMat& B, const TileMat& C, const int* counts,
+                     const int* jlist, EpiMode mode, double* trace_part, const int* done, int* err, cudaStream_t st);
 
 }  // namespace spamm

@@ -1,0 +1,115 @@
+"""GPU parity of the tensor-core (SPAMM_EMU64) leaf products against the FP64 CPU oracle.
+
+Error model (derived in kernels_emu.cu): each operand entry is held to
+2^-49 of its row (A role) or column (B role) magnitude bound 2^e <= 2 max|.|;
+slice pairs p+q >= 6 are dropped except (1,5), (3,3), (5,1).  Per product
+element the error is at most about K * 2^-46 * 2^(eA_r + eB_c) plus the FP64
+rounding of the final value, K = inner length.  The tests use
+  |C - C_oracle| <= K 2^-44 rowmax(A)_r colmax(B)_c + 4 K u (|A||B|)_rc
+(2^(eA) <= 2 rowmax, 2^(eB) <= 2 colmax).  Integer inputs whose row and column
+maxima are powers of two are represented exactly, so tau = 0 products are
+then bitwise equal to the exact product.  Newton-Schulz with these products:
+||Z - Z_oracle||_F / ||Z_oracle||_F <= 1e-9 (the iteration carries product
+errors forward without damping them; a numpy model of this arithmetic gives
+about 1e-10 residuals on KMS at N = 512-1024).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+sp = pytest.importorskip("paper_1508_05856_gb300")
+
+pytestmark = pytest.mark.gpu
+U = 2.0 ** -53
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+def _tol(A, B, K):
+    ra = np.abs(A).max(axis=1)[:, None]
+    cb = np.abs(B).max(axis=0)[None, :]
+    return K * 2.0 ** -44 * ra * cb + 4 * K * U * (np.abs(A) @ np.abs(B)) + 1e-300
+
+
+@pytest.mark.parametrize("n", [64, 128, 200, 512])
+def test_emu_integer_tau0_bitwise(n):
+    rng = np.random.default_rng(n)
+    A = rng.integers(-2, 3, size=(n, n)).astype(np.float64)
+    B = rng.integers(-2, 3, size=(n, n)).astype(np.float64)
+    A[:, 0] = 2.0          # every row / column maximum is exactly 2
+    B[0, :] = -2.0
+    C, st = sp.multiply(dev(A), dev(B), 0.0, leaf=64, precision=sp.EMU64)
+    exact = (A.astype(np.int64) @ B.astype(np.int64)).astype(np.float64)
+    np.testing.assert_array_equal(C.cpu().numpy(), exact)
+
+
+@pytest.mark.parametrize("n,tau", [(256, 1e-3), (300, 1e-6), (640, 0.0), (1024, 1e-8)])
+def test_emu_multiply_matches_oracle(n, tau):
+    A = synth.decay_matrix(n, seed=11, length=n / 10)
+    B = synth.decay_matrix(n, seed=12, length=n / 14)
+    C, st = sp.multiply(dev(A), dev(B), tau, leaf=64, precision=sp.EMU64)
+    C = C.cpu().numpy()
+    gt, _, _ = sp.cull(dev(A), dev(B), tau, 64)
+    Co = oracle.leaf_products(A, B, 64, gt)
+    assert st["tasks_total"] == len(gt)
+    m = (n + 63) // 64
+    assert (np.abs(C - Co) <= _tol(A, B, m * 64)).all()
+
+
+def test_emu_multiply_kms_scales():
+    """Rows with very different magnitudes (scaled KMS): per-row scales keep small rows accurate."""
+    n = 384
+    S = synth.kms(n, 0.8)
+    d = np.exp(np.linspace(-8, 3, n))
+    A = d[:, None] * S
+    B = S * d[None, :]
+    C, _ = sp.multiply(dev(A), dev(B), 0.0, leaf=64, precision=sp.EMU64)
+    Co, _ = oracle.spamm(A, B, 64, 0.0)
+    assert (np.abs(C.cpu().numpy() - Co) <= _tol(A, B, n)).all()
+
+
+def _emu_ns(S, tau, maxit, **kw):
+    Y, Z, st = sp.sqrt_invsqrt(dev(S), tau, maxit, leaf=64, precision=sp.EMU64, **kw)
+    ref = oracle.sqrt_invsqrt(S, 64, tau, maxit, **{k: v for k, v in kw.items() if k in ("order", "mu_rel")})
+    ez = np.linalg.norm(Z.cpu().numpy() - ref["Z"]) / np.linalg.norm(ref["Z"])
+    ey = np.linalg.norm(Y.cpu().numpy() - ref["Y"]) / np.linalg.norm(ref["Y"])
+    return ez, ey, st, ref
+
+
+@pytest.mark.parametrize("kind,n,tau", [("gauss", 256, 1e-6), ("kms", 512, 1e-10), ("gauss", 700, 1e-9)])
+def test_emu_ns_matches_oracle(kind, n, tau):
+    S = synth.gaussian_lattice(n, 0.6, seed=0) if kind == "gauss" else synth.kms(n, 0.9)
+    ez, ey, st, ref = _emu_ns(S, tau, 30)
+    assert ez <= 1e-9 and ey <= 1e-9, (ez, ey)
+
+
+def test_emu_ns_transposed_order():
+    S = synth.gaussian_lattice(320, 0.7, seed=4)
+    ez, ey, st, ref = _emu_ns(S, 1e-9, 25, order=sp.ORDER_TRANSPOSED)
+    assert ez <= 1e-9 and ey <= 1e-9, (ez, ey)
+
+
+def test_emu_ns_residual_gate():
+    S = synth.kms(1024, 0.9)
+    Y, Z, st = sp.sqrt_invsqrt(dev(S), 1e-14, 30, leaf=64, precision=sp.EMU64, residual=True)
+    assert st["resid_F"] <= 1e-8, st["resid_F"]
+
+
+def test_emu_batched_equals_single():
+    specs = synth.batch_mix(5, lo=128, hi=640, seed=7)
+    Ss = [synth.make(s) for s in specs]
+    Ys, Zs, _ = sp.sqrt_invsqrt_batched([dev(S) for S in Ss], [1e-8] * len(Ss), 20, leaf=64, precision=sp.EMU64)
+    for S, Yb, Zb in zip(Ss, Ys, Zs):
+        Y1, Z1, _ = sp.sqrt_invsqrt(dev(S), 1e-8, 20, leaf=64, precision=sp.EMU64)
+        assert torch.equal(Yb, Y1) and torch.equal(Zb, Z1)
+
+
+def test_emu_rejects_other_leaf_sizes():
+    S = synth.kms(128, 0.5)
+    with pytest.raises(sp.SpammError):
+        sp.sqrt_invsqrt(dev(S), 1e-8, 5, leaf=32, precision=sp.EMU64)
