@@ -355,6 +355,92 @@ def run_gpu(args, ws, rank, local):
     return 0
 
 
+def run_batched(args, local):
+    """Batched configuration: many independent SPD decay matrices of mixed sizes in one call, against the
+    same matrices solved one call at a time."""
+    import torch
+
+    import paper_1508_05856_gb300 as sp
+    import synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = sp.EMU64 if args.precision == "emu64" else sp.FP64
+    specs = synth.batch_mix(args.batch, lo=128, hi=2048, seed=0)
+    Ss = [torch.from_numpy(synth.make(sp_)).to(dev) for sp_ in specs]
+    taus = [args.batch_tau] * len(Ss)
+    sp.sqrt_invsqrt_batched(Ss[:16], taus[:16], MAXIT, leaf=LEAF, precision=prec)   # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Ys, Zs, sts = sp.sqrt_invsqrt_batched(Ss, taus, MAXIT, leaf=LEAF, precision=prec)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for S, t in zip(Ss, taus):
+        sp.sqrt_invsqrt(S, t, MAXIT, leaf=LEAF, precision=prec)
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    line = {"metric": "batched NS solves/s (mixed KMS / 3D Gaussian, N in [128, 2048])", "value": len(Ss) / t_batch,
+            "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": "f64" if prec == sp.FP64 else "bf16-split",
+            "data": "synthetic",
+            "config": {"workload": f"{len(Ss)} matrices, sizes log-uniform in [128, 2048] (multiples of 32), "
+                                   f"50% KMS rho~U(0.5,0.95), 50% Gaussian sigma~U(0.6,0.9), tau={args.batch_tau:g}, "
+                                   f"{MAXIT} iterations", "precision": args.precision},
+            "one_call_per_matrix": {"value": len(Ss) / t_seq, "unit": UNIT},
+            "tasks": int(sum(st["tasks_total"] for st in sts))}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(args, local):
+    """Serving configuration: Poisson arrivals of square-root requests on 3D Gaussian-decay matrices, served
+    with continuous batching; p50/p99 latency and solves/s, against one request at a time."""
+    import numpy as np
+    import torch
+
+    import paper_1508_05856_gb300 as sp
+    import synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = sp.EMU64 if args.precision == "emu64" else sp.FP64
+    trace = synth.serving_trace(args.requests, rate=args.rate, lo=256, hi=args.serve_max_n, seed=0)
+    mats = [torch.from_numpy(synth.make(r)).to(dev) for r in trace]
+    with sp.Server(bytes_budget=int(args.budget_gb * (1 << 30)), max_active=args.max_active, leaf=LEAF,
+                   precision=prec) as srv:
+        for S, r in list(zip(mats, trace))[:4]:
+            srv.wait(srv.submit(S, r["tau"], MAXIT))     # warm-up
+        t0 = time.perf_counter()
+        ids = []
+        for S, r in zip(mats, trace):
+            delay = r["arrival"] - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            ids.append(srv.submit(S, r["tau"], MAXIT))
+        lats = [srv.wait(i)[3] for i in ids]
+        t_all = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    seq_lat = []
+    for S, r in zip(mats, trace):
+        a = time.perf_counter()
+        sp.sqrt_invsqrt(S, r["tau"], MAXIT, leaf=LEAF, precision=prec)
+        seq_lat.append(time.perf_counter() - a)
+    t_seq = time.perf_counter() - t0
+    lat = np.array(lats) * 1e3
+    line = {"metric": "served NS requests: solves/s with p50/p99 latency", "value": len(ids) / t_all, "unit": UNIT,
+            "n_gpus": 1, "higher_is_better": True, "dtype": "f64" if prec == sp.FP64 else "bf16-split",
+            "data": "synthetic",
+            "config": {"workload": f"{len(ids)} requests, Poisson arrivals at {args.rate:g}/s, N log-uniform in "
+                                   f"[256, {args.serve_max_n}] (multiples of 32), 3D Gaussian decay, tau in "
+                                   "{1e-4, 1e-6, 1e-8}", "max_active": args.max_active, "budget_gb": args.budget_gb,
+                       "precision": args.precision},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "one_request_at_a_time": {"value": len(ids) / t_seq, "unit": UNIT,
+                                      "p50_service_ms": float(np.percentile(np.array(seq_lat) * 1e3, 50))}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -366,12 +452,25 @@ def main():
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle time for cpu_baseline")
+    ap.add_argument("--batched", action="store_true", help="batched configuration instead of the headline solve")
+    ap.add_argument("--batch", type=int, default=512)
+    ap.add_argument("--batch-tau", type=float, default=1e-6)
+    ap.add_argument("--serve", action="store_true", help="serving configuration instead of the headline solve")
+    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--serve-max-n", type=int, default=8192)
+    ap.add_argument("--max-active", type=int, default=8)
+    ap.add_argument("--budget-gb", type=float, default=64.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     ws, rank, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, ws, rank)
+    if args.batched:
+        return run_batched(args, local)
+    if args.serve:
+        return run_serve(args, local)
     return run_gpu(args, ws, rank, local)
 
 

@@ -35,6 +35,8 @@
 #ifndef SPAMM_H
 #define SPAMM_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -173,6 +175,50 @@ int spamm_cull(const double* A, const double* B, int n, double tau, int leaf, in
 #define SPAMM_NOALLOC_MAX_N 512
 int spamm_multiply_noalloc(const double* A, const double* B, double* C, int n, double tau, int leaf,
                            void* stream);
+
+/* ---- serving: a request loop over spamm_sqrt_invsqrt ------------------
+ * Requests of any size arrive at any time and are admitted in arrival order
+ * as soon as one of `max_active` workers is free and the request's device
+ * footprint (the scratch spamm_sqrt_invsqrt needs for its size, leaf and
+ * arithmetic, plus staging when its matrices are in host memory) fits in
+ * `bytes_budget` next to the requests already running.  Each worker has its
+ * own CUDA stream, so admitted requests overlap on the device.  Y and Z of a
+ * request are written exactly as spamm_sqrt_invsqrt(S, n, tau, maxit, Y, Z,
+ * opts) writes them: a result does not depend on the other requests.  Work
+ * runs on the device that is current when the server is created.  The
+ * caller keeps S, Y and Z valid until the request is waited for.
+ */
+typedef struct spamm_server spamm_server;
+
+#define SPAMM_REQ_QUEUED 0
+#define SPAMM_REQ_RUNNING 1
+#define SPAMM_REQ_DONE 2
+
+/* Create a server; opts as for spamm_sqrt_invsqrt (residual unsupported,
+ * stream ignored).  SPAMM_ERR_ARG for a zero budget or max_active outside
+ * 1..64. */
+int spamm_server_create(size_t bytes_budget, int max_active, const spamm_opts* opts, spamm_server** server);
+
+/* Queue a request; *id identifies it.  SPAMM_ERR_ADMIT when its footprint
+ * alone exceeds the budget (it could never run); SPAMM_ERR_ARG as for
+ * spamm_sqrt_invsqrt. */
+int spamm_server_submit(spamm_server* server, const double* S, int n, double tau, int maxit, double* Y,
+                        double* Z, long long* id);
+
+/* *state = SPAMM_REQ_QUEUED, _RUNNING or _DONE; SPAMM_ERR_NOTFOUND for an
+ * unknown (or already waited-for) id. */
+int spamm_server_poll(spamm_server* server, long long id, int* state);
+
+/* Wait up to timeout_s seconds (< 0: no limit) for a request, then return
+ * its status (as spamm_sqrt_invsqrt would) and forget it.  stats (may be
+ * NULL; its t_hist/task_hist are not filled) and *latency_s (submit to
+ * completion, may be NULL) are written.  SPAMM_ERR_TIMEOUT if the request is
+ * still pending (it stays queued), SPAMM_ERR_NOTFOUND for an unknown id. */
+int spamm_server_wait(spamm_server* server, long long id, double timeout_s, spamm_stats* stats,
+                      double* latency_s);
+
+/* Finish every queued and running request, then free the server. */
+int spamm_server_destroy(spamm_server* server);
 
 /* Message for the calling thread's last failure ("" if none). */
 const char* spamm_last_error(void);

@@ -37,7 +37,8 @@ STATUS = {0: "SPAMM_OK", -1: "SPAMM_ERR_ARG", -2: "SPAMM_ERR_NOMEM", -3: "SPAMM_
 # every extern "C" function declared in include/spamm.h
 HEADER_SYMBOLS = ["spamm_opts_init", "spamm_multiply", "spamm_sqrt_invsqrt", "spamm_sqrt_invsqrt_batched",
                   "spamm_norm_tree", "spamm_cull", "spamm_last_error", "spamm_strerror", "spamm_release",
-                  "spamm_kernel_launches", "spamm_version", "spamm_multiply_noalloc"]
+                  "spamm_kernel_launches", "spamm_version", "spamm_multiply_noalloc", "spamm_server_create",
+                  "spamm_server_submit", "spamm_server_poll", "spamm_server_wait", "spamm_server_destroy"]
 
 
 class SpammError(RuntimeError):
@@ -108,6 +109,17 @@ def lib(build_if_missing: bool = True):
         L.spamm_release.restype = ip
         L.spamm_multiply_noalloc.argtypes = [vp, vp, vp, ip, ctypes.c_double, ip, vp]
         L.spamm_multiply_noalloc.restype = ip
+        L.spamm_server_create.argtypes = [ctypes.c_size_t, ip, ctypes.POINTER(Opts), ctypes.POINTER(vp)]
+        L.spamm_server_create.restype = ip
+        L.spamm_server_submit.argtypes = [vp, vp, ip, ctypes.c_double, ip, vp, vp, ctypes.POINTER(ctypes.c_longlong)]
+        L.spamm_server_submit.restype = ip
+        L.spamm_server_poll.argtypes = [vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_int)]
+        L.spamm_server_poll.restype = ip
+        L.spamm_server_wait.argtypes = [vp, ctypes.c_longlong, ctypes.c_double, ctypes.POINTER(Stats),
+                                        ctypes.POINTER(ctypes.c_double)]
+        L.spamm_server_wait.restype = ip
+        L.spamm_server_destroy.argtypes = [vp]
+        L.spamm_server_destroy.restype = ip
         L.spamm_kernel_launches.argtypes = []
         L.spamm_kernel_launches.restype = ctypes.c_longlong
         L.spamm_version.argtypes = []
@@ -278,6 +290,58 @@ def cull(A, B, tau: float, leaf: int = 64, stream=None):
             rows.append((i, int(j), k))
     tasks = np.array(rows, dtype=np.int32).reshape(-1, 3)
     return tasks, thr.value, tot.value
+
+
+class Server:
+    """Request loop over sqrt_invsqrt: submit() queues a solve, wait() returns (Y, Z, stats, latency_s).
+
+    Requests are admitted in arrival order when a worker is free and their device footprint fits in the
+    memory budget; admitted requests run concurrently on separate CUDA streams."""
+
+    def __init__(self, bytes_budget: int, max_active: int = 4, leaf: int = 64, precision: int = FP64, tau_s=None,
+                 mu_rel=0.0, tol_t=0.0, order=ORDER_PAPER):
+        self._h = ctypes.c_void_p(0)
+        o = _opts(leaf, precision, tau_s, mu_rel, tol_t, order, False, None)
+        _check(lib().spamm_server_create(int(bytes_budget), int(max_active), ctypes.byref(o), ctypes.byref(self._h)))
+        self._keep = {}
+
+    def submit(self, S, tau: float, maxit: int):
+        s, ps, n, _ = _prep(S)
+        Y, Z = _like(s, n), _like(s, n)
+        rid = ctypes.c_longlong(0)
+        _check(lib().spamm_server_submit(self._h, ps, n, float(tau), int(maxit), _ptr(Y), _ptr(Z), ctypes.byref(rid)))
+        self._keep[rid.value] = (s, Y, Z)
+        return rid.value
+
+    def poll(self, rid: int) -> int:
+        st = ctypes.c_int(0)
+        _check(lib().spamm_server_poll(self._h, int(rid), ctypes.byref(st)))
+        return st.value
+
+    def wait(self, rid: int, timeout: float = -1.0, raise_on=True):
+        stats = Stats()
+        lat = ctypes.c_double(0.0)
+        status = lib().spamm_server_wait(self._h, int(rid), float(timeout), ctypes.byref(stats), ctypes.byref(lat))
+        if status == -5 and timeout >= 0:
+            raise TimeoutError(f"request {rid} still pending")
+        s, Y, Z = self._keep.pop(rid, (None, None, None))
+        d = _stats_dict(stats)
+        d["status"] = status
+        if raise_on:
+            _check(status)
+        return Y, Z, d, lat.value
+
+    def close(self):
+        if self._h:
+            _check(lib().spamm_server_destroy(self._h))
+            self._h = ctypes.c_void_p(0)
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def kernel_launches() -> int:

@@ -5,21 +5,23 @@
 // about FP64; GB300 has little FP64 throughput but a large BF16 one.  Every
 // matrix is therefore held both as FP64 tiles and as six 8-bit "slices":
 //
-//   x ~ 2^e * sum_{p=0..5} d_p 2^{-8(p+1)},  balanced digits |d_p| <= 128
-//                                            (|d_0| <= 256), error <= 2^{-49} 2^e
+//   x ~ 2^e * sum_{p=0..5} d_p 2^{-8(p+1)},  balanced digits |d_p| <= 128,
+//                                            error <= 2^{-49} 2^e,
 //
-// where 2^e bounds the largest magnitude of x's row (operand A role) or of
-// x's column (operand B role) over the whole matrix.  Each digit times its
+// where 2^(e-1) bounds the largest magnitude of x's row (operand A role) or
+// of x's column (operand B role) over the whole matrix.  Each digit times its
 // power of two is exact in BF16.  A product of slices p and q is a sum over
-// 64 terms of integers of magnitude <= 2^16 in units of 2^{-8(p+q+2)}, so the
-// FP32 tensor-core accumulator holds these partial sums exactly (below 2^24
-// even for the two pairs that share an accumulator group).  Per output
-// tile and per task the partial sums are moved from TMEM to registers in five
-// groups (top-half diagonals p+q = 0, 1, 2, 3 exactly, and >= 4 rounded to
-// 2^{-48}) and added, as integers, into a 64-bit fixed-point accumulator with
-// quantum 2^{-48} relative to 2^{e_row + e_col}.  The dropped pairs
-// p+q >= 6 and the truncated digits contribute below ~2^{-46} relative to
-// the row/column scales: a normwise FP64-class product.
+// 64 terms of integers of magnitude <= 2^14 in units of 2^{-8(p+q+2)}: at most
+// 2^20 per pair and task, 2^21 for the two pairs that share an accumulator
+// group.  The FP32 tensor-core accumulators in TMEM therefore hold the sums
+// of up to 7 tasks exactly (7 * 2^21 < 2^24).  Every 7 tasks (and at the end
+// of an output tile) the partial sums are moved from TMEM to registers in
+// five groups (top-half diagonals p+q = 0, 1, 2, 3 exactly, and >= 4 rounded
+// to 2^{-48}) and added, as integers, into a 64-bit fixed-point accumulator
+// with quantum 2^{-48} relative to 2^{e_row + e_col}.  Dropped pairs
+// (p+q >= 6, except the (1,5), (3,3), (5,1) that come with the stacking) and
+// the digit truncation leave an error of a few 2^{-48} per product term
+// relative to 2^{e_row + e_col}: a normwise FP64-class product.
 //
 // Layout (no swizzle, K-major canonical core matrices of 8 rows x 16 bytes,
 // core (row_group, k_group) at ((row_group * 8 + k_group) * 128) bytes):
@@ -30,6 +32,8 @@
 // One M=128, N=64, K=16 MMA (stack s, slice q) yields slice pairs (2s, q) in
 // TMEM lanes 0-63 and (2s+1, q) in lanes 64-127.
 #include <cuda_bf16.h>
+
+#include <algorithm>
 
 #include "spamm_internal.cuh"
 #include "tc_ptx.cuh"
@@ -47,15 +51,20 @@ constexpr uint32_t STAGE_BYTES = A_TILE_BYTES + B_TILE_BYTES;
 constexpr int NSTAGE = 2;
 constexpr uint32_t SMEM_DYN = NSTAGE * STAGE_BYTES + 1024;
 constexpr uint32_t TMEM_COLS = 512;
-constexpr int kThreads = 192;
-constexpr int kMaxTasks = 1024;
+constexpr int kEpiWarps = 4;                 // one per TMEM lane quarter
+constexpr int kThreads = 32 * (2 + kEpiWarps);
+constexpr int kGroups = 5;                   // accumulator groups (64 TMEM columns each)
+constexpr int kChunk = 7;                    // tasks accumulated in TMEM between flushes (exactness bound)
+constexpr int kMaxTasks = 256;
 constexpr long long kSpin = 1ll << 22;
 
-// exponent e with |x| < 2^e for every x of a row/column whose largest
-// magnitude has the IEEE bits `bits` (0 for an all-zero or subnormal row)
+// exponent e with |x| < 2^(e-1) for every x of a row/column whose largest
+// magnitude has the IEEE bits `bits` (0 for an all-zero or subnormal row):
+// the scaled entries x * 2^-e lie in (-1/2, 1/2), so every balanced digit,
+// the leading one included, is at most 128 in magnitude.
 __device__ __forceinline__ int expo_of(unsigned long long bits) {
     const int E = (int)((bits >> 52) & 0x7FF);
-    return E == 0 ? 0 : E - 1022;
+    return E == 0 ? 0 : E - 1021;
 }
 
 // x * 2^-e rounded to a signed fixed-point integer with 48 fractional bits
@@ -84,24 +93,36 @@ __device__ __forceinline__ void balanced_digits(long long F, int (&d)[6]) {
     d[0] = (int)F;
 }
 
-__device__ __forceinline__ __nv_bfloat16 digit_bf16(int d, int p) {
-    const float scale = __int_as_float((127 - 8 * (p + 1)) << 23);  // 2^{-8(p+1)}
-    return __float2bfloat16_rn((float)d * scale);
+// BF16 bits of d * 2^{-8(p+1)} for |d| <= 256, built with integer operations.
+__device__ __forceinline__ uint16_t digit_bf16_bits(int d, int p) {
+    if (d == 0) return 0;
+    const uint32_t sgn = d < 0 ? 0x8000u : 0u;
+    const uint32_t a = (uint32_t)(d < 0 ? -d : d);
+    const int len = 32 - __clz(a);                               // 1..9
+    const uint32_t ex = (uint32_t)(127 + (len - 1) - 8 * (p + 1));
+    const uint32_t mant = len <= 8 ? ((a << (8 - len)) & 0x7Fu) : ((a >> (len - 8)) & 0x7Fu);
+    return (uint16_t)(sgn | (ex << 7) | mant);
 }
 
 // ------------------------------------------------------------------ slicing
 // Leaf tiles with nu == 0 are skipped: the leaf-product kernel never reads
 // them (their products are exactly zero).
+// Grid-stride over the listed tiles (tile_list / tile_count), or over all
+// m*m tiles when tile_list is null.
 __global__ void __launch_bounds__(256) k_slice(const double* __restrict__ X, const double* __restrict__ leaf,
                                                const unsigned long long* __restrict__ rmax,
                                                const unsigned long long* __restrict__ cmax,
                                                uint8_t* __restrict__ sA, uint8_t* __restrict__ sB, int m,
+                                               const int* __restrict__ tile_list, const int* __restrict__ tile_count,
                                                const int* __restrict__ done) {
     if (done && *done) return;
-    const int tile = blockIdx.x;
-    if (leaf[tile] == 0.0) return;
     __shared__ double xs[NB][NB + 1];
     __shared__ int eR[NB], eC[NB];
+    const int ntiles = tile_list ? *tile_count : m * m;
+    for (int idx = blockIdx.x; idx < ntiles; idx += gridDim.x) {
+    const int tile = tile_list ? tile_list[idx] : idx;
+    if (leaf[tile] == 0.0) continue;
+    __syncthreads();
     const int i = tile / m, j = tile - (tile / m) * m;
     const double* x = X + (size_t)tile * NB * NB;
     for (int idx = threadIdx.x; idx < NB * NB; idx += 256) xs[idx >> 6][idx & 63] = x[idx];
@@ -113,15 +134,16 @@ __global__ void __launch_bounds__(256) k_slice(const double* __restrict__ X, con
     for (int item = threadIdx.x; item < 2 * 512; item += 256) {
         const bool arole = item < 512;
         const int it = arole ? item : item - 512;
-        const int r = it >> 3, g = it & 7;  // A: row r, k-group g; B: column r, k-group g
+        // 8 consecutive items fill one 128-byte core matrix, 32 consecutive items 512 contiguous bytes
+        const int r = (it >> 6) * 8 + (it & 7), g = (it >> 3) & 7;  // A: row r, k-group g; B: column r, k-group g
         int D[8][6];
         for (int q = 0; q < 8; ++q) {
             const double v = arole ? xs[r][8 * g + q] : xs[8 * g + q][r];
             balanced_digits(fixed48(v, arole ? eR[r] : eC[r]), D[q]);
         }
         for (int p = 0; p < NSLICE; ++p) {
-            __align__(16) __nv_bfloat16 w[8];
-            for (int q = 0; q < 8; ++q) w[q] = digit_bf16(D[q][p], p);
+            __align__(16) uint16_t w[8];
+            for (int q = 0; q < 8; ++q) w[q] = digit_bf16_bits(D[q][p], p);
             uint32_t off;
             if (arole) {
                 const int row = (p & 1) * 64 + r;
@@ -132,6 +154,7 @@ __global__ void __launch_bounds__(256) k_slice(const double* __restrict__ X, con
                 *reinterpret_cast<uint4*>(b + off) = *reinterpret_cast<const uint4*>(w);
             }
         }
+    }
     }
 }
 
@@ -172,6 +195,8 @@ struct EmuArgs {
     unsigned long long* cmaxC;
     const int* counts;
     const int* jlist;
+    const int* tile_list;               // compacted output tiles with work
+    const int* tile_count;
     double* trace_part;
     const int* done;
     int* err;
@@ -180,6 +205,37 @@ struct EmuArgs {
 
 __device__ __forceinline__ uint32_t stage_addr(uint32_t base, int s) { return base + (uint32_t)s * STAGE_BYTES; }
 
+// int64 -> double as integer operations (round to nearest even), times 2^s.
+__device__ __forceinline__ double fixed_to_double(long long tot, int s) {
+    if (tot == 0) return 0.0;
+    const unsigned long long neg = tot < 0 ? 1ull : 0ull;
+    const unsigned long long u = neg ? (unsigned long long)(-tot) : (unsigned long long)tot;
+    const int lz = __clzll(u);
+    const unsigned long long mnorm = u << lz;  // leading one at bit 63
+    unsigned long long keep = mnorm >> 11;     // 53 bits
+    const unsigned long long rem = mnorm & 0x7FFull;
+    if (rem > 0x400ull || (rem == 0x400ull && (keep & 1ull))) ++keep;
+    int ex = 63 - lz + s;
+    if (keep >> 53) {
+        keep >>= 1;
+        ++ex;
+    }
+    const unsigned long long bits = (neg << 63) | ((unsigned long long)(ex + 1023) << 52) | (keep & 0xFFFFFFFFFFFFFull);
+    return __longlong_as_double((long long)bits);
+}
+
+// -x/2 by exponent arithmetic (exact; normal and zero inputs)
+__device__ __forceinline__ double neg_half(double x) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long ef = (b >> 52) & 0x7FF;
+    if (ef <= 1) return -0.5 * x;  // zero or subnormal: plain arithmetic
+    b ^= 1ull << 63;
+    b -= 1ull << 52;
+    return __longlong_as_double((long long)b);
+}
+
+// Persistent: one CTA per SM walks the compacted output-tile list.  The
+// stage, chunk and barrier phase counters run on across tiles.
 __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
     if (a.done && *a.done) return;
     extern __shared__ uint8_t dyn_smem[];
@@ -187,35 +243,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
     __shared__ uint32_t tmem_base_sh;
     __shared__ int tasks_sh[kMaxTasks];
     __shared__ int ntask_sh;
+    __shared__ int fail_sh;
     __shared__ int eA_sh[NB], eB_sh[NB];
     __shared__ double red_sh[4];
 
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dyn_smem) + 1023) & ~uintptr_t(1023));
     const uint32_t sbase = ptx::smem_addr(smem);
     const int m = a.m;
-    const int tile = blockIdx.x;
-    const int i = tile / m, k = tile - (tile / m) * m;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ntiles = *a.tile_count;
+    if ((int)blockIdx.x >= ntiles) return;
 
-    if (threadIdx.x == 0) {
-        const int cnt = a.counts[tile];
-        const int* js = a.jlist + (size_t)tile * m;
-        int T = 0;
-        for (int t = 0; t < cnt; ++t) {
-            const int j = js[t];
-            if (a.leafA[(size_t)i * m + j] != 0.0 && a.leafB[(size_t)j * m + k] != 0.0) tasks_sh[T++] = j;
-        }
-        ntask_sh = T;
+    if (warp == 2 && lane == 0) {
         for (int s = 0; s < NSTAGE; ++s) {
             ptx::mbar_init(&bar_full[s], 1);
             ptx::mbar_init(&bar_empty[s], 1);
         }
         ptx::mbar_init(&bar_accf, 1);
-        ptx::mbar_init(&bar_acce, 4);
+        ptx::mbar_init(&bar_acce, kEpiWarps);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (threadIdx.x < NB) eA_sh[threadIdx.x] = expo_of(a.rmaxA[i * NB + threadIdx.x]);
-    else if (threadIdx.x < 2 * NB) eB_sh[threadIdx.x - NB] = expo_of(a.cmaxB[k * NB + threadIdx.x - NB]);
     if (warp == 0) {
         ptx::tmem_alloc(&tmem_base_sh, TMEM_COLS);
         ptx::tmem_relinquish();
@@ -224,173 +271,219 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
     __syncthreads();
     ptx::tc_fence_after();
     const uint32_t tmem = tmem_base_sh;
-    const int T = ntask_sh;
 
-    if (warp == 0) {
-        // ---------------- producer: bulk copies of the slices of A_ij and B_jk
-        if (lane == 0) {
-            for (int t = 0; t < T; ++t) {
-                const int s = t & 1;
-                if (t >= 2 && !ptx::mbar_wait_bounded(&bar_empty[s], ((t >> 1) & 1) ^ 1, kSpin)) {
-                    atomicExch(a.err, 1);
-                    break;
+    long long gtask = 0;   // tasks issued by this CTA before the current tile
+    long long gchunk = 0;  // accumulator chunks before the current tile
+    bool fail = false;
+
+    for (int idx = blockIdx.x; idx < ntiles && !fail; idx += gridDim.x) {
+        const int tile = a.tile_list[idx];
+        const int i = tile / m, k = tile - (tile / m) * m;
+        if (warp == 1) {
+            // compact the task list: skip operand tiles of zero norm (exact zero products)
+            const int cnt = a.counts[tile];
+            const int* js = a.jlist + (size_t)tile * m;
+            int T = 0;
+            for (int base = 0; base < cnt; base += 32) {
+                const int t = base + lane;
+                int j = 0;
+                bool keep = false;
+                if (t < cnt) {
+                    j = js[t];
+                    keep = a.leafA[(size_t)i * m + j] != 0.0 && a.leafB[(size_t)j * m + k] != 0.0;
                 }
-                const int j = tasks_sh[t];
-                uint8_t* dst = smem + (size_t)s * STAGE_BYTES;
-                ptx::mbar_arrive_expect_tx(&bar_full[s], STAGE_BYTES);
-                ptx::bulk_g2s(dst, a.sliceA + ((size_t)i * m + j) * A_TILE_BYTES, A_TILE_BYTES, &bar_full[s]);
-                ptx::bulk_g2s(dst + A_TILE_BYTES, a.sliceB + ((size_t)j * m + k) * B_TILE_BYTES, B_TILE_BYTES,
-                              &bar_full[s]);
+                const unsigned bal = __ballot_sync(0xffffffffu, keep);
+                if (keep) tasks_sh[T + __popc(bal & ((1u << lane) - 1u))] = j;
+                T += __popc(bal);
             }
+            if (lane == 0) ntask_sh = T;
+        } else if (warp >= 2 && warp < 4) {
+            const int r = (warp - 2) * 32 + lane;
+            eA_sh[r] = expo_of(a.rmaxA[i * NB + r]);
+        } else if (warp >= 4) {
+            const int r = (warp - 4) * 32 + lane;
+            eB_sh[r] = expo_of(a.cmaxB[k * NB + r]);
         }
-    } else if (warp == 1) {
-        // ---------------- MMA issuer
-        if (lane == 0) {
-            constexpr uint32_t idesc = ptx::idesc_bf16_f32(128, 64);
-            // (stack, slice) pairs in the order of their accumulator group: the
-            // group is the diagonal 2*stack + slice of the top half, capped at 4
-            const int8_t ps[12] = {0, 0, 0, 1, 0, 1, 0, 0, 1, 1, 2, 2};
-            const int8_t qs[12] = {0, 1, 2, 0, 3, 1, 4, 5, 2, 3, 0, 1};
-            for (int t = 0; t < T; ++t) {
-                const int s = t & 1;
-                if (!ptx::mbar_wait_bounded(&bar_full[s], (t >> 1) & 1, kSpin)) {
-                    atomicExch(a.err, 2);
-                    break;
+        __syncthreads();
+        const int T = ntask_sh;
+        const int nchunks = (T + kChunk - 1) / kChunk;
+
+        if (warp == 0) {
+            // ---------------- producer: bulk copies of the slices of A_ij and B_jk
+            if (lane == 0) {
+                for (int t = 0; t < T; ++t) {
+                    const long long G = gtask + t;
+                    const int s = (int)(G & 1);
+                    if (G >= 2 && !ptx::mbar_wait_bounded(&bar_empty[s], (uint32_t)(((G >> 1) & 1) ^ 1), kSpin)) {
+                        atomicExch(a.err, 1);
+                        break;
+                    }
+                    const int j = tasks_sh[t];
+                    uint8_t* dst = smem + (size_t)s * STAGE_BYTES;
+                    ptx::mbar_arrive_expect_tx(&bar_full[s], STAGE_BYTES);
+                    ptx::bulk_g2s(dst, a.sliceA + ((size_t)i * m + j) * A_TILE_BYTES, A_TILE_BYTES, &bar_full[s]);
+                    ptx::bulk_g2s(dst + A_TILE_BYTES, a.sliceB + ((size_t)j * m + k) * B_TILE_BYTES, B_TILE_BYTES,
+                                  &bar_full[s]);
                 }
-                // the accumulators are single-buffered: wait until the epilogue read task t-1
-                if (t >= 1 && !ptx::mbar_wait_bounded(&bar_acce, (t - 1) & 1, kSpin)) {
-                    atomicExch(a.err, 3);
+            }
+            __syncwarp();
+        } else if (warp == 1) {
+            // ---------------- MMA issuer: tasks are accumulated in TMEM in chunks of kChunk
+            if (lane == 0) {
+                constexpr uint32_t idesc = ptx::idesc_bf16_f32(128, 64);
+                // stacks {0,0,0,1,0,1,0,0,1,1,2,2} and slices {0,1,2,0,3,1,4,5,2,3,0,1}: pairs ordered by
+                // accumulator group = diagonal 2*stack + slice of the top half, capped at 4
+                constexpr uint32_t kStacks = (1u << 6) | (1u << 10) | (1u << 16) | (1u << 18) | (2u << 20) | (2u << 22);
+                constexpr uint64_t kSlices = (1ull << 4) | (2ull << 8) | (3ull << 16) | (1ull << 20) | (4ull << 24) |
+                                             (5ull << 28) | (2ull << 32) | (3ull << 36) | (1ull << 44);
+                for (int t = 0; t < T; ++t) {
+                    const long long G = gtask + t;
+                    const int s = (int)(G & 1);
+                    const long long C = gchunk + t / kChunk;
+                    const bool chunk_start = (t % kChunk) == 0;
+                    if (!ptx::mbar_wait_bounded(&bar_full[s], (uint32_t)((G >> 1) & 1), kSpin)) {
+                        atomicExch(a.err, 2);
+                        break;
+                    }
+                    // a new chunk overwrites the accumulators: the epilogue must have read the previous one
+                    if (chunk_start && C > 0 && !ptx::mbar_wait_bounded(&bar_acce, (uint32_t)((C - 1) & 1), kSpin)) {
+                        atomicExch(a.err, 3);
+                        break;
+                    }
+                    ptx::tc_fence_after();
+                    const uint32_t sA = stage_addr(sbase, s), sB = sA + A_TILE_BYTES;
+                    int prev_g = -1;
+                    for (int u = 0; u < 12; ++u) {
+                        const int sg = (int)((kStacks >> (2 * u)) & 3u), q = (int)((kSlices >> (4 * u)) & 15ull);
+                        const int g = min(2 * sg + q, 4);
+                        const uint32_t d = tmem + (uint32_t)(g * 64);
+                        for (int ks = 0; ks < 4; ++ks) {
+                            const uint64_t ad = ptx::smem_desc(sA + sg * A_STACK_BYTES + ks * 256, 128, 1024);
+                            const uint64_t bd = ptx::smem_desc(sB + q * B_SLICE_BYTES + ks * 256, 128, 1024);
+                            // the first MMA into a group in a chunk overwrites it, the rest accumulate
+                            const bool fresh = chunk_start && ks == 0 && g != prev_g;
+                            ptx::mma_bf16(d, ad, bd, idesc, fresh ? 0u : 1u);
+                            prev_g = g;
+                        }
+                    }
+                    ptx::mma_commit(&bar_empty[s]);
+                    if ((t % kChunk) == kChunk - 1 || t == T - 1) ptx::mma_commit(&bar_accf);
+                }
+            }
+            __syncwarp();
+        } else {
+            // ---------------- epilogue warps 2..5: TMEM lane quarter warp%4 (lanes 32q .. 32q+31)
+            const int quarter = warp & 3;
+            const int half = quarter >> 1;  // 0: MMA rows 0-63 (even slices), 1: rows 64-127 (odd slices)
+            const int row = (quarter & 1) * 32 + lane;
+            const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+            long long acc[NB];
+#pragma unroll
+            for (int c = 0; c < NB; ++c) acc[c] = 0;
+            for (int ck = 0; ck < nchunks; ++ck) {
+                const long long C = gchunk + ck;
+                if (!ptx::mbar_wait_bounded(&bar_accf, (uint32_t)(C & 1), kSpin)) {
+                    atomicExch(a.err, 4);
                     break;
                 }
                 ptx::tc_fence_after();
-                const uint32_t sA = stage_addr(sbase, s), sB = sA + A_TILE_BYTES;
-                int prev_g = -1;
-                for (int u = 0; u < 12; ++u) {
-                    const int sg = ps[u], q = qs[u];
-                    const int g = min(2 * sg + q, 4);
-                    const uint32_t d = tmem + (uint32_t)(g * 64);
-                    for (int ks = 0; ks < 4; ++ks) {
-                        const uint64_t ad = ptx::smem_desc(sA + sg * A_STACK_BYTES + ks * 256, 128, 1024);
-                        const uint64_t bd = ptx::smem_desc(sB + q * B_SLICE_BYTES + ks * 256, 128, 1024);
-                        // the first MMA into a group overwrites it, the rest accumulate
-                        ptx::mma_bf16(d, ad, bd, idesc, (ks > 0 || g == prev_g) ? 1u : 0u);
-                        prev_g = g;
+#pragma unroll
+                for (int g = 0; g < kGroups; ++g) {
+                    // groups 0-3 hold exact integers in units 2^{-8(diag+2)}, diag = g + half; group 4
+                    // (diagonals >= 4 + half) is rounded to units of 2^{-48}
+                    const int diag = g + half;
+                    const float up =
+                        g < 4 ? __int_as_float((127 + 8 * (diag + 2)) << 23) : __int_as_float((127 + 48) << 23);
+                    const int sh = g < 4 ? 32 - 8 * diag : 0;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        uint32_t r[32];
+                        ptx::tmem_ld32(lane_base + (uint32_t)(g * 64 + h * 32), r);
+                        ptx::tmem_ld_wait();
+#pragma unroll
+                        for (int c = 0; c < 32; ++c)
+                            acc[h * 32 + c] += (long long)__float2int_rn(__uint_as_float(r[c]) * up) << sh;
                     }
                 }
-                ptx::mma_commit(&bar_empty[s]);
-                ptx::mma_commit(&bar_accf);
+                ptx::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) ptx::mbar_arrive(&bar_acce);
             }
-        }
-    }
-
-    // ---------------- epilogue warps 2..5: TMEM lanes 32*(warp%4) + lane
-    long long acc[NB];
+            // combine the odd-slice half (MMA rows 64-127) into the even half
+            long long* comb = reinterpret_cast<long long*>(smem);  // [64][65] int64; stage memory is idle now
+            if (half == 1) {
 #pragma unroll
-    for (int c = 0; c < NB; ++c) acc[c] = 0;
-    const int quarter = warp & 3;
-    const int half = quarter >> 1;  // 0: rows 0-63 of the MMA (even slices), 1: rows 64-127 (odd slices)
-    if (warp >= 2) {
-        const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
-        for (int t = 0; t < T; ++t) {
-            if (!ptx::mbar_wait_bounded(&bar_accf, t & 1, kSpin)) {
-                atomicExch(a.err, 4);
-                break;
+                for (int c = 0; c < NB; ++c) comb[c * 65 + row] = acc[c];
             }
-            ptx::tc_fence_after();
+            ptx::named_sync(1, 32 * kEpiWarps);
+            unsigned long long* colbuf = reinterpret_cast<unsigned long long*>(smem + 65 * 64 * 8);  // [64][65]
+            double nu = 0.0, tr = 0.0;
+            if (half == 0) {
+                // eight independent partial sums of squares (FP64 latency is long on this part)
+                double nup[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+                const int gi = i * NB + row;
+                const int eAr = eA_sh[row];
+                unsigned long long rmx = 0;
 #pragma unroll
-            for (int g = 0; g < 4; ++g) {
-                // exact integer partial sums of diagonal g + half in units 2^{-8(diag+2)}
-                const int diag = g + half;
-                const float up = __int_as_float((127 + 8 * (diag + 2)) << 23);
-                const int sh = 32 - 8 * diag;
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    uint32_t r[32];
-                    ptx::tmem_ld32(lane_base + (uint32_t)(g * 64 + h * 32), r);
-                    ptx::tmem_ld_wait();
-#pragma unroll
-                    for (int c = 0; c < 32; ++c) {
-                        const int v = __float2int_rn(__uint_as_float(r[c]) * up);
-                        acc[h * 32 + c] += (long long)v << sh;
+                for (int c = 0; c < NB; ++c) {
+                    const long long t64 = acc[c] + comb[c * 65 + row];
+                    const double x = fixed_to_double(t64, eAr + eB_sh[c] - 48);
+                    const int gj = k * NB + c;
+                    double v = x;
+                    if (a.mode == EPI_NS_X) {
+                        if (gi == gj && gi < a.n) {
+                            tr += x;
+                            v = 1.5 - 0.5 * x;
+                        } else {
+                            v = neg_half(x);
+                        }
                     }
+                    // staged in place of the combine buffer, stored coalesced below
+                    comb[c * 65 + row] = __double_as_longlong(v);
+                    nup[c & 7] = fma(v, v, nup[c & 7]);
+                    const unsigned long long vb = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+                    rmx = max(rmx, vb);
+                    colbuf[c * 65 + row] = vb;
                 }
+                nu = ((nup[0] + nup[1]) + (nup[2] + nup[3])) + ((nup[4] + nup[5]) + (nup[6] + nup[7]));
+                if (rmx) atomicMax(a.rmaxC + gi, rmx);
             }
+            ptx::named_sync(1, 32 * kEpiWarps);
             {
-                // diagonals >= 4 (top) / >= 5 (bottom): rounded to the 2^{-48} quantum
-                const float up48 = __int_as_float((127 + 48) << 23);
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    uint32_t r[32];
-                    ptx::tmem_ld32(lane_base + (uint32_t)(4 * 64 + h * 32), r);
-                    ptx::tmem_ld_wait();
-#pragma unroll
-                    for (int c = 0; c < 32; ++c) acc[h * 32 + c] += (long long)__float2int_rn(__uint_as_float(r[c]) * up48);
+                // coalesced store of the tile: epilogue warp e writes rows 16e .. 16e+15
+                double* outt = a.C + (size_t)tile * NB * NB;
+                const int e = warp - 2;
+                for (int rr = 0; rr < 16; ++rr) {
+                    const int r = e * 16 + rr;
+                    outt[r * NB + lane] = __longlong_as_double(comb[lane * 65 + r]);
+                    outt[r * NB + lane + 32] = __longlong_as_double(comb[(lane + 32) * 65 + r]);
                 }
             }
-            ptx::tc_fence_before();
-            __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(&bar_acce);
-        }
-        // combine the odd-slice half (rows 64-127) into the even half (rows 0-63)
-        long long* comb = reinterpret_cast<long long*>(smem);  // [64][65] int64; stage memory is idle now
-        const int row = (quarter & 1) * 32 + lane;
-        if (half == 1) {
-#pragma unroll
-            for (int c = 0; c < NB; ++c) comb[c * 65 + row] = acc[c];
-        }
-        ptx::named_sync(1, 128);
-        double nu = 0.0, tr = 0.0;
-        unsigned long long* colbuf = reinterpret_cast<unsigned long long*>(smem + 65 * 64 * 8);  // [64][65]
-        if (half == 0) {
-            const int gi = i * NB + row;
-            const int eAr = eA_sh[row];
-            double* out = a.C + (size_t)tile * NB * NB + (size_t)row * NB;
-            unsigned long long rmx = 0;
-#pragma unroll
-            for (int c = 0; c < NB; ++c) {
-                const long long tot = acc[c] + comb[c * 65 + row];
-                double x = (double)tot;
-                if (tot != 0) {
-                    long long bits = __double_as_longlong(x);
-                    bits += (long long)(eAr + eB_sh[c] - 48) << 52;
-                    x = __longlong_as_double(bits);
+            if (half == 0) {
+                unsigned long long cmx = 0;
+                for (int r = 0; r < NB; ++r) cmx = max(cmx, colbuf[row * 65 + r]);
+                if (cmx) atomicMax(a.cmaxC + k * NB + row, cmx);
+                for (int o = 16; o > 0; o >>= 1) {
+                    nu += __shfl_xor_sync(0xffffffffu, nu, o);
+                    tr += __shfl_xor_sync(0xffffffffu, tr, o);
                 }
-                const int gj = k * NB + c;
-                double v = x;
-                if (a.mode == EPI_NS_X) {
-                    const bool dg = (gi == gj) && (gi < a.n);
-                    if (dg) tr += x;
-                    v = dg ? 1.5 - 0.5 * x : -0.5 * x;
+                if (lane == 0) {
+                    red_sh[quarter & 1] = nu;
+                    red_sh[2 + (quarter & 1)] = tr;
                 }
-                out[c] = v;
-                nu = fma(v, v, nu);
-                const unsigned long long vb = (unsigned long long)__double_as_longlong(fabs(v));
-                rmx = max(rmx, vb);
-                colbuf[c * 65 + row] = vb;
             }
-            if (rmx) atomicMax(a.rmaxC + gi, rmx);
-        }
-        ptx::named_sync(1, 128);
-        if (half == 0) {
-            // column maxima: thread `row` reduces column `row`
-            unsigned long long cmx = 0;
-            for (int r = 0; r < NB; ++r) cmx = max(cmx, colbuf[row * 65 + r]);
-            if (cmx) atomicMax(a.cmaxC + k * NB + row, cmx);
-            // fixed-order reductions of nu and the trace over the 64 rows (2 warps)
-            for (int o = 16; o > 0; o >>= 1) {
-                nu += __shfl_xor_sync(0xffffffffu, nu, o);
-                tr += __shfl_xor_sync(0xffffffffu, tr, o);
-            }
-            if (lane == 0) {
-                red_sh[quarter & 1] = nu;
-                red_sh[2 + (quarter & 1)] = tr;
+            ptx::named_sync(1, 32 * kEpiWarps);
+            if (warp == 4 && lane == 0) {
+                a.leafC[tile] = red_sh[0] + red_sh[1];
+                if (a.mode == EPI_NS_X && i == k) a.trace_part[i] = red_sh[2] + red_sh[3];
             }
         }
-        ptx::named_sync(1, 128);
-        if (warp >= 2 && half == 0 && (quarter & 1) == 0 && lane == 0) {
-            a.leafC[tile] = red_sh[0] + red_sh[1];
-            if (a.mode == EPI_NS_X && i == k) a.trace_part[i] = red_sh[2] + red_sh[3];
-        }
+        gtask += T;
+        gchunk += nchunks;
+        // the next tile reuses the stages and the task list; a recorded error stops every CTA
+        if (threadIdx.x == 0) fail_sh = *(volatile int*)a.err != 0;
+        __syncthreads();
+        fail = fail_sh;
     }
 
     ptx::tc_fence_before();
@@ -402,6 +495,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
 
 size_t emu_slice_bytes_per_tile() { return emu::A_TILE_BYTES; }
 
+void emu_kernel_attributes() {
+    cudaFuncSetAttribute(emu::k_gemm_emu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)emu::SMEM_DYN);
+}
+
 void launch_rowcol_max(const double* X, const Geometry& g, unsigned long long* rmax, unsigned long long* cmax,
                        cudaStream_t st) {
     emu::k_rowcol_max<<<g.m * g.m, 256, 0, st>>>(X, g.m, rmax, cmax);
@@ -409,13 +506,16 @@ void launch_rowcol_max(const double* X, const Geometry& g, unsigned long long* r
 }
 
 void launch_slice(const double* X, const double* leaf, const unsigned long long* rmax, const unsigned long long* cmax,
-                  uint8_t* sA, uint8_t* sB, const Geometry& g, const int* done, cudaStream_t st) {
-    emu::k_slice<<<g.m * g.m, 256, 0, st>>>(X, leaf, rmax, cmax, sA, sB, g.m, done);
+                  uint8_t* sA, uint8_t* sB, const Geometry& g, const int* tile_list, const int* tile_count,
+                  const int* done, cudaStream_t st) {
+    const int grid = std::min(device_sm_count() * 4, g.m * g.m);
+    emu::k_slice<<<grid, 256, 0, st>>>(X, leaf, rmax, cmax, sA, sB, g.m, tile_list, tile_count, done);
     note_launch();
 }
 
 void launch_gemm_emu(const Geometry& g, const TileMat& A, const TileMat& B, const TileMat& C, const int* counts,
-                     const int* jlist, EpiMode mode, double* trace_part, const int* done, int* err, cudaStream_t st) {
+                     const int* jlist, const int* tile_list, const int* tile_count, EpiMode mode, double* trace_part,
+                     const int* done, int* err, cudaStream_t st) {
     emu::EmuArgs a;
     a.sliceA = A.sliceA;
     a.sliceB = B.sliceB;
@@ -429,14 +529,16 @@ void launch_gemm_emu(const Geometry& g, const TileMat& A, const TileMat& B, cons
     a.cmaxC = C.cmax;
     a.counts = counts;
     a.jlist = jlist;
+    a.tile_list = tile_list;
+    a.tile_count = tile_count;
     a.trace_part = trace_part;
     a.done = done;
     a.err = err;
     a.m = g.m;
     a.n = g.n;
     a.mode = (int)mode;
-    cudaFuncSetAttribute(emu::k_gemm_emu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)emu::SMEM_DYN);
-    emu::k_gemm_emu<<<g.m * g.m, emu::kThreads, emu::SMEM_DYN, st>>>(a);
+    const int grid = std::min(device_sm_count(), g.m * g.m);
+    emu::k_gemm_emu<<<grid, emu::kThreads, emu::SMEM_DYN, st>>>(a);
     note_launch();
 }
 

@@ -20,11 +20,15 @@ constexpr int kKC = 32;  // inner-dimension chunk staged in shared memory
 
 template <int NB>
 __global__ void __launch_bounds__(kThreads) k_gemm_f64(const double* __restrict__ A, const double* __restrict__ B,
-                                                       double* __restrict__ C, double* __restrict__ leafC,
+                                                       double* __restrict__ C, const double* __restrict__ leafA,
+                                                       const double* __restrict__ leafB, double* __restrict__ leafC,
                                                        const int* __restrict__ counts, const int* __restrict__ jlist,
-                                                       int m, int n, int dense, int mode,
-                                                       double* __restrict__ trace_part, const int* __restrict__ done) {
+                                                       const int* __restrict__ tile_list,
+                                                       const int* __restrict__ tile_count, int m, int n, int dense,
+                                                       int mode, double* __restrict__ trace_part,
+                                                       const int* __restrict__ done) {
     if (done && *done) return;
+    if (tile_list && (int)blockIdx.x >= *tile_count) return;
     constexpr int TM = NB / 16;  // each thread owns TM x TM outputs
     constexpr int LDS = NB + 1;  // padded row of the staged chunks
     extern __shared__ double smem[];
@@ -32,7 +36,7 @@ __global__ void __launch_bounds__(kThreads) k_gemm_f64(const double* __restrict_
     double* Bs = smem + kKC * LDS;  // [kKC][LDS]  B chunk
     __shared__ double red[8];
 
-    const int tile = blockIdx.x;
+    const int tile = tile_list ? tile_list[blockIdx.x] : (int)blockIdx.x;
     const int i = tile / m, k = tile - (tile / m) * m;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int nt = dense ? m : counts[tile];
@@ -46,6 +50,8 @@ __global__ void __launch_bounds__(kThreads) k_gemm_f64(const double* __restrict_
 
     for (int t = 0; t < nt; ++t) {
         const int j = dense ? t : js[t];
+        // an operand tile with zero norm contributes exact zeros (and its data may be stale)
+        if (!dense && (leafA[(size_t)i * m + j] == 0.0 || leafB[(size_t)j * m + k] == 0.0)) continue;
         const double* Aij = A + ((size_t)i * m + j) * NB * NB;
         const double* Bjk = B + ((size_t)j * m + k) * NB * NB;
         for (int kc = 0; kc < NB; kc += kKC) {
@@ -114,24 +120,46 @@ __global__ void __launch_bounds__(kThreads) k_gemm_f64(const double* __restrict_
 }
 
 template <int NB>
-void launch_nb(const Geometry& g, const double* A, const double* B, double* C, double* treeC, const int* counts,
-               const int* jlist, int dense, EpiMode mode, double* trace_part, const int* done, cudaStream_t st) {
+void launch_nb(const Geometry& g, const double* A, const double* B, double* C, const double* leafA,
+               const double* leafB, double* treeC, const int* counts, const int* jlist, const int* tile_list,
+               const int* tile_count, int dense, EpiMode mode, double* trace_part, const int* done, cudaStream_t st) {
+    const size_t smem = 2 * (size_t)kKC * (NB + 1) * sizeof(double);
+    k_gemm_f64<NB><<<g.m * g.m, kThreads, smem, st>>>(A, B, C, leafA, leafB, treeC, counts, jlist, tile_list,
+                                                       tile_count, g.m, g.n, dense, (int)mode, trace_part, done);
+    note_launch();
+}
+
+template <int NB>
+void set_attr() {
     const size_t smem = 2 * (size_t)kKC * (NB + 1) * sizeof(double);
     cudaFuncSetAttribute(k_gemm_f64<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_gemm_f64<NB><<<g.m * g.m, kThreads, smem, st>>>(A, B, C, treeC, counts, jlist, g.m, g.n, dense, (int)mode,
-                                                       trace_part, done);
-    note_launch();
 }
 
 }  // namespace
 
-void launch_gemm_f64(const Geometry& g, const double* A, const double* B, double* C, double* treeC,
-                     const int* counts, const int* jlist, int dense, EpiMode mode, double* trace_part,
-                     const int* done, cudaStream_t st) {
+void f64_kernel_attributes() {
+    set_attr<32>();
+    set_attr<64>();
+    set_attr<128>();
+}
+
+void launch_gemm_f64(const Geometry& g, const double* A, const double* B, double* C, const double* leafA,
+                     const double* leafB, double* treeC, const int* counts, const int* jlist, const int* tile_list,
+                     const int* tile_count, int dense, EpiMode mode, double* trace_part, const int* done,
+                     cudaStream_t st) {
     switch (g.nb) {
-        case 32: launch_nb<32>(g, A, B, C, treeC, counts, jlist, dense, mode, trace_part, done, st); break;
-        case 64: launch_nb<64>(g, A, B, C, treeC, counts, jlist, dense, mode, trace_part, done, st); break;
-        case 128: launch_nb<128>(g, A, B, C, treeC, counts, jlist, dense, mode, trace_part, done, st); break;
+        case 32:
+            launch_nb<32>(g, A, B, C, leafA, leafB, treeC, counts, jlist, tile_list, tile_count, dense, mode,
+                          trace_part, done, st);
+            break;
+        case 64:
+            launch_nb<64>(g, A, B, C, leafA, leafB, treeC, counts, jlist, tile_list, tile_count, dense, mode,
+                          trace_part, done, st);
+            break;
+        case 128:
+            launch_nb<128>(g, A, B, C, leafA, leafB, treeC, counts, jlist, tile_list, tile_count, dense, mode,
+                           trace_part, done, st);
+            break;
         default: break;
     }
 }

@@ -234,8 +234,7 @@ void launch_tree(const Geometry& g, double* tree, const int* done, cudaStream_t 
 // surviving leaf pair under it; the surviving set is exactly the leaf test
 // nuA(i,j) * nuB(j,k) >= thr, i.e. the recursion of Eq. (newspamm).
 __global__ void __launch_bounds__(128) k_cull(TreeDev td, const double* __restrict__ treeA,
-                                              const double* __restrict__ treeB, double tau,
-                                              int* __restrict__ counts, int* __restrict__ jlist,
+                                              const double* __restrict__ treeB, double tau, CullOut co,
                                               unsigned long long* __restrict__ total, double* __restrict__ thr_out,
                                               const int* __restrict__ done) {
     if (done && *done) return;
@@ -252,7 +251,7 @@ __global__ void __launch_bounds__(128) k_cull(TreeDev td, const double* __restri
         const int I = i >> td.shift, K = k >> td.shift;
         const double* nA = treeA;   // leaf level at offset 0
         const double* nB = treeB;
-        int* out = jlist + ((size_t)i * m + k) * m;
+        int* out = co.jlist + ((size_t)i * m + k) * m;
         for (int J = 0; J < dc; ++J) {
             if (cA[(size_t)I * dc + J] * cB[(size_t)J * dc + K] < thr) continue;
             const int j0 = J << td.shift;
@@ -260,7 +259,12 @@ __global__ void __launch_bounds__(128) k_cull(TreeDev td, const double* __restri
             for (int j = j0; j < j1; ++j)
                 if (!(nA[(size_t)i * m + j] * nB[(size_t)j * m + k] < thr)) out[cnt++] = j;
         }
-        counts[(size_t)i * m + k] = cnt;
+        const int tile = i * m + k;
+        co.counts[tile] = cnt;
+        if (co.tile_list) {
+            if (cnt > 0 || (co.force_diag && i == k)) co.tile_list[atomicAdd(co.tile_count, 1)] = tile;
+            else if (co.leafC) co.leafC[tile] = 0.0;
+        }
     }
     if (thr_out && i == 0 && k == 0) *thr_out = thr;
     if (total) {
@@ -275,28 +279,29 @@ __global__ void __launch_bounds__(128) k_cull(TreeDev td, const double* __restri
     }
 }
 
-void launch_cull(const Geometry& g, const double* treeA, const double* treeB, double tau, int* counts,
-                 int* jlist, unsigned long long* total, double* thr_out, const int* done, cudaStream_t st) {
+void launch_cull(const Geometry& g, const double* treeA, const double* treeB, double tau, const CullOut& out,
+                 unsigned long long* total, double* thr_out, const int* done, cudaStream_t st) {
     dim3 grid((g.m + 127) / 128, g.m);
-    k_cull<<<grid, 128, 0, st>>>(tree_dev(g), treeA, treeB, tau, counts, jlist, total, thr_out, done);
+    k_cull<<<grid, 128, 0, st>>>(tree_dev(g), treeA, treeB, tau, out, total, thr_out, done);
     note_launch();
 }
 
 // ---------------------------------------------------------------- unpack
-__global__ void __launch_bounds__(256) k_unpack(const double* __restrict__ src, int n, int m, int nb,
-                                                double* __restrict__ dst, const double* __restrict__ mul,
-                                                const double* __restrict__ div) {
+__global__ void __launch_bounds__(256) k_unpack(const double* __restrict__ src, const double* __restrict__ leaf,
+                                                int n, int m, int nb, double* __restrict__ dst,
+                                                const double* __restrict__ mul, const double* __restrict__ div) {
     const int tile = blockIdx.x;
     const int i = tile / m, j = tile % m;
     const int ne = nb * nb;
     const double* s = src + (size_t)tile * ne;
     const double fm = mul ? *mul : 1.0;
     const double fd = div ? *div : 1.0;
+    const bool zero = leaf && leaf[tile] == 0.0;
     for (int idx = threadIdx.x; idx < ne; idx += 256) {
         const int r = idx / nb, cc = idx - r * nb;
         const int gi = i * nb + r, gj = j * nb + cc;
         if (gi < n && gj < n) {
-            double v = s[idx];
+            double v = zero ? 0.0 : s[idx];
             if (mul) v = v * fm;
             if (div) v = v / fd;
             dst[(size_t)gi * n + gj] = v;
@@ -304,9 +309,9 @@ __global__ void __launch_bounds__(256) k_unpack(const double* __restrict__ src, 
     }
 }
 
-void launch_unpack(const double* src, const Geometry& g, double* dst, const double* mul, const double* div,
-                   cudaStream_t st) {
-    k_unpack<<<g.m * g.m, 256, 0, st>>>(src, g.n, g.m, g.nb, dst, mul, div);
+void launch_unpack(const double* src, const double* leaf, const Geometry& g, double* dst, const double* mul,
+                   const double* div, cudaStream_t st) {
+    k_unpack<<<g.m * g.m, 256, 0, st>>>(src, leaf, g.n, g.m, g.nb, dst, mul, div);
     note_launch();
 }
 

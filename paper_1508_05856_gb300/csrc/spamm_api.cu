@@ -7,6 +7,7 @@
 // host/device boundary when the caller passes host pointers.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -23,6 +24,29 @@ namespace spamm {
 
 static std::atomic<long long> g_launches{0};
 void note_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+static std::mutex g_attr_mu;
+static bool g_attr_done[64] = {};
+static int g_sm_count[64] = {};
+
+void init_device_attributes() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    if (g_attr_done[dev]) return;
+    f64_kernel_attributes();
+    emu_kernel_attributes();
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    g_sm_count[dev] = sms > 0 ? sms : 1;
+    g_attr_done[dev] = true;
+}
+
+int device_sm_count() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return (dev >= 0 && dev < 64 && g_sm_count[dev] > 0) ? g_sm_count[dev] : 148;
+}
 
 static thread_local std::string g_last_error;
 
@@ -64,6 +88,20 @@ static bool is_device_ptr(const void* p) {
 }
 
 // ----------------------------------------------------------------------------
+// What a captured solve graph depends on besides the plan's own buffers.
+struct GraphKey {
+    const double* S = nullptr;
+    double* Y = nullptr;
+    double* Z = nullptr;
+    int n = 0, leaf = 0, precision = 0, order = 0, maxit = 0, profile = 0;
+    double tau = 0.0, tau_s = 0.0, mu_rel = 0.0;
+    bool operator==(const GraphKey& o) const {
+        return S == o.S && Y == o.Y && Z == o.Z && n == o.n && leaf == o.leaf && precision == o.precision &&
+               order == o.order && maxit == o.maxit && profile == o.profile && tau == o.tau && tau_s == o.tau_s &&
+               mu_rel == o.mu_rel;
+    }
+};
+
 // Scratch of one problem size on one device.
 struct Plan {
     int device = 0;
@@ -71,13 +109,14 @@ struct Plan {
     TileMat buf[6];
     int* counts = nullptr;
     int* jlist = nullptr;
+    int* tile_list = nullptr;                // [m*m] compacted output tiles of one product
     unsigned long long* task_ctr = nullptr;  // [3 * maxit_cap + 4]
     double* t_hist = nullptr;                // [maxit_cap]
     int maxit_cap = 0;
     double* trace_part = nullptr;  // [m]
     double* scal = nullptr;        // c0, mu, c, sqrt c, thr, resid, spare...
     double* rowsum = nullptr;      // [n]
-    int* flags = nullptr;          // done, iters
+    int* flags = nullptr;          // done, iters, device error, output-tile count
     double* partial = nullptr;     // [m*m]
     double* stage[3] = {nullptr, nullptr, nullptr};  // n*n row-major staging
     // profiling: event pairs around each leaf-product kernel of a call
@@ -87,6 +126,14 @@ struct Plan {
     long long gemm_launches = 0;
     bool emu = false;        // this call uses the tensor-core (SPAMM_EMU64) leaf products
     bool emu_ready = false;  // slice buffers allocated
+    // CUDA graph of the last fixed-iteration solve and what it was captured for
+    cudaGraphExec_t gexec = nullptr;
+    GraphKey gkey;
+    long long graph_kernels = 0;
+    int graph_events = 0;       // profiling events recorded inside the graph
+    long long graph_gemm = 0;   // leaf-product launches inside the graph
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 };
 
 static void free_plan(Plan* p) {
@@ -102,6 +149,7 @@ static void free_plan(Plan* p) {
     }
     cudaFree(p->counts);
     cudaFree(p->jlist);
+    cudaFree(p->tile_list);
     cudaFree(p->task_ctr);
     cudaFree(p->t_hist);
     cudaFree(p->trace_part);
@@ -111,6 +159,10 @@ static void free_plan(Plan* p) {
     cudaFree(p->partial);
     for (auto& s : p->stage) cudaFree(s);
     for (auto e : p->ev) cudaEventDestroy(e);
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    if (p->gstream) cudaStreamDestroy(p->gstream);
+    if (p->ev_in) cudaEventDestroy(p->ev_in);
+    if (p->ev_out) cudaEventDestroy(p->ev_out);
     cudaSetDevice(cur);
     delete p;
 }
@@ -124,6 +176,7 @@ static int alloc_plan(Plan* p, int n, int nb) {
     }
     CKA(cudaMalloc(&p->counts, (size_t)g.m * g.m * sizeof(int)));
     CKA(cudaMalloc(&p->jlist, (size_t)g.m * g.m * g.m * sizeof(int)));
+    CKA(cudaMalloc(&p->tile_list, (size_t)g.m * g.m * sizeof(int)));
     CKA(cudaMalloc(&p->trace_part, (size_t)g.m * sizeof(double)));
     CKA(cudaMalloc(&p->scal, 16 * sizeof(double)));
     CKA(cudaMalloc(&p->rowsum, (size_t)n * sizeof(double)));
@@ -165,6 +218,23 @@ static int ensure_stage(Plan* p, int which) {
     return SPAMM_OK;
 }
 
+// Device bytes one plan holds (tile buffers, trees, task lists, slices for
+// the tensor-core path, row-major staging when the caller passes host memory).
+size_t plan_footprint(int n, int nb, int precision, bool host_io) {
+    const Geometry g = make_geometry(n, nb);
+    size_t b = 6 * (g.elems() + (size_t)g.tree_size) * sizeof(double);
+    b += ((size_t)g.m * g.m * (g.m + 2)) * sizeof(int) + (size_t)g.m * sizeof(double) + (size_t)n * sizeof(double) +
+         (size_t)g.m * g.m * sizeof(double) + 4096;
+    if (precision == SPAMM_EMU64)
+        b += 6 * (2 * emu_slice_bytes_per_tile() * (size_t)g.m * g.m + 2 * (size_t)g.m * g.nb * 8);
+    if (host_io) b += 3 * (size_t)n * n * sizeof(double);
+    return b;
+}
+
+static size_t plan_bytes(const Plan* p) {
+    return plan_footprint(p->g.n, p->g.nb, p->emu_ready ? SPAMM_EMU64 : SPAMM_FP64, p->stage[0] != nullptr);
+}
+
 class PlanPool {
   public:
     int acquire(int n, int nb, Plan** out) {
@@ -199,6 +269,21 @@ class PlanPool {
         for (auto& kv : free_)
             for (Plan* p : kv.second) free_plan(p);
         free_.clear();
+    }
+    // Free idle plans until the idle ones hold at most keep_bytes.
+    void trim(size_t keep_bytes) {
+        std::lock_guard<std::mutex> lk(mu_);
+        size_t idle = 0;
+        for (auto& kv : free_)
+            for (Plan* p : kv.second) idle += plan_bytes(p);
+        for (auto& kv : free_) {
+            while (idle > keep_bytes && !kv.second.empty()) {
+                Plan* p = kv.second.back();
+                kv.second.pop_back();
+                idle -= std::min(idle, plan_bytes(p));
+                free_plan(p);
+            }
+        }
     }
 
   private:
@@ -278,6 +363,7 @@ static double profiled_ms(Plan* p) {
     for (int q = 0; q + 1 < p->ev_used; q += 2) {
         float t = 0.f;
         if (cudaEventElapsedTime(&t, p->ev[q], p->ev[q + 1]) == cudaSuccess) ms += t;
+        else cudaGetLastError();  // leave no error behind for the caller
     }
     return ms;
 }
@@ -286,23 +372,29 @@ static double profiled_ms(Plan* p) {
 static void product(Plan* p, const TileMat& A, const TileMat& B, TileMat& C, double tau, EpiMode mode,
                     unsigned long long* ctr, cudaStream_t st) {
     const Geometry& g = p->g;
-    launch_cull(g, A.tree, B.tree, tau, p->counts, p->jlist, ctr, nullptr, p->flags, st);
+    cudaMemsetAsync(p->flags + 3, 0, sizeof(int), st);
+    const CullOut co{p->counts, p->jlist, p->tile_list, p->flags + 3, C.tree, mode == EPI_NS_X ? 1 : 0};
+    launch_cull(g, A.tree, B.tree, tau, co, ctr, nullptr, p->flags, st);
     if (p->emu) cudaMemsetAsync(C.rmax, 0, 2 * (size_t)g.m * g.nb * sizeof(unsigned long long), st);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (p->profile) {
         e0 = next_event(p);
         e1 = next_event(p);
-        if (e0 && e1) cudaEventRecord(e0, st);
+        // "external" records become event-record nodes when the solve is captured into a graph
+        if (e0 && e1) cudaEventRecordWithFlags(e0, st, cudaEventRecordExternal);
     }
     if (p->emu) {
-        launch_gemm_emu(g, A, B, C, p->counts, p->jlist, mode, p->trace_part, p->flags, p->flags + 2, st);
+        launch_gemm_emu(g, A, B, C, p->counts, p->jlist, p->tile_list, p->flags + 3, mode, p->trace_part, p->flags,
+                        p->flags + 2, st);
     } else {
-        launch_gemm_f64(g, A.t, B.t, C.t, C.tree, p->counts, p->jlist, 0, mode, p->trace_part, p->flags, st);
+        launch_gemm_f64(g, A.t, B.t, C.t, A.tree, B.tree, C.tree, p->counts, p->jlist, p->tile_list, p->flags + 3, 0,
+                        mode, p->trace_part, p->flags, st);
     }
-    if (e0 && e1) cudaEventRecord(e1, st);
+    if (e0 && e1) cudaEventRecordWithFlags(e1, st, cudaEventRecordExternal);
     p->gemm_launches++;
     launch_tree(g, C.tree, p->flags, st);
-    if (p->emu) launch_slice(C.t, C.tree, C.rmax, C.cmax, C.sliceA, C.sliceB, g, p->flags, st);
+    if (p->emu)
+        launch_slice(C.t, C.tree, C.rmax, C.cmax, C.sliceA, C.sliceB, g, p->tile_list, p->flags + 3, p->flags, st);
 }
 
 // Row/column maxima and slices of a freshly packed matrix (tensor-core path).
@@ -310,12 +402,13 @@ static void prepare_emu(Plan* p, const TileMat& M, cudaStream_t st) {
     const Geometry& g = p->g;
     cudaMemsetAsync(M.rmax, 0, 2 * (size_t)g.m * g.nb * sizeof(unsigned long long), st);
     launch_rowcol_max(M.t, g, M.rmax, M.cmax, st);
-    launch_slice(M.t, M.tree, M.rmax, M.cmax, M.sliceA, M.sliceB, g, nullptr, st);
+    launch_slice(M.t, M.tree, M.rmax, M.cmax, M.sliceA, M.sliceB, g, nullptr, nullptr, nullptr, st);
 }
 
 static int multiply_impl(const double* A, const double* B, double* C, int n, double tau, const spamm_opts& o,
                          spamm_stats* stats) {
     cudaStream_t st = (cudaStream_t)o.stream;
+    init_device_attributes();
     PlanGuard pg;
     int e = g_pool.acquire(n, o.leaf, &pg.p);
     if (e) return e;
@@ -340,7 +433,7 @@ static int multiply_impl(const double* A, const double* B, double* C, int n, dou
         prepare_emu(p, p->buf[1], st);
     }
     product(p, p->buf[0], p->buf[1], p->buf[2], tau, EPI_PLAIN, p->task_ctr, st);
-    launch_unpack(p->buf[2].t, g, dC, nullptr, nullptr, st);
+    launch_unpack(p->buf[2].t, p->buf[2].tree, g, dC, nullptr, nullptr, st);
     CK(cudaGetLastError());
     if ((e = stage_out(p, 2, C, dC, st))) return e;
     unsigned long long tasks = 0;
@@ -371,34 +464,23 @@ static int residual_impl(Plan* p, const double* dS, const double* dZ, double* ou
     const Geometry& g = p->g;
     launch_pack(dS, g.n, g, nullptr, nullptr, p->buf[3], st);
     launch_pack(dZ, g.n, g, nullptr, nullptr, p->buf[4], st);
-    launch_gemm_f64(g, p->buf[4].t, p->buf[3].t, p->buf[5].t, p->buf[5].tree, nullptr, nullptr, 1, EPI_PLAIN,
-                    nullptr, nullptr, st);
-    launch_gemm_f64(g, p->buf[5].t, p->buf[4].t, p->buf[3].t, p->buf[3].tree, nullptr, nullptr, 1, EPI_PLAIN,
-                    nullptr, nullptr, st);
+    launch_gemm_f64(g, p->buf[4].t, p->buf[3].t, p->buf[5].t, p->buf[4].tree, p->buf[3].tree, p->buf[5].tree,
+                    nullptr, nullptr, nullptr, nullptr, 1, EPI_PLAIN, nullptr, nullptr, st);
+    launch_gemm_f64(g, p->buf[5].t, p->buf[4].t, p->buf[3].t, p->buf[5].tree, p->buf[4].tree, p->buf[3].tree,
+                    nullptr, nullptr, nullptr, nullptr, 1, EPI_PLAIN, nullptr, nullptr, st);
     launch_resid_norm(p->buf[3].t, g, p->partial, p->scal + 5, st);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(out, p->scal + 5, sizeof(double), cudaMemcpyDeviceToHost, st));
     return SPAMM_OK;
 }
 
-static int sqrt_impl(const double* S, int n, double tau, int maxit, double* Y, double* Z, const spamm_opts& o,
-                     spamm_stats* stats) {
-    cudaStream_t st = (cudaStream_t)o.stream;
-    const double tau_s = o.tau_s < 0.0 ? 0.01 * tau : o.tau_s;
-    PlanGuard pg;
-    int e = g_pool.acquire(n, o.leaf, &pg.p);
-    if (e) return e;
-    Plan* p = pg.p;
+// Enqueue the device work of one solve on st: scaling, packing, the NS loop
+// and unpacking (a1-a7).  With tol_t > 0 the host reads the stop flag after
+// every iteration; otherwise nothing here synchronises (so it can be captured
+// in a CUDA graph).  *iters gets the number of iterations enqueued.
+static int enqueue_solve(Plan* p, const double* dS, double* dY, double* dZ, int n, double tau, double tau_s,
+                         int maxit, const spamm_opts& o, cudaStream_t st, int* iters) {
     const Geometry& g = p->g;
-    if ((e = ensure_hist(p, maxit > 0 ? maxit : 1))) return e;
-    const double* dS;
-    double *dY, *dZ;
-    if ((e = stage_in(p, 0, S, st, &dS))) return e;
-    if ((e = out_target(p, 1, Y, &dY))) return e;
-    if ((e = out_target(p, 2, Z, &dZ))) return e;
-    begin_call(p, o.profile != 0, o.precision == SPAMM_EMU64);
-    if (p->emu && (e = ensure_emu(p))) return e;
-
     CK(cudaMemsetAsync(p->flags, 0, 4 * sizeof(int), st));
     CK(cudaMemsetAsync(p->task_ctr, 0, (3 * (size_t)p->maxit_cap + 4) * sizeof(unsigned long long), st));
     CK(cudaMemsetAsync(p->t_hist, 0, (size_t)p->maxit_cap * sizeof(double), st));
@@ -461,9 +543,95 @@ static int sqrt_impl(const double* S, int n, double tau, int maxit, double* Y, d
     }
 
     // a7: unscale and unpack
-    launch_unpack(Yb.t, g, dY, sqc, nullptr, st);
-    launch_unpack(Zb.t, g, dZ, nullptr, sqc, st);
+    launch_unpack(Yb.t, Yb.tree, g, dY, sqc, nullptr, st);
+    launch_unpack(Zb.t, Zb.tree, g, dZ, nullptr, sqc, st);
     CK(cudaGetLastError());
+    *iters = it_host;
+    return SPAMM_OK;
+}
+
+static bool graphs_enabled() {
+    static const bool on = [] {
+        const char* v = getenv("SPAMM_NO_GRAPH");
+        return !(v && v[0] && v[0] != '0');
+    }();
+    return on;
+}
+
+// Replay (or capture, then replay) the whole fixed-iteration solve as one
+// CUDA graph on the plan's own stream, ordered after and before `st`.
+static int solve_graph(Plan* p, const double* dS, double* dY, double* dZ, int n, double tau, double tau_s, int maxit,
+                       const spamm_opts& o, cudaStream_t st) {
+    if (!p->gstream) {
+        CK(cudaStreamCreateWithFlags(&p->gstream, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&p->ev_out, cudaEventDisableTiming));
+    }
+    const GraphKey key{dS, dY, dZ, n, o.leaf, o.precision, o.order, maxit, o.profile ? 1 : 0, tau, tau_s, o.mu_rel};
+    CK(cudaEventRecord(p->ev_in, st));
+    CK(cudaStreamWaitEvent(p->gstream, p->ev_in, 0));
+    if (!p->gexec || !(p->gkey == key)) {
+        if (p->gexec) {
+            cudaGraphExecDestroy(p->gexec);
+            p->gexec = nullptr;
+        }
+        const long long l0 = g_launches.load();
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(p->gstream, cudaStreamCaptureModeThreadLocal));
+        int iters = 0;
+        const int e = enqueue_solve(p, dS, dY, dZ, n, tau, tau_s, maxit, o, p->gstream, &iters);
+        const cudaError_t ce = cudaStreamEndCapture(p->gstream, &graph);
+        if (e) {
+            if (graph) cudaGraphDestroy(graph);
+            return e;
+        }
+        CK(ce);
+        const cudaError_t ie = cudaGraphInstantiate(&p->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        CK(ie);
+        p->gkey = key;
+        p->graph_kernels = g_launches.load() - l0;
+        g_launches.fetch_sub(p->graph_kernels);  // counted again when the graph runs
+        p->graph_events = p->ev_used;
+        p->graph_gemm = p->gemm_launches;
+    }
+    // the profiling events and launch counts of this call are those recorded in the graph
+    p->ev_used = p->graph_events;
+    p->gemm_launches = p->graph_gemm;
+    CK(cudaGraphLaunch(p->gexec, p->gstream));
+    note_launch((int)p->graph_kernels);
+    CK(cudaEventRecord(p->ev_out, p->gstream));
+    CK(cudaStreamWaitEvent(st, p->ev_out, 0));
+    return SPAMM_OK;
+}
+
+static int sqrt_impl(const double* S, int n, double tau, int maxit, double* Y, double* Z, const spamm_opts& o,
+                     spamm_stats* stats) {
+    cudaStream_t st = (cudaStream_t)o.stream;
+    const double tau_s = o.tau_s < 0.0 ? 0.01 * tau : o.tau_s;
+    init_device_attributes();
+    PlanGuard pg;
+    int e = g_pool.acquire(n, o.leaf, &pg.p);
+    if (e) return e;
+    Plan* p = pg.p;
+    const Geometry& g = p->g;
+    if ((e = ensure_hist(p, maxit > 0 ? maxit : 1))) return e;
+    const double* dS;
+    double *dY, *dZ;
+    if ((e = stage_in(p, 0, S, st, &dS))) return e;
+    if ((e = out_target(p, 1, Y, &dY))) return e;
+    if ((e = out_target(p, 2, Z, &dZ))) return e;
+    begin_call(p, o.profile != 0, o.precision == SPAMM_EMU64);
+    if (p->emu && (e = ensure_emu(p))) return e;
+
+    int it_host = 0;
+    if (o.tol_t == 0.0 && graphs_enabled()) {
+        if ((e = solve_graph(p, dS, dY, dZ, n, tau, tau_s, maxit, o, st))) return e;
+        it_host = maxit;
+    } else {
+        if ((e = enqueue_solve(p, dS, dY, dZ, n, tau, tau_s, maxit, o, st, &it_host))) return e;
+    }
+    double* c = p->scal + 2;
     double resid = -1.0;
     if (o.residual) {
         if ((e = residual_impl(p, dS, dZ, &resid, st))) return e;
@@ -555,6 +723,21 @@ static int check_common(int n, double tau, const spamm_opts& o) {
     }
     return SPAMM_OK;
 }
+
+// Internal entry points used by the request server (spamm_server.cu).
+int run_sqrt(const double* S, int n, double tau, int maxit, double* Y, double* Z, const spamm_opts& o,
+             spamm_stats* stats) {
+    try {
+        return sqrt_impl(S, n, tau, maxit, Y, Z, o, stats);
+    } catch (...) {
+        g_last_error = "internal exception";
+        return SPAMM_ERR_CUDA;
+    }
+}
+int check_args(int n, double tau, const spamm_opts& o) { return check_common(n, tau, o); }
+spamm_opts resolved(const spamm_opts* o) { return resolve_opts(o); }
+void trim_plans(size_t keep_bytes) { g_pool.trim(keep_bytes); }
+const char* last_error_message() { return g_last_error.c_str(); }
 
 }  // namespace spamm
 
@@ -720,8 +903,8 @@ int spamm_cull(const double* A, const double* B, int n, double tau, int leaf, in
         launch_tree(g, p->buf[0].tree, nullptr, st);
         launch_pack(dB, n, g, nullptr, nullptr, p->buf[1], st);
         launch_tree(g, p->buf[1].tree, nullptr, st);
-        launch_cull(g, p->buf[0].tree, p->buf[1].tree, tau, p->counts, p->jlist, p->task_ctr, p->scal + 4, nullptr,
-                    st);
+        const CullOut co{p->counts, p->jlist, nullptr, nullptr, nullptr, 0};
+        launch_cull(g, p->buf[0].tree, p->buf[1].tree, tau, co, p->task_ctr, p->scal + 4, nullptr, st);
         CK(cudaGetLastError());
         unsigned long long tot = 0;
         double thr_h = 0.0;

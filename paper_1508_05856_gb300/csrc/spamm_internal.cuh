@@ -54,6 +54,14 @@ enum EpiMode { EPI_PLAIN = 0, EPI_NS_X = 1 };
 // Counts kernel launches (spamm_kernel_launches); every launcher calls it.
 void note_launch(int k = 1);
 
+// Once per device and process: shared-memory limits of the big kernels and
+// the SM count (kept out of the launchers so that launches can be captured
+// into CUDA graphs).
+void init_device_attributes();
+int device_sm_count();
+void f64_kernel_attributes();
+void emu_kernel_attributes();
+
 // ---- kernels_tree.cu -------------------------------------------------------
 // c = max_i sum_j |s_ij + mu delta_ij|; mu read from *mu_dev (may be null = 0).
 void launch_gershgorin(const double* S, int n, const double* mu_dev, double* rowsum, double* out_c,
@@ -72,11 +80,24 @@ void launch_identity(const Geometry& g, TileMat Z, cudaStream_t st);
 void launch_tree(const Geometry& g, double* tree, const int* done, cudaStream_t st);
 // Task lists of A (x) B: counts[i*m+k], jlist[(i*m+k)*m + ...] ascending j.
 // thr = ((tau*tau) * rootA) * rootB.  total (may be null) gets += task count.
-void launch_cull(const Geometry& g, const double* treeA, const double* treeB, double tau, int* counts,
-                 int* jlist, unsigned long long* total, double* thr_out, const int* done, cudaStream_t st);
-// Tile-major -> row-major with out = in * (*mul) or in / (*div) (one of them null or both null).
-void launch_unpack(const double* src, const Geometry& g, double* dst, const double* mul, const double* div,
-                   cudaStream_t st);
+// Output tiles with a task (or, with force_diag, on the diagonal) are
+// appended to tile_list (*tile_count must be zero on entry, order
+// unspecified); for every other output tile leafC[tile] is set to 0: that
+// tile is exactly zero and its data are not written (readers check nu == 0).
+struct CullOut {
+    int* counts;
+    int* jlist;
+    int* tile_list;
+    int* tile_count;
+    double* leafC;
+    int force_diag;
+};
+void launch_cull(const Geometry& g, const double* treeA, const double* treeB, double tau, const CullOut& out,
+                 unsigned long long* total, double* thr_out, const int* done, cudaStream_t st);
+// Tile-major -> row-major with out = in * (*mul) or in / (*div) (one of them
+// null or both null).  Tiles whose leaf norm is 0 are written as zeros.
+void launch_unpack(const double* src, const double* leaf, const Geometry& g, double* dst, const double* mul,
+                   const double* div, cudaStream_t st);
 // t_k = (n - sum trace_part)/n into hist[k]; done/iters bookkeeping.
 void launch_tk(const double* trace_part, const Geometry& g, int k, double tol_t, double* t_hist, int* done,
                int* iters, cudaStream_t st);
@@ -89,22 +110,44 @@ void launch_resid_norm(const double* R, const Geometry& g, double* partial, doub
 // C_ik = sum_{j in list(i,k)} A_ij B_jk in FP64 (dense = every j), epilogue
 // per mode; writes leaf norms of the stored tile into treeC[0..m*m) and, for
 // EPI_NS_X, the diagonal-tile trace partials of X.
-void launch_gemm_f64(const Geometry& g, const double* A, const double* B, double* C, double* treeC,
-                     const int* counts, const int* jlist, int dense, EpiMode mode, double* trace_part,
-                     const int* done, cudaStream_t st);
+// Sparse form: one CTA per entry of the compacted output-tile list; tasks
+// whose operand tile has leaf norm 0 are skipped (exact zeros).  Dense form
+// (dense = 1, tile_list null): every output tile, every j.
+void launch_gemm_f64(const Geometry& g, const double* A, const double* B, double* C, const double* leafA,
+                     const double* leafB, double* treeC, const int* counts, const int* jlist, const int* tile_list,
+                     const int* tile_count, int dense, EpiMode mode, double* trace_part, const int* done,
+                     cudaStream_t st);
+
+// ---- spamm_api.cu, for the request server --------------------------------
+}  // namespace spamm
+struct spamm_opts;
+struct spamm_stats;
+namespace spamm {
+size_t plan_footprint(int n, int nb, int precision, bool host_io);
+int run_sqrt(const double* S, int n, double tau, int maxit, double* Y, double* Z, const spamm_opts& o,
+             spamm_stats* stats);
+int check_args(int n, double tau, const spamm_opts& o);
+spamm_opts resolved(const spamm_opts* o);
+void trim_plans(size_t keep_bytes);
+const char* last_error_message();
+void set_error_message(const char* msg);
 
 // ---- kernels_emu.cu (leaf tile 64 only) -----------------------------------
 size_t emu_slice_bytes_per_tile();  // bytes of one tile's slices in one operand role
 // Row/column magnitude maxima of a packed matrix (arrays must be zeroed first).
 void launch_rowcol_max(const double* X, const Geometry& g, unsigned long long* rmax, unsigned long long* cmax,
                        cudaStream_t st);
-// BF16 slices of both operand roles from FP64 tiles and row/column maxima.
+// BF16 slices of both operand roles from FP64 tiles and row/column maxima,
+// for the listed tiles (or all tiles when tile_list is null); tiles of zero
+// norm are skipped.
 void launch_slice(const double* X, const double* leaf, const unsigned long long* rmax, const unsigned long long* cmax,
-                  uint8_t* sA, uint8_t* sB, const Geometry& g, const int* done, cudaStream_t st);
+                  uint8_t* sA, uint8_t* sB, const Geometry& g, const int* tile_list, const int* tile_count,
+                  const int* done, cudaStream_t st);
 // Leaf products on the tensor cores; writes C's FP64 tiles, leaf norms and
 // row/column maxima (pre-zeroed), trace partials for EPI_NS_X; *err set on a
 // timed-out internal wait.
 void launch_gemm_emu(const Geometry& g, const TileMat& A, const TileMat& B, const TileMat& C, const int* counts,
-                     const int* jlist, EpiMode mode, double* trace_part, const int* done, int* err, cudaStream_t st);
+                     const int* jlist, const int* tile_list, const int* tile_count, EpiMode mode, double* trace_part,
+                     const int* done, int* err, cudaStream_t st);
 
 }  // namespace spamm

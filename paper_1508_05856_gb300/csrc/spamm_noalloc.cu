@@ -28,7 +28,8 @@ namespace {
 constexpr int kNoAllocMaxN = SPAMM_NOALLOC_MAX_N;
 constexpr size_t kTileDoubles = (size_t)kNoAllocMaxN * kNoAllocMaxN;  // m*nb <= 512 for nb in {32, 64, 128}
 constexpr size_t kTreeDoubles = 512;   // all quadtree levels for m <= 16 (341 nodes)
-constexpr size_t kListDoubles = 4096;  // counts (m^2 <= 256 ints) + task lists (m^3 <= 4096 ints) + counter
+constexpr size_t kListDoubles = 4096;  // counts (m^2 <= 256 ints), task lists (m^3 <= 4096 ints), counters,
+                                       // compacted output tiles (m^2 <= 256 ints)
 constexpr size_t kScratchDoubles = 3 * kTileDoubles + 3 * kTreeDoubles + kListDoubles;
 
 // The scratch itself: about 6.3 MB per GPU.  In host code this name is only
@@ -99,6 +100,7 @@ extern "C" int spamm_multiply_noalloc(const double* A, const double* B, double* 
     double* base = nullptr;
     int st = scratch_address(&base);
     if (st) return st;
+    init_device_attributes();
 
     const Geometry g = make_geometry(n, leaf);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -108,10 +110,12 @@ extern "C" int spamm_multiply_noalloc(const double* A, const double* B, double* 
     int* counts = reinterpret_cast<int*>(base + 3 * kTileDoubles + 3 * kTreeDoubles);
     int* jlist = counts + 256;
     unsigned long long* ctr = reinterpret_cast<unsigned long long*>(counts + 256 + 4096);
+    int* tile_count = reinterpret_cast<int*>(ctr + 1);
+    int* tile_list = tile_count + 2;
 
-    // Only the task counter must start from zero; every other word the
-    // kernels read is written earlier in this same call.
-    cudaError_t e = cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), s);
+    // Only the task counter and the output-tile count must start from zero;
+    // every other word the kernels read is written earlier in this same call.
+    cudaError_t e = cudaMemsetAsync(ctr, 0, sizeof(unsigned long long) + sizeof(int), s);
     if (e != cudaSuccess) {
         set_error_message((std::string("cudaMemsetAsync: ") + cudaGetErrorString(e)).c_str());
         return SPAMM_ERR_CUDA;
@@ -120,9 +124,11 @@ extern "C" int spamm_multiply_noalloc(const double* A, const double* B, double* 
     launch_tree(g, a.tree, nullptr, s);
     launch_pack(B, n, g, nullptr, nullptr, b, s);
     launch_tree(g, b.tree, nullptr, s);
-    launch_cull(g, a.tree, b.tree, tau, counts, jlist, ctr, nullptr, nullptr, s);
-    launch_gemm_f64(g, a.t, b.t, c.t, c.tree, counts, jlist, 0, EPI_PLAIN, nullptr, nullptr, s);
-    launch_unpack(c.t, g, C, nullptr, nullptr, s);
+    const CullOut co{counts, jlist, tile_list, tile_count, c.tree, 0};
+    launch_cull(g, a.tree, b.tree, tau, co, ctr, nullptr, nullptr, s);
+    launch_gemm_f64(g, a.t, b.t, c.t, a.tree, b.tree, c.tree, counts, jlist, tile_list, tile_count, 0, EPI_PLAIN,
+                    nullptr, nullptr, s);
+    launch_unpack(c.t, c.tree, g, C, nullptr, nullptr, s);
     e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_error_message((std::string("kernel launch: ") + cudaGetErrorString(e)).c_str());

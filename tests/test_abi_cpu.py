@@ -72,3 +72,11 @@ def test_bad_option_fields_rejected():
     assert L.spamm_sqrt_invsqrt(None, 4, 0.0, 5, buf, buf, ctypes.byref(o), None) == -1
     assert L.spamm_sqrt_invsqrt_batched(-1, None, None, None, 5, None, None, None, None) == -1
     assert L.spamm_sqrt_invsqrt_batched(0, None, None, None, 5, None, None, None, None) == 0
+
+
+def test_server_create_rejects_bad_budget_without_device():
+    L = sp.lib()
+    h = ctypes.c_void_p(0)
+    assert L.spamm_server_create(0, 2, None, ctypes.byref(h)) == -1
+    assert L.spamm_server_create(1 << 20, 0, None, ctypes.byref(h)) == -1
+    assert L.spamm_server_destroy(None) == -1

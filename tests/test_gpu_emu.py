@@ -1,12 +1,12 @@
 """GPU parity of the tensor-core (SPAMM_EMU64) leaf products against the FP64 CPU oracle.
 
 Error model (derived in kernels_emu.cu): each operand entry is held to
-2^-49 of its row (A role) or column (B role) magnitude bound 2^e <= 2 max|.|;
+2^-49 2^e of its row (A role) or column (B role) scale 2^e <= 4 max|.|;
 slice pairs p+q >= 6 are dropped except (1,5), (3,3), (5,1).  Per product
-element the error is at most about K * 2^-46 * 2^(eA_r + eB_c) plus the FP64
+element the error is at most a few K 2^-48 2^(eA_r + eB_c) plus the FP64
 rounding of the final value, K = inner length.  The tests use
-  |C - C_oracle| <= K 2^-44 rowmax(A)_r colmax(B)_c + 4 K u (|A||B|)_rc
-(2^(eA) <= 2 rowmax, 2^(eB) <= 2 colmax).  Integer inputs whose row and column
+  |C - C_oracle| <= K 2^-42 rowmax(A)_r colmax(B)_c + 4 K u (|A||B|)_rc
+(2^(eA) <= 4 rowmax, 2^(eB) <= 4 colmax).  Integer inputs whose row and column
 maxima are powers of two are represented exactly, so tau = 0 products are
 then bitwise equal to the exact product.  Newton-Schulz with these products:
 ||Z - Z_oracle||_F / ||Z_oracle||_F <= 1e-9 (the iteration carries product
@@ -33,7 +33,7 @@ def dev(a):
 def _tol(A, B, K):
     ra = np.abs(A).max(axis=1)[:, None]
     cb = np.abs(B).max(axis=0)[None, :]
-    return K * 2.0 ** -44 * ra * cb + 4 * K * U * (np.abs(A) @ np.abs(B)) + 1e-300
+    return K * 2.0 ** -42 * ra * cb + 4 * K * U * (np.abs(A) @ np.abs(B)) + 1e-300
 
 
 @pytest.mark.parametrize("n", [64, 128, 200, 512])

@@ -193,3 +193,15 @@ def test_ns_kms_4096_full_size():
     """KMS rho 0.9, N 4096, N_b 64 (the benchmark workload's geometry) at tau 1e-8: full iteration vs oracle."""
     S = synth.kms(4096, 0.9)
     _ns_compare(S, 64, 1e-8, 30)
+
+
+def test_graph_replay_identical_and_profiled():
+    """Repeated fixed-iteration solves replay a captured CUDA graph: identical results, kernel timings recorded,
+    and no CUDA error left behind for the caller."""
+    S = dev(synth.kms(512, 0.9))
+    outs = [sp.sqrt_invsqrt(S, 1e-10, 12, leaf=64, profile=True) for _ in range(3)]
+    for Y, Z, st in outs[1:]:
+        assert torch.equal(Y, outs[0][0]) and torch.equal(Z, outs[0][1])
+        assert st["gemm_ms"] > 0 and st["gemm_launches"] == 36
+    torch.zeros(4, device="cuda").add_(1)
+    torch.cuda.synchronize()
