@@ -23,12 +23,13 @@
 // the digit truncation leave an error of a few 2^{-48} per product term
 // relative to 2^{e_row + e_col}: a normwise FP64-class product.
 //
-// Layout (no swizzle, K-major canonical core matrices of 8 rows x 16 bytes,
-// core (row_group, k_group) at ((row_group * 8 + k_group) * 128) bytes):
-//   A role: per tile 3 stacks of 128 x 64 bf16; stack s = slices 2s (rows
-//           0-63) and 2s+1 (rows 64-127) of the tile, K = tile column.
-//   B role: per tile 6 slices of 64 x 64 bf16, stored transposed (row =
-//           tile column c = MMA N index, K = tile row).
+// Layout (no swizzle, K-major canonical core matrices of 8 rows x 16 bytes;
+// per K-half of 32, core (row_group, k_group) at ((row_group * 4 + k_group) *
+// 128) bytes, so the descriptors use LBO = 128 and SBO = 512):
+//   A role: per tile and K-half 3 stacks of 128 x 32 bf16; stack s = slices
+//           2s (rows 0-63) and 2s+1 (rows 64-127), K = tile column.
+//   B role: per tile and K-half 6 slices of 64 x 32 bf16, stored transposed
+//           (row = tile column c = MMA N index, K = tile row).
 // One M=128, N=64, K=16 MMA (stack s, slice q) yields slice pairs (2s, q) in
 // TMEM lanes 0-63 and (2s+1, q) in lanes 64-127.
 #include <cuda_bf16.h>
@@ -43,20 +44,25 @@ namespace emu {
 
 constexpr int NB = 64;
 constexpr int NSLICE = 6;
-constexpr uint32_t A_STACK_BYTES = 128 * 64 * 2;
-constexpr uint32_t A_TILE_BYTES = 3 * A_STACK_BYTES;
-constexpr uint32_t B_SLICE_BYTES = 64 * 64 * 2;
-constexpr uint32_t B_TILE_BYTES = NSLICE * B_SLICE_BYTES;
-constexpr uint32_t STAGE_BYTES = A_TILE_BYTES + B_TILE_BYTES;
-constexpr int NSTAGE = 2;
-constexpr uint32_t SMEM_DYN = NSTAGE * STAGE_BYTES + 1024;
+// One task is split into two K-halves of 32.  Per tile and operand role the
+// slices are stored as [K-half][stack or slice][core matrices], so a half-task's
+// A data and B data are each one contiguous 24 KB block.
+constexpr uint32_t A_HALF_STACK = 128 * 32 * 2;          // 128 rows x 32 K
+constexpr uint32_t A_HALF_BYTES = 3 * A_HALF_STACK;      // 3 stacks
+constexpr uint32_t A_TILE_BYTES = 2 * A_HALF_BYTES;
+constexpr uint32_t B_HALF_SLICE = 64 * 32 * 2;           // 64 columns x 32 K
+constexpr uint32_t B_HALF_BYTES = NSLICE * B_HALF_SLICE;  // 6 slices
+constexpr uint32_t B_TILE_BYTES = 2 * B_HALF_BYTES;
+constexpr uint32_t STAGE_BYTES = A_HALF_BYTES + B_HALF_BYTES;
+constexpr int NSTAGE = 3;
+constexpr uint32_t EPI_BYTES = 2 * 64 * 65 * 8;          // epilogue staging of the two 64-bit halves
+constexpr uint32_t SMEM_DYN = NSTAGE * STAGE_BYTES + EPI_BYTES + 1024;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int kEpiWarps = 4;                 // one per TMEM lane quarter
 constexpr int kThreads = 32 * (2 + kEpiWarps);
 constexpr int kGroups = 5;                   // accumulator groups (64 TMEM columns each)
 constexpr int kChunk = 7;                    // tasks accumulated in TMEM between flushes (exactness bound)
 constexpr int kMaxTasks = 256;
-constexpr long long kSpin = 1ll << 22;
 
 // exponent e with |x| < 2^(e-1) for every x of a row/column whose largest
 // magnitude has the IEEE bits `bits` (0 for an all-zero or subnormal row):
@@ -135,7 +141,8 @@ __global__ void __launch_bounds__(256) k_slice(const double* __restrict__ X, con
         const bool arole = item < 512;
         const int it = arole ? item : item - 512;
         // 8 consecutive items fill one 128-byte core matrix, 32 consecutive items 512 contiguous bytes
-        const int r = (it >> 6) * 8 + (it & 7), g = (it >> 3) & 7;  // A: row r, k-group g; B: column r, k-group g
+        const int kgi = (it >> 3) & 3, kh = (it >> 5) & 1;
+        const int r = (it >> 6) * 8 + (it & 7), g = kh * 4 + kgi;  // A: row r, k-group g; B: column r, k-group g
         int D[8][6];
         for (int q = 0; q < 8; ++q) {
             const double v = arole ? xs[r][8 * g + q] : xs[8 * g + q][r];
@@ -147,10 +154,12 @@ __global__ void __launch_bounds__(256) k_slice(const double* __restrict__ X, con
             uint32_t off;
             if (arole) {
                 const int row = (p & 1) * 64 + r;
-                off = (uint32_t)(p >> 1) * A_STACK_BYTES + (uint32_t)(((row >> 3) * 8 + g) * 128 + (row & 7) * 16);
+                off = (uint32_t)kh * A_HALF_BYTES + (uint32_t)(p >> 1) * A_HALF_STACK +
+                      (uint32_t)(((row >> 3) * 4 + kgi) * 128 + (row & 7) * 16);
                 *reinterpret_cast<uint4*>(a + off) = *reinterpret_cast<const uint4*>(w);
             } else {
-                off = (uint32_t)p * B_SLICE_BYTES + (uint32_t)(((r >> 3) * 8 + g) * 128 + (r & 7) * 16);
+                off = (uint32_t)kh * B_HALF_BYTES + (uint32_t)p * B_HALF_SLICE +
+                      (uint32_t)(((r >> 3) * 4 + kgi) * 128 + (r & 7) * 16);
                 *reinterpret_cast<uint4*>(b + off) = *reinterpret_cast<const uint4*>(w);
             }
         }
@@ -205,6 +214,37 @@ struct EmuArgs {
 
 __device__ __forceinline__ uint32_t stage_addr(uint32_t base, int s) { return base + (uint32_t)s * STAGE_BYTES; }
 
+// Double-word FP32 accumulation (hi + lo, about 2^-44 relative) of the
+// squares of FP64 values: FP64 arithmetic has long latency on this part, so
+// the per-tile sums of squares avoid dependent FP64 chains.
+struct DFloat {
+    float hi, lo;
+};
+__device__ __forceinline__ DFloat df_add(DFloat x, DFloat y) {
+    const float s = x.hi + y.hi;
+    const float bb = s - x.hi;
+    const float e = ((x.hi - (s - bb)) + (y.hi - bb)) + (x.lo + y.lo);
+    const float h = s + e;
+    return DFloat{h, e - (h - s)};
+}
+// v * v as a double-word: v split into its leading 24 mantissa bits and the rest.
+__device__ __forceinline__ DFloat df_square(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+    const int E = (int)(b >> 52);
+    const int fe = E - 1023 + 127;
+    if (E == 0 || fe <= 0 || fe >= 255) return DFloat{0.f, 0.f};  // zero, or below FP32 range (negligible)
+    const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
+    const float hi = __uint_as_float(((unsigned)fe << 23) | (unsigned)(mant >> 29));
+    const int le = E - 1023 - 52 + 127;  // exponent of the low 29 bits' unit
+    const float lo = le > 0 ? (float)(unsigned)(mant & 0x1FFFFFFFull) * __uint_as_float((unsigned)le << 23) : 0.f;
+    const float p = hi * hi;
+    const float pe = fmaf(hi, hi, -p);
+    return DFloat{p, fmaf(2.0f * hi, lo, pe)};
+}
+__device__ __forceinline__ DFloat df_shfl_xor(DFloat x, int o) {
+    return DFloat{__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o)};
+}
+
 // int64 -> double as integer operations (round to nearest even), times 2^s.
 __device__ __forceinline__ double fixed_to_double(long long tot, int s) {
     if (tot == 0) return 0.0;
@@ -228,27 +268,64 @@ __device__ __forceinline__ double fixed_to_double(long long tot, int s) {
 __device__ __forceinline__ double neg_half(double x) {
     unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const unsigned long long ef = (b >> 52) & 0x7FF;
-    if (ef <= 1) return -0.5 * x;  // zero or subnormal: plain arithmetic
+    if (ef <= 1) return __longlong_as_double((long long)((b & 0x8000000000000000ull) ^ 0x8000000000000000ull));  // +-0 and subnormals -> -+0
     b ^= 1ull << 63;
     b -= 1ull << 52;
     return __longlong_as_double((long long)b);
 }
 
-// Persistent: one CTA per SM walks the compacted output-tile list.  The
-// stage, chunk and barrier phase counters run on across tiles.
+// Move one chunk's accumulator groups from TMEM into the 64-bit fixed-point
+// sums of this thread's row.  Groups 0-3 hold exact integers in units of
+// 2^{-8(diag+2)}, diag = group + half (half = 1 for the odd-slice lanes);
+// group 4 (diagonals >= 4 + half) is rounded to units of 2^{-48}.
+__device__ __forceinline__ void flush_groups(uint32_t lane_base, int half, long long (&acc)[NB]) {
+#pragma unroll
+    for (int g = 0; g < kGroups; ++g) {
+        const int diag = g + half;
+        const float up = g < 4 ? __int_as_float((127 + 8 * (diag + 2)) << 23) : __int_as_float((127 + 48) << 23);
+        const int sh = g < 4 ? 32 - 8 * diag : 0;
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            uint32_t r[16];
+            ptx::tmem_ld16(lane_base + (uint32_t)(g * 64 + h * 16), r);
+            ptx::tmem_ld_wait();
+#pragma unroll
+            for (int c = 0; c < 16; ++c) acc[h * 16 + c] += (long long)__float2int_rn(__uint_as_float(r[c]) * up) << sh;
+        }
+    }
+}
+
+// Bounded wait that also gives up when another role of this CTA aborted.
+__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+    for (long long it = 0; it < (1ll << 22); ++it) {
+        if (ptx::mbar_try_wait(bar, parity)) return true;
+        if ((it & 255) == 255 && *abort_flag) return false;
+    }
+    *abort_flag = 1;
+    return false;
+}
+
+// Persistent: one CTA per SM walks the compacted output-tile list.  The three
+// roles run decoupled: the producer warp prepares tile t+1 (task list,
+// scales) and streams its half-tasks while the MMA warp is still on tile t
+// and the epilogue warps finish tile t-1; mbarriers order them.
 __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
     if (a.done && *a.done) return;
     extern __shared__ uint8_t dyn_smem[];
     __shared__ __align__(8) uint64_t bar_full[NSTAGE], bar_empty[NSTAGE], bar_accf, bar_acce;
+    __shared__ __align__(8) uint64_t bar_tready[2], bar_tfree[2];
     __shared__ uint32_t tmem_base_sh;
-    __shared__ int tasks_sh[kMaxTasks];
-    __shared__ int ntask_sh;
-    __shared__ int fail_sh;
-    __shared__ int eA_sh[NB], eB_sh[NB];
-    __shared__ double red_sh[4];
+    __shared__ int tasks_sh[2][kMaxTasks];
+    __shared__ int ntask_sh[2];
+    __shared__ int eA_sh[2][NB], eB_sh[2][NB];
+    __shared__ float red_sh[8];
+    __shared__ double tr_sh[4];
+    __shared__ int abort_sh;
 
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dyn_smem) + 1023) & ~uintptr_t(1023));
     const uint32_t sbase = ptx::smem_addr(smem);
+    long long* sTop = reinterpret_cast<long long*>(smem + NSTAGE * STAGE_BYTES);  // [64][65]
+    long long* sBot = sTop + NB * 65;                                             // [64][65]
     const int m = a.m;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ntiles = *a.tile_count;
@@ -261,6 +338,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
         }
         ptx::mbar_init(&bar_accf, 1);
         ptx::mbar_init(&bar_acce, kEpiWarps);
+        for (int q = 0; q < 2; ++q) {
+            ptx::mbar_init(&bar_tready[q], 1);
+            ptx::mbar_init(&bar_tfree[q], kEpiWarps);
+        }
+        abort_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -271,16 +353,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
     __syncthreads();
     ptx::tc_fence_after();
     const uint32_t tmem = tmem_base_sh;
+    volatile int* abort_flag = &abort_sh;
 
-    long long gtask = 0;   // tasks issued by this CTA before the current tile
-    long long gchunk = 0;  // accumulator chunks before the current tile
-    bool fail = false;
-
-    for (int idx = blockIdx.x; idx < ntiles && !fail; idx += gridDim.x) {
-        const int tile = a.tile_list[idx];
-        const int i = tile / m, k = tile - (tile / m) * m;
-        if (warp == 1) {
-            // compact the task list: skip operand tiles of zero norm (exact zero products)
+    if (warp == 0) {
+        // ---------------- producer: per tile the task list and scales, then the half-task stream
+        long long H = 0;
+        int tau = 0;
+        for (int idx = blockIdx.x; idx < ntiles && !*abort_flag; idx += gridDim.x, ++tau) {
+            const int slot = tau & 1;
+            const int tile = a.tile_list[idx];
+            const int i = tile / m, k = tile - (tile / m) * m;
+            if (tau >= 2) {
+                bool ok = true;
+                if (lane == 0) ok = wait_or_abort(&bar_tfree[slot], (uint32_t)(((tau >> 1) & 1) ^ 1), abort_flag);
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (!ok) {
+                    if (lane == 0) atomicExch(a.err, 1);
+                    break;
+                }
+            }
             const int cnt = a.counts[tile];
             const int* js = a.jlist + (size_t)tile * m;
             int T = 0;
@@ -293,142 +384,156 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
                     keep = a.leafA[(size_t)i * m + j] != 0.0 && a.leafB[(size_t)j * m + k] != 0.0;
                 }
                 const unsigned bal = __ballot_sync(0xffffffffu, keep);
-                if (keep) tasks_sh[T + __popc(bal & ((1u << lane) - 1u))] = j;
+                if (keep) tasks_sh[slot][T + __popc(bal & ((1u << lane) - 1u))] = j;
                 T += __popc(bal);
             }
-            if (lane == 0) ntask_sh = T;
-        } else if (warp >= 2 && warp < 4) {
-            const int r = (warp - 2) * 32 + lane;
-            eA_sh[r] = expo_of(a.rmaxA[i * NB + r]);
-        } else if (warp >= 4) {
-            const int r = (warp - 4) * 32 + lane;
-            eB_sh[r] = expo_of(a.cmaxB[k * NB + r]);
-        }
-        __syncthreads();
-        const int T = ntask_sh;
-        const int nchunks = (T + kChunk - 1) / kChunk;
-
-        if (warp == 0) {
-            // ---------------- producer: bulk copies of the slices of A_ij and B_jk
-            if (lane == 0) {
-                for (int t = 0; t < T; ++t) {
-                    const long long G = gtask + t;
-                    const int s = (int)(G & 1);
-                    if (G >= 2 && !ptx::mbar_wait_bounded(&bar_empty[s], (uint32_t)(((G >> 1) & 1) ^ 1), kSpin)) {
-                        atomicExch(a.err, 1);
-                        break;
-                    }
-                    const int j = tasks_sh[t];
-                    uint8_t* dst = smem + (size_t)s * STAGE_BYTES;
-                    ptx::mbar_arrive_expect_tx(&bar_full[s], STAGE_BYTES);
-                    ptx::bulk_g2s(dst, a.sliceA + ((size_t)i * m + j) * A_TILE_BYTES, A_TILE_BYTES, &bar_full[s]);
-                    ptx::bulk_g2s(dst + A_TILE_BYTES, a.sliceB + ((size_t)j * m + k) * B_TILE_BYTES, B_TILE_BYTES,
-                                  &bar_full[s]);
-                }
+            for (int r = lane; r < NB; r += 32) {
+                eA_sh[slot][r] = expo_of(a.rmaxA[i * NB + r]);
+                eB_sh[slot][r] = expo_of(a.cmaxB[k * NB + r]);
             }
+            if (lane == 0) ntask_sh[slot] = T;
             __syncwarp();
-        } else if (warp == 1) {
-            // ---------------- MMA issuer: tasks are accumulated in TMEM in chunks of kChunk
             if (lane == 0) {
-                constexpr uint32_t idesc = ptx::idesc_bf16_f32(128, 64);
-                // stacks {0,0,0,1,0,1,0,0,1,1,2,2} and slices {0,1,2,0,3,1,4,5,2,3,0,1}: pairs ordered by
-                // accumulator group = diagonal 2*stack + slice of the top half, capped at 4
-                constexpr uint32_t kStacks = (1u << 6) | (1u << 10) | (1u << 16) | (1u << 18) | (2u << 20) | (2u << 22);
-                constexpr uint64_t kSlices = (1ull << 4) | (2ull << 8) | (3ull << 16) | (1ull << 20) | (4ull << 24) |
-                                             (5ull << 28) | (2ull << 32) | (3ull << 36) | (1ull << 44);
+                ptx::mbar_arrive(&bar_tready[slot]);  // release: the task list and scales are visible
                 for (int t = 0; t < T; ++t) {
-                    const long long G = gtask + t;
-                    const int s = (int)(G & 1);
-                    const long long C = gchunk + t / kChunk;
-                    const bool chunk_start = (t % kChunk) == 0;
-                    if (!ptx::mbar_wait_bounded(&bar_full[s], (uint32_t)((G >> 1) & 1), kSpin)) {
-                        atomicExch(a.err, 2);
-                        break;
-                    }
-                    // a new chunk overwrites the accumulators: the epilogue must have read the previous one
-                    if (chunk_start && C > 0 && !ptx::mbar_wait_bounded(&bar_acce, (uint32_t)((C - 1) & 1), kSpin)) {
-                        atomicExch(a.err, 3);
-                        break;
-                    }
-                    ptx::tc_fence_after();
-                    const uint32_t sA = stage_addr(sbase, s), sB = sA + A_TILE_BYTES;
-                    int prev_g = -1;
-                    for (int u = 0; u < 12; ++u) {
-                        const int sg = (int)((kStacks >> (2 * u)) & 3u), q = (int)((kSlices >> (4 * u)) & 15ull);
-                        const int g = min(2 * sg + q, 4);
-                        const uint32_t d = tmem + (uint32_t)(g * 64);
-                        for (int ks = 0; ks < 4; ++ks) {
-                            const uint64_t ad = ptx::smem_desc(sA + sg * A_STACK_BYTES + ks * 256, 128, 1024);
-                            const uint64_t bd = ptx::smem_desc(sB + q * B_SLICE_BYTES + ks * 256, 128, 1024);
-                            // the first MMA into a group in a chunk overwrites it, the rest accumulate
-                            const bool fresh = chunk_start && ks == 0 && g != prev_g;
-                            ptx::mma_bf16(d, ad, bd, idesc, fresh ? 0u : 1u);
-                            prev_g = g;
+                    const int j = tasks_sh[slot][t];
+                    const uint8_t* srcA = a.sliceA + ((size_t)i * m + j) * A_TILE_BYTES;
+                    const uint8_t* srcB = a.sliceB + ((size_t)j * m + k) * B_TILE_BYTES;
+                    for (int h = 0; h < 2; ++h, ++H) {
+                        const int s = (int)(H % NSTAGE);
+                        if (H >= NSTAGE &&
+                            !wait_or_abort(&bar_empty[s], (uint32_t)(((H / NSTAGE) - 1) & 1), abort_flag)) {
+                            atomicExch(a.err, 1);
+                            break;
                         }
+                        uint8_t* dst = smem + (size_t)s * STAGE_BYTES;
+                        ptx::mbar_arrive_expect_tx(&bar_full[s], STAGE_BYTES);
+                        ptx::bulk_g2s(dst, srcA + h * A_HALF_BYTES, A_HALF_BYTES, &bar_full[s]);
+                        ptx::bulk_g2s(dst + A_HALF_BYTES, srcB + h * B_HALF_BYTES, B_HALF_BYTES, &bar_full[s]);
                     }
-                    ptx::mma_commit(&bar_empty[s]);
-                    if ((t % kChunk) == kChunk - 1 || t == T - 1) ptx::mma_commit(&bar_accf);
+                    if (*abort_flag) break;
                 }
             }
             __syncwarp();
-        } else {
-            // ---------------- epilogue warps 2..5: TMEM lane quarter warp%4 (lanes 32q .. 32q+31)
-            const int quarter = warp & 3;
-            const int half = quarter >> 1;  // 0: MMA rows 0-63 (even slices), 1: rows 64-127 (odd slices)
-            const int row = (quarter & 1) * 32 + lane;
-            const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer: tasks accumulate in TMEM in chunks of kChunk
+        if (lane == 0) {
+            constexpr uint32_t idesc = ptx::idesc_bf16_f32(128, 64);
+            // stacks {0,0,0,1,0,1,0,0,1,1,2,2} and slices {0,1,2,0,3,1,4,5,2,3,0,1}: pairs ordered by
+            // accumulator group = diagonal 2*stack + slice of the top half, capped at 4
+            constexpr uint32_t kStacks = (1u << 6) | (1u << 10) | (1u << 16) | (1u << 18) | (2u << 20) | (2u << 22);
+            constexpr uint64_t kSlices = (1ull << 4) | (2ull << 8) | (3ull << 16) | (1ull << 20) | (4ull << 24) |
+                                         (5ull << 28) | (2ull << 32) | (3ull << 36) | (1ull << 44);
+            long long H = 0, C = 0;
+            int tau = 0;
+            bool ok = true;
+            for (int idx = blockIdx.x; idx < ntiles && ok; idx += gridDim.x, ++tau) {
+                const int slot = tau & 1;
+                if (!wait_or_abort(&bar_tready[slot], (uint32_t)((tau >> 1) & 1), abort_flag)) {
+                    atomicExch(a.err, 2);
+                    break;
+                }
+                const int T = ntask_sh[slot];
+                for (int t = 0; t < T && ok; ++t) {
+                    const bool chunk_start = (t % kChunk) == 0;
+                    for (int h = 0; h < 2; ++h, ++H) {
+                        const int s = (int)(H % NSTAGE);
+                        if (!wait_or_abort(&bar_full[s], (uint32_t)((H / NSTAGE) & 1), abort_flag)) {
+                            atomicExch(a.err, 2);
+                            ok = false;
+                            break;
+                        }
+                        // a new chunk overwrites the accumulators: the epilogue must have read the previous one
+                        if (chunk_start && h == 0 && C > 0 &&
+                            !wait_or_abort(&bar_acce, (uint32_t)((C - 1) & 1), abort_flag)) {
+                            atomicExch(a.err, 3);
+                            ok = false;
+                            break;
+                        }
+                        ptx::tc_fence_after();
+                        const uint32_t sA = stage_addr(sbase, s), sB = sA + A_HALF_BYTES;
+                        int prev_g = -1;
+                        for (int u = 0; u < 12; ++u) {
+                            const int sg = (int)((kStacks >> (2 * u)) & 3u), q = (int)((kSlices >> (4 * u)) & 15ull);
+                            const int g = min(2 * sg + q, 4);
+                            const uint32_t d = tmem + (uint32_t)(g * 64);
+                            for (int ks = 0; ks < 2; ++ks) {
+                                const uint64_t ad = ptx::smem_desc(sA + sg * A_HALF_STACK + ks * 256, 128, 512);
+                                const uint64_t bd = ptx::smem_desc(sB + q * B_HALF_SLICE + ks * 256, 128, 512);
+                                // the first MMA into a group in a chunk overwrites it, the rest accumulate
+                                const bool fresh = chunk_start && h == 0 && ks == 0 && g != prev_g;
+                                ptx::mma_bf16(d, ad, bd, idesc, fresh ? 0u : 1u);
+                                prev_g = g;
+                            }
+                        }
+                        ptx::mma_commit(&bar_empty[s]);
+                    }
+                    if (ok && ((t % kChunk) == kChunk - 1 || t == T - 1)) {
+                        ptx::mma_commit(&bar_accf);
+                        ++C;
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue warps 2..5: TMEM lane quarter warp%4 (lanes 32q .. 32q+31)
+        const int quarter = warp & 3;
+        const int half = quarter >> 1;  // 0: MMA rows 0-63 (even slices), 1: rows 64-127 (odd slices)
+        const int row = (quarter & 1) * 32 + lane;
+        const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+        const int et = threadIdx.x - 64;  // 0..127
+        long long C = 0;
+        int tau = 0;
+        for (int idx = blockIdx.x; idx < ntiles; idx += gridDim.x, ++tau) {
+            const int slot = tau & 1;
+            const int tile = a.tile_list[idx];
+            const int i = tile / m, k = tile - (tile / m) * m;
+            if (!wait_or_abort(&bar_tready[slot], (uint32_t)((tau >> 1) & 1), abort_flag)) {
+                atomicExch(a.err, 4);
+                break;
+            }
+            const int T = ntask_sh[slot];
+            const int nchunks = (T + kChunk - 1) / kChunk;
             long long acc[NB];
 #pragma unroll
             for (int c = 0; c < NB; ++c) acc[c] = 0;
-            for (int ck = 0; ck < nchunks; ++ck) {
-                const long long C = gchunk + ck;
-                if (!ptx::mbar_wait_bounded(&bar_accf, (uint32_t)(C & 1), kSpin)) {
+            bool ok = true;
+            for (int ck = 0; ck < nchunks; ++ck, ++C) {
+                if (!wait_or_abort(&bar_accf, (uint32_t)(C & 1), abort_flag)) {
                     atomicExch(a.err, 4);
+                    ok = false;
                     break;
                 }
                 ptx::tc_fence_after();
-#pragma unroll
-                for (int g = 0; g < kGroups; ++g) {
-                    // groups 0-3 hold exact integers in units 2^{-8(diag+2)}, diag = g + half; group 4
-                    // (diagonals >= 4 + half) is rounded to units of 2^{-48}
-                    const int diag = g + half;
-                    const float up =
-                        g < 4 ? __int_as_float((127 + 8 * (diag + 2)) << 23) : __int_as_float((127 + 48) << 23);
-                    const int sh = g < 4 ? 32 - 8 * diag : 0;
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        uint32_t r[32];
-                        ptx::tmem_ld32(lane_base + (uint32_t)(g * 64 + h * 32), r);
-                        ptx::tmem_ld_wait();
-#pragma unroll
-                        for (int c = 0; c < 32; ++c)
-                            acc[h * 32 + c] += (long long)__float2int_rn(__uint_as_float(r[c]) * up) << sh;
-                    }
-                }
+                flush_groups(lane_base, half, acc);
                 ptx::tc_fence_before();
                 __syncwarp();
                 if (lane == 0) ptx::mbar_arrive(&bar_acce);
             }
-            // combine the odd-slice half (MMA rows 64-127) into the even half
-            long long* comb = reinterpret_cast<long long*>(smem);  // [64][65] int64; stage memory is idle now
-            if (half == 1) {
+            if (!ok) break;
+            // stage both halves' 64-bit sums, then finish the tile element-parallel:
+            // thread et owns column c and every other row
+            long long* dst = half ? sBot : sTop;
 #pragma unroll
-                for (int c = 0; c < NB; ++c) comb[c * 65 + row] = acc[c];
-            }
+            for (int c = 0; c < NB; ++c) dst[c * 65 + row] = acc[c];
             ptx::named_sync(1, 32 * kEpiWarps);
-            unsigned long long* colbuf = reinterpret_cast<unsigned long long*>(smem + 65 * 64 * 8);  // [64][65]
-            double nu = 0.0, tr = 0.0;
-            if (half == 0) {
-                // eight independent partial sums of squares (FP64 latency is long on this part)
-                double nup[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-                const int gi = i * NB + row;
-                const int eAr = eA_sh[row];
-                unsigned long long rmx = 0;
+            const int c = et & 63;
+            const int r0 = et >> 6;
+            const int gj = k * NB + c;
+            const int eBc = eB_sh[slot][c];
+            double* outt = a.C + (size_t)tile * NB * NB;
+            DFloat nup[2] = {{0.f, 0.f}, {0.f, 0.f}};
+            double tr = 0.0;
+            unsigned long long cmx = 0;
+            for (int q0 = 0; q0 < 32; q0 += 8) {
 #pragma unroll
-                for (int c = 0; c < NB; ++c) {
-                    const long long t64 = acc[c] + comb[c * 65 + row];
-                    const double x = fixed_to_double(t64, eAr + eB_sh[c] - 48);
-                    const int gj = k * NB + c;
+                for (int u = 0; u < 8; ++u) {
+                    const int r = r0 + 2 * (q0 + u);
+                    const int gi = i * NB + r;
+                    const long long t64 = sTop[c * 65 + r] + sBot[c * 65 + r];
+                    const double x = fixed_to_double(t64, eA_sh[slot][r] + eBc - 48);
                     double v = x;
                     if (a.mode == EPI_NS_X) {
                         if (gi == gj && gi < a.n) {
@@ -438,52 +543,42 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
                             v = neg_half(x);
                         }
                     }
-                    // staged in place of the combine buffer, stored coalesced below
-                    comb[c * 65 + row] = __double_as_longlong(v);
-                    nup[c & 7] = fma(v, v, nup[c & 7]);
+                    outt[r * NB + c] = v;  // consecutive lanes: consecutive columns
+                    nup[u & 1] = df_add(nup[u & 1], df_square(v));
                     const unsigned long long vb = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
-                    rmx = max(rmx, vb);
-                    colbuf[c * 65 + row] = vb;
+                    cmx = max(cmx, vb);
+                    sTop[c * 65 + r] = (long long)vb;  // in place: magnitudes for the row maxima below
                 }
-                nu = ((nup[0] + nup[1]) + (nup[2] + nup[3])) + ((nup[4] + nup[5]) + (nup[6] + nup[7]));
-                if (rmx) atomicMax(a.rmaxC + gi, rmx);
+            }
+            if (cmx) atomicMax(a.cmaxC + gj, cmx);
+            DFloat nu = df_add(nup[0], nup[1]);
+            for (int o = 16; o > 0; o >>= 1) nu = df_add(nu, df_shfl_xor(nu, o));
+            if (a.mode == EPI_NS_X && i == k) {
+                for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+            }
+            if (lane == 0) {
+                red_sh[2 * (warp - 2)] = nu.hi;
+                red_sh[2 * (warp - 2) + 1] = nu.lo;
+                tr_sh[warp - 2] = tr;
             }
             ptx::named_sync(1, 32 * kEpiWarps);
-            {
-                // coalesced store of the tile: epilogue warp e writes rows 16e .. 16e+15
-                double* outt = a.C + (size_t)tile * NB * NB;
-                const int e = warp - 2;
-                for (int rr = 0; rr < 16; ++rr) {
-                    const int r = e * 16 + rr;
-                    outt[r * NB + lane] = __longlong_as_double(comb[lane * 65 + r]);
-                    outt[r * NB + lane + 32] = __longlong_as_double(comb[(lane + 32) * 65 + r]);
-                }
+            if (et < NB) {
+                // row maxima: thread et reduces row et over its 64 columns
+                unsigned long long rmx = 0;
+#pragma unroll 16
+                for (int cc = 0; cc < NB; ++cc) rmx = max(rmx, (unsigned long long)sTop[cc * 65 + et]);
+                if (rmx) atomicMax(a.rmaxC + i * NB + et, rmx);
             }
-            if (half == 0) {
-                unsigned long long cmx = 0;
-                for (int r = 0; r < NB; ++r) cmx = max(cmx, colbuf[row * 65 + r]);
-                if (cmx) atomicMax(a.cmaxC + k * NB + row, cmx);
-                for (int o = 16; o > 0; o >>= 1) {
-                    nu += __shfl_xor_sync(0xffffffffu, nu, o);
-                    tr += __shfl_xor_sync(0xffffffffu, tr, o);
-                }
-                if (lane == 0) {
-                    red_sh[quarter & 1] = nu;
-                    red_sh[2 + (quarter & 1)] = tr;
-                }
+            if (warp == 2 && lane == 0) {
+                DFloat t = DFloat{red_sh[0], red_sh[1]};
+                for (int w = 1; w < 4; ++w) t = df_add(t, DFloat{red_sh[2 * w], red_sh[2 * w + 1]});
+                a.leafC[tile] = (double)t.hi + (double)t.lo;
+                if (a.mode == EPI_NS_X && i == k) a.trace_part[i] = (tr_sh[0] + tr_sh[1]) + (tr_sh[2] + tr_sh[3]);
             }
+            // every epilogue warp is done with the staging buffer and this slot's scales
             ptx::named_sync(1, 32 * kEpiWarps);
-            if (warp == 4 && lane == 0) {
-                a.leafC[tile] = red_sh[0] + red_sh[1];
-                if (a.mode == EPI_NS_X && i == k) a.trace_part[i] = red_sh[2] + red_sh[3];
-            }
+            if (lane == 0) ptx::mbar_arrive(&bar_tfree[slot]);
         }
-        gtask += T;
-        gchunk += nchunks;
-        // the next tile reuses the stages and the task list; a recorded error stops every CTA
-        if (threadIdx.x == 0) fail_sh = *(volatile int*)a.err != 0;
-        __syncthreads();
-        fail = fail_sh;
     }
 
     ptx::tc_fence_before();

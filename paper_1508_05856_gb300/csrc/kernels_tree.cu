@@ -68,12 +68,26 @@ __global__ void k_rowsum(const double* __restrict__ S, int n, const double* __re
     if (row >= n) return;
     const double mu = mu_dev ? *mu_dev : 0.0;
     const double* r = S + (size_t)row * n;
-    double s = 0.0;
-    for (int j = lane; j < n; j += 32) {
+    // four independent partial sums per lane (FP64 latency is long), fixed order
+    double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
+    int j = lane;
+    for (; j + 96 < n; j += 128) {
+        double v0 = r[j], v1 = r[j + 32], v2 = r[j + 64], v3 = r[j + 96];
+        if (j == row) v0 += mu;
+        if (j + 32 == row) v1 += mu;
+        if (j + 64 == row) v2 += mu;
+        if (j + 96 == row) v3 += mu;
+        p0 += fabs(v0);
+        p1 += fabs(v1);
+        p2 += fabs(v2);
+        p3 += fabs(v3);
+    }
+    for (; j < n; j += 32) {
         double v = r[j];
         if (j == row) v += mu;
-        s += fabs(v);
+        p0 += fabs(v);
     }
+    double s = (p0 + p1) + (p2 + p3);
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) rowsum[row] = s;
 }
@@ -210,13 +224,12 @@ __global__ void __launch_bounds__(1024) k_tree(TreeDev td, double* __restrict__ 
         double* pa = tree + td.off[l];
         for (int idx = threadIdx.x; idx < d * d; idx += blockDim.x) {
             const int I = idx / d, J = idx - I * d;
-            double s = 0.0;
-            for (int a = 0; a < 2; ++a)
-                for (int b = 0; b < 2; ++b) {
-                    const int ci = 2 * I + a, cj = 2 * J + b;
-                    if (ci < dc && cj < dc) s += ch[(size_t)ci * dc + cj];
-                }
-            pa[idx] = s;
+            // existing children, summed pairwise (rows first): depth 2 instead of a chain of 4
+            const int ci = 2 * I, cj = 2 * J;
+            const bool r1 = ci + 1 < dc, c1 = cj + 1 < dc;
+            const double s0 = ch[(size_t)ci * dc + cj] + (c1 ? ch[(size_t)ci * dc + cj + 1] : 0.0);
+            const double s1 = r1 ? ch[(size_t)(ci + 1) * dc + cj] + (c1 ? ch[(size_t)(ci + 1) * dc + cj + 1] : 0.0) : 0.0;
+            pa[idx] = s0 + s1;
         }
         __syncthreads();
     }
@@ -228,61 +241,68 @@ void launch_tree(const Geometry& g, double* tree, const int* done, cudaStream_t 
 }
 
 // ---------------------------------------------------------------- the cull
-// One thread per output tile (i, k): scan j ascending, skipping whole coarse
-// blocks J whose coarse pair product is below the threshold.  Parents hold
-// sums of non-negative children, so a coarse pair below the threshold has no
-// surviving leaf pair under it; the surviving set is exactly the leaf test
-// nuA(i,j) * nuB(j,k) >= thr, i.e. the recursion of Eq. (newspamm).
-__global__ void __launch_bounds__(128) k_cull(TreeDev td, const double* __restrict__ treeA,
+// One warp per output tile (i, k).  Lanes test 32 consecutive j at a time
+// (independent FP64 products, so the long FP64 latency overlaps) and the
+// survivors are compacted with a ballot in ascending j.  A chunk of 32 j is
+// skipped when no coarse block J under it passes the coarse test: parents
+// hold sums of non-negative children, so a coarse pair below the threshold
+// has no surviving leaf pair under it.  The surviving set is exactly the leaf
+// test nuA(i,j) * nuB(j,k) >= thr, i.e. the recursion of Eq. (newspamm).
+__global__ void __launch_bounds__(256) k_cull(TreeDev td, const double* __restrict__ treeA,
                                               const double* __restrict__ treeB, double tau, CullOut co,
                                               unsigned long long* __restrict__ total, double* __restrict__ thr_out,
                                               const int* __restrict__ done) {
     if (done && *done) return;
-    __shared__ int red[4];
+    __shared__ int red[8];
     const int m = td.m;
-    const int i = blockIdx.y;
-    const int k = blockIdx.x * 128 + threadIdx.x;
+    const int wid = blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
     const double thr = ((tau * tau) * treeA[td.off[0]]) * treeB[td.off[0]];
     int cnt = 0;
-    if (k < m) {
+    if (wid < m * m) {
+        const int i = wid / m, k = wid - (wid / m) * m;
         const int dc = td.dim[td.coarse];
         const double* cA = treeA + td.off[td.coarse];
         const double* cB = treeB + td.off[td.coarse];
         const int I = i >> td.shift, K = k >> td.shift;
-        const double* nA = treeA;   // leaf level at offset 0
-        const double* nB = treeB;
-        int* out = co.jlist + ((size_t)i * m + k) * m;
-        for (int J = 0; J < dc; ++J) {
-            if (cA[(size_t)I * dc + J] * cB[(size_t)J * dc + K] < thr) continue;
-            const int j0 = J << td.shift;
-            const int j1 = min(m, (J + 1) << td.shift);
-            for (int j = j0; j < j1; ++j)
-                if (!(nA[(size_t)i * m + j] * nB[(size_t)j * m + k] < thr)) out[cnt++] = j;
+        int* out = co.jlist + (size_t)wid * m;
+        for (int j0 = 0; j0 < m; j0 += 32) {
+            const int j = j0 + lane;
+            bool coarse = false;
+            if (j < m) {
+                const int J = j >> td.shift;
+                coarse = !(cA[(size_t)I * dc + J] * cB[(size_t)J * dc + K] < thr);
+            }
+            if (!__any_sync(0xffffffffu, coarse)) continue;
+            const bool keep = coarse && !(treeA[(size_t)i * m + j] * treeB[(size_t)j * m + k] < thr);
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            if (keep) out[cnt + __popc(bal & ((1u << lane) - 1u))] = j;
+            cnt += __popc(bal);
         }
-        const int tile = i * m + k;
-        co.counts[tile] = cnt;
-        if (co.tile_list) {
-            if (cnt > 0 || (co.force_diag && i == k)) co.tile_list[atomicAdd(co.tile_count, 1)] = tile;
-            else if (co.leafC) co.leafC[tile] = 0.0;
+        if (lane == 0) {
+            co.counts[wid] = cnt;
+            if (co.tile_list) {
+                if (cnt > 0 || (co.force_diag && i == k)) co.tile_list[atomicAdd(co.tile_count, 1)] = wid;
+                else if (co.leafC) co.leafC[wid] = 0.0;
+            }
         }
     }
-    if (thr_out && i == 0 && k == 0) *thr_out = thr;
+    if (thr_out && wid == 0 && lane == 0) *thr_out = thr;
     if (total) {
-        int v = cnt;
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+        if (lane == 0) red[threadIdx.x >> 5] = cnt;
         __syncthreads();
         if (threadIdx.x == 0) {
-            const int s = red[0] + red[1] + red[2] + red[3];
-            if (s) atomicAdd(total, (unsigned long long)s);
+            int sacc = 0;
+            for (int w = 0; w < 8; ++w) sacc += red[w];
+            if (sacc) atomicAdd(total, (unsigned long long)sacc);
         }
     }
 }
 
 void launch_cull(const Geometry& g, const double* treeA, const double* treeB, double tau, const CullOut& out,
                  unsigned long long* total, double* thr_out, const int* done, cudaStream_t st) {
-    dim3 grid((g.m + 127) / 128, g.m);
-    k_cull<<<grid, 128, 0, st>>>(tree_dev(g), treeA, treeB, tau, out, total, thr_out, done);
+    const int warps = g.m * g.m;
+    k_cull<<<(warps + 7) / 8, 256, 0, st>>>(tree_dev(g), treeA, treeB, tau, out, total, thr_out, done);
     note_launch();
 }
 
@@ -319,8 +339,11 @@ void launch_unpack(const double* src, const double* leaf, const Geometry& g, dou
 __global__ void k_tk(const double* __restrict__ trace_part, int n, int m, int k, double tol_t,
                      double* __restrict__ t_hist, int* __restrict__ done, int* __restrict__ iters) {
     if (*done) return;
+    // fixed-order warp reduction (FP64 latency is long: no serial chain over m)
     double tr = 0.0;
-    for (int i = 0; i < m; ++i) tr += trace_part[i];
+    for (int i = threadIdx.x; i < m; i += 32) tr += trace_part[i];
+    for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+    if (threadIdx.x != 0) return;
     const double t = ((double)n - tr) / (double)n;
     t_hist[k] = t;
     *iters = k + 1;
@@ -329,7 +352,7 @@ __global__ void k_tk(const double* __restrict__ trace_part, int n, int m, int k,
 
 void launch_tk(const double* trace_part, const Geometry& g, int k, double tol_t, double* t_hist, int* done,
                int* iters, cudaStream_t st) {
-    k_tk<<<1, 1, 0, st>>>(trace_part, g.n, g.m, k, tol_t, t_hist, done, iters);
+    k_tk<<<1, 32, 0, st>>>(trace_part, g.n, g.m, k, tol_t, t_hist, done, iters);
     note_launch();
 }
 
