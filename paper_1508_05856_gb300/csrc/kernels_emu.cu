@@ -87,27 +87,28 @@ __device__ __forceinline__ long long fixed48(double x, int e) {
 }
 
 // Balanced signed base-256 digits of F = sum_p d_p 2^{8(5-p)}: |d_p| <= 128
-// for p >= 1 and |d_0| <= 256, so every digit times 2^{-8(p+1)} is exact in
-// BF16 and the truncation error is symmetric.
+// (d_p in [-128, 127] for p >= 1), so every digit times 2^{-8(p+1)} is exact
+// in BF16 and the truncation error is symmetric.  Adding 0x80 to each of the
+// five low bytes turns them into plain bytes d_p + 128; the top digit is what
+// remains above bit 40.
 __device__ __forceinline__ void balanced_digits(long long F, int (&d)[6]) {
-#pragma unroll
-    for (int p = 5; p >= 1; --p) {
-        const int lo = (int)((F & 0xFF) ^ 0x80) - 0x80;
-        d[p] = lo;
-        F = (F - lo) >> 8;
-    }
-    d[0] = (int)F;
+    const long long G = F + 0x8080808080ll;
+    const unsigned lo = (unsigned)G;
+    d[5] = (int)(lo & 0xFFu) - 128;
+    d[4] = (int)((lo >> 8) & 0xFFu) - 128;
+    d[3] = (int)((lo >> 16) & 0xFFu) - 128;
+    d[2] = (int)(lo >> 24) - 128;
+    const int hi = (int)(G >> 32);
+    d[1] = (hi & 0xFF) - 128;
+    d[0] = hi >> 8;
 }
 
-// BF16 bits of d * 2^{-8(p+1)} for |d| <= 256, built with integer operations.
+// BF16 bits of d * 2^{-8(p+1)} for |d| <= 256: the integer becomes an exact
+// FP32 value through the 1.5 * 2^23 magic number, the power of two is exact,
+// and a value with at most 8 significant bits keeps its upper 16 bits.
 __device__ __forceinline__ uint16_t digit_bf16_bits(int d, int p) {
-    if (d == 0) return 0;
-    const uint32_t sgn = d < 0 ? 0x8000u : 0u;
-    const uint32_t a = (uint32_t)(d < 0 ? -d : d);
-    const int len = 32 - __clz(a);                               // 1..9
-    const uint32_t ex = (uint32_t)(127 + (len - 1) - 8 * (p + 1));
-    const uint32_t mant = len <= 8 ? ((a << (8 - len)) & 0x7Fu) : ((a >> (len - 8)) & 0x7Fu);
-    return (uint16_t)(sgn | (ex << 7) | mant);
+    const float f = __int_as_float(0x4B400000 + d) - 12582912.0f;
+    return (uint16_t)(__float_as_uint(f * __int_as_float((127 - 8 * (p + 1)) << 23)) >> 16);
 }
 
 // ------------------------------------------------------------------ slicing
