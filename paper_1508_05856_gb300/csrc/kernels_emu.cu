@@ -58,7 +58,7 @@ constexpr int NSTAGE = 3;
 constexpr uint32_t EPI_BYTES = 2 * 64 * 65 * 8;          // epilogue staging of the two 64-bit halves
 constexpr uint32_t SMEM_DYN = NSTAGE * STAGE_BYTES + EPI_BYTES + 1024;
 constexpr uint32_t TMEM_COLS = 512;
-constexpr int kEpiWarps = 4;                 // one per TMEM lane quarter
+constexpr int kEpiWarps = 8;                 // two per TMEM lane quarter (32 output columns each)
 constexpr int kThreads = 32 * (2 + kEpiWarps);
 constexpr int kGroups = 5;                   // accumulator groups (64 TMEM columns each)
 constexpr int kChunk = 7;                    // tasks accumulated in TMEM between flushes (exactness bound)
@@ -276,19 +276,19 @@ __device__ __forceinline__ double neg_half(double x) {
 }
 
 // Move one chunk's accumulator groups from TMEM into the 64-bit fixed-point
-// sums of this thread's row.  Groups 0-3 hold exact integers in units of
+// sums of this thread's row (32 of the 64 output columns).  Groups 0-3 hold exact integers in units of
 // 2^{-8(diag+2)}, diag = group + half (half = 1 for the odd-slice lanes);
 // group 4 (diagonals >= 4 + half) is rounded to units of 2^{-48}.
-__device__ __forceinline__ void flush_groups(uint32_t lane_base, int half, long long (&acc)[NB]) {
+__device__ __forceinline__ void flush_groups(uint32_t lane_col_base, int half, long long (&acc)[32]) {
 #pragma unroll
     for (int g = 0; g < kGroups; ++g) {
         const int diag = g + half;
         const float up = g < 4 ? __int_as_float((127 + 8 * (diag + 2)) << 23) : __int_as_float((127 + 48) << 23);
         const int sh = g < 4 ? 32 - 8 * diag : 0;
 #pragma unroll
-        for (int h = 0; h < 4; ++h) {
+        for (int h = 0; h < 2; ++h) {
             uint32_t r[16];
-            ptx::tmem_ld16(lane_base + (uint32_t)(g * 64 + h * 16), r);
+            ptx::tmem_ld16(lane_col_base + (uint32_t)(g * 64 + h * 16), r);
             ptx::tmem_ld_wait();
 #pragma unroll
             for (int c = 0; c < 16; ++c) acc[h * 16 + c] += (long long)__float2int_rn(__uint_as_float(r[c]) * up) << sh;
@@ -319,8 +319,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
     __shared__ int tasks_sh[2][kMaxTasks];
     __shared__ int ntask_sh[2];
     __shared__ int eA_sh[2][NB], eB_sh[2][NB];
-    __shared__ float red_sh[8];
-    __shared__ double tr_sh[4];
+    __shared__ float red_sh[2 * kEpiWarps];
+    __shared__ double tr_sh[kEpiWarps];
     __shared__ int abort_sh;
 
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dyn_smem) + 1023) & ~uintptr_t(1023));
@@ -479,12 +479,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
         }
         __syncwarp();
     } else {
-        // ---------------- epilogue warps 2..5: TMEM lane quarter warp%4 (lanes 32q .. 32q+31)
+        // ---------------- epilogue warps 2..9: TMEM lane quarter warp%4 (lanes 32q .. 32q+31),
+        // columns 32*ch .. 32*ch+31 with ch = (warp-2)/4
         const int quarter = warp & 3;
         const int half = quarter >> 1;  // 0: MMA rows 0-63 (even slices), 1: rows 64-127 (odd slices)
+        const int ch = (warp - 2) >> 2;
         const int row = (quarter & 1) * 32 + lane;
-        const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
-        const int et = threadIdx.x - 64;  // 0..127
+        const uint32_t lane_col_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ch * 32);
+        const int et = threadIdx.x - 64;  // 0..255
+        const int ew = warp - 2;          // 0..7
         long long C = 0;
         int tau = 0;
         for (int idx = blockIdx.x; idx < ntiles; idx += gridDim.x, ++tau) {
@@ -497,9 +500,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
             }
             const int T = ntask_sh[slot];
             const int nchunks = (T + kChunk - 1) / kChunk;
-            long long acc[NB];
+            long long acc[32];
 #pragma unroll
-            for (int c = 0; c < NB; ++c) acc[c] = 0;
+            for (int c = 0; c < 32; ++c) acc[c] = 0;
             bool ok = true;
             for (int ck = 0; ck < nchunks; ++ck, ++C) {
                 if (!wait_or_abort(&bar_accf, (uint32_t)(C & 1), abort_flag)) {
@@ -508,30 +511,30 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
                     break;
                 }
                 ptx::tc_fence_after();
-                flush_groups(lane_base, half, acc);
+                flush_groups(lane_col_base, half, acc);
                 ptx::tc_fence_before();
                 __syncwarp();
                 if (lane == 0) ptx::mbar_arrive(&bar_acce);
             }
             if (!ok) break;
             // stage both halves' 64-bit sums, then finish the tile element-parallel:
-            // thread et owns column c and every other row
+            // thread et owns column c and every fourth row
             long long* dst = half ? sBot : sTop;
 #pragma unroll
-            for (int c = 0; c < NB; ++c) dst[c * 65 + row] = acc[c];
+            for (int c = 0; c < 32; ++c) dst[(ch * 32 + c) * 65 + row] = acc[c];
             ptx::named_sync(1, 32 * kEpiWarps);
             const int c = et & 63;
-            const int r0 = et >> 6;
+            const int r0 = et >> 6;  // 0..3
             const int gj = k * NB + c;
             const int eBc = eB_sh[slot][c];
             double* outt = a.C + (size_t)tile * NB * NB;
             DFloat nup[2] = {{0.f, 0.f}, {0.f, 0.f}};
             double tr = 0.0;
             unsigned long long cmx = 0;
-            for (int q0 = 0; q0 < 32; q0 += 8) {
+            for (int q0 = 0; q0 < 16; q0 += 8) {
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
-                    const int r = r0 + 2 * (q0 + u);
+                    const int r = r0 + 4 * (q0 + u);
                     const int gi = i * NB + r;
                     const long long t64 = sTop[c * 65 + r] + sBot[c * 65 + r];
                     const double x = fixed_to_double(t64, eA_sh[slot][r] + eBc - 48);
@@ -551,17 +554,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
                     sTop[c * 65 + r] = (long long)vb;  // in place: magnitudes for the row maxima below
                 }
             }
-            if (cmx) atomicMax(a.cmaxC + gj, cmx);
             DFloat nu = df_add(nup[0], nup[1]);
             for (int o = 16; o > 0; o >>= 1) nu = df_add(nu, df_shfl_xor(nu, o));
             if (a.mode == EPI_NS_X && i == k) {
                 for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
             }
             if (lane == 0) {
-                red_sh[2 * (warp - 2)] = nu.hi;
-                red_sh[2 * (warp - 2) + 1] = nu.lo;
-                tr_sh[warp - 2] = tr;
+                red_sh[2 * ew] = nu.hi;
+                red_sh[2 * ew + 1] = nu.lo;
+                tr_sh[ew] = tr;
             }
+            if (cmx) atomicMax(a.cmaxC + gj, cmx);
             ptx::named_sync(1, 32 * kEpiWarps);
             if (et < NB) {
                 // row maxima: thread et reduces row et over its 64 columns
@@ -569,12 +572,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
 #pragma unroll 16
                 for (int cc = 0; cc < NB; ++cc) rmx = max(rmx, (unsigned long long)sTop[cc * 65 + et]);
                 if (rmx) atomicMax(a.rmaxC + i * NB + et, rmx);
-            }
-            if (warp == 2 && lane == 0) {
+            } else if (et == NB) {
                 DFloat t = DFloat{red_sh[0], red_sh[1]};
-                for (int w = 1; w < 4; ++w) t = df_add(t, DFloat{red_sh[2 * w], red_sh[2 * w + 1]});
+                for (int w = 1; w < kEpiWarps; ++w) t = df_add(t, DFloat{red_sh[2 * w], red_sh[2 * w + 1]});
                 a.leafC[tile] = (double)t.hi + (double)t.lo;
-                if (a.mode == EPI_NS_X && i == k) a.trace_part[i] = (tr_sh[0] + tr_sh[1]) + (tr_sh[2] + tr_sh[3]);
+                if (a.mode == EPI_NS_X && i == k) {
+                    double s8 = 0.0;
+                    for (int w = 0; w < kEpiWarps; ++w) s8 += tr_sh[w];
+                    a.trace_part[i] = s8;
+                }
             }
             // every epilogue warp is done with the staging buffer and this slot's scales
             ptx::named_sync(1, 32 * kEpiWarps);
