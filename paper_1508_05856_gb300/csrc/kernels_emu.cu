@@ -16,7 +16,7 @@
 // group.  The FP32 tensor-core accumulators in TMEM therefore hold the sums
 // of up to 7 tasks exactly (7 * 2^21 < 2^24).  Every 7 tasks (and at the end
 // of an output tile) the partial sums are moved from TMEM to registers in
-// five groups (top-half diagonals p+q = 0, 1, 2, 3 exactly, and >= 4 rounded
+// six groups (top-half diagonals p+q = 0, 1, 2, 3 exactly, 4 and 5 rounded
 // to 2^{-48}) and added, as integers, into a 64-bit fixed-point accumulator
 // with quantum 2^{-48} relative to 2^{e_row + e_col}.  Dropped pairs
 // (p+q >= 6, except the (1,5), (3,3), (5,1) that come with the stacking) and
@@ -30,8 +30,13 @@
 //           2s (rows 0-63) and 2s+1 (rows 64-127), K = tile column.
 //   B role: per tile and K-half 6 slices of 64 x 32 bf16, stored transposed
 //           (row = tile column c = MMA N index, K = tile row).
-// One M=128, N=64, K=16 MMA (stack s, slice q) yields slice pairs (2s, q) in
-// TMEM lanes 0-63 and (2s+1, q) in lanes 64-127.
+// The B slices of a K-half are consecutive 64-column blocks of one N-major
+// operand, so one M=128, N=64n, K=16 MMA (stack s, slices q0 .. q0+n-1)
+// yields the slice pairs (2s, q) in TMEM lanes 0-63 and (2s+1, q) in lanes
+// 64-127 for n slices at once.  Accumulator group g = 2s + q (the top-half
+// diagonal) sits at TMEM columns 64g .. 64g+63, so the pairs of one stack land
+// in consecutive groups and four MMAs per K step cover all twelve pairs:
+// stack 0 with slices 0-3 and 4-5, stack 1 with 0-3, stack 2 with 0-1.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -60,7 +65,7 @@ constexpr uint32_t SMEM_DYN = NSTAGE * STAGE_BYTES + EPI_BYTES + 1024;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int kEpiWarps = 8;                 // two per TMEM lane quarter (32 output columns each)
 constexpr int kThreads = 32 * (2 + kEpiWarps);
-constexpr int kGroups = 5;                   // accumulator groups (64 TMEM columns each)
+constexpr int kGroups = 6;                   // accumulator groups (64 TMEM columns each)
 constexpr int kChunk = 7;                    // tasks accumulated in TMEM between flushes (exactness bound)
 constexpr int kMaxTasks = 256;
 
@@ -276,9 +281,9 @@ __device__ __forceinline__ double neg_half(double x) {
 }
 
 // Move one chunk's accumulator groups from TMEM into the 64-bit fixed-point
-// sums of this thread's row (32 of the 64 output columns).  Groups 0-3 hold exact integers in units of
-// 2^{-8(diag+2)}, diag = group + half (half = 1 for the odd-slice lanes);
-// group 4 (diagonals >= 4 + half) is rounded to units of 2^{-48}.
+// sums of this thread's row (32 of the 64 output columns).  Groups 0-3 hold
+// exact integers in units of 2^{-8(diag+2)}, diag = group + half (half = 1
+// for the odd-slice lanes); groups 4 and 5 are rounded to units of 2^{-48}.
 __device__ __forceinline__ void flush_groups(uint32_t lane_col_base, int half, long long (&acc)[32]) {
 #pragma unroll
     for (int g = 0; g < kGroups; ++g) {
@@ -420,12 +425,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
     } else if (warp == 1) {
         // ---------------- MMA issuer: tasks accumulate in TMEM in chunks of kChunk
         if (lane == 0) {
-            constexpr uint32_t idesc = ptx::idesc_bf16_f32(128, 64);
-            // stacks {0,0,0,1,0,1,0,0,1,1,2,2} and slices {0,1,2,0,3,1,4,5,2,3,0,1}: pairs ordered by
-            // accumulator group = diagonal 2*stack + slice of the top half, capped at 4
-            constexpr uint32_t kStacks = (1u << 6) | (1u << 10) | (1u << 16) | (1u << 18) | (2u << 20) | (2u << 22);
-            constexpr uint64_t kSlices = (1ull << 4) | (2ull << 8) | (3ull << 16) | (1ull << 20) | (4ull << 24) |
-                                         (5ull << 28) | (2ull << 32) | (3ull << 36) | (1ull << 44);
+            constexpr uint32_t idesc256 = ptx::idesc_bf16_f32(128, 256);
+            constexpr uint32_t idesc128 = ptx::idesc_bf16_f32(128, 128);
             long long H = 0, C = 0;
             int tau = 0;
             bool ok = true;
@@ -454,19 +455,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
                         }
                         ptx::tc_fence_after();
                         const uint32_t sA = stage_addr(sbase, s), sB = sA + A_HALF_BYTES;
-                        int prev_g = -1;
-                        for (int u = 0; u < 12; ++u) {
-                            const int sg = (int)((kStacks >> (2 * u)) & 3u), q = (int)((kSlices >> (4 * u)) & 15ull);
-                            const int g = min(2 * sg + q, 4);
-                            const uint32_t d = tmem + (uint32_t)(g * 64);
-                            for (int ks = 0; ks < 2; ++ks) {
-                                const uint64_t ad = ptx::smem_desc(sA + sg * A_HALF_STACK + ks * 256, 128, 512);
-                                const uint64_t bd = ptx::smem_desc(sB + q * B_HALF_SLICE + ks * 256, 128, 512);
-                                // the first MMA into a group in a chunk overwrites it, the rest accumulate
-                                const bool fresh = chunk_start && h == 0 && ks == 0 && g != prev_g;
-                                ptx::mma_bf16(d, ad, bd, idesc, fresh ? 0u : 1u);
-                                prev_g = g;
-                            }
+                        // the chunk's first K step overwrites groups 0-5 (stack 0 covers them all);
+                        // stacks 1 and 2 always accumulate onto it
+                        const uint32_t fresh = chunk_start && h == 0;
+                        for (int ks = 0; ks < 2; ++ks) {
+                            const uint32_t acc = fresh && ks == 0 ? 0u : 1u;
+                            const uint32_t b0 = sB + ks * 256;
+                            ptx::mma_bf16(tmem, ptx::smem_desc(sA + ks * 256, 128, 512),
+                                          ptx::smem_desc(b0, 128, 512), idesc256, acc);
+                            ptx::mma_bf16(tmem + 256u, ptx::smem_desc(sA + ks * 256, 128, 512),
+                                          ptx::smem_desc(b0 + 4 * B_HALF_SLICE, 128, 512), idesc128, acc);
+                            ptx::mma_bf16(tmem + 128u, ptx::smem_desc(sA + A_HALF_STACK + ks * 256, 128, 512),
+                                          ptx::smem_desc(b0, 128, 512), idesc256, 1u);
+                            ptx::mma_bf16(tmem + 256u, ptx::smem_desc(sA + 2 * A_HALF_STACK + ks * 256, 128, 512),
+                                          ptx::smem_desc(b0, 128, 512), idesc128, 1u);
                         }
                         ptx::mma_commit(&bar_empty[s]);
                     }
