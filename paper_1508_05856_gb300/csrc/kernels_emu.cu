@@ -116,12 +116,47 @@ __device__ __forceinline__ uint16_t digit_bf16_bits(int d, int p) {
     return (uint16_t)(__float_as_uint(f * __int_as_float((127 - 8 * (p + 1)) << 23)) >> 16);
 }
 
+// Double-word FP32 accumulation (hi + lo, about 2^-44 relative) of the
+// squares of FP64 values: FP64 arithmetic is slow on this part, so the
+// per-tile sums of squares use FP32 pairs.
+struct DFloat {
+    float hi, lo;
+};
+__device__ __forceinline__ DFloat df_add(DFloat x, DFloat y) {
+    const float s = x.hi + y.hi;
+    const float bb = s - x.hi;
+    const float e = ((x.hi - (s - bb)) + (y.hi - bb)) + (x.lo + y.lo);
+    const float h = s + e;
+    return DFloat{h, e - (h - s)};
+}
+// v * v as a double-word: v split into its leading 24 mantissa bits and the rest.
+__device__ __forceinline__ DFloat df_square(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+    const int E = (int)(b >> 52);
+    const int fe = E - 1023 + 127;
+    if (E == 0 || fe <= 0 || fe >= 255) return DFloat{0.f, 0.f};  // zero, or below FP32 range (negligible)
+    const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
+    const float hi = __uint_as_float(((unsigned)fe << 23) | (unsigned)(mant >> 29));
+    const int le = E - 1023 - 52 + 127;  // exponent of the low 29 bits' unit
+    const float lo = le > 0 ? (float)(unsigned)(mant & 0x1FFFFFFFull) * __uint_as_float((unsigned)le << 23) : 0.f;
+    const float p = hi * hi;
+    const float pe = fmaf(hi, hi, -p);
+    return DFloat{p, fmaf(2.0f * hi, lo, pe)};
+}
+__device__ __forceinline__ DFloat df_shfl_xor(DFloat x, int o) {
+    return DFloat{__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o)};
+}
+
 // ------------------------------------------------------------------ slicing
-// Leaf tiles with nu == 0 are skipped: the leaf-product kernel never reads
-// them (their products are exactly zero).
 // Grid-stride over the listed tiles (tile_list / tile_count), or over all
-// m*m tiles when tile_list is null.
+// m*m tiles when tile_list is null.  With leaf_out null, leaf tiles with
+// nu == 0 are skipped (the leaf-product kernel never reads them: their
+// products are exactly zero).  With leaf_out set, the kernel also computes
+// each listed tile's squared Frobenius norm nu (a double-word FP32 sum of
+// the squares, about 2^-44 relative) into leaf_out[tile]; unlisted tiles keep
+// the zero the cull wrote for them.
 __global__ void __launch_bounds__(256) k_slice(const double* __restrict__ X, const double* __restrict__ leaf,
+                                               double* __restrict__ leaf_out,
                                                const unsigned long long* __restrict__ rmax,
                                                const unsigned long long* __restrict__ cmax,
                                                uint8_t* __restrict__ sA, uint8_t* __restrict__ sB, int m,
@@ -130,17 +165,34 @@ __global__ void __launch_bounds__(256) k_slice(const double* __restrict__ X, con
     if (done && *done) return;
     __shared__ double xs[NB][NB + 1];
     __shared__ int eR[NB], eC[NB];
+    __shared__ DFloat nu_sh[8];
     const int ntiles = tile_list ? *tile_count : m * m;
     for (int idx = blockIdx.x; idx < ntiles; idx += gridDim.x) {
     const int tile = tile_list ? tile_list[idx] : idx;
-    if (leaf[tile] == 0.0) continue;
+    if (!leaf_out && leaf[tile] == 0.0) continue;
     __syncthreads();
     const int i = tile / m, j = tile - (tile / m) * m;
     const double* x = X + (size_t)tile * NB * NB;
-    for (int idx = threadIdx.x; idx < NB * NB; idx += 256) xs[idx >> 6][idx & 63] = x[idx];
+    DFloat nup[2] = {{0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll 4
+    for (int idx = threadIdx.x; idx < NB * NB; idx += 256) {
+        const double v = x[idx];
+        xs[idx >> 6][idx & 63] = v;
+        if (leaf_out) nup[(idx >> 8) & 1] = df_add(nup[(idx >> 8) & 1], df_square(v));
+    }
+    if (leaf_out) {
+        DFloat nu = df_add(nup[0], nup[1]);
+        for (int o = 16; o > 0; o >>= 1) nu = df_add(nu, df_shfl_xor(nu, o));
+        if ((threadIdx.x & 31) == 0) nu_sh[threadIdx.x >> 5] = nu;
+    }
     if (threadIdx.x < NB) eR[threadIdx.x] = expo_of(rmax[i * NB + threadIdx.x]);
     else if (threadIdx.x < 2 * NB) eC[threadIdx.x - NB] = expo_of(cmax[j * NB + threadIdx.x - NB]);
     __syncthreads();
+    if (leaf_out && threadIdx.x == 0) {
+        DFloat t = nu_sh[0];
+        for (int w = 1; w < 8; ++w) t = df_add(t, nu_sh[w]);
+        leaf_out[tile] = (double)t.hi + (double)t.lo;
+    }
     uint8_t* a = sA + (size_t)tile * A_TILE_BYTES;
     uint8_t* b = sB + (size_t)tile * B_TILE_BYTES;
     for (int item = threadIdx.x; item < 2 * 512; item += 256) {
@@ -205,7 +257,6 @@ struct EmuArgs {
     const unsigned long long* rmaxA;    // row maxima of the left operand
     const unsigned long long* cmaxB;    // column maxima of the right operand
     double* C;                          // FP64 output tiles
-    double* leafC;
     unsigned long long* rmaxC;          // output row / column maxima (pre-zeroed)
     unsigned long long* cmaxC;
     const int* counts;
@@ -220,64 +271,22 @@ struct EmuArgs {
 
 __device__ __forceinline__ uint32_t stage_addr(uint32_t base, int s) { return base + (uint32_t)s * STAGE_BYTES; }
 
-// Double-word FP32 accumulation (hi + lo, about 2^-44 relative) of the
-// squares of FP64 values: FP64 arithmetic has long latency on this part, so
-// the per-tile sums of squares avoid dependent FP64 chains.
-struct DFloat {
-    float hi, lo;
-};
-__device__ __forceinline__ DFloat df_add(DFloat x, DFloat y) {
-    const float s = x.hi + y.hi;
-    const float bb = s - x.hi;
-    const float e = ((x.hi - (s - bb)) + (y.hi - bb)) + (x.lo + y.lo);
-    const float h = s + e;
-    return DFloat{h, e - (h - s)};
-}
-// v * v as a double-word: v split into its leading 24 mantissa bits and the rest.
-__device__ __forceinline__ DFloat df_square(double v) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
-    const int E = (int)(b >> 52);
-    const int fe = E - 1023 + 127;
-    if (E == 0 || fe <= 0 || fe >= 255) return DFloat{0.f, 0.f};  // zero, or below FP32 range (negligible)
-    const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
-    const float hi = __uint_as_float(((unsigned)fe << 23) | (unsigned)(mant >> 29));
-    const int le = E - 1023 - 52 + 127;  // exponent of the low 29 bits' unit
-    const float lo = le > 0 ? (float)(unsigned)(mant & 0x1FFFFFFFull) * __uint_as_float((unsigned)le << 23) : 0.f;
-    const float p = hi * hi;
-    const float pe = fmaf(hi, hi, -p);
-    return DFloat{p, fmaf(2.0f * hi, lo, pe)};
-}
-__device__ __forceinline__ DFloat df_shfl_xor(DFloat x, int o) {
-    return DFloat{__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o)};
-}
-
-// int64 -> double as integer operations (round to nearest even), times 2^s.
+// int64 -> double as integer operations (round to nearest even), times 2^s;
+// results below the normal range flush to zero.
 __device__ __forceinline__ double fixed_to_double(long long tot, int s) {
     if (tot == 0) return 0.0;
-    const unsigned long long neg = tot < 0 ? 1ull : 0ull;
-    const unsigned long long u = neg ? (unsigned long long)(-tot) : (unsigned long long)tot;
+    const unsigned long long sign = (unsigned long long)tot & 0x8000000000000000ull;
+    const unsigned long long u = sign ? 0ull - (unsigned long long)tot : (unsigned long long)tot;
     const int lz = __clzll(u);
     const unsigned long long mnorm = u << lz;  // leading one at bit 63
-    unsigned long long keep = mnorm >> 11;     // 53 bits
-    const unsigned long long rem = mnorm & 0x7FFull;
-    if (rem > 0x400ull || (rem == 0x400ull && (keep & 1ull))) ++keep;
-    int ex = 63 - lz + s;
-    if (keep >> 53) {
-        keep >>= 1;
-        ++ex;
-    }
-    const unsigned long long bits = (neg << 63) | ((unsigned long long)(ex + 1023) << 52) | (keep & 0xFFFFFFFFFFFFFull);
-    return __longlong_as_double((long long)bits);
-}
-
-// -x/2 by exponent arithmetic (exact; normal and zero inputs)
-__device__ __forceinline__ double neg_half(double x) {
-    unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const unsigned long long ef = (b >> 52) & 0x7FF;
-    if (ef <= 1) return __longlong_as_double((long long)((b & 0x8000000000000000ull) ^ 0x8000000000000000ull));  // +-0 and subnormals -> -+0
-    b ^= 1ull << 63;
-    b -= 1ull << 52;
-    return __longlong_as_double((long long)b);
+    const unsigned long long keep = mnorm >> 11;  // 53 bits, leading one at bit 52
+    const unsigned rem = (unsigned)mnorm & 0x7FFu;
+    const unsigned up = (rem + 0x3FFu + ((unsigned)keep & 1u)) >> 11;  // round half to even
+    const int ef = 62 - lz + s + 1023;  // the leading one of keep adds the missing 1 to the exponent field
+    if (ef < 0) return 0.0;
+    // a rounding carry out of the 52 mantissa bits moves into the exponent field
+    const unsigned long long bits = ((unsigned long long)ef << 52) + keep + up;
+    return __longlong_as_double((long long)(bits | sign));
 }
 
 // Move one chunk's accumulator groups from TMEM into the 64-bit fixed-point
@@ -324,7 +333,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
     __shared__ int tasks_sh[2][kMaxTasks];
     __shared__ int ntask_sh[2];
     __shared__ int eA_sh[2][NB], eB_sh[2][NB];
-    __shared__ float red_sh[2 * kEpiWarps];
     __shared__ double tr_sh[kEpiWarps];
     __shared__ int abort_sh;
 
@@ -530,62 +538,48 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
             const int gj = k * NB + c;
             const int eBc = eB_sh[slot][c];
             double* outt = a.C + (size_t)tile * NB * NB;
-            DFloat nup[2] = {{0.f, 0.f}, {0.f, 0.f}};
-            double tr = 0.0;
+            const bool nsx = a.mode == EPI_NS_X;
+            // T = 1.5 I - 0.5 X: off the diagonal -x/2 is the conversion of -t64 one binade lower; the one
+            // thread per column that owns the diagonal entry computes it up front
+            const int rd = (nsx && i == k && (c & 3) == r0 && gj < a.n) ? c : -1;
+            double xd = 0.0, vd = 0.0;
+            if (rd >= 0) {
+                xd = fixed_to_double(sTop[c * 65 + c] + sBot[c * 65 + c], eA_sh[slot][c] + eBc - 48);
+                vd = 1.5 - 0.5 * xd;
+            }
+            const int sc = eBc - 48 - (nsx ? 1 : 0);
             unsigned long long cmx = 0;
+            unsigned rowm = 0;  // lane q: upper magnitude bits of row r0 + 4q over this warp's 32 columns
             for (int q0 = 0; q0 < 16; q0 += 8) {
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     const int r = r0 + 4 * (q0 + u);
-                    const int gi = i * NB + r;
                     const long long t64 = sTop[c * 65 + r] + sBot[c * 65 + r];
-                    const double x = fixed_to_double(t64, eA_sh[slot][r] + eBc - 48);
-                    double v = x;
-                    if (a.mode == EPI_NS_X) {
-                        if (gi == gj && gi < a.n) {
-                            tr += x;
-                            v = 1.5 - 0.5 * x;
-                        } else {
-                            v = neg_half(x);
-                        }
-                    }
+                    double v = fixed_to_double(nsx ? -t64 : t64, eA_sh[slot][r] + sc);
+                    v = r == rd ? vd : v;
                     outt[r * NB + c] = v;  // consecutive lanes: consecutive columns
-                    nup[u & 1] = df_add(nup[u & 1], df_square(v));
                     const unsigned long long vb = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
                     cmx = max(cmx, vb);
-                    sTop[c * 65 + r] = (long long)vb;  // in place: magnitudes for the row maxima below
+                    // the maxima only feed the slicing exponents: the upper 32 bits carry the exponent exactly
+                    const unsigned rm = __reduce_max_sync(0xffffffffu, (unsigned)(vb >> 32));
+                    if (lane == q0 + u) rowm = rm;
                 }
-            }
-            DFloat nu = df_add(nup[0], nup[1]);
-            for (int o = 16; o > 0; o >>= 1) nu = df_add(nu, df_shfl_xor(nu, o));
-            if (a.mode == EPI_NS_X && i == k) {
-                for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
-            }
-            if (lane == 0) {
-                red_sh[2 * ew] = nu.hi;
-                red_sh[2 * ew + 1] = nu.lo;
-                tr_sh[ew] = tr;
             }
             if (cmx) atomicMax(a.cmaxC + gj, cmx);
-            ptx::named_sync(1, 32 * kEpiWarps);
-            if (et < NB) {
-                // row maxima: thread et reduces row et over its 64 columns
-                unsigned long long rmx = 0;
-#pragma unroll 16
-                for (int cc = 0; cc < NB; ++cc) rmx = max(rmx, (unsigned long long)sTop[cc * 65 + et]);
-                if (rmx) atomicMax(a.rmaxC + i * NB + et, rmx);
-            } else if (et == NB) {
-                DFloat t = DFloat{red_sh[0], red_sh[1]};
-                for (int w = 1; w < kEpiWarps; ++w) t = df_add(t, DFloat{red_sh[2 * w], red_sh[2 * w + 1]});
-                a.leafC[tile] = (double)t.hi + (double)t.lo;
-                if (a.mode == EPI_NS_X && i == k) {
-                    double s8 = 0.0;
-                    for (int w = 0; w < kEpiWarps; ++w) s8 += tr_sh[w];
-                    a.trace_part[i] = s8;
-                }
+            if (lane < 16 && rowm) atomicMax(a.rmaxC + i * NB + r0 + 4 * lane, (unsigned long long)rowm << 32);
+            const bool diag_tile = nsx && i == k;
+            if (diag_tile) {
+                double tr = rd >= 0 ? xd : 0.0;
+                for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+                if (lane == 0) tr_sh[ew] = tr;
             }
-            // every epilogue warp is done with the staging buffer and this slot's scales
+            // every epilogue warp is done with the staging buffer (and tr_sh holds the trace partials)
             ptx::named_sync(1, 32 * kEpiWarps);
+            if (diag_tile && et == 0) {
+                double s8 = 0.0;
+                for (int w = 0; w < kEpiWarps; ++w) s8 += tr_sh[w];
+                a.trace_part[i] = s8;
+            }
             if (lane == 0) ptx::mbar_arrive(&bar_tfree[slot]);
         }
     }
@@ -609,11 +603,11 @@ void launch_rowcol_max(const double* X, const Geometry& g, unsigned long long* r
     note_launch();
 }
 
-void launch_slice(const double* X, const double* leaf, const unsigned long long* rmax, const unsigned long long* cmax,
-                  uint8_t* sA, uint8_t* sB, const Geometry& g, const int* tile_list, const int* tile_count,
-                  const int* done, cudaStream_t st) {
+void launch_slice(const double* X, const double* leaf, double* leaf_out, const unsigned long long* rmax,
+                  const unsigned long long* cmax, uint8_t* sA, uint8_t* sB, const Geometry& g, const int* tile_list,
+                  const int* tile_count, const int* done, cudaStream_t st) {
     const int grid = std::min(device_sm_count() * 4, g.m * g.m);
-    emu::k_slice<<<grid, 256, 0, st>>>(X, leaf, rmax, cmax, sA, sB, g.m, tile_list, tile_count, done);
+    emu::k_slice<<<grid, 256, 0, st>>>(X, leaf, leaf_out, rmax, cmax, sA, sB, g.m, tile_list, tile_count, done);
     note_launch();
 }
 
@@ -628,7 +622,6 @@ void launch_gemm_emu(const Geometry& g, const TileMat& A, const TileMat& B, cons
     a.rmaxA = A.rmax;
     a.cmaxB = B.cmax;
     a.C = C.t;
-    a.leafC = C.tree;
     a.rmaxC = C.rmax;
     a.cmaxC = C.cmax;
     a.counts = counts;

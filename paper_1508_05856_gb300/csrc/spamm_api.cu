@@ -392,9 +392,11 @@ static void product(Plan* p, const TileMat& A, const TileMat& B, TileMat& C, dou
     }
     if (e0 && e1) cudaEventRecordWithFlags(e1, st, cudaEventRecordExternal);
     p->gemm_launches++;
-    launch_tree(g, C.tree, p->flags, st);
+    // tensor-core path: the slicing pass also computes the output's leaf norms, before the tree sums them
     if (p->emu)
-        launch_slice(C.t, C.tree, C.rmax, C.cmax, C.sliceA, C.sliceB, g, p->tile_list, p->flags + 3, p->flags, st);
+        launch_slice(C.t, nullptr, C.tree, C.rmax, C.cmax, C.sliceA, C.sliceB, g, p->tile_list, p->flags + 3,
+                     p->flags, st);
+    launch_tree(g, C.tree, p->flags, st);
 }
 
 // Row/column maxima and slices of a freshly packed matrix (tensor-core path).
@@ -402,7 +404,7 @@ static void prepare_emu(Plan* p, const TileMat& M, cudaStream_t st) {
     const Geometry& g = p->g;
     cudaMemsetAsync(M.rmax, 0, 2 * (size_t)g.m * g.nb * sizeof(unsigned long long), st);
     launch_rowcol_max(M.t, g, M.rmax, M.cmax, st);
-    launch_slice(M.t, M.tree, M.rmax, M.cmax, M.sliceA, M.sliceB, g, nullptr, nullptr, nullptr, st);
+    launch_slice(M.t, M.tree, nullptr, M.rmax, M.cmax, M.sliceA, M.sliceB, g, nullptr, nullptr, nullptr, st);
 }
 
 static int multiply_impl(const double* A, const double* B, double* C, int n, double tau, const spamm_opts& o,

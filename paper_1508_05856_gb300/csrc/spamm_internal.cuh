@@ -138,14 +138,15 @@ size_t emu_slice_bytes_per_tile();  // bytes of one tile's slices in one operand
 void launch_rowcol_max(const double* X, const Geometry& g, unsigned long long* rmax, unsigned long long* cmax,
                        cudaStream_t st);
 // BF16 slices of both operand roles from FP64 tiles and row/column maxima,
-// for the listed tiles (or all tiles when tile_list is null); tiles of zero
-// norm are skipped.
-void launch_slice(const double* X, const double* leaf, const unsigned long long* rmax, const unsigned long long* cmax,
-                  uint8_t* sA, uint8_t* sB, const Geometry& g, const int* tile_list, const int* tile_count,
-                  const int* done, cudaStream_t st);
-// Leaf products on the tensor cores; writes C's FP64 tiles, leaf norms and
-// row/column maxima (pre-zeroed), trace partials for EPI_NS_X; *err set on a
-// timed-out internal wait.
+// for the listed tiles (or all tiles when tile_list is null).  With leaf_out
+// null, tiles whose leaf[] norm is zero are skipped; with leaf_out set, every
+// listed tile is sliced and its squared Frobenius norm written to leaf_out.
+void launch_slice(const double* X, const double* leaf, double* leaf_out, const unsigned long long* rmax,
+                  const unsigned long long* cmax, uint8_t* sA, uint8_t* sB, const Geometry& g, const int* tile_list,
+                  const int* tile_count, const int* done, cudaStream_t st);
+// Leaf products on the tensor cores; writes C's FP64 tiles and row/column
+// maxima (pre-zeroed), trace partials for EPI_NS_X; *err set on a timed-out
+// internal wait.  C's leaf norms come from launch_slice with leaf_out set.
 void launch_gemm_emu(const Geometry& g, const TileMat& A, const TileMat& B, const TileMat& C, const int* counts,
                      const int* jlist, const int* tile_list, const int* tile_count, EpiMode mode, double* trace_part,
                      const int* done, int* err, cudaStream_t st);
