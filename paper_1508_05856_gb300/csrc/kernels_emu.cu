@@ -9,11 +9,12 @@
 //                                            error <= 2^{-49} 2^e,
 //
 // where 2^(e-1) bounds the largest magnitude of x's row (operand A role) or
-// of x's column (operand B role) over the whole matrix.  Each digit times its
-// power of two is exact in BF16.  A product of slices p and q is a sum over
-// 64 terms of integers of magnitude <= 2^14 in units of 2^{-8(p+q+2)}: at most
-// 2^20 per pair and task, 2^21 for the two pairs that share an accumulator
-// group.  The FP32 tensor-core accumulators in TMEM therefore hold the sums
+// of x's column (operand B role) over the whole matrix.  A slice holds the
+// digits d_p themselves, integers that BF16 represents exactly; the power of
+// two of a slice pair is applied when its partial sums leave TMEM.  A product
+// of slices p and q is a sum over 64 terms of integers of magnitude <= 2^14
+// (weight 2^{-8(p+q+2)}): at most 2^20 per pair and task, 2^21 for the two
+// pairs that share an accumulator group.  The FP32 tensor-core accumulators in TMEM therefore hold the sums
 // of up to 7 tasks exactly (7 * 2^21 < 2^24).  Every 7 tasks (and at the end
 // of an output tile) the partial sums are moved from TMEM to registers in
 // six groups (top-half diagonals p+q = 0, 1, 2, 3 exactly, 4 and 5 rounded
@@ -92,28 +93,29 @@ __device__ __forceinline__ long long fixed48(double x, int e) {
 }
 
 // Balanced signed base-256 digits of F = sum_p d_p 2^{8(5-p)}: |d_p| <= 128
-// (d_p in [-128, 127] for p >= 1), so every digit times 2^{-8(p+1)} is exact
-// in BF16 and the truncation error is symmetric.  Adding 0x80 to each of the
-// five low bytes turns them into plain bytes d_p + 128; the top digit is what
-// remains above bit 40.
-__device__ __forceinline__ void balanced_digits(long long F, int (&d)[6]) {
+// (d_p in [-128, 127] for p >= 1), so the truncation error is symmetric.
+// Adding 0x80 to each of the five low bytes of F turns them into plain bytes
+// d_p + 128 (p = 1..5, byte 5-p); the top digit d_0 is what remains above bit
+// 40.  digit_value returns d_p as an exact FP32 value: the byte is placed in
+// the low byte of the magic number 1.5 * 2^23, whose unit is 1.
+struct Digits {
+    unsigned lo;  // bytes d_5+128, d_4+128, d_3+128, d_2+128
+    int hi;       // byte 0: d_1 + 128; bits 8 and up: d_0 (signed)
+};
+__device__ __forceinline__ Digits balanced_digits(long long F) {
     const long long G = F + 0x8080808080ll;
-    const unsigned lo = (unsigned)G;
-    d[5] = (int)(lo & 0xFFu) - 128;
-    d[4] = (int)((lo >> 8) & 0xFFu) - 128;
-    d[3] = (int)((lo >> 16) & 0xFFu) - 128;
-    d[2] = (int)(lo >> 24) - 128;
-    const int hi = (int)(G >> 32);
-    d[1] = (hi & 0xFF) - 128;
-    d[0] = hi >> 8;
+    return Digits{(unsigned)G, (int)(G >> 32)};
 }
-
-// BF16 bits of d * 2^{-8(p+1)} for |d| <= 256: the integer becomes an exact
-// FP32 value through the 1.5 * 2^23 magic number, the power of two is exact,
-// and a value with at most 8 significant bits keeps its upper 16 bits.
-__device__ __forceinline__ uint16_t digit_bf16_bits(int d, int p) {
-    const float f = __int_as_float(0x4B400000 + d) - 12582912.0f;
-    return (uint16_t)(__float_as_uint(f * __int_as_float((127 - 8 * (p + 1)) << 23)) >> 16);
+template <int P>
+__device__ __forceinline__ float digit_value(const Digits& d) {
+    if (P == 0) return __int_as_float(0x4B400000 + (d.hi >> 8)) - 12582912.0f;
+    if (P == 1) return __int_as_float((int)__byte_perm((unsigned)d.hi, 0x4B400000u, 0x7650)) - 12583040.0f;
+    return __int_as_float((int)__byte_perm(d.lo, 0x4B400000u, 0x7650 | (5 - P))) - 12583040.0f;
+}
+// two exact small integers as a packed BF16 pair (first value in the low half)
+__device__ __forceinline__ uint32_t bf16x2_bits(float a, float b) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
 }
 
 // Double-word FP32 accumulation (hi + lo, about 2^-44 relative) of the
@@ -155,7 +157,7 @@ __device__ __forceinline__ DFloat df_shfl_xor(DFloat x, int o) {
 // each listed tile's squared Frobenius norm nu (a double-word FP32 sum of
 // the squares, about 2^-44 relative) into leaf_out[tile]; unlisted tiles keep
 // the zero the cull wrote for them.
-__global__ void __launch_bounds__(256) k_slice(const double* __restrict__ X, const double* __restrict__ leaf,
+__global__ void __launch_bounds__(256, 6) k_slice(const double* __restrict__ X, const double* __restrict__ leaf,
                                                double* __restrict__ leaf_out,
                                                const unsigned long long* __restrict__ rmax,
                                                const unsigned long long* __restrict__ cmax,
@@ -174,11 +176,18 @@ __global__ void __launch_bounds__(256) k_slice(const double* __restrict__ X, con
     const int i = tile / m, j = tile - (tile / m) * m;
     const double* x = X + (size_t)tile * NB * NB;
     DFloat nup[2] = {{0.f, 0.f}, {0.f, 0.f}};
-#pragma unroll 4
-    for (int idx = threadIdx.x; idx < NB * NB; idx += 256) {
-        const double v = x[idx];
-        xs[idx >> 6][idx & 63] = v;
-        if (leaf_out) nup[(idx >> 8) & 1] = df_add(nup[(idx >> 8) & 1], df_square(v));
+    // two batches of eight independent loads per thread
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        double v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = x[threadIdx.x + 256 * (8 * h + q)];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int idx = threadIdx.x + 256 * (8 * h + q);
+            xs[idx >> 6][idx & 63] = v[q];
+            if (leaf_out) nup[q & 1] = df_add(nup[q & 1], df_square(v[q]));
+        }
     }
     if (leaf_out) {
         DFloat nu = df_add(nup[0], nup[1]);
@@ -201,26 +210,42 @@ __global__ void __launch_bounds__(256) k_slice(const double* __restrict__ X, con
         // 8 consecutive items fill one 128-byte core matrix, 32 consecutive items 512 contiguous bytes
         const int kgi = (it >> 3) & 3, kh = (it >> 5) & 1;
         const int r = (it >> 6) * 8 + (it & 7), g = kh * 4 + kgi;  // A: row r, k-group g; B: column r, k-group g
-        int D[8][6];
+        Digits D[8];
+#pragma unroll
         for (int q = 0; q < 8; ++q) {
             const double v = arole ? xs[r][8 * g + q] : xs[8 * g + q][r];
-            balanced_digits(fixed48(v, arole ? eR[r] : eC[r]), D[q]);
+            D[q] = balanced_digits(fixed48(v, arole ? eR[r] : eC[r]));
         }
-        for (int p = 0; p < NSLICE; ++p) {
-            __align__(16) uint16_t w[8];
-            for (int q = 0; q < 8; ++q) w[q] = digit_bf16_bits(D[q][p], p);
-            uint32_t off;
-            if (arole) {
-                const int row = (p & 1) * 64 + r;
-                off = (uint32_t)kh * A_HALF_BYTES + (uint32_t)(p >> 1) * A_HALF_STACK +
-                      (uint32_t)(((row >> 3) * 4 + kgi) * 128 + (row & 7) * 16);
-                *reinterpret_cast<uint4*>(a + off) = *reinterpret_cast<const uint4*>(w);
-            } else {
-                off = (uint32_t)kh * B_HALF_BYTES + (uint32_t)p * B_HALF_SLICE +
-                      (uint32_t)(((r >> 3) * 4 + kgi) * 128 + (r & 7) * 16);
-                *reinterpret_cast<uint4*>(b + off) = *reinterpret_cast<const uint4*>(w);
-            }
+        uint8_t* base;
+        uint32_t pstride;
+        if (arole) {
+            // slice p sits in stack p/2, rows 64 (p%2) + r
+            base = a + (uint32_t)kh * A_HALF_BYTES + (uint32_t)(((r >> 3) * 4 + kgi) * 128 + (r & 7) * 16);
+            pstride = A_HALF_STACK;
+        } else {
+            base = b + (uint32_t)kh * B_HALF_BYTES + (uint32_t)(((r >> 3) * 4 + kgi) * 128 + (r & 7) * 16);
+            pstride = B_HALF_SLICE;
         }
+        // odd slices of the A role: rows 64..127 of the stack, 8 row groups (4 KB) further on
+        const uint32_t aodd = arole ? 8u * 4u * 128u : 0u;
+#define SPAMM_STORE_SLICE(P)                                                                                 \
+        {                                                                                                    \
+            uint4 w;                                                                                         \
+            w.x = bf16x2_bits(digit_value<P>(D[0]), digit_value<P>(D[1]));                                   \
+            w.y = bf16x2_bits(digit_value<P>(D[2]), digit_value<P>(D[3]));                                   \
+            w.z = bf16x2_bits(digit_value<P>(D[4]), digit_value<P>(D[5]));                                   \
+            w.w = bf16x2_bits(digit_value<P>(D[6]), digit_value<P>(D[7]));                                   \
+            const uint32_t off = arole ? (uint32_t)(P >> 1) * pstride + (uint32_t)(P & 1) * aodd             \
+                                       : (uint32_t)P * pstride;                                              \
+            *reinterpret_cast<uint4*>(base + off) = w;                                                       \
+        }
+        SPAMM_STORE_SLICE(0)
+        SPAMM_STORE_SLICE(1)
+        SPAMM_STORE_SLICE(2)
+        SPAMM_STORE_SLICE(3)
+        SPAMM_STORE_SLICE(4)
+        SPAMM_STORE_SLICE(5)
+#undef SPAMM_STORE_SLICE
     }
     }
 }
@@ -290,15 +315,16 @@ __device__ __forceinline__ double fixed_to_double(long long tot, int s) {
 }
 
 // Move one chunk's accumulator groups from TMEM into the 64-bit fixed-point
-// sums of this thread's row (32 of the 64 output columns).  Groups 0-3 hold
-// exact integers in units of 2^{-8(diag+2)}, diag = group + half (half = 1
-// for the odd-slice lanes); groups 4 and 5 are rounded to units of 2^{-48}.
+// sums (unit 2^{-48}) of this thread's row (32 of the 64 output columns).
+// Group g holds integer sums of digit products of weight 2^{-8(diag+2)},
+// diag = g + half (half = 1 for the odd-slice lanes): exact for diag <= 4
+// (shifted left by 32 - 8 diag), rounded to the unit for diag 5 and 6.
 __device__ __forceinline__ void flush_groups(uint32_t lane_col_base, int half, long long (&acc)[32]) {
 #pragma unroll
     for (int g = 0; g < kGroups; ++g) {
         const int diag = g + half;
-        const float up = g < 4 ? __int_as_float((127 + 8 * (diag + 2)) << 23) : __int_as_float((127 + 48) << 23);
-        const int sh = g < 4 ? 32 - 8 * diag : 0;
+        const float up = diag <= 4 ? 1.0f : __int_as_float((127 + 32 - 8 * diag) << 23);
+        const int sh = diag <= 4 ? 32 - 8 * diag : 0;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             uint32_t r[16];
@@ -606,7 +632,8 @@ void launch_rowcol_max(const double* X, const Geometry& g, unsigned long long* r
 void launch_slice(const double* X, const double* leaf, double* leaf_out, const unsigned long long* rmax,
                   const unsigned long long* cmax, uint8_t* sA, uint8_t* sB, const Geometry& g, const int* tile_list,
                   const int* tile_count, const int* done, cudaStream_t st) {
-    const int grid = std::min(device_sm_count() * 4, g.m * g.m);
+    // six 34 KB blocks fit on an SM: one resident wave covers up to 6 tiles per SM
+    const int grid = std::min(device_sm_count() * 6, g.m * g.m);
     emu::k_slice<<<grid, 256, 0, st>>>(X, leaf, leaf_out, rmax, cmax, sA, sB, g.m, tile_list, tile_count, done);
     note_launch();
 }
