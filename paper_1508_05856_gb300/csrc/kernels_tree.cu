@@ -216,15 +216,45 @@ void launch_identity(const Geometry& g, TileMat Z, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------- quadtree levels
-__global__ void __launch_bounds__(1024) k_tree(TreeDev td, double* __restrict__ tree, const int* __restrict__ done) {
+// Parent = sum of its existing children, summed pairwise (rows first).
+__device__ __forceinline__ double child_sum(const double* ch, int dc, int I, int J) {
+    const int ci = 2 * I, cj = 2 * J;
+    const bool r1 = ci + 1 < dc, c1 = cj + 1 < dc;
+    const double s0 = ch[ci * dc + cj] + (c1 ? ch[ci * dc + cj + 1] : 0.0);
+    const double s1 = r1 ? ch[(ci + 1) * dc + cj] + (c1 ? ch[(ci + 1) * dc + cj + 1] : 0.0) : 0.0;
+    return s0 + s1;
+}
+
+// t_k = (n - tr X)/n from the diagonal-tile trace partials (fixed-order warp
+// reduction), t_hist[k], iteration count and the tolerance stop.
+__device__ __forceinline__ void trace_error(const double* __restrict__ trace_part, int n, int m, int k, double tol_t,
+                                            double* __restrict__ t_hist, int* __restrict__ done,
+                                            int* __restrict__ iters) {
+    double tr = 0.0;
+    for (int i = threadIdx.x; i < m; i += 32) tr += trace_part[i];
+    for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+    if (threadIdx.x != 0) return;
+    const double t = ((double)n - tr) / (double)n;
+    t_hist[k] = t;
+    *iters = k + 1;
+    if (tol_t > 0.0 && fabs(t) <= tol_t) *done = 1;
+}
+
+// Levels whose children exceed 64 x 64 go through global memory; from there
+// on the children are held in shared memory (each level is still written
+// out), so the top levels cost shared-memory latency instead of global.
+__global__ void __launch_bounds__(1024) k_tree(TreeDev td, double* __restrict__ tree, const int* __restrict__ done,
+                                               TreeExtra ex) {
     if (done && *done) return;
-    for (int l = td.L - 1; l >= 0; --l) {
+    __shared__ double bufA[64 * 64];
+    __shared__ double bufB[32 * 32];
+    int l = td.L - 1;
+    for (; l >= 0 && td.dim[l + 1] > 64; --l) {
         const int d = td.dim[l], dc = td.dim[l + 1];
         const double* ch = tree + td.off[l + 1];
         double* pa = tree + td.off[l];
         for (int idx = threadIdx.x; idx < d * d; idx += blockDim.x) {
             const int I = idx / d, J = idx - I * d;
-            // existing children, summed pairwise (rows first): depth 2 instead of a chain of 4
             const int ci = 2 * I, cj = 2 * J;
             const bool r1 = ci + 1 < dc, c1 = cj + 1 < dc;
             const double s0 = ch[(size_t)ci * dc + cj] + (c1 ? ch[(size_t)ci * dc + cj + 1] : 0.0);
@@ -233,10 +263,35 @@ __global__ void __launch_bounds__(1024) k_tree(TreeDev td, double* __restrict__ 
         }
         __syncthreads();
     }
+    if (l >= 0) {
+        const int dc0 = td.dim[l + 1];
+        const double* ch0 = tree + td.off[l + 1];
+        for (int idx = threadIdx.x; idx < dc0 * dc0; idx += blockDim.x) bufA[idx] = ch0[idx];
+        __syncthreads();
+        double* cur = bufA;
+        double* nxt = bufB;
+        for (; l >= 0; --l) {
+            const int d = td.dim[l], dc = td.dim[l + 1];
+            double* pa = tree + td.off[l];
+            for (int idx = threadIdx.x; idx < d * d; idx += blockDim.x) {
+                const int I = idx / d, J = idx - I * d;
+                const double s = child_sum(cur, dc, I, J);
+                nxt[idx] = s;
+                pa[idx] = s;
+            }
+            __syncthreads();
+            double* t = cur;
+            cur = nxt;
+            nxt = t;
+        }
+    }
+    if (ex.zero_int && threadIdx.x == 0) *ex.zero_int = 0;
+    if (ex.trace_part && threadIdx.x < 32)
+        trace_error(ex.trace_part, ex.n, td.m, ex.k, ex.tol_t, ex.t_hist, ex.done, ex.iters);
 }
 
-void launch_tree(const Geometry& g, double* tree, const int* done, cudaStream_t st) {
-    k_tree<<<1, 1024, 0, st>>>(tree_dev(g), tree, done);
+void launch_tree(const Geometry& g, double* tree, const int* done, cudaStream_t st, const TreeExtra& ex) {
+    k_tree<<<1, 1024, 0, st>>>(tree_dev(g), tree, done, ex);
     note_launch();
 }
 
@@ -254,11 +309,15 @@ __global__ void __launch_bounds__(256) k_cull(TreeDev td, const double* __restri
                                               const int* __restrict__ done) {
     if (done && *done) return;
     __shared__ int red[8];
+    __shared__ int lst[8];
+    for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < co.zero_n; q += (long)gridDim.x * blockDim.x)
+        co.zero_u64[q] = 0ull;
     const int m = td.m;
     const int wid = blockIdx.x * 8 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     const double thr = ((tau * tau) * treeA[td.off[0]]) * treeB[td.off[0]];
     int cnt = 0;
+    bool listed = false;
     if (wid < m * m) {
         const int i = wid / m, k = wid - (wid / m) * m;
         const int dc = td.dim[td.coarse];
@@ -282,8 +341,22 @@ __global__ void __launch_bounds__(256) k_cull(TreeDev td, const double* __restri
         if (lane == 0) {
             co.counts[wid] = cnt;
             if (co.tile_list) {
-                if (cnt > 0 || (co.force_diag && i == k)) co.tile_list[atomicAdd(co.tile_count, 1)] = wid;
-                else if (co.leafC) co.leafC[wid] = 0.0;
+                listed = cnt > 0 || (co.force_diag && i == k);
+                if (!listed && co.leafC) co.leafC[wid] = 0.0;
+            }
+        }
+    }
+    if (co.tile_list) {
+        // one atomic per block appends the block's listed output tiles
+        if (lane == 0) lst[threadIdx.x >> 5] = listed ? wid : -1;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int c = 0;
+            for (int w = 0; w < 8; ++w) c += lst[w] >= 0;
+            if (c) {
+                int q = atomicAdd(co.tile_count, c);
+                for (int w = 0; w < 8; ++w)
+                    if (lst[w] >= 0) co.tile_list[q++] = lst[w];
             }
         }
     }
@@ -332,27 +405,6 @@ __global__ void __launch_bounds__(256) k_unpack(const double* __restrict__ src, 
 void launch_unpack(const double* src, const double* leaf, const Geometry& g, double* dst, const double* mul,
                    const double* div, cudaStream_t st) {
     k_unpack<<<g.m * g.m, 256, 0, st>>>(src, leaf, g.n, g.m, g.nb, dst, mul, div);
-    note_launch();
-}
-
-// ---------------------------------------------------------------- t_k
-__global__ void k_tk(const double* __restrict__ trace_part, int n, int m, int k, double tol_t,
-                     double* __restrict__ t_hist, int* __restrict__ done, int* __restrict__ iters) {
-    if (*done) return;
-    // fixed-order warp reduction (FP64 latency is long: no serial chain over m)
-    double tr = 0.0;
-    for (int i = threadIdx.x; i < m; i += 32) tr += trace_part[i];
-    for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
-    if (threadIdx.x != 0) return;
-    const double t = ((double)n - tr) / (double)n;
-    t_hist[k] = t;
-    *iters = k + 1;
-    if (tol_t > 0.0 && fabs(t) <= tol_t) *done = 1;
-}
-
-void launch_tk(const double* trace_part, const Geometry& g, int k, double tol_t, double* t_hist, int* done,
-               int* iters, cudaStream_t st) {
-    k_tk<<<1, 32, 0, st>>>(trace_part, g.n, g.m, k, tol_t, t_hist, done, iters);
     note_launch();
 }
 

@@ -369,13 +369,18 @@ static double profiled_ms(Plan* p) {
 }
 
 // One SpAMM product of two packed operands into dst (tree leaves + levels).
+// The output-tile counter (flags[3]) is zero on entry (the call's flag reset,
+// then the tree pass of the previous product); the tree pass may also carry
+// the iteration's trace error (tk).
 static void product(Plan* p, const TileMat& A, const TileMat& B, TileMat& C, double tau, EpiMode mode,
-                    unsigned long long* ctr, cudaStream_t st) {
+                    unsigned long long* ctr, cudaStream_t st, const TreeExtra* tk = nullptr) {
     const Geometry& g = p->g;
-    cudaMemsetAsync(p->flags + 3, 0, sizeof(int), st);
-    const CullOut co{p->counts, p->jlist, p->tile_list, p->flags + 3, C.tree, mode == EPI_NS_X ? 1 : 0};
+    CullOut co{p->counts, p->jlist, p->tile_list, p->flags + 3, C.tree, mode == EPI_NS_X ? 1 : 0};
+    if (p->emu) {
+        co.zero_u64 = C.rmax;  // rmax and cmax, contiguous
+        co.zero_n = 2 * (long)g.m * g.nb;
+    }
     launch_cull(g, A.tree, B.tree, tau, co, ctr, nullptr, p->flags, st);
-    if (p->emu) cudaMemsetAsync(C.rmax, 0, 2 * (size_t)g.m * g.nb * sizeof(unsigned long long), st);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (p->profile) {
         e0 = next_event(p);
@@ -396,7 +401,9 @@ static void product(Plan* p, const TileMat& A, const TileMat& B, TileMat& C, dou
     if (p->emu)
         launch_slice(C.t, nullptr, C.tree, C.rmax, C.cmax, C.sliceA, C.sliceB, g, p->tile_list, p->flags + 3,
                      p->flags, st);
-    launch_tree(g, C.tree, p->flags, st);
+    TreeExtra ex = tk ? *tk : TreeExtra();
+    ex.zero_int = p->flags + 3;
+    launch_tree(g, C.tree, p->flags, st, ex);
 }
 
 // Row/column maxima and slices of a freshly packed matrix (tensor-core path).
@@ -520,20 +527,28 @@ static int enqueue_solve(Plan* p, const double* dS, double* dY, double* dZ, int 
     int it_host = 0;
     for (int k = 0; k < maxit; ++k) {
         unsigned long long* ctr = p->task_ctr + 3 * (size_t)k;
+        // t_k rides on the X product's tree pass
+        TreeExtra tk;
+        tk.trace_part = p->trace_part;
+        tk.n = g.n;
+        tk.k = k;
+        tk.tol_t = o.tol_t;
+        tk.t_hist = p->t_hist;
+        tk.done = p->flags;
+        tk.iters = p->flags + 1;
         if (o.order == SPAMM_ORDER_PAPER) {
             product(p, Tb, Yb, Y2, tau_s, EPI_PLAIN, ctr + 0, st);  // Y <- T (x)_{tau_s} Y
             product(p, Zb, Tb, Z2, tau, EPI_PLAIN, ctr + 1, st);    // Z <- Z (x)_tau T
             std::swap(Yb, Y2);
             std::swap(Zb, Z2);
-            product(p, Yb, Zb, Tb, tau, EPI_NS_X, ctr + 2, st);     // X <- Y (x)_tau Z, T = h[X]
+            product(p, Yb, Zb, Tb, tau, EPI_NS_X, ctr + 2, st, &tk);  // X <- Y (x)_tau Z, T = h[X]
         } else {
             product(p, Yb, Tb, Y2, tau_s, EPI_PLAIN, ctr + 0, st);  // Y <- Y (x)_{tau_s} T
             product(p, Tb, Zb, Z2, tau, EPI_PLAIN, ctr + 1, st);    // Z <- T (x)_tau Z
             std::swap(Yb, Y2);
             std::swap(Zb, Z2);
-            product(p, Zb, Yb, Tb, tau, EPI_NS_X, ctr + 2, st);     // X <- Z (x)_tau Y, T = h[X]
+            product(p, Zb, Yb, Tb, tau, EPI_NS_X, ctr + 2, st, &tk);  // X <- Z (x)_tau Y, T = h[X]
         }
-        launch_tk(p->trace_part, g, k, o.tol_t, p->t_hist, p->flags, p->flags + 1, st);
         CK(cudaGetLastError());
         it_host = k + 1;
         if (o.tol_t > 0.0) {

@@ -76,14 +76,30 @@ void launch_pack(const double* src, int n, const Geometry& g, const double* mu, 
 void launch_hmap(const double* X, const Geometry& g, TileMat T, cudaStream_t st);
 // Z = I_n in tile-major form, with leaf norms.
 void launch_identity(const Geometry& g, TileMat Z, cudaStream_t st);
-// Upper quadtree levels from the leaf level.
-void launch_tree(const Geometry& g, double* tree, const int* done, cudaStream_t st);
+// Work fused into the quadtree pass, all optional.  After the levels:
+// *zero_int = 0 (the output-tile counter, ready for the next cull); with
+// trace_part set, the iteration's trace error t_k = (n - sum trace_part)/n
+// into t_hist[k], *iters = k + 1, and *done = 1 once |t_k| <= tol_t > 0.
+struct TreeExtra {
+    int* zero_int = nullptr;
+    const double* trace_part = nullptr;
+    int n = 0, k = 0;
+    double tol_t = 0.0;
+    double* t_hist = nullptr;
+    int* done = nullptr;
+    int* iters = nullptr;
+};
+// Upper quadtree levels from the leaf level (skipped when *done is set).
+void launch_tree(const Geometry& g, double* tree, const int* done, cudaStream_t st,
+                 const TreeExtra& ex = TreeExtra());
 // Task lists of A (x) B: counts[i*m+k], jlist[(i*m+k)*m + ...] ascending j.
 // thr = ((tau*tau) * rootA) * rootB.  total (may be null) gets += task count.
 // Output tiles with a task (or, with force_diag, on the diagonal) are
 // appended to tile_list (*tile_count must be zero on entry, order
 // unspecified); for every other output tile leafC[tile] is set to 0: that
 // tile is exactly zero and its data are not written (readers check nu == 0).
+// zero_u64[0 .. zero_n) is cleared on the way (the output's row/column
+// maxima, which the leaf products accumulate with atomics).
 struct CullOut {
     int* counts;
     int* jlist;
@@ -91,6 +107,8 @@ struct CullOut {
     int* tile_count;
     double* leafC;
     int force_diag;
+    unsigned long long* zero_u64 = nullptr;
+    long zero_n = 0;
 };
 void launch_cull(const Geometry& g, const double* treeA, const double* treeB, double tau, const CullOut& out,
                  unsigned long long* total, double* thr_out, const int* done, cudaStream_t st);
@@ -98,9 +116,6 @@ void launch_cull(const Geometry& g, const double* treeA, const double* treeB, do
 // null or both null).  Tiles whose leaf norm is 0 are written as zeros.
 void launch_unpack(const double* src, const double* leaf, const Geometry& g, double* dst, const double* mul,
                    const double* div, cudaStream_t st);
-// t_k = (n - sum trace_part)/n into hist[k]; done/iters bookkeeping.
-void launch_tk(const double* trace_part, const Geometry& g, int k, double tol_t, double* t_hist, int* done,
-               int* iters, cudaStream_t st);
 // sqrt of device scalar: out = sqrt(*c)
 void launch_sqrt_scalar(const double* c, double* out, cudaStream_t st);
 // sum over logical entries of (R - I)^2 -> *out (deterministic)
