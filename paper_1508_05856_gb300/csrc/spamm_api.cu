@@ -110,13 +110,20 @@ struct Plan {
     int* counts = nullptr;
     int* jlist = nullptr;
     int* tile_list = nullptr;                // [m*m] compacted output tiles of one product
+    // second product scratch and stream: the iteration's two independent
+    // products (Y and Z updates) run on two branches
+    int* counts2 = nullptr;
+    int* jlist2 = nullptr;
+    int* tile_list2 = nullptr;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     unsigned long long* task_ctr = nullptr;  // [3 * maxit_cap + 4]
     double* t_hist = nullptr;                // [maxit_cap]
     int maxit_cap = 0;
     double* trace_part = nullptr;  // [m]
     double* scal = nullptr;        // c0, mu, c, sqrt c, thr, resid, spare...
     double* rowsum = nullptr;      // [n]
-    int* flags = nullptr;          // done, iters, device error, output-tile count
+    int* flags = nullptr;          // done, iters, device error, output-tile counts of the two branches
     double* partial = nullptr;     // [m*m]
     double* stage[3] = {nullptr, nullptr, nullptr};  // n*n row-major staging
     // profiling: event pairs around each leaf-product kernel of a call
@@ -150,6 +157,12 @@ static void free_plan(Plan* p) {
     cudaFree(p->counts);
     cudaFree(p->jlist);
     cudaFree(p->tile_list);
+    cudaFree(p->counts2);
+    cudaFree(p->jlist2);
+    cudaFree(p->tile_list2);
+    if (p->side) cudaStreamDestroy(p->side);
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    if (p->ev_join) cudaEventDestroy(p->ev_join);
     cudaFree(p->task_ctr);
     cudaFree(p->t_hist);
     cudaFree(p->trace_part);
@@ -177,10 +190,16 @@ static int alloc_plan(Plan* p, int n, int nb) {
     CKA(cudaMalloc(&p->counts, (size_t)g.m * g.m * sizeof(int)));
     CKA(cudaMalloc(&p->jlist, (size_t)g.m * g.m * g.m * sizeof(int)));
     CKA(cudaMalloc(&p->tile_list, (size_t)g.m * g.m * sizeof(int)));
+    CKA(cudaMalloc(&p->counts2, (size_t)g.m * g.m * sizeof(int)));
+    CKA(cudaMalloc(&p->jlist2, (size_t)g.m * g.m * g.m * sizeof(int)));
+    CKA(cudaMalloc(&p->tile_list2, (size_t)g.m * g.m * sizeof(int)));
+    CKA(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
+    CKA(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
+    CKA(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
     CKA(cudaMalloc(&p->trace_part, (size_t)g.m * sizeof(double)));
     CKA(cudaMalloc(&p->scal, 16 * sizeof(double)));
     CKA(cudaMalloc(&p->rowsum, (size_t)n * sizeof(double)));
-    CKA(cudaMalloc(&p->flags, 4 * sizeof(int)));
+    CKA(cudaMalloc(&p->flags, 8 * sizeof(int)));
     CKA(cudaMalloc(&p->partial, (size_t)g.m * g.m * sizeof(double)));
     return SPAMM_OK;
 }
@@ -223,7 +242,7 @@ static int ensure_stage(Plan* p, int which) {
 size_t plan_footprint(int n, int nb, int precision, bool host_io) {
     const Geometry g = make_geometry(n, nb);
     size_t b = 6 * (g.elems() + (size_t)g.tree_size) * sizeof(double);
-    b += ((size_t)g.m * g.m * (g.m + 2)) * sizeof(int) + (size_t)g.m * sizeof(double) + (size_t)n * sizeof(double) +
+    b += 2 * ((size_t)g.m * g.m * (g.m + 2)) * sizeof(int) + (size_t)g.m * sizeof(double) + (size_t)n * sizeof(double) +
          (size_t)g.m * g.m * sizeof(double) + 4096;
     if (precision == SPAMM_EMU64)
         b += 6 * (2 * emu_slice_bytes_per_tile() * (size_t)g.m * g.m + 2 * (size_t)g.m * g.nb * 8);
@@ -373,9 +392,13 @@ static double profiled_ms(Plan* p) {
 // then the tree pass of the previous product); the tree pass may also carry
 // the iteration's trace error (tk).
 static void product(Plan* p, const TileMat& A, const TileMat& B, TileMat& C, double tau, EpiMode mode,
-                    unsigned long long* ctr, cudaStream_t st, const TreeExtra* tk = nullptr) {
+                    unsigned long long* ctr, cudaStream_t st, const TreeExtra* tk = nullptr, int slot = 0) {
     const Geometry& g = p->g;
-    CullOut co{p->counts, p->jlist, p->tile_list, p->flags + 3, C.tree, mode == EPI_NS_X ? 1 : 0};
+    int* counts = slot ? p->counts2 : p->counts;
+    int* jlist = slot ? p->jlist2 : p->jlist;
+    int* tile_list = slot ? p->tile_list2 : p->tile_list;
+    int* tile_count = p->flags + 3 + slot;
+    CullOut co{counts, jlist, tile_list, tile_count, C.tree, mode == EPI_NS_X ? 1 : 0};
     if (p->emu) {
         co.zero_u64 = C.rmax;  // rmax and cmax, contiguous
         co.zero_n = 2 * (long)g.m * g.nb;
@@ -389,20 +412,20 @@ static void product(Plan* p, const TileMat& A, const TileMat& B, TileMat& C, dou
         if (e0 && e1) cudaEventRecordWithFlags(e0, st, cudaEventRecordExternal);
     }
     if (p->emu) {
-        launch_gemm_emu(g, A, B, C, p->counts, p->jlist, p->tile_list, p->flags + 3, mode, p->trace_part, p->flags,
+        launch_gemm_emu(g, A, B, C, counts, jlist, tile_list, tile_count, mode, p->trace_part, p->flags,
                         p->flags + 2, st);
     } else {
-        launch_gemm_f64(g, A.t, B.t, C.t, A.tree, B.tree, C.tree, p->counts, p->jlist, p->tile_list, p->flags + 3, 0,
+        launch_gemm_f64(g, A.t, B.t, C.t, A.tree, B.tree, C.tree, counts, jlist, tile_list, tile_count, 0,
                         mode, p->trace_part, p->flags, st);
     }
     if (e0 && e1) cudaEventRecordWithFlags(e1, st, cudaEventRecordExternal);
     p->gemm_launches++;
     // tensor-core path: the slicing pass also computes the output's leaf norms, before the tree sums them
     if (p->emu)
-        launch_slice(C.t, nullptr, C.tree, C.rmax, C.cmax, C.sliceA, C.sliceB, g, p->tile_list, p->flags + 3,
+        launch_slice(C.t, nullptr, C.tree, C.rmax, C.cmax, C.sliceA, C.sliceB, g, tile_list, tile_count,
                      p->flags, st);
     TreeExtra ex = tk ? *tk : TreeExtra();
-    ex.zero_int = p->flags + 3;
+    ex.zero_int = tile_count;
     launch_tree(g, C.tree, p->flags, st, ex);
 }
 
@@ -431,7 +454,7 @@ static int multiply_impl(const double* A, const double* B, double* C, int n, dou
     if ((e = out_target(p, 2, C, &dC))) return e;
     begin_call(p, o.profile != 0, o.precision == SPAMM_EMU64);
     if (p->emu && (e = ensure_emu(p))) return e;
-    CK(cudaMemsetAsync(p->flags, 0, 4 * sizeof(int), st));
+    CK(cudaMemsetAsync(p->flags, 0, 8 * sizeof(int), st));
     CK(cudaMemsetAsync(p->task_ctr, 0, 4 * sizeof(unsigned long long), st));
     launch_pack(dA, n, g, nullptr, nullptr, p->buf[0], st);
     launch_tree(g, p->buf[0].tree, nullptr, st);
@@ -490,7 +513,7 @@ static int residual_impl(Plan* p, const double* dS, const double* dZ, double* ou
 static int enqueue_solve(Plan* p, const double* dS, double* dY, double* dZ, int n, double tau, double tau_s,
                          int maxit, const spamm_opts& o, cudaStream_t st, int* iters) {
     const Geometry& g = p->g;
-    CK(cudaMemsetAsync(p->flags, 0, 4 * sizeof(int), st));
+    CK(cudaMemsetAsync(p->flags, 0, 8 * sizeof(int), st));
     CK(cudaMemsetAsync(p->task_ctr, 0, (3 * (size_t)p->maxit_cap + 4) * sizeof(unsigned long long), st));
     CK(cudaMemsetAsync(p->t_hist, 0, (size_t)p->maxit_cap * sizeof(double), st));
 
@@ -536,15 +559,29 @@ static int enqueue_solve(Plan* p, const double* dS, double* dY, double* dZ, int 
         tk.t_hist = p->t_hist;
         tk.done = p->flags;
         tk.iters = p->flags + 1;
+        // the Y and Z updates are independent: the Z update runs on the side branch (a profiled call
+        // keeps them in order, so that each leaf-product timing is that kernel's own)
+        cudaStream_t zs = p->profile ? st : p->side;
+        if (zs != st) {
+            CK(cudaEventRecord(p->ev_fork, st));
+            CK(cudaStreamWaitEvent(zs, p->ev_fork, 0));
+        }
         if (o.order == SPAMM_ORDER_PAPER) {
-            product(p, Tb, Yb, Y2, tau_s, EPI_PLAIN, ctr + 0, st);  // Y <- T (x)_{tau_s} Y
-            product(p, Zb, Tb, Z2, tau, EPI_PLAIN, ctr + 1, st);    // Z <- Z (x)_tau T
+            product(p, Tb, Yb, Y2, tau_s, EPI_PLAIN, ctr + 0, st);           // Y <- T (x)_{tau_s} Y
+            product(p, Zb, Tb, Z2, tau, EPI_PLAIN, ctr + 1, zs, nullptr, 1);  // Z <- Z (x)_tau T
+        } else {
+            product(p, Yb, Tb, Y2, tau_s, EPI_PLAIN, ctr + 0, st);           // Y <- Y (x)_{tau_s} T
+            product(p, Tb, Zb, Z2, tau, EPI_PLAIN, ctr + 1, zs, nullptr, 1);  // Z <- T (x)_tau Z
+        }
+        if (zs != st) {
+            CK(cudaEventRecord(p->ev_join, zs));
+            CK(cudaStreamWaitEvent(st, p->ev_join, 0));
+        }
+        if (o.order == SPAMM_ORDER_PAPER) {
             std::swap(Yb, Y2);
             std::swap(Zb, Z2);
             product(p, Yb, Zb, Tb, tau, EPI_NS_X, ctr + 2, st, &tk);  // X <- Y (x)_tau Z, T = h[X]
         } else {
-            product(p, Yb, Tb, Y2, tau_s, EPI_PLAIN, ctr + 0, st);  // Y <- Y (x)_{tau_s} T
-            product(p, Tb, Zb, Z2, tau, EPI_PLAIN, ctr + 1, st);    // Z <- T (x)_tau Z
             std::swap(Yb, Y2);
             std::swap(Zb, Z2);
             product(p, Zb, Yb, Tb, tau, EPI_NS_X, ctr + 2, st, &tk);  // X <- Z (x)_tau Y, T = h[X]
