@@ -68,7 +68,8 @@ constexpr int kEpiWarps = 8;                 // two per TMEM lane quarter (32 ou
 constexpr int kThreads = 32 * (2 + kEpiWarps);
 constexpr int kGroups = 6;                   // accumulator groups (64 TMEM columns each)
 constexpr int kChunk = 7;                    // tasks accumulated in TMEM between flushes (exactness bound)
-constexpr int kMaxTasks = 256;
+// tasks of one output tile: at most m, and the API limits SPAMM_EMU64 to m <= 512
+constexpr int kMaxTasks = 512;
 
 // exponent e with |x| < 2^(e-1) for every x of a row/column whose largest
 // magnitude has the IEEE bits `bits` (0 for an all-zero or subnormal row):
@@ -279,6 +280,9 @@ struct EmuArgs {
     const uint8_t* sliceB;              // B-role slices of the right operand
     const double* leafA;                // leaf norms (quadtree leaf level)
     const double* leafB;
+    const double* rootA;                // quadtree roots: thr = ((tau*tau) * rootA) * rootB as in the cull
+    const double* rootB;
+    double tau;
     const unsigned long long* rmaxA;    // row maxima of the left operand
     const unsigned long long* cmaxB;    // column maxima of the right operand
     double* C;                          // FP64 output tiles
@@ -397,12 +401,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
 
     if (warp == 0) {
         // ---------------- producer: per tile the task list and scales, then the half-task stream
+        const bool zero_filter = !(((a.tau * a.tau) * *a.rootA) * *a.rootB > 0.0);
         long long H = 0;
         int tau = 0;
         for (int idx = blockIdx.x; idx < ntiles && !*abort_flag; idx += gridDim.x, ++tau) {
             const int slot = tau & 1;
             const int tile = a.tile_list[idx];
             const int i = tile / m, k = tile - (tile / m) * m;
+            // this tile's metadata, fetched before waiting for its slot
+            const int cnt = a.counts[tile];
+            const int* js = a.jlist + (size_t)tile * m;
+            const int jpre0 = lane < cnt ? js[lane] : 0;
+            const int jpre1 = lane + 32 < cnt ? js[lane + 32] : 0;
+            const unsigned long long ra0 = a.rmaxA[i * NB + lane], ra1 = a.rmaxA[i * NB + 32 + lane];
+            const unsigned long long cb0 = a.cmaxB[k * NB + lane], cb1 = a.cmaxB[k * NB + 32 + lane];
             if (tau >= 2) {
                 bool ok = true;
                 if (lane == 0) ok = wait_or_abort(&bar_tfree[slot], (uint32_t)(((tau >> 1) & 1) ^ 1), abort_flag);
@@ -412,25 +424,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
                     break;
                 }
             }
-            const int cnt = a.counts[tile];
-            const int* js = a.jlist + (size_t)tile * m;
             int T = 0;
             for (int base = 0; base < cnt; base += 32) {
                 const int t = base + lane;
-                int j = 0;
-                bool keep = false;
-                if (t < cnt) {
-                    j = js[t];
-                    keep = a.leafA[(size_t)i * m + j] != 0.0 && a.leafB[(size_t)j * m + k] != 0.0;
-                }
+                int j = base == 0 ? jpre0 : (base == 32 ? jpre1 : 0);
+                bool keep = t < cnt;
+                if (keep && base >= 64) j = js[t];
+                // with thr > 0 every listed task has two nonzero operand tiles; with thr = 0 the
+                // tasks with an exactly zero operand contribute nothing and are skipped
+                if (keep && zero_filter) keep = a.leafA[(size_t)i * m + j] != 0.0 && a.leafB[(size_t)j * m + k] != 0.0;
                 const unsigned bal = __ballot_sync(0xffffffffu, keep);
                 if (keep) tasks_sh[slot][T + __popc(bal & ((1u << lane) - 1u))] = j;
                 T += __popc(bal);
             }
-            for (int r = lane; r < NB; r += 32) {
-                eA_sh[slot][r] = expo_of(a.rmaxA[i * NB + r]);
-                eB_sh[slot][r] = expo_of(a.cmaxB[k * NB + r]);
-            }
+            eA_sh[slot][lane] = expo_of(ra0);
+            eA_sh[slot][lane + 32] = expo_of(ra1);
+            eB_sh[slot][lane] = expo_of(cb0);
+            eB_sh[slot][lane + 32] = expo_of(cb1);
             if (lane == 0) ntask_sh[slot] = T;
             __syncwarp();
             if (lane == 0) {
@@ -640,12 +650,15 @@ void launch_slice(const double* X, const double* leaf, double* leaf_out, const u
 
 void launch_gemm_emu(const Geometry& g, const TileMat& A, const TileMat& B, const TileMat& C, const int* counts,
                      const int* jlist, const int* tile_list, const int* tile_count, EpiMode mode, double* trace_part,
-                     const int* done, int* err, cudaStream_t st) {
+                     const int* done, int* err, double tau, cudaStream_t st) {
     emu::EmuArgs a;
     a.sliceA = A.sliceA;
     a.sliceB = B.sliceB;
     a.leafA = A.tree;
     a.leafB = B.tree;
+    a.rootA = A.tree + g.off[0];
+    a.rootB = B.tree + g.off[0];
+    a.tau = tau;
     a.rmaxA = A.rmax;
     a.cmaxB = B.cmax;
     a.C = C.t;

@@ -413,7 +413,7 @@ static void product(Plan* p, const TileMat& A, const TileMat& B, TileMat& C, dou
     }
     if (p->emu) {
         launch_gemm_emu(g, A, B, C, counts, jlist, tile_list, tile_count, mode, p->trace_part, p->flags,
-                        p->flags + 2, st);
+                        p->flags + 2, tau, st);
     } else {
         launch_gemm_f64(g, A.t, B.t, C.t, A.tree, B.tree, C.tree, counts, jlist, tile_list, tile_count, 0,
                         mode, p->trace_part, p->flags, st);

@@ -164,6 +164,6 @@ void launch_slice(const double* X, const double* leaf, double* leaf_out, const u
 // internal wait.  C's leaf norms come from launch_slice with leaf_out set.
 void launch_gemm_emu(const Geometry& g, const TileMat& A, const TileMat& B, const TileMat& C, const int* counts,
                      const int* jlist, const int* tile_list, const int* tile_count, EpiMode mode, double* trace_part,
-                     const int* done, int* err, cudaStream_t st);
+                     const int* done, int* err, double tau, cudaStream_t st);
 
 }  // namespace spamm

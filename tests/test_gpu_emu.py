@@ -113,3 +113,27 @@ def test_emu_rejects_other_leaf_sizes():
     S = synth.kms(128, 0.5)
     with pytest.raises(sp.SpammError):
         sp.sqrt_invsqrt(dev(S), 1e-8, 5, leaf=32, precision=sp.EMU64)
+
+
+def test_emu_output_tile_with_more_than_256_tasks():
+    """m = 257 leaf tiles per side: only block row 0 of A and block column 0 of B are nonzero, so output tile
+    (0, 0) carries all 257 products (more tasks than one 256-entry list could hold) and every other tile is
+    exactly zero."""
+    nb, m = 64, 257
+    n = nb * m
+    rng = np.random.default_rng(257)
+    A = np.zeros((n, n))
+    B = np.zeros((n, n))
+    A[:nb, :] = rng.standard_normal((nb, n))
+    B[:, :nb] = rng.standard_normal((n, nb))
+    C, st = sp.multiply(dev(A), dev(B), 1e-12, leaf=nb, precision=sp.EMU64)
+    assert st["tasks_total"] == m
+    C00 = C[:nb, :nb].cpu().numpy()
+    rest = C.clone()
+    rest[:nb, :nb] = 0
+    assert int(torch.count_nonzero(rest)) == 0
+    del rest, C
+    tasks = np.array([(0, j, 0) for j in range(m)], dtype=np.int32)
+    Co = oracle.leaf_products(A, B, nb, tasks)[:nb, :nb]
+    As, Bs = A[:nb, :], B[:, :nb]
+    assert (np.abs(C00 - Co) <= _tol(As, Bs, n)).all()
