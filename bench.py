@@ -44,6 +44,23 @@ def workload_name(tau: float, precision: str) -> str:
             f"{precision} leaf products")
 
 
+def max_over_ranks(x: float, ws: int, device=None) -> float:
+    """Largest x over the ranks of the job (x itself for a single process).  The bench's
+    timed region ends when the slowest rank ends."""
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(ws: int, steps: int, t_max: float) -> float:
+    """Whole-job throughput: every rank solves `steps` problems; the job takes t_max seconds."""
+    return ws * steps / t_max
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -256,13 +273,8 @@ def run_gpu(args, ws, rank, local):
         gemm_launches += st["gemm_launches"]
         gemm_flops += st["flops"]
     tot = sum(step_s)
-    if ws > 1:
-        t = torch.tensor([tot], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_max = float(t.item())
-    else:
-        tot_max = tot
-    value = ws * args.steps / tot_max
+    tot_max = max_over_ranks(tot, ws, dev)
+    value = job_rate(ws, args.steps, tot_max)
 
     # end to end through the C ABI with pinned host buffers (H2D of S, D2H of Y and Z inside the region)
     Sh = torch.from_numpy(S).pin_memory()
@@ -276,11 +288,24 @@ def run_gpu(args, ws, rank, local):
         t0 = time.perf_counter()
         sp.sqrt_invsqrt(Sh, tau, MAXIT, leaf=LEAF, precision=prec, Y=Yh, Z=Zh)
         e2e_t.append(time.perf_counter() - t0)
-    e2e_tot = sum(e2e_t)
-    if ws > 1:
-        t = torch.tensor([e2e_tot], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_tot = float(t.item())
+    e2e_tot = max_over_ranks(sum(e2e_t), ws, dev)
+
+    # the plain FP64-pipe method on the same workload, for comparison with the tensor-core path
+    fp64_path = None
+    if prec == sp.EMU64 and not args.no_fp64_path:
+        _, _, fst = sp.sqrt_invsqrt(Sd, tau, MAXIT, leaf=LEAF, precision=sp.FP64, Y=Yd, Z=Zd, residual=True)
+        ft = []
+        for _ in range(3):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sp.sqrt_invsqrt(Sd, tau, MAXIT, leaf=LEAF, precision=sp.FP64, Y=Yd, Z=Zd)
+            e1.record(stream)
+            e1.synchronize()
+            ft.append(e0.elapsed_time(e1) / 1e3)
+        fp64_path = {"value": job_rate(ws, len(ft), max_over_ranks(sum(ft), ws, dev)), "unit": UNIT,
+                     "resid_F": fst["resid_F"], "gate_met": bool(fst["resid_F"] <= GATE)}
 
     # tau sweep (the configuration's cull-count / error study)
     sweep = []
@@ -354,8 +379,9 @@ def run_gpu(args, ws, rank, local):
             "tasks_per_solve": vst["tasks_total"], "volume_pct": 100.0 * vst["tasks_total"] / vst["tasks_dense"],
             "t_final": vst["t_final"],
             "roofline": roof,
+            "fp64_path": fp64_path,
             "cpu_baseline": cpu,
-            "e2e": {"value": ws * args.steps / e2e_tot, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+            "e2e": {"value": job_rate(ws, args.steps, e2e_tot), "unit": UNIT, "h2d_bytes_per_step": nbytes,
                     "d2h_bytes_per_step": 2 * nbytes},
             "gpu_launches": launches,
             "clocks": clk,
@@ -453,16 +479,22 @@ def run_serve(args, local):
 
 
 def main():
+    global N, MAXIT
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "emu64"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "emu64"], default="emu64",
+                    help="leaf-product arithmetic: emu64 (FP64-class products on the BF16 tensor cores, the "
+                         "default) or fp64 (FP64 pipe)")
     ap.add_argument("--tau", type=float, default=TAU_HEADLINE)
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle time for cpu_baseline")
+    ap.add_argument("--size", type=int, default=N, help="matrix size N (a smaller case for profiler captures)")
+    ap.add_argument("--maxit", type=int, default=MAXIT, help="iterations per solve (fewer for profiler captures)")
+    ap.add_argument("--no-fp64-path", action="store_true", help="skip timing the FP64-pipe solve beside EMU64")
     ap.add_argument("--batched", action="store_true", help="batched configuration instead of the headline solve")
     ap.add_argument("--batch", type=int, default=512)
     ap.add_argument("--batch-tau", type=float, default=1e-6)
@@ -475,6 +507,7 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    N, MAXIT = args.size, args.maxit
     ws, rank, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, ws, rank)
