@@ -292,6 +292,7 @@ struct EmuArgs {
     const int* jlist;
     const int* tile_list;               // compacted output tiles with work
     const int* tile_count;
+    int* sched;                         // [2] tile ticket counter and finished-CTA counter, zero between launches
     double* trace_part;
     const int* done;
     int* err;
@@ -323,21 +324,40 @@ __device__ __forceinline__ double fixed_to_double(long long tot, int s) {
 // Group g holds integer sums of digit products of weight 2^{-8(diag+2)},
 // diag = g + half (half = 1 for the odd-slice lanes): exact for diag <= 4
 // (shifted left by 32 - 8 diag), rounded to the unit for diag 5 and 6.
+template <int U>
+__device__ __forceinline__ void flush_convert(const uint32_t (&r)[16], int half, long long (&acc)[32]) {
+    const int diag = (U >> 1) + half;
+    const float up = diag <= 4 ? 1.0f : __int_as_float((127 + 32 - 8 * diag) << 23);
+    const int sh = diag <= 4 ? 32 - 8 * diag : 0;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) acc[(U & 1) * 16 + c] += (long long)__float2int_rn(__uint_as_float(r[c]) * up) << sh;
+}
+// The twelve 16-column loads (group g = u/2, column half u%2) are double-buffered: load u+1 is in flight
+// while load u is converted.
+template <int U>
+__device__ __forceinline__ void flush_step(uint32_t lane_col_base, int half, long long (&acc)[32], uint32_t (&cur)[16],
+                                           uint32_t (&nxt)[16]) {
+    if (U + 1 < 2 * kGroups) ptx::tmem_ld16(lane_col_base + (uint32_t)(((U + 1) >> 1) * 64 + ((U + 1) & 1) * 16), nxt);
+    flush_convert<U>(cur, half, acc);
+    ptx::tmem_ld_wait(nxt);
+}
 __device__ __forceinline__ void flush_groups(uint32_t lane_col_base, int half, long long (&acc)[32]) {
-#pragma unroll
-    for (int g = 0; g < kGroups; ++g) {
-        const int diag = g + half;
-        const float up = diag <= 4 ? 1.0f : __int_as_float((127 + 32 - 8 * diag) << 23);
-        const int sh = diag <= 4 ? 32 - 8 * diag : 0;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            uint32_t r[16];
-            ptx::tmem_ld16(lane_col_base + (uint32_t)(g * 64 + h * 16), r);
-            ptx::tmem_ld_wait();
-#pragma unroll
-            for (int c = 0; c < 16; ++c) acc[h * 16 + c] += (long long)__float2int_rn(__uint_as_float(r[c]) * up) << sh;
-        }
-    }
+    static_assert(kGroups == 6, "flush schedule written for six groups");
+    uint32_t ra[16], rb[16];
+    ptx::tmem_ld16(lane_col_base, ra);
+    ptx::tmem_ld_wait(ra);
+    flush_step<0>(lane_col_base, half, acc, ra, rb);
+    flush_step<1>(lane_col_base, half, acc, rb, ra);
+    flush_step<2>(lane_col_base, half, acc, ra, rb);
+    flush_step<3>(lane_col_base, half, acc, rb, ra);
+    flush_step<4>(lane_col_base, half, acc, ra, rb);
+    flush_step<5>(lane_col_base, half, acc, rb, ra);
+    flush_step<6>(lane_col_base, half, acc, ra, rb);
+    flush_step<7>(lane_col_base, half, acc, rb, ra);
+    flush_step<8>(lane_col_base, half, acc, ra, rb);
+    flush_step<9>(lane_col_base, half, acc, rb, ra);
+    flush_step<10>(lane_col_base, half, acc, ra, rb);
+    flush_step<11>(lane_col_base, half, acc, rb, ra);
 }
 
 // Bounded wait that also gives up when another role of this CTA aborted.
@@ -350,10 +370,13 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, vo
     return false;
 }
 
-// Persistent: one CTA per SM walks the compacted output-tile list.  The three
-// roles run decoupled: the producer warp prepares tile t+1 (task list,
-// scales) and streams its half-tasks while the MMA warp is still on tile t
-// and the epilogue warps finish tile t-1; mbarriers order them.
+// Persistent: one CTA per SM takes output tiles from the compacted list with
+// an atomic ticket (a CTA that draws cheap tiles draws more of them).  The
+// three roles run decoupled: the producer warp draws and prepares tile t+1
+// (task list, scales) and streams its half-tasks while the MMA warp is still
+// on tile t and the epilogue warps finish tile t-1; the tile id travels in
+// the slot, and mbarriers order the roles.  The last CTA to finish resets
+// the ticket counters for the next launch.
 __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
     if (a.done && *a.done) return;
     extern __shared__ uint8_t dyn_smem[];
@@ -362,6 +385,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
     __shared__ uint32_t tmem_base_sh;
     __shared__ int tasks_sh[2][kMaxTasks];
     __shared__ int ntask_sh[2];
+    __shared__ int tile_sh[2];
     __shared__ int eA_sh[2][NB], eB_sh[2][NB];
     __shared__ double tr_sh[kEpiWarps];
     __shared__ int abort_sh;
@@ -404,17 +428,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
         const bool zero_filter = !(((a.tau * a.tau) * *a.rootA) * *a.rootB > 0.0);
         long long H = 0;
         int tau = 0;
-        for (int idx = blockIdx.x; idx < ntiles && !*abort_flag; idx += gridDim.x, ++tau) {
+        int idx = lane == 0 ? atomicAdd(a.sched, 1) : 0;
+        idx = __shfl_sync(0xffffffffu, idx, 0);
+        for (;; ++tau) {
             const int slot = tau & 1;
-            const int tile = a.tile_list[idx];
+            const bool end = idx >= ntiles || *abort_flag;
+            // the following ticket is in flight while this tile is prepared
+            int nxt = 0;
+            if (!end && lane == 0) nxt = atomicAdd(a.sched, 1);
+            const int tile = end ? 0 : a.tile_list[idx];
             const int i = tile / m, k = tile - (tile / m) * m;
             // this tile's metadata, fetched before waiting for its slot
-            const int cnt = a.counts[tile];
+            const int cnt = end ? 0 : a.counts[tile];
             const int* js = a.jlist + (size_t)tile * m;
             const int jpre0 = lane < cnt ? js[lane] : 0;
             const int jpre1 = lane + 32 < cnt ? js[lane + 32] : 0;
-            const unsigned long long ra0 = a.rmaxA[i * NB + lane], ra1 = a.rmaxA[i * NB + 32 + lane];
-            const unsigned long long cb0 = a.cmaxB[k * NB + lane], cb1 = a.cmaxB[k * NB + 32 + lane];
+            unsigned long long ra0 = 0, ra1 = 0, cb0 = 0, cb1 = 0;
+            if (!end) {
+                ra0 = a.rmaxA[i * NB + lane];
+                ra1 = a.rmaxA[i * NB + 32 + lane];
+                cb0 = a.cmaxB[k * NB + lane];
+                cb1 = a.cmaxB[k * NB + 32 + lane];
+            }
             if (tau >= 2) {
                 bool ok = true;
                 if (lane == 0) ok = wait_or_abort(&bar_tfree[slot], (uint32_t)(((tau >> 1) & 1) ^ 1), abort_flag);
@@ -423,6 +458,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
                     if (lane == 0) atomicExch(a.err, 1);
                     break;
                 }
+            }
+            if (end) {
+                // no more tiles: the other roles see tile -1 in this slot and stop
+                if (lane == 0) {
+                    tile_sh[slot] = -1;
+                    ptx::mbar_arrive(&bar_tready[slot]);
+                }
+                break;
             }
             int T = 0;
             for (int base = 0; base < cnt; base += 32) {
@@ -441,7 +484,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
             eA_sh[slot][lane + 32] = expo_of(ra1);
             eB_sh[slot][lane] = expo_of(cb0);
             eB_sh[slot][lane + 32] = expo_of(cb1);
-            if (lane == 0) ntask_sh[slot] = T;
+            if (lane == 0) {
+                ntask_sh[slot] = T;
+                tile_sh[slot] = tile;
+            }
             __syncwarp();
             if (lane == 0) {
                 ptx::mbar_arrive(&bar_tready[slot]);  // release: the task list and scales are visible
@@ -465,6 +511,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
                 }
             }
             __syncwarp();
+            idx = __shfl_sync(0xffffffffu, nxt, 0);
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer: tasks accumulate in TMEM in chunks of kChunk
@@ -474,12 +521,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
             long long H = 0, C = 0;
             int tau = 0;
             bool ok = true;
-            for (int idx = blockIdx.x; idx < ntiles && ok; idx += gridDim.x, ++tau) {
+            for (; ok; ++tau) {
                 const int slot = tau & 1;
                 if (!wait_or_abort(&bar_tready[slot], (uint32_t)((tau >> 1) & 1), abort_flag)) {
                     atomicExch(a.err, 2);
                     break;
                 }
+                if (tile_sh[slot] < 0) break;
                 const int T = ntask_sh[slot];
                 for (int t = 0; t < T && ok; ++t) {
                     const bool chunk_start = (t % kChunk) == 0;
@@ -536,14 +584,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
         const int ew = warp - 2;          // 0..7
         long long C = 0;
         int tau = 0;
-        for (int idx = blockIdx.x; idx < ntiles; idx += gridDim.x, ++tau) {
+        for (;; ++tau) {
             const int slot = tau & 1;
-            const int tile = a.tile_list[idx];
-            const int i = tile / m, k = tile - (tile / m) * m;
             if (!wait_or_abort(&bar_tready[slot], (uint32_t)((tau >> 1) & 1), abort_flag)) {
                 atomicExch(a.err, 4);
                 break;
             }
+            const int tile = tile_sh[slot];
+            if (tile < 0) break;
+            const int i = tile / m, k = tile - (tile / m) * m;
             const int T = ntask_sh[slot];
             const int nchunks = (T + kChunk - 1) / kChunk;
             long long acc[32];
@@ -623,6 +672,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
     ptx::tc_fence_before();
     __syncthreads();
     if (warp == 0) ptx::tmem_dealloc(tmem, TMEM_COLS);
+    if (threadIdx.x == 0) {
+        // every participating CTA has drawn its last ticket: the last one out resets both counters
+        __threadfence();
+        const int participants = min((int)gridDim.x, ntiles);
+        if (atomicAdd(a.sched + 1, 1) == participants - 1) {
+            a.sched[0] = 0;
+            a.sched[1] = 0;
+        }
+    }
 }
 
 }  // namespace emu
@@ -650,7 +708,7 @@ void launch_slice(const double* X, const double* leaf, double* leaf_out, const u
 
 void launch_gemm_emu(const Geometry& g, const TileMat& A, const TileMat& B, const TileMat& C, const int* counts,
                      const int* jlist, const int* tile_list, const int* tile_count, EpiMode mode, double* trace_part,
-                     const int* done, int* err, double tau, cudaStream_t st) {
+                     int* sched, const int* done, int* err, double tau, cudaStream_t st) {
     emu::EmuArgs a;
     a.sliceA = A.sliceA;
     a.sliceB = B.sliceB;
@@ -668,6 +726,7 @@ void launch_gemm_emu(const Geometry& g, const TileMat& A, const TileMat& B, cons
     a.jlist = jlist;
     a.tile_list = tile_list;
     a.tile_count = tile_count;
+    a.sched = sched;
     a.trace_part = trace_part;
     a.done = done;
     a.err = err;

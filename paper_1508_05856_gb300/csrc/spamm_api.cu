@@ -123,7 +123,8 @@ struct Plan {
     double* trace_part = nullptr;  // [m]
     double* scal = nullptr;        // c0, mu, c, sqrt c, thr, resid, spare...
     double* rowsum = nullptr;      // [n]
-    int* flags = nullptr;          // done, iters, device error, output-tile counts of the two branches
+    int* flags = nullptr;          // done, iters, device error, output-tile counts of the two branches,
+                                   // [8..11] tile tickets of the tensor-core kernel per branch
     double* partial = nullptr;     // [m*m]
     double* stage[3] = {nullptr, nullptr, nullptr};  // n*n row-major staging
     // profiling: event pairs around each leaf-product kernel of a call
@@ -199,7 +200,7 @@ static int alloc_plan(Plan* p, int n, int nb) {
     CKA(cudaMalloc(&p->trace_part, (size_t)g.m * sizeof(double)));
     CKA(cudaMalloc(&p->scal, 16 * sizeof(double)));
     CKA(cudaMalloc(&p->rowsum, (size_t)n * sizeof(double)));
-    CKA(cudaMalloc(&p->flags, 8 * sizeof(int)));
+    CKA(cudaMalloc(&p->flags, 16 * sizeof(int)));
     CKA(cudaMalloc(&p->partial, (size_t)g.m * g.m * sizeof(double)));
     return SPAMM_OK;
 }
@@ -412,8 +413,8 @@ static void product(Plan* p, const TileMat& A, const TileMat& B, TileMat& C, dou
         if (e0 && e1) cudaEventRecordWithFlags(e0, st, cudaEventRecordExternal);
     }
     if (p->emu) {
-        launch_gemm_emu(g, A, B, C, counts, jlist, tile_list, tile_count, mode, p->trace_part, p->flags,
-                        p->flags + 2, tau, st);
+        launch_gemm_emu(g, A, B, C, counts, jlist, tile_list, tile_count, mode, p->trace_part,
+                        p->flags + 8 + 2 * slot, p->flags, p->flags + 2, tau, st);
     } else {
         launch_gemm_f64(g, A.t, B.t, C.t, A.tree, B.tree, C.tree, counts, jlist, tile_list, tile_count, 0,
                         mode, p->trace_part, p->flags, st);
@@ -454,7 +455,7 @@ static int multiply_impl(const double* A, const double* B, double* C, int n, dou
     if ((e = out_target(p, 2, C, &dC))) return e;
     begin_call(p, o.profile != 0, o.precision == SPAMM_EMU64);
     if (p->emu && (e = ensure_emu(p))) return e;
-    CK(cudaMemsetAsync(p->flags, 0, 8 * sizeof(int), st));
+    CK(cudaMemsetAsync(p->flags, 0, 16 * sizeof(int), st));
     CK(cudaMemsetAsync(p->task_ctr, 0, 4 * sizeof(unsigned long long), st));
     launch_pack(dA, n, g, nullptr, nullptr, p->buf[0], st);
     launch_tree(g, p->buf[0].tree, nullptr, st);
@@ -513,7 +514,7 @@ static int residual_impl(Plan* p, const double* dS, const double* dZ, double* ou
 static int enqueue_solve(Plan* p, const double* dS, double* dY, double* dZ, int n, double tau, double tau_s,
                          int maxit, const spamm_opts& o, cudaStream_t st, int* iters) {
     const Geometry& g = p->g;
-    CK(cudaMemsetAsync(p->flags, 0, 8 * sizeof(int), st));
+    CK(cudaMemsetAsync(p->flags, 0, 16 * sizeof(int), st));
     CK(cudaMemsetAsync(p->task_ctr, 0, (3 * (size_t)p->maxit_cap + 4) * sizeof(unsigned long long), st));
     CK(cudaMemsetAsync(p->t_hist, 0, (size_t)p->maxit_cap * sizeof(double), st));
 

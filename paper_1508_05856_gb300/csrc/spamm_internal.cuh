@@ -162,8 +162,9 @@ void launch_slice(const double* X, const double* leaf, double* leaf_out, const u
 // Leaf products on the tensor cores; writes C's FP64 tiles and row/column
 // maxima (pre-zeroed), trace partials for EPI_NS_X; *err set on a timed-out
 // internal wait.  C's leaf norms come from launch_slice with leaf_out set.
+// sched: two ints, zero before the first launch; the kernel leaves them zero.
 void launch_gemm_emu(const Geometry& g, const TileMat& A, const TileMat& B, const TileMat& C, const int* counts,
                      const int* jlist, const int* tile_list, const int* tile_count, EpiMode mode, double* trace_part,
-                     const int* done, int* err, double tau, cudaStream_t st);
+                     int* sched, const int* done, int* err, double tau, cudaStream_t st);
 
 }  // namespace spamm
