@@ -17,8 +17,9 @@
 // pairs that share an accumulator group.  The FP32 tensor-core accumulators in TMEM therefore hold the sums
 // of up to 7 tasks exactly (7 * 2^21 < 2^24).  Every 7 tasks (and at the end
 // of an output tile) the partial sums are moved from TMEM to registers in
-// six groups (top-half diagonals p+q = 0, 1, 2, 3 exactly, 4 and 5 rounded
-// to 2^{-48}) and added, as integers, into a 64-bit fixed-point accumulator
+// six groups (diagonals p+q <= 3 exactly, the groups of diagonal >= 4 added
+// in FP32 and rounded to 2^{-48}) and added, as integers, into a 64-bit
+// fixed-point accumulator
 // with quantum 2^{-48} relative to 2^{e_row + e_col}.  Dropped pairs
 // (p+q >= 6, except the (1,5), (3,3), (5,1) that come with the stacking) and
 // the digit truncation leave an error of a few 2^{-48} per product term
@@ -165,6 +166,7 @@ __global__ void __launch_bounds__(256, 6) k_slice(const double* __restrict__ X, 
                                                uint8_t* __restrict__ sA, uint8_t* __restrict__ sB, int m,
                                                const int* __restrict__ tile_list, const int* __restrict__ tile_count,
                                                const int* __restrict__ done) {
+    grid_dependency_wait();
     if (done && *done) return;
     __shared__ double xs[NB][NB + 1];
     __shared__ int eR[NB], eC[NB];
@@ -322,42 +324,70 @@ __device__ __forceinline__ double fixed_to_double(long long tot, int s) {
 // Move one chunk's accumulator groups from TMEM into the 64-bit fixed-point
 // sums (unit 2^{-48}) of this thread's row (32 of the 64 output columns).
 // Group g holds integer sums of digit products of weight 2^{-8(diag+2)},
-// diag = g + half (half = 1 for the odd-slice lanes): exact for diag <= 4
-// (shifted left by 32 - 8 diag), rounded to the unit for diag 5 and 6.
-template <int U>
-__device__ __forceinline__ void flush_convert(const uint32_t (&r)[16], int half, long long (&acc)[32]) {
-    const int diag = (U >> 1) + half;
-    const float up = diag <= 4 ? 1.0f : __int_as_float((127 + 32 - 8 * diag) << 23);
-    const int sh = diag <= 4 ? 32 - 8 * diag : 0;
+// diag = g + half (half = 1 for the odd-slice lanes).  Groups of diagonal
+// 0..3 are exact integers, shifted left by 32 - 8 diag.  The groups of
+// diagonal >= 4 (weight <= one unit) are added in FP32 first and converted
+// once: |sum| < 2^25 units, so the FP32 additions and the final rounding cost
+// at most 1.5 units per chunk, the size of the quantum itself.
+// The loads are double-buffered: load g+1 is in flight while g is converted.
+template <int SH>
+__device__ __forceinline__ void flush_exact(const uint32_t (&r)[16], int h, long long (&acc)[32]) {
 #pragma unroll
-    for (int c = 0; c < 16; ++c) acc[(U & 1) * 16 + c] += (long long)__float2int_rn(__uint_as_float(r[c]) * up) << sh;
+    for (int c = 0; c < 16; ++c) acc[h * 16 + c] += (long long)__float2int_rn(__uint_as_float(r[c])) << SH;
 }
-// The twelve 16-column loads (group g = u/2, column half u%2) are double-buffered: load u+1 is in flight
-// while load u is converted.
-template <int U>
-__device__ __forceinline__ void flush_step(uint32_t lane_col_base, int half, long long (&acc)[32], uint32_t (&cur)[16],
-                                           uint32_t (&nxt)[16]) {
-    if (U + 1 < 2 * kGroups) ptx::tmem_ld16(lane_col_base + (uint32_t)(((U + 1) >> 1) * 64 + ((U + 1) & 1) * 16), nxt);
-    flush_convert<U>(cur, half, acc);
-    ptx::tmem_ld_wait(nxt);
-}
+__device__ __forceinline__ uint32_t col16(uint32_t base, int g, int h) { return base + (uint32_t)(g * 64 + h * 16); }
 __device__ __forceinline__ void flush_groups(uint32_t lane_col_base, int half, long long (&acc)[32]) {
     static_assert(kGroups == 6, "flush schedule written for six groups");
+    const uint32_t b = lane_col_base;
     uint32_t ra[16], rb[16];
-    ptx::tmem_ld16(lane_col_base, ra);
-    ptx::tmem_ld_wait(ra);
-    flush_step<0>(lane_col_base, half, acc, ra, rb);
-    flush_step<1>(lane_col_base, half, acc, rb, ra);
-    flush_step<2>(lane_col_base, half, acc, ra, rb);
-    flush_step<3>(lane_col_base, half, acc, rb, ra);
-    flush_step<4>(lane_col_base, half, acc, ra, rb);
-    flush_step<5>(lane_col_base, half, acc, rb, ra);
-    flush_step<6>(lane_col_base, half, acc, ra, rb);
-    flush_step<7>(lane_col_base, half, acc, rb, ra);
-    flush_step<8>(lane_col_base, half, acc, ra, rb);
-    flush_step<9>(lane_col_base, half, acc, rb, ra);
-    flush_step<10>(lane_col_base, half, acc, ra, rb);
-    flush_step<11>(lane_col_base, half, acc, rb, ra);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        ptx::tmem_ld16(col16(b, 0, h), ra);
+        ptx::tmem_ld_wait(ra);
+        if (half == 0) {
+            // diagonals 0, 1, 2, 3 exact; 4 + 5/2^8 rounded
+            ptx::tmem_ld16(col16(b, 1, h), rb);
+            flush_exact<32>(ra, h, acc);
+            ptx::tmem_ld_wait(rb);
+            ptx::tmem_ld16(col16(b, 2, h), ra);
+            flush_exact<24>(rb, h, acc);
+            ptx::tmem_ld_wait(ra);
+            ptx::tmem_ld16(col16(b, 3, h), rb);
+            flush_exact<16>(ra, h, acc);
+            ptx::tmem_ld_wait(rb);
+            ptx::tmem_ld16(col16(b, 4, h), ra);
+            flush_exact<8>(rb, h, acc);
+            ptx::tmem_ld_wait(ra);
+            ptx::tmem_ld16(col16(b, 5, h), rb);
+            ptx::tmem_ld_wait(rb);
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+                acc[h * 16 + c] += (long long)__float2int_rn(
+                    fmaf(__uint_as_float(rb[c]), 0x1p-8f, __uint_as_float(ra[c])));
+        } else {
+            // diagonals 1, 2, 3 exact; 4 + 5/2^8 + 6/2^16 rounded
+            ptx::tmem_ld16(col16(b, 1, h), rb);
+            flush_exact<24>(ra, h, acc);
+            ptx::tmem_ld_wait(rb);
+            ptx::tmem_ld16(col16(b, 2, h), ra);
+            flush_exact<16>(rb, h, acc);
+            ptx::tmem_ld_wait(ra);
+            ptx::tmem_ld16(col16(b, 3, h), rb);
+            flush_exact<8>(ra, h, acc);
+            ptx::tmem_ld_wait(rb);
+            ptx::tmem_ld16(col16(b, 4, h), ra);
+            ptx::tmem_ld_wait(ra);
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+                rb[c] = __float_as_uint(fmaf(__uint_as_float(ra[c]), 0x1p-8f, __uint_as_float(rb[c])));
+            ptx::tmem_ld16(col16(b, 5, h), ra);
+            ptx::tmem_ld_wait(ra);
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+                acc[h * 16 + c] += (long long)__float2int_rn(
+                    fmaf(__uint_as_float(ra[c]), 0x1p-16f, __uint_as_float(rb[c])));
+        }
+    }
 }
 
 // Bounded wait that also gives up when another role of this CTA aborted.
@@ -378,6 +408,7 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, vo
 // the slot, and mbarriers order the roles.  The last CTA to finish resets
 // the ticket counters for the next launch.
 __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
+    grid_dependency_wait();
     if (a.done && *a.done) return;
     extern __shared__ uint8_t dyn_smem[];
     __shared__ __align__(8) uint64_t bar_full[NSTAGE], bar_empty[NSTAGE], bar_accf, bar_acce;
@@ -702,7 +733,8 @@ void launch_slice(const double* X, const double* leaf, double* leaf_out, const u
                   const int* tile_count, const int* done, cudaStream_t st) {
     // six 34 KB blocks fit on an SM: one resident wave covers up to 6 tiles per SM
     const int grid = std::min(device_sm_count() * 6, g.m * g.m);
-    emu::k_slice<<<grid, 256, 0, st>>>(X, leaf, leaf_out, rmax, cmax, sA, sB, g.m, tile_list, tile_count, done);
+    launch_dependent(emu::k_slice, dim3(grid), dim3(256), 0, st, X, leaf, leaf_out, rmax, cmax, sA, sB, g.m,
+                     tile_list, tile_count, done);
     note_launch();
 }
 
@@ -734,7 +766,7 @@ void launch_gemm_emu(const Geometry& g, const TileMat& A, const TileMat& B, cons
     a.n = g.n;
     a.mode = (int)mode;
     const int grid = std::min(device_sm_count(), g.m * g.m);
-    emu::k_gemm_emu<<<grid, emu::kThreads, emu::SMEM_DYN, st>>>(a);
+    launch_dependent(emu::k_gemm_emu, dim3(grid), dim3(emu::kThreads), emu::SMEM_DYN, st, a);
     note_launch();
 }
 

@@ -27,6 +27,7 @@ __global__ void __launch_bounds__(kThreads) k_gemm_f64(const double* __restrict_
                                                        const int* __restrict__ tile_count, int m, int n, int dense,
                                                        int mode, double* __restrict__ trace_part,
                                                        const int* __restrict__ done) {
+    grid_dependency_wait();
     if (done && *done) return;
     if (tile_list && (int)blockIdx.x >= *tile_count) return;
     constexpr int TM = NB / 16;  // each thread owns TM x TM outputs
@@ -124,8 +125,8 @@ void launch_nb(const Geometry& g, const double* A, const double* B, double* C, c
                const double* leafB, double* treeC, const int* counts, const int* jlist, const int* tile_list,
                const int* tile_count, int dense, EpiMode mode, double* trace_part, const int* done, cudaStream_t st) {
     const size_t smem = 2 * (size_t)kKC * (NB + 1) * sizeof(double);
-    k_gemm_f64<NB><<<g.m * g.m, kThreads, smem, st>>>(A, B, C, leafA, leafB, treeC, counts, jlist, tile_list,
-                                                       tile_count, g.m, g.n, dense, (int)mode, trace_part, done);
+    launch_dependent(k_gemm_f64<NB>, dim3(g.m * g.m), dim3(kThreads), smem, st, A, B, C, leafA, leafB, treeC, counts,
+                     jlist, tile_list, tile_count, g.m, g.n, dense, (int)mode, trace_part, done);
     note_launch();
 }
 

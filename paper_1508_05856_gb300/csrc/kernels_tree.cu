@@ -245,6 +245,7 @@ __device__ __forceinline__ void trace_error(const double* __restrict__ trace_par
 // out), so the top levels cost shared-memory latency instead of global.
 __global__ void __launch_bounds__(1024) k_tree(TreeDev td, double* __restrict__ tree, const int* __restrict__ done,
                                                TreeExtra ex) {
+    grid_dependency_wait();
     if (done && *done) return;
     __shared__ double bufA[64 * 64];
     __shared__ double bufB[32 * 32];
@@ -291,7 +292,7 @@ __global__ void __launch_bounds__(1024) k_tree(TreeDev td, double* __restrict__ 
 }
 
 void launch_tree(const Geometry& g, double* tree, const int* done, cudaStream_t st, const TreeExtra& ex) {
-    k_tree<<<1, 1024, 0, st>>>(tree_dev(g), tree, done, ex);
+    launch_dependent(k_tree, dim3(1), dim3(1024), 0, st, tree_dev(g), tree, done, ex);
     note_launch();
 }
 
@@ -307,6 +308,7 @@ __global__ void __launch_bounds__(256) k_cull(TreeDev td, const double* __restri
                                               const double* __restrict__ treeB, double tau, CullOut co,
                                               unsigned long long* __restrict__ total, double* __restrict__ thr_out,
                                               const int* __restrict__ done) {
+    grid_dependency_wait();
     if (done && *done) return;
     __shared__ int red[8];
     __shared__ int lst[8];
@@ -375,7 +377,8 @@ __global__ void __launch_bounds__(256) k_cull(TreeDev td, const double* __restri
 void launch_cull(const Geometry& g, const double* treeA, const double* treeB, double tau, const CullOut& out,
                  unsigned long long* total, double* thr_out, const int* done, cudaStream_t st) {
     const int warps = g.m * g.m;
-    k_cull<<<(warps + 7) / 8, 256, 0, st>>>(tree_dev(g), treeA, treeB, tau, out, total, thr_out, done);
+    launch_dependent(k_cull, dim3((warps + 7) / 8), dim3(256), 0, st, tree_dev(g), treeA, treeB, tau, out, total,
+                     thr_out, done);
     note_launch();
 }
 

@@ -54,6 +54,38 @@ enum EpiMode { EPI_PLAIN = 0, EPI_NS_X = 1 };
 // Counts kernel launches (spamm_kernel_launches); every launcher calls it.
 void note_launch(int k = 1);
 
+// Kernels of the product chain (cull -> leaf products -> slicing -> tree) are
+// launched as programmatic dependents of the previous kernel in their stream:
+// the launch overlaps the tail of the predecessor, and the kernel itself
+// waits (grid_dependency_wait, first statement) until the predecessor grid
+// has finished and its writes are visible.  Every grid of the chain is
+// resident in one wave or waits without holding back its predecessor, whose
+// blocks never wait on a dependent.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                    Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+// Device side of the above: wait for the predecessor grid, then let the
+// next kernel in the stream start launching.
+__device__ __forceinline__ void grid_dependency_wait() {
+#if defined(__CUDA_ARCH__)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#endif
+}
+
 // Once per device and process: shared-memory limits of the big kernels and
 // the SM count (kept out of the launchers so that launches can be captured
 // into CUDA graphs).
