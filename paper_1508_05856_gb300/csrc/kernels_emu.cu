@@ -65,7 +65,7 @@ constexpr int NSTAGE = 3;
 constexpr uint32_t EPI_BYTES = 2 * 64 * 65 * 8;          // epilogue staging of the two 64-bit halves
 constexpr uint32_t SMEM_DYN = NSTAGE * STAGE_BYTES + EPI_BYTES + 1024;
 constexpr uint32_t TMEM_COLS = 512;
-constexpr int kEpiWarps = 8;                 // two per TMEM lane quarter (32 output columns each)
+constexpr int kEpiWarps = 16;                // four per TMEM lane quarter (16 output columns each)
 constexpr int kThreads = 32 * (2 + kEpiWarps);
 constexpr int kGroups = 6;                   // accumulator groups (64 TMEM columns each)
 constexpr int kChunk = 7;                    // tasks accumulated in TMEM between flushes (exactness bound)
@@ -322,7 +322,7 @@ __device__ __forceinline__ double fixed_to_double(long long tot, int s) {
 }
 
 // Move one chunk's accumulator groups from TMEM into the 64-bit fixed-point
-// sums (unit 2^{-48}) of this thread's row (32 of the 64 output columns).
+// sums (unit 2^{-48}) of this thread's row (16 of the 64 output columns).
 // Group g holds integer sums of digit products of weight 2^{-8(diag+2)},
 // diag = g + half (half = 1 for the odd-slice lanes).  Groups of diagonal
 // 0..3 are exact integers, shifted left by 32 - 8 diag.  The groups of
@@ -331,17 +331,17 @@ __device__ __forceinline__ double fixed_to_double(long long tot, int s) {
 // at most 1.5 units per chunk, the size of the quantum itself.
 // The loads are double-buffered: load g+1 is in flight while g is converted.
 template <int SH>
-__device__ __forceinline__ void flush_exact(const uint32_t (&r)[16], int h, long long (&acc)[32]) {
+__device__ __forceinline__ void flush_exact(const uint32_t (&r)[16], int h, long long (&acc)[16]) {
 #pragma unroll
     for (int c = 0; c < 16; ++c) acc[h * 16 + c] += (long long)__float2int_rn(__uint_as_float(r[c])) << SH;
 }
 __device__ __forceinline__ uint32_t col16(uint32_t base, int g, int h) { return base + (uint32_t)(g * 64 + h * 16); }
-__device__ __forceinline__ void flush_groups(uint32_t lane_col_base, int half, long long (&acc)[32]) {
+__device__ __forceinline__ void flush_groups(uint32_t lane_col_base, int half, long long (&acc)[16]) {
     static_assert(kGroups == 6, "flush schedule written for six groups");
     const uint32_t b = lane_col_base;
     uint32_t ra[16], rb[16];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < 1; ++h) {
         ptx::tmem_ld16(col16(b, 0, h), ra);
         ptx::tmem_ld_wait(ra);
         if (half == 0) {
@@ -604,15 +604,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
         }
         __syncwarp();
     } else {
-        // ---------------- epilogue warps 2..9: TMEM lane quarter warp%4 (lanes 32q .. 32q+31),
-        // columns 32*ch .. 32*ch+31 with ch = (warp-2)/4
+        // ---------------- epilogue warps 2..17: TMEM lane quarter warp%4 (lanes 32q .. 32q+31),
+        // columns 16*cq .. 16*cq+15 with cq = (warp-2)/4
         const int quarter = warp & 3;
         const int half = quarter >> 1;  // 0: MMA rows 0-63 (even slices), 1: rows 64-127 (odd slices)
-        const int ch = (warp - 2) >> 2;
+        const int cq = (warp - 2) >> 2;
         const int row = (quarter & 1) * 32 + lane;
-        const uint32_t lane_col_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ch * 32);
-        const int et = threadIdx.x - 64;  // 0..255
-        const int ew = warp - 2;          // 0..7
+        const uint32_t lane_col_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(cq * 16);
+        const int et = threadIdx.x - 64;  // 0..511
+        const int ew = warp - 2;          // 0..15
         long long C = 0;
         int tau = 0;
         for (;; ++tau) {
@@ -626,9 +626,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
             const int i = tile / m, k = tile - (tile / m) * m;
             const int T = ntask_sh[slot];
             const int nchunks = (T + kChunk - 1) / kChunk;
-            long long acc[32];
+            long long acc[16];
 #pragma unroll
-            for (int c = 0; c < 32; ++c) acc[c] = 0;
+            for (int c = 0; c < 16; ++c) acc[c] = 0;
             bool ok = true;
             for (int ck = 0; ck < nchunks; ++ck, ++C) {
                 if (!wait_or_abort(&bar_accf, (uint32_t)(C & 1), abort_flag)) {
@@ -644,20 +644,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
             }
             if (!ok) break;
             // stage both halves' 64-bit sums, then finish the tile element-parallel:
-            // thread et owns column c and every fourth row
+            // thread et owns column c and every eighth row
             long long* dst = half ? sBot : sTop;
 #pragma unroll
-            for (int c = 0; c < 32; ++c) dst[(ch * 32 + c) * 65 + row] = acc[c];
+            for (int c = 0; c < 16; ++c) dst[(cq * 16 + c) * 65 + row] = acc[c];
             ptx::named_sync(1, 32 * kEpiWarps);
             const int c = et & 63;
-            const int r0 = et >> 6;  // 0..3
+            const int r0 = et >> 6;  // 0..7
             const int gj = k * NB + c;
             const int eBc = eB_sh[slot][c];
             double* outt = a.C + (size_t)tile * NB * NB;
             const bool nsx = a.mode == EPI_NS_X;
             // T = 1.5 I - 0.5 X: off the diagonal -x/2 is the conversion of -t64 one binade lower; the one
             // thread per column that owns the diagonal entry computes it up front
-            const int rd = (nsx && i == k && (c & 3) == r0 && gj < a.n) ? c : -1;
+            const int rd = (nsx && i == k && (c & 7) == r0 && gj < a.n) ? c : -1;
             double xd = 0.0, vd = 0.0;
             if (rd >= 0) {
                 xd = fixed_to_double(sTop[c * 65 + c] + sBot[c * 65 + c], eA_sh[slot][c] + eBc - 48);
@@ -665,11 +665,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
             }
             const int sc = eBc - 48 - (nsx ? 1 : 0);
             unsigned long long cmx = 0;
-            unsigned rowm = 0;  // lane q: upper magnitude bits of row r0 + 4q over this warp's 32 columns
-            for (int q0 = 0; q0 < 16; q0 += 8) {
+            unsigned rowm = 0;  // lane q: upper magnitude bits of row r0 + 8q over this warp's 32 columns
+            for (int q0 = 0; q0 < 8; q0 += 8) {
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
-                    const int r = r0 + 4 * (q0 + u);
+                    const int r = r0 + 8 * (q0 + u);
                     const long long t64 = sTop[c * 65 + r] + sBot[c * 65 + r];
                     double v = fixed_to_double(nsx ? -t64 : t64, eA_sh[slot][r] + sc);
                     v = r == rd ? vd : v;
@@ -682,7 +682,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
                 }
             }
             if (cmx) atomicMax(a.cmaxC + gj, cmx);
-            if (lane < 16 && rowm) atomicMax(a.rmaxC + i * NB + r0 + 4 * lane, (unsigned long long)rowm << 32);
+            if (lane < 8 && rowm) atomicMax(a.rmaxC + i * NB + r0 + 8 * lane, (unsigned long long)rowm << 32);
             const bool diag_tile = nsx && i == k;
             if (diag_tile) {
                 double tr = rd >= 0 ? xd : 0.0;
