@@ -200,6 +200,23 @@ def measure_dgemm_tflops(torch, dev) -> float:
     return 2.0 * n ** 3 / best / 1e12
 
 
+def captured_traffic(kernel: str, tasks_per_launch: float):
+    """DRAM bytes (read + write) per launch from the committed ncu capture of `kernel`, scaled by tasks
+    to this run's mean launch; None when the kernel source changed since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path)).get(kernel)
+    if not rec:
+        return None
+    src = os.path.join(ROOT, rec["source"])
+    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["source_sha256"]:
+        return None
+    per_task = (rec["dram_read_bytes"] + rec["dram_write_bytes"]) / rec["tasks"]
+    return per_task * tasks_per_launch
+
+
 def run_gpu(args, ws, rank, local):
     import numpy as np
     import torch
@@ -348,8 +365,10 @@ def run_gpu(args, ws, rank, local):
         peak = peaks.get("bf16_tflops", 1900.0)
         # 12 stacked M=128 x N=64 MMA pairs x 4 K-steps of 16 per task: 2*128*64*64*12 flop on the tensor pipe
         issued = achieved * (2.0 * 128 * 64 * 64 * 12) / (2.0 * LEAF ** 3)
+        tasks_per_launch = gemm_flops / max(1, gemm_launches) / (2.0 * LEAF ** 3)
         roof = {"bound": "tensor", "achieved": issued, "peak": peak, "unit": "TFLOP/s",
-                "frac": issued / peak if peak else None, "traffic": None, "kernel": "spamm::emu::k_gemm_emu",
+                "frac": issued / peak if peak else None,
+                "traffic": captured_traffic("k_gemm_emu", tasks_per_launch), "kernel": "spamm::emu::k_gemm_emu",
                 "achieved_counts": "BF16 tensor-pipe flops issued (24x the FP64-equivalent useful flops)",
                 "useful_fp64_equiv_tflops": achieved,
                 "peak_source": "bf16_tflops of measured" if peaks else "fallback 1.9 PFLOP/s",
