@@ -81,21 +81,22 @@ __device__ __forceinline__ int expo_of(unsigned long long bits) {
     return E == 0 ? 0 : E - 1021;
 }
 
-// x * 2^-e rounded to a signed fixed-point integer with 48 fractional bits
-// (|result| <= 2^48 because |x| < 2^e).
-__device__ __forceinline__ long long fixed48(double x, int e) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const int E = (int)((b >> 52) & 0x7FF);
-    if (E == 0 || E == 0x7FF) return 0ll;
-    const unsigned long long M = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    const int s = e + 1027 - E;  // >= 5 when |x| < 2^e
-    if (s >= 64) return 0ll;
-    const long long F = s < 5 ? (long long)(1ull << 48) : (long long)((M + (1ull << (s - 1))) >> s);
-    return (b >> 63) ? -F : F;
+// |x| * 2^(48-e) rounded (half up) to an integer, from the IEEE bits of x and
+// se = e + 1027: the shift s = se - E is at least 6 for every entry of a row
+// (column) whose largest magnitude defines e, so |F| <= 2^47.  Zeros give 0;
+// a shift beyond 63 gives 0.
+__device__ __forceinline__ unsigned long long fixed48_mag(unsigned long long b, int se) {
+    const unsigned hw = (unsigned)(b >> 32);
+    const int E = (int)((hw >> 20) & 0x7FFu);
+    const unsigned long long M = E ? ((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) : 0ull;
+    const int s = min(se - E, 63);
+    return ((M >> (s - 1)) + 1ull) >> 1;
 }
 
 // Balanced signed base-256 digits of F = sum_p d_p 2^{8(5-p)}: |d_p| <= 128
-// (d_p in [-128, 127] for p >= 1), so the truncation error is symmetric.
+// (d_p in [-128, 127] for p >= 1), so the truncation error is symmetric.  The
+// slicing pass takes the digits of |F| and negates them (BF16 sign bit) for a
+// negative entry: still |d_p| <= 128.
 // Adding 0x80 to each of the five low bytes of F turns them into plain bytes
 // d_p + 128 (p = 1..5, byte 5-p); the top digit d_0 is what remains above bit
 // 40.  digit_value returns d_p as an exact FP32 value: the byte is placed in
@@ -120,45 +121,14 @@ __device__ __forceinline__ uint32_t bf16x2_bits(float a, float b) {
     return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-// Double-word FP32 accumulation (hi + lo, about 2^-44 relative) of the
-// squares of FP64 values: FP64 arithmetic is slow on this part, so the
-// per-tile sums of squares use FP32 pairs.
-struct DFloat {
-    float hi, lo;
-};
-__device__ __forceinline__ DFloat df_add(DFloat x, DFloat y) {
-    const float s = x.hi + y.hi;
-    const float bb = s - x.hi;
-    const float e = ((x.hi - (s - bb)) + (y.hi - bb)) + (x.lo + y.lo);
-    const float h = s + e;
-    return DFloat{h, e - (h - s)};
-}
-// v * v as a double-word: v split into its leading 24 mantissa bits and the rest.
-__device__ __forceinline__ DFloat df_square(double v) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
-    const int E = (int)(b >> 52);
-    const int fe = E - 1023 + 127;
-    if (E == 0 || fe <= 0 || fe >= 255) return DFloat{0.f, 0.f};  // zero, or below FP32 range (negligible)
-    const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
-    const float hi = __uint_as_float(((unsigned)fe << 23) | (unsigned)(mant >> 29));
-    const int le = E - 1023 - 52 + 127;  // exponent of the low 29 bits' unit
-    const float lo = le > 0 ? (float)(unsigned)(mant & 0x1FFFFFFFull) * __uint_as_float((unsigned)le << 23) : 0.f;
-    const float p = hi * hi;
-    const float pe = fmaf(hi, hi, -p);
-    return DFloat{p, fmaf(2.0f * hi, lo, pe)};
-}
-__device__ __forceinline__ DFloat df_shfl_xor(DFloat x, int o) {
-    return DFloat{__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o)};
-}
-
 // ------------------------------------------------------------------ slicing
 // Grid-stride over the listed tiles (tile_list / tile_count), or over all
 // m*m tiles when tile_list is null.  With leaf_out null, leaf tiles with
 // nu == 0 are skipped (the leaf-product kernel never reads them: their
 // products are exactly zero).  With leaf_out set, the kernel also computes
-// each listed tile's squared Frobenius norm nu (a double-word FP32 sum of
-// the squares, about 2^-44 relative) into leaf_out[tile]; unlisted tiles keep
-// the zero the cull wrote for them.
+// each listed tile's squared Frobenius norm nu (FP64 fused multiply-adds, a
+// fixed-order reduction) into leaf_out[tile]; unlisted tiles keep the zero
+// the cull wrote for them.
 __global__ void __launch_bounds__(256, 6) k_slice(const double* __restrict__ X, const double* __restrict__ leaf,
                                                double* __restrict__ leaf_out,
                                                const unsigned long long* __restrict__ rmax,
@@ -170,7 +140,7 @@ __global__ void __launch_bounds__(256, 6) k_slice(const double* __restrict__ X, 
     if (done && *done) return;
     __shared__ double xs[NB][NB + 1];
     __shared__ int eR[NB], eC[NB];
-    __shared__ DFloat nu_sh[8];
+    __shared__ double nu_sh[8];
     const int ntiles = tile_list ? *tile_count : m * m;
     for (int idx = blockIdx.x; idx < ntiles; idx += gridDim.x) {
     const int tile = tile_list ? tile_list[idx] : idx;
@@ -178,7 +148,7 @@ __global__ void __launch_bounds__(256, 6) k_slice(const double* __restrict__ X, 
     __syncthreads();
     const int i = tile / m, j = tile - (tile / m) * m;
     const double* x = X + (size_t)tile * NB * NB;
-    DFloat nup[2] = {{0.f, 0.f}, {0.f, 0.f}};
+    double nup[2] = {0.0, 0.0};
     // two batches of eight independent loads per thread
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -189,21 +159,22 @@ __global__ void __launch_bounds__(256, 6) k_slice(const double* __restrict__ X, 
         for (int q = 0; q < 8; ++q) {
             const int idx = threadIdx.x + 256 * (8 * h + q);
             xs[idx >> 6][idx & 63] = v[q];
-            if (leaf_out) nup[q & 1] = df_add(nup[q & 1], df_square(v[q]));
+            if (leaf_out) nup[q & 1] = fma(v[q], v[q], nup[q & 1]);
         }
     }
     if (leaf_out) {
-        DFloat nu = df_add(nup[0], nup[1]);
-        for (int o = 16; o > 0; o >>= 1) nu = df_add(nu, df_shfl_xor(nu, o));
+        double nu = nup[0] + nup[1];
+        for (int o = 16; o > 0; o >>= 1) nu += __shfl_xor_sync(0xffffffffu, nu, o);
         if ((threadIdx.x & 31) == 0) nu_sh[threadIdx.x >> 5] = nu;
     }
     if (threadIdx.x < NB) eR[threadIdx.x] = expo_of(rmax[i * NB + threadIdx.x]);
     else if (threadIdx.x < 2 * NB) eC[threadIdx.x - NB] = expo_of(cmax[j * NB + threadIdx.x - NB]);
     __syncthreads();
     if (leaf_out && threadIdx.x == 0) {
-        DFloat t = nu_sh[0];
-        for (int w = 1; w < 8; ++w) t = df_add(t, nu_sh[w]);
-        leaf_out[tile] = (double)t.hi + (double)t.lo;
+        // pairwise, fixed order
+        const double s01 = nu_sh[0] + nu_sh[1], s23 = nu_sh[2] + nu_sh[3];
+        const double s45 = nu_sh[4] + nu_sh[5], s67 = nu_sh[6] + nu_sh[7];
+        leaf_out[tile] = (s01 + s23) + (s45 + s67);
     }
     uint8_t* a = sA + (size_t)tile * A_TILE_BYTES;
     uint8_t* b = sB + (size_t)tile * B_TILE_BYTES;
@@ -213,11 +184,16 @@ __global__ void __launch_bounds__(256, 6) k_slice(const double* __restrict__ X, 
         // 8 consecutive items fill one 128-byte core matrix, 32 consecutive items 512 contiguous bytes
         const int kgi = (it >> 3) & 3, kh = (it >> 5) & 1;
         const int r = (it >> 6) * 8 + (it & 7), g = kh * 4 + kgi;  // A: row r, k-group g; B: column r, k-group g
+        // digits of |F| with F = round(|x| 2^(48-e)); the sign goes onto the BF16 digits afterwards
         Digits D[8];
+        unsigned neg = 0;
+        const int se = (arole ? eR[r] : eC[r]) + 1027;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const double v = arole ? xs[r][8 * g + q] : xs[8 * g + q][r];
-            D[q] = balanced_digits(fixed48(v, arole ? eR[r] : eC[r]));
+            const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+            neg |= (unsigned)(b >> 63) << q;
+            D[q] = balanced_digits((long long)fixed48_mag(b, se));
         }
         uint8_t* base;
         uint32_t pstride;
@@ -231,13 +207,18 @@ __global__ void __launch_bounds__(256, 6) k_slice(const double* __restrict__ X, 
         }
         // odd slices of the A role: rows 64..127 of the stack, 8 row groups (4 KB) further on
         const uint32_t aodd = arole ? 8u * 4u * 128u : 0u;
+        // BF16 sign bits of element pairs (2h, 2h+1): bit 15 and bit 31 of word h
+        const uint32_t m0 = ((neg & 1u) << 15) | ((neg & 2u) << 30);
+        const uint32_t m1 = ((neg & 4u) << 13) | ((neg & 8u) << 28);
+        const uint32_t m2 = ((neg & 16u) << 11) | ((neg & 32u) << 26);
+        const uint32_t m3 = ((neg & 64u) << 9) | ((neg & 128u) << 24);
 #define SPAMM_STORE_SLICE(P)                                                                                 \
         {                                                                                                    \
             uint4 w;                                                                                         \
-            w.x = bf16x2_bits(digit_value<P>(D[0]), digit_value<P>(D[1]));                                   \
-            w.y = bf16x2_bits(digit_value<P>(D[2]), digit_value<P>(D[3]));                                   \
-            w.z = bf16x2_bits(digit_value<P>(D[4]), digit_value<P>(D[5]));                                   \
-            w.w = bf16x2_bits(digit_value<P>(D[6]), digit_value<P>(D[7]));                                   \
+            w.x = bf16x2_bits(digit_value<P>(D[0]), digit_value<P>(D[1])) ^ m0;                              \
+            w.y = bf16x2_bits(digit_value<P>(D[2]), digit_value<P>(D[3])) ^ m1;                              \
+            w.z = bf16x2_bits(digit_value<P>(D[4]), digit_value<P>(D[5])) ^ m2;                              \
+            w.w = bf16x2_bits(digit_value<P>(D[6]), digit_value<P>(D[7])) ^ m3;                              \
             const uint32_t off = arole ? (uint32_t)(P >> 1) * pstride + (uint32_t)(P & 1) * aodd             \
                                        : (uint32_t)P * pstride;                                              \
             *reinterpret_cast<uint4*>(base + off) = w;                                                       \
