@@ -267,7 +267,18 @@ __global__ void __launch_bounds__(1024) k_tree(TreeDev td, double* __restrict__ 
     if (l >= 0) {
         const int dc0 = td.dim[l + 1];
         const double* ch0 = tree + td.off[l + 1];
-        for (int idx = threadIdx.x; idx < dc0 * dc0; idx += blockDim.x) bufA[idx] = ch0[idx];
+        // up to 4096 children: four independent loads per thread, then the shared-memory stores
+        double v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int idx = threadIdx.x + q * 1024;
+            v[q] = idx < dc0 * dc0 ? ch0[idx] : 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int idx = threadIdx.x + q * 1024;
+            if (idx < dc0 * dc0) bufA[idx] = v[q];
+        }
         __syncthreads();
         double* cur = bufA;
         double* nxt = bufB;
