@@ -5,6 +5,7 @@
 // Every arithmetic step runs in the CUDA kernels of kernels_*.cu; this file
 // only orders the launches on the caller's stream and moves data across the
 // host/device boundary when the caller passes host pointers.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -132,6 +133,7 @@ struct Plan {
     int ev_used = 0;
     bool profile = false;
     long long gemm_launches = 0;
+    unsigned long long last_use = 0;  // release order, for evicting the least recently used idle plan
     bool emu = false;        // this call uses the tensor-core (SPAMM_EMU64) leaf products
     bool emu_ready = false;  // slice buffers allocated
     // CUDA graph of the last fixed-iteration solve and what it was captured for
@@ -181,27 +183,45 @@ static void free_plan(Plan* p) {
     delete p;
 }
 
+// Idle cached plans are freed when a device allocation fails; defined after the pool.
+static void free_idle_plans();
+
+// cudaMalloc that, when the device is out of memory, frees the idle cached plans and tries once more.
+static cudaError_t dev_alloc(void** ptr, size_t bytes) {
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        free_idle_plans();
+        e = cudaMalloc(ptr, bytes);
+    }
+    return e;
+}
+template <typename T>
+static cudaError_t dev_alloc(T** ptr, size_t bytes) {
+    return dev_alloc(reinterpret_cast<void**>(ptr), bytes);
+}
+
 static int alloc_plan(Plan* p, int n, int nb) {
     p->g = make_geometry(n, nb);
     const Geometry& g = p->g;
     for (auto& b : p->buf) {
-        CKA(cudaMalloc(&b.t, g.elems() * sizeof(double)));
-        CKA(cudaMalloc(&b.tree, g.tree_size * sizeof(double)));
+        CKA(dev_alloc(&b.t, g.elems() * sizeof(double)));
+        CKA(dev_alloc(&b.tree, g.tree_size * sizeof(double)));
     }
-    CKA(cudaMalloc(&p->counts, (size_t)g.m * g.m * sizeof(int)));
-    CKA(cudaMalloc(&p->jlist, (size_t)g.m * g.m * g.m * sizeof(int)));
-    CKA(cudaMalloc(&p->tile_list, (size_t)g.m * g.m * sizeof(int)));
-    CKA(cudaMalloc(&p->counts2, (size_t)g.m * g.m * sizeof(int)));
-    CKA(cudaMalloc(&p->jlist2, (size_t)g.m * g.m * g.m * sizeof(int)));
-    CKA(cudaMalloc(&p->tile_list2, (size_t)g.m * g.m * sizeof(int)));
+    CKA(dev_alloc(&p->counts, (size_t)g.m * g.m * sizeof(int)));
+    CKA(dev_alloc(&p->jlist, (size_t)g.m * g.m * g.m * sizeof(int)));
+    CKA(dev_alloc(&p->tile_list, (size_t)g.m * g.m * sizeof(int)));
+    CKA(dev_alloc(&p->counts2, (size_t)g.m * g.m * sizeof(int)));
+    CKA(dev_alloc(&p->jlist2, (size_t)g.m * g.m * g.m * sizeof(int)));
+    CKA(dev_alloc(&p->tile_list2, (size_t)g.m * g.m * sizeof(int)));
     CKA(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
     CKA(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
     CKA(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
-    CKA(cudaMalloc(&p->trace_part, (size_t)g.m * sizeof(double)));
-    CKA(cudaMalloc(&p->scal, 16 * sizeof(double)));
-    CKA(cudaMalloc(&p->rowsum, (size_t)n * sizeof(double)));
-    CKA(cudaMalloc(&p->flags, 16 * sizeof(int)));
-    CKA(cudaMalloc(&p->partial, (size_t)g.m * g.m * sizeof(double)));
+    CKA(dev_alloc(&p->trace_part, (size_t)g.m * sizeof(double)));
+    CKA(dev_alloc(&p->scal, 16 * sizeof(double)));
+    CKA(dev_alloc(&p->rowsum, (size_t)n * sizeof(double)));
+    CKA(dev_alloc(&p->flags, 16 * sizeof(int)));
+    CKA(dev_alloc(&p->partial, (size_t)g.m * g.m * sizeof(double)));
     return SPAMM_OK;
 }
 
@@ -212,8 +232,8 @@ static int ensure_hist(Plan* p, int maxit) {
     p->task_ctr = nullptr;
     p->t_hist = nullptr;
     int cap = maxit < 64 ? 64 : maxit;
-    CKA(cudaMalloc(&p->task_ctr, (3 * (size_t)cap + 4) * sizeof(unsigned long long)));
-    CKA(cudaMalloc(&p->t_hist, (size_t)cap * sizeof(double)));
+    CKA(dev_alloc(&p->task_ctr, (3 * (size_t)cap + 4) * sizeof(unsigned long long)));
+    CKA(dev_alloc(&p->t_hist, (size_t)cap * sizeof(double)));
     p->maxit_cap = cap;
     return SPAMM_OK;
 }
@@ -223,9 +243,9 @@ static int ensure_emu(Plan* p) {
     const Geometry& g = p->g;
     const size_t per = emu_slice_bytes_per_tile() * (size_t)g.m * g.m;
     for (auto& b : p->buf) {
-        CKA(cudaMalloc(&b.sliceA, per));
-        CKA(cudaMalloc(&b.sliceB, per));
-        CKA(cudaMalloc(&b.rmax, 2 * (size_t)g.m * g.nb * sizeof(unsigned long long)));
+        CKA(dev_alloc(&b.sliceA, per));
+        CKA(dev_alloc(&b.sliceB, per));
+        CKA(dev_alloc(&b.rmax, 2 * (size_t)g.m * g.nb * sizeof(unsigned long long)));
         b.cmax = b.rmax + (size_t)g.m * g.nb;
     }
     p->emu_ready = true;
@@ -234,7 +254,7 @@ static int ensure_emu(Plan* p) {
 
 static int ensure_stage(Plan* p, int which) {
     if (p->stage[which]) return SPAMM_OK;
-    CKA(cudaMalloc(&p->stage[which], (size_t)p->g.n * p->g.n * sizeof(double)));
+    CKA(dev_alloc(&p->stage[which], (size_t)p->g.n * p->g.n * sizeof(double)));
     return SPAMM_OK;
 }
 
@@ -280,9 +300,30 @@ class PlanPool {
         *out = p;
         return SPAMM_OK;
     }
+    // Idle plans are kept for reuse up to a quarter of the device's memory; beyond that the least
+    // recently released ones are freed.
     void release(Plan* p) {
         std::lock_guard<std::mutex> lk(mu_);
+        p->last_use = ++clock_;
         free_[std::make_tuple(p->device, p->g.n, p->g.nb)].push_back(p);
+        const size_t cap = idle_cap(p->device);
+        for (;;) {
+            size_t idle = 0;
+            Plan* oldest = nullptr;
+            std::vector<Plan*>* where = nullptr;
+            for (auto& kv : free_)
+                for (Plan* q : kv.second) {
+                    if (q->device != p->device) continue;
+                    idle += plan_bytes(q);
+                    if (!oldest || q->last_use < oldest->last_use) {
+                        oldest = q;
+                        where = &kv.second;
+                    }
+                }
+            if (idle <= cap || !oldest || oldest == p) break;
+            where->erase(std::find(where->begin(), where->end(), oldest));
+            free_plan(oldest);
+        }
     }
     void clear() {
         std::lock_guard<std::mutex> lk(mu_);
@@ -307,11 +348,31 @@ class PlanPool {
     }
 
   private:
+    static size_t idle_cap(int device) {
+        static std::mutex m;
+        static std::map<int, size_t> caps;
+        std::lock_guard<std::mutex> lk(m);
+        auto it = caps.find(device);
+        if (it != caps.end()) return it->second;
+        size_t fr = 0, tot = 0;
+        int cur = 0;
+        cudaGetDevice(&cur);
+        cudaSetDevice(device);
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+            cudaGetLastError();
+            tot = (size_t)16 << 30;
+        }
+        cudaSetDevice(cur);
+        return caps[device] = tot / 4;
+    }
     std::mutex mu_;
+    unsigned long long clock_ = 0;
     std::map<std::tuple<int, int, int>, std::vector<Plan*>> free_;
 };
 
 static PlanPool g_pool;
+
+static void free_idle_plans() { g_pool.clear(); }
 
 struct PlanGuard {
     Plan* p = nullptr;

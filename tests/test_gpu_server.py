@@ -53,3 +53,20 @@ def test_server_rejects_oversize_and_unknown():
         with pytest.raises(sp.SpammError) as ei:
             srv.poll(12345)
         assert ei.value.status == -9
+
+
+def test_plan_cache_stays_bounded_over_many_sizes():
+    """Plans are cached per size; across many distinct sizes the idle cache is evicted (least recently used
+    first) so that it never holds more than a quarter of the device, and the caller's own allocations keep
+    succeeding."""
+    free0, total = torch.cuda.mem_get_info()
+    for k in range(48):
+        n = 3008 + 64 * k
+        S = torch.eye(n, dtype=torch.float64, device="cuda") * 0.5
+        Y, Z, st = sp.sqrt_invsqrt(S, 1e-8, 1, leaf=64, precision=sp.EMU64)
+        del S, Y, Z
+        torch.cuda.empty_cache()
+        free, _ = torch.cuda.mem_get_info()
+        # idle plans <= total/4, plus the plan in use, plus torch's own tensors of this step
+        assert free0 - free <= total // 4 + (4 << 30), (k, free0 - free)
+    sp.release()
