@@ -69,7 +69,8 @@ extern "C" {
                                      transpose of the printed iteration        */
 
 typedef struct spamm_opts {
-    int leaf;          /* N_b: 32, 64 or 128; 0 selects 64                      */
+    int leaf;          /* N_b: 32, 64 or 128; 0 = chosen by spamm_autotune_leaf
+                          on the call's own input                               */
     int precision;     /* SPAMM_FP64 or SPAMM_EMU64                             */
     double tau_s;      /* y-channel threshold; < 0 selects 0.01 * tau           */
     double mu_rel;     /* Tikhonov shift S + mu I (Sec. 6) with
@@ -101,6 +102,18 @@ typedef struct spamm_stats {
 /* Fill *opts with defaults: leaf 64, SPAMM_FP64, tau_s = 0.01 tau, no shift,
  * fixed iteration count, paper order, no residual, default stream. */
 void spamm_opts_init(spamm_opts* opts);
+
+/*
+ * Leaf-tile size for problems like S: times one SpAMM product S (x)_tau S
+ * at every leaf size the arithmetic supports (32, 64 and 128 for
+ * SPAMM_FP64; SPAMM_EMU64 runs on 64 only) and returns the fastest in
+ * *leaf.  The choice is cached per device, n, arithmetic and decade of tau,
+ * so later calls return at once; entry points given opts->leaf = 0 use it.
+ * S is n x n row-major FP64, host or device; opts may be NULL (its leaf is
+ * ignored).  The trial products run on opts->stream and are synchronised.
+ * Errors: SPAMM_ERR_ARG (n, tau, null pointer), SPAMM_ERR_NOMEM, SPAMM_ERR_CUDA.
+ */
+int spamm_autotune_leaf(const double* S, int n, double tau, const spamm_opts* opts, int* leaf);
 
 /*
  * C = A (x)_tau B, Eq. (newspamm), with the relative criterion

@@ -234,6 +234,37 @@ __global__ void __launch_bounds__(256, 6) k_slice(const double* __restrict__ X, 
     }
 }
 
+// Double-word FP32 accumulation (hi + lo, about 2^-44 relative) of the
+// squares of FP64 values: FP64 arithmetic is slow on this part, so the
+// per-tile sums of squares use FP32 pairs.
+struct DFloat {
+    float hi, lo;
+};
+__device__ __forceinline__ DFloat df_add(DFloat x, DFloat y) {
+    const float s = x.hi + y.hi;
+    const float bb = s - x.hi;
+    const float e = ((x.hi - (s - bb)) + (y.hi - bb)) + (x.lo + y.lo);
+    const float h = s + e;
+    return DFloat{h, e - (h - s)};
+}
+// v * v as a double-word: v split into its leading 24 mantissa bits and the rest.
+__device__ __forceinline__ DFloat df_square(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+    const int E = (int)(b >> 52);
+    const int fe = E - 1023 + 127;
+    if (E == 0 || fe <= 0 || fe >= 255) return DFloat{0.f, 0.f};  // zero, or below FP32 range (negligible)
+    const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
+    const float hi = __uint_as_float(((unsigned)fe << 23) | (unsigned)(mant >> 29));
+    const int le = E - 1023 - 52 + 127;  // exponent of the low 29 bits' unit
+    const float lo = le > 0 ? (float)(unsigned)(mant & 0x1FFFFFFFull) * __uint_as_float((unsigned)le << 23) : 0.f;
+    const float p = hi * hi;
+    const float pe = fmaf(hi, hi, -p);
+    return DFloat{p, fmaf(2.0f * hi, lo, pe)};
+}
+__device__ __forceinline__ DFloat df_shfl_xor(DFloat x, int o) {
+    return DFloat{__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o)};
+}
+
 // Row and column magnitude maxima (as IEEE bits) of a packed FP64 matrix.
 __global__ void __launch_bounds__(256) k_rowcol_max(const double* __restrict__ X, int m,
                                                     unsigned long long* __restrict__ rmax,
@@ -269,6 +300,8 @@ struct EmuArgs {
     const unsigned long long* rmaxA;    // row maxima of the left operand
     const unsigned long long* cmaxB;    // column maxima of the right operand
     double* C;                          // FP64 output tiles
+    double* leafC;                      // output leaf norms (squared Frobenius, double-word FP32 sums)
+    int* slice_list;                    // copy of the drawn tiles ([m*m] ids, count at [m*m]) for slicing
     unsigned long long* rmaxC;          // output row / column maxima (pre-zeroed)
     unsigned long long* cmaxC;
     const int* counts;
@@ -400,6 +433,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
     __shared__ int tile_sh[2];
     __shared__ int eA_sh[2][NB], eB_sh[2][NB];
     __shared__ double tr_sh[kEpiWarps];
+    __shared__ DFloat nu_sh[kEpiWarps];
     __shared__ int abort_sh;
 
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dyn_smem) + 1023) & ~uintptr_t(1023));
@@ -409,6 +443,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
     const int m = a.m;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ntiles = *a.tile_count;
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.slice_list[m * m] = ntiles;
     if ((int)blockIdx.x >= ntiles) return;
 
     if (warp == 2 && lane == 0) {
@@ -499,6 +534,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
             if (lane == 0) {
                 ntask_sh[slot] = T;
                 tile_sh[slot] = tile;
+                a.slice_list[idx] = tile;
             }
             __syncwarp();
             if (lane == 0) {
@@ -646,6 +682,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
             }
             const int sc = eBc - 48 - (nsx ? 1 : 0);
             unsigned long long cmx = 0;
+            DFloat nup = {0.f, 0.f};
             unsigned rowm = 0;  // lane q: upper magnitude bits of row r0 + 8q over this warp's 32 columns
             for (int q0 = 0; q0 < 8; q0 += 8) {
 #pragma unroll
@@ -655,6 +692,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
                     double v = fixed_to_double(nsx ? -t64 : t64, eA_sh[slot][r] + sc);
                     v = r == rd ? vd : v;
                     outt[r * NB + c] = v;  // consecutive lanes: consecutive columns
+                    nup = df_add(nup, df_square(v));
                     const unsigned long long vb = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
                     cmx = max(cmx, vb);
                     // the maxima only feed the slicing exponents: the upper 32 bits carry the exponent exactly
@@ -664,6 +702,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
             }
             if (cmx) atomicMax(a.cmaxC + gj, cmx);
             if (lane < 8 && rowm) atomicMax(a.rmaxC + i * NB + r0 + 8 * lane, (unsigned long long)rowm << 32);
+            for (int o = 16; o > 0; o >>= 1) nup = df_add(nup, df_shfl_xor(nup, o));
+            if (lane == 0) nu_sh[ew] = nup;
             const bool diag_tile = nsx && i == k;
             if (diag_tile) {
                 double tr = rd >= 0 ? xd : 0.0;
@@ -672,10 +712,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
             }
             // every epilogue warp is done with the staging buffer (and tr_sh holds the trace partials)
             ptx::named_sync(1, 32 * kEpiWarps);
-            if (diag_tile && et == 0) {
-                double s8 = 0.0;
-                for (int w = 0; w < kEpiWarps; ++w) s8 += tr_sh[w];
-                a.trace_part[i] = s8;
+            if (et == 0) {
+                DFloat t = nu_sh[0];
+                for (int w = 1; w < kEpiWarps; ++w) t = df_add(t, nu_sh[w]);
+                a.leafC[tile] = (double)t.hi + (double)t.lo;
+                if (diag_tile) {
+                    double s8 = 0.0;
+                    for (int w = 0; w < kEpiWarps; ++w) s8 += tr_sh[w];
+                    a.trace_part[i] = s8;
+                }
             }
             if (lane == 0) ptx::mbar_arrive(&bar_tfree[slot]);
         }
@@ -733,6 +778,8 @@ void launch_gemm_emu(const Geometry& g, const TileMat& A, const TileMat& B, cons
     a.rmaxA = A.rmax;
     a.cmaxB = B.cmax;
     a.C = C.t;
+    a.leafC = C.tree;
+    a.slice_list = C.slice_list;
     a.rmaxC = C.rmax;
     a.cmaxC = C.cmax;
     a.counts = counts;

@@ -6,6 +6,7 @@
 // only orders the launches on the caller's stream and moves data across the
 // host/device boundary when the caller passes host pointers.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -118,6 +119,11 @@ struct Plan {
     int* tile_list2 = nullptr;
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // tensor-core path: the slicing of a product output runs on its own stream per branch, beside the
+    // tree and the next culls; ev_norm orders it after the output's norm pass
+    cudaStream_t slice_st[2] = {nullptr, nullptr};
+    cudaEvent_t ev_norm[2] = {nullptr, nullptr};
+    unsigned sliced_mask = 0;  // buffers whose `sliced` event this call recorded
     unsigned long long* task_ctr = nullptr;  // [3 * maxit_cap + 4]
     double* t_hist = nullptr;                // [maxit_cap]
     int maxit_cap = 0;
@@ -156,6 +162,12 @@ static void free_plan(Plan* p) {
         cudaFree(b.sliceA);
         cudaFree(b.sliceB);
         cudaFree(b.rmax);
+        cudaFree(b.slice_list);
+        if (b.sliced) cudaEventDestroy(b.sliced);
+    }
+    for (int q = 0; q < 2; ++q) {
+        if (p->slice_st[q]) cudaStreamDestroy(p->slice_st[q]);
+        if (p->ev_norm[q]) cudaEventDestroy(p->ev_norm[q]);
     }
     cudaFree(p->counts);
     cudaFree(p->jlist);
@@ -247,6 +259,12 @@ static int ensure_emu(Plan* p) {
         CKA(dev_alloc(&b.sliceB, per));
         CKA(dev_alloc(&b.rmax, 2 * (size_t)g.m * g.nb * sizeof(unsigned long long)));
         b.cmax = b.rmax + (size_t)g.m * g.nb;
+        CKA(dev_alloc(&b.slice_list, ((size_t)g.m * g.m + 1) * sizeof(int)));
+        CKA(cudaEventCreateWithFlags(&b.sliced, cudaEventDisableTiming));
+    }
+    for (int q = 0; q < 2; ++q) {
+        CKA(cudaStreamCreateWithFlags(&p->slice_st[q], cudaStreamNonBlocking));
+        CKA(cudaEventCreateWithFlags(&p->ev_norm[q], cudaEventDisableTiming));
     }
     p->emu_ready = true;
     return SPAMM_OK;
@@ -261,12 +279,15 @@ static int ensure_stage(Plan* p, int which) {
 // Device bytes one plan holds (tile buffers, trees, task lists, slices for
 // the tensor-core path, row-major staging when the caller passes host memory).
 size_t plan_footprint(int n, int nb, int precision, bool host_io) {
+    // leaf 0 (chosen later by the autotuner): the largest scratch among the sizes it may pick
+    if (nb == 0) nb = precision == SPAMM_EMU64 ? 64 : 32;
     const Geometry g = make_geometry(n, nb);
     size_t b = 6 * (g.elems() + (size_t)g.tree_size) * sizeof(double);
     b += 2 * ((size_t)g.m * g.m * (g.m + 2)) * sizeof(int) + (size_t)g.m * sizeof(double) + (size_t)n * sizeof(double) +
          (size_t)g.m * g.m * sizeof(double) + 4096;
     if (precision == SPAMM_EMU64)
-        b += 6 * (2 * emu_slice_bytes_per_tile() * (size_t)g.m * g.m + 2 * (size_t)g.m * g.nb * 8);
+        b += 6 * (2 * emu_slice_bytes_per_tile() * (size_t)g.m * g.m + 2 * (size_t)g.m * g.nb * 8 +
+                  ((size_t)g.m * g.m + 1) * sizeof(int));
     if (host_io) b += 3 * (size_t)n * n * sizeof(double);
     return b;
 }
@@ -387,8 +408,7 @@ static spamm_opts resolve_opts(const spamm_opts* o) {
     spamm_opts r;
     spamm_opts_init(&r);
     if (o) r = *o;
-    if (r.leaf == 0) r.leaf = 64;
-    return r;
+    return r;  // leaf 0 stays 0: the call resolves it with the autotuner
 }
 
 // Device view of a caller matrix: the pointer itself, or a staged copy.
@@ -427,6 +447,7 @@ static void begin_call(Plan* p, bool profile, bool emu) {
     p->emu = emu;
     p->ev_used = 0;
     p->gemm_launches = 0;
+    p->sliced_mask = 0;
 }
 
 static cudaEvent_t next_event(Plan* p) {
@@ -450,6 +471,15 @@ static double profiled_ms(Plan* p) {
 }
 
 // One SpAMM product of two packed operands into dst (tree leaves + levels).
+// Records that M's slices are complete once `st` reaches this point.
+static void mark_sliced(Plan* p, const TileMat& M, cudaStream_t st) {
+    for (int q = 0; q < 6; ++q)
+        if (p->buf[q].t == M.t) {
+            cudaEventRecord(p->buf[q].sliced, st);
+            p->sliced_mask |= 1u << q;
+        }
+}
+
 // The output-tile counter (flags[3]) is zero on entry (the call's flag reset,
 // then the tree pass of the previous product); the tree pass may also carry
 // the iteration's trace error (tk).
@@ -466,6 +496,11 @@ static void product(Plan* p, const TileMat& A, const TileMat& B, TileMat& C, dou
         co.zero_n = 2 * (long)g.m * g.nb;
     }
     launch_cull(g, A.tree, B.tree, tau, co, ctr, nullptr, p->flags, st);
+    if (p->emu) {
+        // the operands' slices may still be in flight on a slicing stream
+        cudaStreamWaitEvent(st, A.sliced, 0);
+        if (B.sliced != A.sliced) cudaStreamWaitEvent(st, B.sliced, 0);
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (p->profile) {
         e0 = next_event(p);
@@ -482,10 +517,20 @@ static void product(Plan* p, const TileMat& A, const TileMat& B, TileMat& C, dou
     }
     if (e0 && e1) cudaEventRecordWithFlags(e1, st, cudaEventRecordExternal);
     p->gemm_launches++;
-    // tensor-core path: the slicing pass also computes the output's leaf norms, before the tree sums them
-    if (p->emu)
-        launch_slice(C.t, nullptr, C.tree, C.rmax, C.cmax, C.sliceA, C.sliceB, g, tile_list, tile_count,
-                     p->flags, st);
+    if (p->emu) {
+        // tensor-core path: the leaf-product kernel wrote the output's leaf norms (all the tree and the next
+        // culls need); its slices follow on the branch's slicing stream, beside the tree and the next culls.
+        // A profiled call keeps everything on one stream so that kernel timings are the kernels' own
+        cudaStream_t ss = p->profile ? st : p->slice_st[slot];
+        if (ss != st) {
+            cudaEventRecord(p->ev_norm[slot], st);
+            cudaStreamWaitEvent(ss, p->ev_norm[slot], 0);
+        }
+        const int mm = g.m * g.m;
+        launch_slice(C.t, C.tree, nullptr, C.rmax, C.cmax, C.sliceA, C.sliceB, g, C.slice_list,
+                     C.slice_list + mm, p->flags, ss);
+        mark_sliced(p, C, ss);
+    }
     TreeExtra ex = tk ? *tk : TreeExtra();
     ex.zero_int = tile_count;
     launch_tree(g, C.tree, p->flags, st, ex);
@@ -497,9 +542,18 @@ static void prepare_emu(Plan* p, const TileMat& M, cudaStream_t st) {
     cudaMemsetAsync(M.rmax, 0, 2 * (size_t)g.m * g.nb * sizeof(unsigned long long), st);
     launch_rowcol_max(M.t, g, M.rmax, M.cmax, st);
     launch_slice(M.t, M.tree, nullptr, M.rmax, M.cmax, M.sliceA, M.sliceB, g, nullptr, nullptr, nullptr, st);
+    mark_sliced(p, M, st);
 }
 
-static int multiply_impl(const double* A, const double* B, double* C, int n, double tau, const spamm_opts& o,
+// Every slicing stream of this call joins the call's stream (before the outputs are read, and before a
+// capture ends); only events recorded by this call are waited on.
+static void join_slicing(Plan* p, cudaStream_t st) {
+    for (int q = 0; q < 6; ++q)
+        if (p->sliced_mask & (1u << q)) cudaStreamWaitEvent(st, p->buf[q].sliced, 0);
+    p->sliced_mask = 0;
+}
+
+static int multiply_core(const double* A, const double* B, double* C, int n, double tau, const spamm_opts& o,
                          spamm_stats* stats) {
     cudaStream_t st = (cudaStream_t)o.stream;
     init_device_attributes();
@@ -527,6 +581,7 @@ static int multiply_impl(const double* A, const double* B, double* C, int n, dou
         prepare_emu(p, p->buf[1], st);
     }
     product(p, p->buf[0], p->buf[1], p->buf[2], tau, EPI_PLAIN, p->task_ctr, st);
+    join_slicing(p, st);
     launch_unpack(p->buf[2].t, p->buf[2].tree, g, dC, nullptr, nullptr, st);
     CK(cudaGetLastError());
     if ((e = stage_out(p, 2, C, dC, st))) return e;
@@ -554,6 +609,78 @@ static int multiply_impl(const double* A, const double* B, double* C, int n, dou
 }
 
 // ||Z S Z - I||_F in FP64 with dense products (verification only).
+// ---- leaf-size autotuner (opts.leaf = 0) --------------------------------
+// Times one SpAMM product S (x)_tau S at every leaf size the arithmetic
+// supports (32, 64, 128 for SPAMM_FP64; SPAMM_EMU64 runs on 64 only) and keeps
+// the fastest, per device, size, arithmetic and decade of tau.
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int, int>, int> g_tune;
+
+static int tau_decade(double tau) { return tau > 0.0 ? (int)std::floor(std::log10(tau)) : -1000; }
+
+static int autotune_leaf_impl(const double* S, int n, double tau, const spamm_opts& o, int* leaf) {
+    if (o.precision == SPAMM_EMU64) {
+        *leaf = 64;
+        return SPAMM_OK;
+    }
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    const auto key = std::make_tuple(dev, n, o.precision, tau_decade(tau));
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            *leaf = it->second;
+            return SPAMM_OK;
+        }
+    }
+    double* C = nullptr;
+    CKA(dev_alloc(&C, (size_t)n * n * sizeof(double)));
+    int best = 64;
+    double best_s = 1e300;
+    const int cands[3] = {32, 64, 128};
+    for (int nb : cands) {
+        if ((n + nb - 1) / nb > 1024) continue;
+        spamm_opts t = o;
+        t.leaf = nb;
+        t.profile = 0;
+        t.residual = 0;
+        int e = multiply_core(S, S, C, n, tau, t, nullptr);  // first call: plan allocation, caches warm
+        if (e == SPAMM_OK) {
+            const auto t0 = std::chrono::steady_clock::now();
+            e = multiply_core(S, S, C, n, tau, t, nullptr);
+            const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            if (e == SPAMM_OK && dt < best_s) {
+                best_s = dt;
+                best = nb;
+            }
+        }
+        if (e) {
+            cudaFree(C);
+            return e;
+        }
+    }
+    cudaFree(C);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = best;
+    *leaf = best;
+    return SPAMM_OK;
+}
+
+// opts with leaf 0 resolved by the autotuner on the call's own input.
+static int with_leaf(const double* S, int n, double tau, const spamm_opts& o, spamm_opts* out) {
+    *out = o;
+    if (o.leaf) return SPAMM_OK;
+    return autotune_leaf_impl(S, n, tau, o, &out->leaf);
+}
+
+static int multiply_impl(const double* A, const double* B, double* C, int n, double tau, const spamm_opts& o_in,
+                         spamm_stats* stats) {
+    spamm_opts o;
+    const int e = with_leaf(A, n, tau, o_in, &o);
+    return e ? e : multiply_core(A, B, C, n, tau, o, stats);
+}
+
 static int residual_impl(Plan* p, const double* dS, const double* dZ, double* out, cudaStream_t st) {
     const Geometry& g = p->g;
     launch_pack(dS, g.n, g, nullptr, nullptr, p->buf[3], st);
@@ -659,6 +786,7 @@ static int enqueue_solve(Plan* p, const double* dS, double* dY, double* dZ, int 
     }
 
     // a7: unscale and unpack
+    join_slicing(p, st);
     launch_unpack(Yb.t, Yb.tree, g, dY, sqc, nullptr, st);
     launch_unpack(Zb.t, Zb.tree, g, dZ, nullptr, sqc, st);
     CK(cudaGetLastError());
@@ -721,8 +849,13 @@ static int solve_graph(Plan* p, const double* dS, double* dY, double* dZ, int n,
     return SPAMM_OK;
 }
 
-static int sqrt_impl(const double* S, int n, double tau, int maxit, double* Y, double* Z, const spamm_opts& o,
+static int sqrt_impl(const double* S, int n, double tau, int maxit, double* Y, double* Z, const spamm_opts& o_in,
                      spamm_stats* stats) {
+    spamm_opts o;
+    {
+        const int e = with_leaf(S, n, tau, o_in, &o);
+        if (e) return e;
+    }
     cudaStream_t st = (cudaStream_t)o.stream;
     const double tau_s = o.tau_s < 0.0 ? 0.01 * tau : o.tau_s;
     init_device_attributes();
@@ -812,8 +945,8 @@ static int check_common(int n, double tau, const spamm_opts& o) {
         g_last_error = "tau must be finite and >= 0";
         return SPAMM_ERR_ARG;
     }
-    if (!leaf_ok(o.leaf)) {
-        g_last_error = "leaf must be 32, 64 or 128";
+    if (o.leaf != 0 && !leaf_ok(o.leaf)) {
+        g_last_error = "leaf must be 0 (autotune), 32, 64 or 128";
         return SPAMM_ERR_ARG;
     }
     if (o.precision != SPAMM_FP64 && o.precision != SPAMM_EMU64) {
@@ -828,8 +961,9 @@ static int check_common(int n, double tau, const spamm_opts& o) {
         g_last_error = "tau_s, mu_rel, tol_t must be numbers (mu_rel, tol_t >= 0)";
         return SPAMM_ERR_ARG;
     }
-    const long m = (n + o.leaf - 1) / o.leaf;
-    if (o.precision == SPAMM_EMU64 && (o.leaf != 64 || m > 512)) {
+    const int leaf = o.leaf ? o.leaf : (o.precision == SPAMM_EMU64 ? 64 : 128);
+    const long m = (n + leaf - 1) / leaf;
+    if (o.precision == SPAMM_EMU64 && (leaf != 64 || m > 512)) {
         g_last_error = "SPAMM_EMU64 needs leaf 64 and n <= 32768";
         return SPAMM_ERR_UNSUPPORTED;
     }
@@ -872,6 +1006,24 @@ void spamm_opts_init(spamm_opts* o) {
     o->order = SPAMM_ORDER_PAPER;
     o->residual = 0;
     o->stream = nullptr;
+}
+
+int spamm_autotune_leaf(const double* S, int n, double tau, const spamm_opts* opts, int* leaf) {
+    try {
+        g_last_error.clear();
+        spamm_opts o = resolve_opts(opts);
+        o.leaf = 0;
+        int e = check_common(n, tau, o);
+        if (e) return e;
+        if (!S || !leaf) {
+            g_last_error = "null pointer";
+            return SPAMM_ERR_ARG;
+        }
+        return autotune_leaf_impl(S, n, tau, o, leaf);
+    } catch (...) {
+        g_last_error = "internal exception";
+        return SPAMM_ERR_CUDA;
+    }
 }
 
 int spamm_multiply(const double* A, const double* B, double* C, int n, double tau, const spamm_opts* opts,

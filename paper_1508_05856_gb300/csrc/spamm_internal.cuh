@@ -39,6 +39,11 @@ struct TileMat {
     uint8_t* sliceB = nullptr;
     unsigned long long* rmax = nullptr;  // [m*nb], followed by
     unsigned long long* cmax = nullptr;  // [m*nb]
+    // tensor-core path: the output tiles to slice ([m*m] tile ids, then their count), copied by the
+    // leaf-product kernel so that slicing can run beside the next cull; and the event recorded once the
+    // slices are written
+    int* slice_list = nullptr;
+    cudaEvent_t sliced = nullptr;
 };
 
 // Geometry passed by value to kernels.
@@ -191,9 +196,10 @@ void launch_rowcol_max(const double* X, const Geometry& g, unsigned long long* r
 void launch_slice(const double* X, const double* leaf, double* leaf_out, const unsigned long long* rmax,
                   const unsigned long long* cmax, uint8_t* sA, uint8_t* sB, const Geometry& g, const int* tile_list,
                   const int* tile_count, const int* done, cudaStream_t st);
-// Leaf products on the tensor cores; writes C's FP64 tiles and row/column
-// maxima (pre-zeroed), trace partials for EPI_NS_X; *err set on a timed-out
-// internal wait.  C's leaf norms come from launch_slice with leaf_out set.
+// Leaf products on the tensor cores; writes C's FP64 tiles, leaf norms
+// (double-word FP32 sums, about 2^-44 relative), row/column maxima
+// (pre-zeroed), trace partials for EPI_NS_X, and C.slice_list; *err set on a
+// timed-out internal wait.
 // sched: two ints, zero before the first launch; the kernel leaves them zero.
 void launch_gemm_emu(const Geometry& g, const TileMat& A, const TileMat& B, const TileMat& C, const int* counts,
                      const int* jlist, const int* tile_list, const int* tile_count, EpiMode mode, double* trace_part,

@@ -80,3 +80,14 @@ def test_server_create_rejects_bad_budget_without_device():
     assert L.spamm_server_create(0, 2, None, ctypes.byref(h)) == -1
     assert L.spamm_server_create(1 << 20, 0, None, ctypes.byref(h)) == -1
     assert L.spamm_server_destroy(None) == -1
+
+
+def test_autotune_rejects_bad_arguments_without_device():
+    L = sp.lib()
+    buf = (ctypes.c_double * 16)()
+    leaf = ctypes.c_int(-1)
+    assert L.spamm_autotune_leaf(buf, 0, 1e-6, None, ctypes.byref(leaf)) == -1
+    assert L.spamm_autotune_leaf(buf, 4, -1.0, None, ctypes.byref(leaf)) == -1
+    assert L.spamm_autotune_leaf(None, 4, 1e-6, None, ctypes.byref(leaf)) == -1
+    assert L.spamm_autotune_leaf(buf, 4, 1e-6, None, None) == -1
+    assert leaf.value == -1

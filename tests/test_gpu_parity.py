@@ -205,3 +205,16 @@ def test_graph_replay_identical_and_profiled():
         assert st["gemm_ms"] > 0 and st["gemm_launches"] == 36
     torch.zeros(4, device="cuda").add_(1)
     torch.cuda.synchronize()
+
+
+def test_leaf_autotuner():
+    """leaf = 0 resolves to the autotuner's choice on the call's input: one of the supported sizes, cached,
+    and the solve is the one that leaf size gives explicitly (bitwise)."""
+    S = dev(synth.gaussian_lattice(600, 0.7, seed=11))
+    leaf = sp.autotune_leaf(S, 1e-8)
+    assert leaf in (32, 64, 128)
+    assert sp.autotune_leaf(S, 1e-8) == leaf
+    Y0, Z0, _ = sp.sqrt_invsqrt(S, 1e-8, 12, leaf=0)
+    Y1, Z1, _ = sp.sqrt_invsqrt(S, 1e-8, 12, leaf=leaf)
+    assert torch.equal(Y0, Y1) and torch.equal(Z0, Z1)
+    assert sp.autotune_leaf(S, 1e-8, precision=sp.EMU64) == 64
