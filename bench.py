@@ -363,15 +363,16 @@ def run_gpu(args, ws, rank, local):
         peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
         peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
         peak = peaks.get("bf16_tflops", 1900.0)
-        # 12 stacked M=128 x N=64 MMA pairs x 4 K-steps of 16 per task: 2*128*64*64*12 flop on the tensor pipe
+        # 12 stacked M=128 x N=64 slice pairs over K = 64 per task: 2*128*64*64*12 flop on the FP16 tensor pipe
         issued = achieved * (2.0 * 128 * 64 * 64 * 12) / (2.0 * LEAF ** 3)
         tasks_per_launch = gemm_flops / max(1, gemm_launches) / (2.0 * LEAF ** 3)
         roof = {"bound": "tensor", "achieved": issued, "peak": peak, "unit": "TFLOP/s",
                 "frac": issued / peak if peak else None,
                 "traffic": captured_traffic("k_gemm_emu", tasks_per_launch), "kernel": "spamm::emu::k_gemm_emu",
-                "achieved_counts": "BF16 tensor-pipe flops issued (24x the FP64-equivalent useful flops)",
+                "achieved_counts": "FP16 tensor-pipe flops issued (24x the FP64-equivalent useful flops)",
                 "useful_fp64_equiv_tflops": achieved,
-                "peak_source": "bf16_tflops of measured" if peaks else "fallback 1.9 PFLOP/s",
+                "peak_source": ("bf16_tflops of measured x 1.0 (FP16 and BF16 dense rates are equal)" if peaks
+                                else "fallback 1.9 PFLOP/s"),
                 "share_of_step": gemm_ms / 1e3 / prof_s if prof_s else None}
 
     cpu = None
@@ -387,7 +388,7 @@ def run_gpu(args, ws, rank, local):
     p99 = sorted(step_s)[min(len(step_s) - 1, int(math.ceil(0.99 * len(step_s))) - 1)] * 1e3
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * tot_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == sp.FP64 else "bf16-split",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == sp.FP64 else "f16-split",
             "data": "synthetic",
             "config": {"workload": workload_name(tau, args.precision.upper()), "n": N, "leaf": LEAF, "tau": tau,
                        "tau_s": 0.01 * tau, "maxit": MAXIT, "precision": args.precision,
@@ -437,7 +438,7 @@ def run_batched(args, local):
     torch.cuda.synchronize()
     t_seq = time.perf_counter() - t0
     line = {"metric": "batched NS solves/s (mixed KMS / 3D Gaussian, N in [128, 2048])", "value": len(Ss) / t_batch,
-            "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": "f64" if prec == sp.FP64 else "bf16-split",
+            "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": "f64" if prec == sp.FP64 else "f16-split",
             "data": "synthetic",
             "config": {"workload": f"{len(Ss)} matrices, sizes log-uniform in [128, 2048] (multiples of 32), "
                                    f"50% KMS rho~U(0.5,0.95), 50% Gaussian sigma~U(0.6,0.9), tau={args.batch_tau:g}, "
@@ -490,7 +491,7 @@ def run_serve(args, local):
     t_seq = time.perf_counter() - t0
     lat = np.array(lats) * 1e3
     line = {"metric": "served NS requests: solves/s with p50/p99 latency", "value": len(ids) / t_all, "unit": UNIT,
-            "n_gpus": 1, "higher_is_better": True, "dtype": "f64" if prec == sp.FP64 else "bf16-split",
+            "n_gpus": 1, "higher_is_better": True, "dtype": "f64" if prec == sp.FP64 else "f16-split",
             "data": "synthetic",
             "config": {"workload": f"{len(ids)} requests, Poisson arrivals at {args.rate:g}/s, N log-uniform in "
                                    f"[256, {args.serve_max_n}] (multiples of 32), 3D Gaussian decay, tau in "
@@ -555,7 +556,7 @@ def run_c3(args, local):
     best = max((r for r in rows if r["gate_met"]), key=lambda r: r["solves_per_s"], default=rows[-1])
     line = {"metric": f"NS solves/s at ||ZSZ-I||_F<=1e-8 (3D Gaussian N={args.c3_n})", "value": best["solves_per_s"],
             "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
-            "dtype": "f64" if prec == sp.FP64 else "bf16-split", "data": "synthetic",
+            "dtype": "f64" if prec == sp.FP64 else "f16-split", "data": "synthetic",
             "config": {"workload": f"3D Gaussian decay sigma={args.c3_sigma} on {args.c3_n} jittered Morton-ordered "
                                    f"lattice points, N_b={LEAF}, {MAXIT} iterations, mu_rel={args.c3_mu}",
                        "precision": args.precision, "tau_best": best["tau"]},

@@ -59,7 +59,7 @@ extern "C" {
 
 /* ---- arithmetic of the leaf-tile products ------------------------------ */
 #define SPAMM_FP64 0   /* FP64 tiles, FP64 fused multiply-add                  */
-#define SPAMM_EMU64 1  /* FP64 tiles split into 8-bit BF16 slices multiplied on
+#define SPAMM_EMU64 1  /* FP64 tiles split into six 8-bit digit slices (FP16) on
                           the tensor cores with exact FP32 partial sums and
                           64-bit accumulation (FP64-class result)              */
 

@@ -1,8 +1,8 @@
-// SPAMM_EMU64: FP64-class SpAMM leaf products on the BF16 tensor cores.
+// SPAMM_EMU64: FP64-class SpAMM leaf products on the 16-bit tensor cores.
 //
 // Why: the dual-channel iteration (Eq. (cannonical)) does not damp errors
 // injected into its products, so a 1e-8 residual needs products accurate to
-// about FP64; GB300 has little FP64 throughput but a large BF16 one.  Every
+// about FP64; GB300 has little FP64 throughput but a large FP16/BF16 one.  Every
 // matrix is therefore held both as FP64 tiles and as six 8-bit "slices":
 //
 //   x ~ 2^e * sum_{p=0..5} d_p 2^{-8(p+1)},  balanced digits |d_p| <= 128,
@@ -10,7 +10,7 @@
 //
 // where 2^(e-1) bounds the largest magnitude of x's row (operand A role) or
 // of x's column (operand B role) over the whole matrix.  A slice holds the
-// digits d_p themselves, integers that BF16 represents exactly; the power of
+// digits d_p themselves, integers that FP16 represents exactly; the power of
 // two of a slice pair is applied when its partial sums leave TMEM.  A product
 // of slices p and q is a sum over 64 terms of integers of magnitude <= 2^14
 // (weight 2^{-8(p+q+2)}): at most 2^20 per pair and task, 2^21 for the two
@@ -28,9 +28,9 @@
 // Layout (no swizzle, K-major canonical core matrices of 8 rows x 16 bytes;
 // per K-half of 32, core (row_group, k_group) at ((row_group * 4 + k_group) *
 // 128) bytes, so the descriptors use LBO = 128 and SBO = 512):
-//   A role: per tile and K-half 3 stacks of 128 x 32 bf16; stack s = slices
+//   A role: per tile and K-half 3 stacks of 128 x 32 fp16; stack s = slices
 //           2s (rows 0-63) and 2s+1 (rows 64-127), K = tile column.
-//   B role: per tile and K-half 6 slices of 64 x 32 bf16, stored transposed
+//   B role: per tile and K-half 6 slices of 64 x 32 fp16, stored transposed
 //           (row = tile column c = MMA N index, K = tile row).
 // The B slices of a K-half are consecutive 64-column blocks of one N-major
 // operand, so one M=128, N=64n, K=16 MMA (stack s, slices q0 .. q0+n-1)
@@ -39,7 +39,7 @@
 // diagonal) sits at TMEM columns 64g .. 64g+63, so the pairs of one stack land
 // in consecutive groups and four MMAs per K step cover all twelve pairs:
 // stack 0 with slices 0-3 and 4-5, stack 1 with 0-3, stack 2 with 0-1.
-#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 
@@ -95,30 +95,35 @@ __device__ __forceinline__ unsigned long long fixed48_mag(unsigned long long b, 
 
 // Balanced signed base-256 digits of F = sum_p d_p 2^{8(5-p)}: |d_p| <= 128
 // (d_p in [-128, 127] for p >= 1), so the truncation error is symmetric.  The
-// slicing pass takes the digits of |F| and negates them (BF16 sign bit) for a
-// negative entry: still |d_p| <= 128.
-// Adding 0x80 to each of the five low bytes of F turns them into plain bytes
-// d_p + 128 (p = 1..5, byte 5-p); the top digit d_0 is what remains above bit
-// 40.  digit_value returns d_p as an exact FP32 value: the byte is placed in
-// the low byte of the magic number 1.5 * 2^23, whose unit is 1.
+// slicing pass takes the digits of |F| (then 0 <= d_0 <= 128) and negates
+// them for a negative entry: still |d_p| <= 128.  Adding 0x80 to each of the
+// five low bytes of F turns them into plain bytes d_p + 128 (p = 1..5, byte
+// 5-p of G); byte 5 of G is d_0 itself.
 struct Digits {
     unsigned lo;  // bytes d_5+128, d_4+128, d_3+128, d_2+128
-    int hi;       // byte 0: d_1 + 128; bits 8 and up: d_0 (signed)
+    unsigned hi;  // byte 0: d_1 + 128, byte 1: d_0
 };
-__device__ __forceinline__ Digits balanced_digits(long long F) {
-    const long long G = F + 0x8080808080ll;
-    return Digits{(unsigned)G, (int)(G >> 32)};
+__device__ __forceinline__ Digits balanced_digits(unsigned long long F) {
+    const unsigned long long G = F + 0x8080808080ull;
+    return Digits{(unsigned)G, (unsigned)(G >> 32)};
 }
+// Digit P of two entries (a: low half, b: high half) as a packed FP16 pair,
+// exact: the two bytes go into the FP16 magic pattern 1024 + byte (unit 1),
+// and one fused multiply-add by (s_a, s_b) = +-1 with addend -1152 s (bias
+// 128 removed; -1024 s for the unbiased top digit) yields s * d_P.
+// sgn: bit 15 / bit 31 set for a negative entry a / b.
 template <int P>
-__device__ __forceinline__ float digit_value(const Digits& d) {
-    if (P == 0) return __int_as_float(0x4B400000 + (d.hi >> 8)) - 12582912.0f;
-    if (P == 1) return __int_as_float((int)__byte_perm((unsigned)d.hi, 0x4B400000u, 0x7650)) - 12583040.0f;
-    return __int_as_float((int)__byte_perm(d.lo, 0x4B400000u, 0x7650 | (5 - P))) - 12583040.0f;
-}
-// two exact small integers as a packed BF16 pair (first value in the low half)
-__device__ __forceinline__ uint32_t bf16x2_bits(float a, float b) {
-    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-    return *reinterpret_cast<const uint32_t*>(&h);
+__device__ __forceinline__ uint32_t digit_pair_f16(const Digits& a, const Digits& b, uint32_t sgn) {
+    uint32_t t;
+    if (P == 0) t = __byte_perm(a.hi, b.hi, 0x0501);
+    else if (P == 1) t = __byte_perm(a.hi, b.hi, 0x0400);
+    else t = __byte_perm(a.lo, b.lo, (5 - P) | ((9 - P) << 8));
+    const uint32_t mag = (t & 0x00FF00FFu) | 0x64006400u;
+    const uint32_t sc = 0x3C003C00u ^ sgn;                                  // (s_a, s_b)
+    const uint32_t add = (P == 0 ? 0xE400E400u : 0xE480E480u) ^ sgn;       // -1024 s or -1152 s
+    const __half2 r = __hfma2(*reinterpret_cast<const __half2*>(&mag), *reinterpret_cast<const __half2*>(&sc),
+                              *reinterpret_cast<const __half2*>(&add));
+    return *reinterpret_cast<const uint32_t*>(&r);
 }
 
 // ------------------------------------------------------------------ slicing
@@ -129,7 +134,7 @@ __device__ __forceinline__ uint32_t bf16x2_bits(float a, float b) {
 // each listed tile's squared Frobenius norm nu (FP64 fused multiply-adds, a
 // fixed-order reduction) into leaf_out[tile]; unlisted tiles keep the zero
 // the cull wrote for them.
-__global__ void __launch_bounds__(256, 6) k_slice(const double* __restrict__ X, const double* __restrict__ leaf,
+__global__ void __launch_bounds__(256, 5) k_slice(const double* __restrict__ X, const double* __restrict__ leaf,
                                                double* __restrict__ leaf_out,
                                                const unsigned long long* __restrict__ rmax,
                                                const unsigned long long* __restrict__ cmax,
@@ -184,7 +189,7 @@ __global__ void __launch_bounds__(256, 6) k_slice(const double* __restrict__ X, 
         // 8 consecutive items fill one 128-byte core matrix, 32 consecutive items 512 contiguous bytes
         const int kgi = (it >> 3) & 3, kh = (it >> 5) & 1;
         const int r = (it >> 6) * 8 + (it & 7), g = kh * 4 + kgi;  // A: row r, k-group g; B: column r, k-group g
-        // digits of |F| with F = round(|x| 2^(48-e)); the sign goes onto the BF16 digits afterwards
+        // digits of |F| with F = round(|x| 2^(48-e)); the sign goes onto the FP16 digits afterwards
         Digits D[8];
         unsigned neg = 0;
         const int se = (arole ? eR[r] : eC[r]) + 1027;
@@ -193,7 +198,7 @@ __global__ void __launch_bounds__(256, 6) k_slice(const double* __restrict__ X, 
             const double v = arole ? xs[r][8 * g + q] : xs[8 * g + q][r];
             const unsigned long long b = (unsigned long long)__double_as_longlong(v);
             neg |= (unsigned)(b >> 63) << q;
-            D[q] = balanced_digits((long long)fixed48_mag(b, se));
+            D[q] = balanced_digits(fixed48_mag(b, se));
         }
         uint8_t* base;
         uint32_t pstride;
@@ -207,7 +212,7 @@ __global__ void __launch_bounds__(256, 6) k_slice(const double* __restrict__ X, 
         }
         // odd slices of the A role: rows 64..127 of the stack, 8 row groups (4 KB) further on
         const uint32_t aodd = arole ? 8u * 4u * 128u : 0u;
-        // BF16 sign bits of element pairs (2h, 2h+1): bit 15 and bit 31 of word h
+        // FP16 sign bits of element pairs (2h, 2h+1): bit 15 and bit 31 of word h
         const uint32_t m0 = ((neg & 1u) << 15) | ((neg & 2u) << 30);
         const uint32_t m1 = ((neg & 4u) << 13) | ((neg & 8u) << 28);
         const uint32_t m2 = ((neg & 16u) << 11) | ((neg & 32u) << 26);
@@ -215,10 +220,10 @@ __global__ void __launch_bounds__(256, 6) k_slice(const double* __restrict__ X, 
 #define SPAMM_STORE_SLICE(P)                                                                                 \
         {                                                                                                    \
             uint4 w;                                                                                         \
-            w.x = bf16x2_bits(digit_value<P>(D[0]), digit_value<P>(D[1])) ^ m0;                              \
-            w.y = bf16x2_bits(digit_value<P>(D[2]), digit_value<P>(D[3])) ^ m1;                              \
-            w.z = bf16x2_bits(digit_value<P>(D[4]), digit_value<P>(D[5])) ^ m2;                              \
-            w.w = bf16x2_bits(digit_value<P>(D[6]), digit_value<P>(D[7])) ^ m3;                              \
+            w.x = digit_pair_f16<P>(D[0], D[1], m0);                                                         \
+            w.y = digit_pair_f16<P>(D[2], D[3], m1);                                                         \
+            w.z = digit_pair_f16<P>(D[4], D[5], m2);                                                         \
+            w.w = digit_pair_f16<P>(D[6], D[7], m3);                                                         \
             const uint32_t off = arole ? (uint32_t)(P >> 1) * pstride + (uint32_t)(P & 1) * aodd             \
                                        : (uint32_t)P * pstride;                                              \
             *reinterpret_cast<uint4*>(base + off) = w;                                                       \
@@ -564,8 +569,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
     } else if (warp == 1) {
         // ---------------- MMA issuer: tasks accumulate in TMEM in chunks of kChunk
         if (lane == 0) {
-            constexpr uint32_t idesc256 = ptx::idesc_bf16_f32(128, 256);
-            constexpr uint32_t idesc128 = ptx::idesc_bf16_f32(128, 128);
+            constexpr uint32_t idesc256 = ptx::idesc_f16_f32(128, 256);
+            constexpr uint32_t idesc128 = ptx::idesc_f16_f32(128, 128);
             long long H = 0, C = 0;
             int tau = 0;
             bool ok = true;
@@ -601,13 +606,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
                         for (int ks = 0; ks < 2; ++ks) {
                             const uint32_t acc = fresh && ks == 0 ? 0u : 1u;
                             const uint32_t b0 = sB + ks * 256;
-                            ptx::mma_bf16(tmem, ptx::smem_desc(sA + ks * 256, 128, 512),
+                            ptx::mma_f16(tmem, ptx::smem_desc(sA + ks * 256, 128, 512),
                                           ptx::smem_desc(b0, 128, 512), idesc256, acc);
-                            ptx::mma_bf16(tmem + 256u, ptx::smem_desc(sA + ks * 256, 128, 512),
+                            ptx::mma_f16(tmem + 256u, ptx::smem_desc(sA + ks * 256, 128, 512),
                                           ptx::smem_desc(b0 + 4 * B_HALF_SLICE, 128, 512), idesc128, acc);
-                            ptx::mma_bf16(tmem + 128u, ptx::smem_desc(sA + A_HALF_STACK + ks * 256, 128, 512),
+                            ptx::mma_f16(tmem + 128u, ptx::smem_desc(sA + A_HALF_STACK + ks * 256, 128, 512),
                                           ptx::smem_desc(b0, 128, 512), idesc256, 1u);
-                            ptx::mma_bf16(tmem + 256u, ptx::smem_desc(sA + 2 * A_HALF_STACK + ks * 256, 128, 512),
+                            ptx::mma_f16(tmem + 256u, ptx::smem_desc(sA + 2 * A_HALF_STACK + ks * 256, 128, 512),
                                           ptx::smem_desc(b0, 128, 512), idesc128, 1u);
                         }
                         ptx::mma_commit(&bar_empty[s]);
@@ -757,8 +762,9 @@ void launch_rowcol_max(const double* X, const Geometry& g, unsigned long long* r
 void launch_slice(const double* X, const double* leaf, double* leaf_out, const unsigned long long* rmax,
                   const unsigned long long* cmax, uint8_t* sA, uint8_t* sB, const Geometry& g, const int* tile_list,
                   const int* tile_count, const int* done, cudaStream_t st) {
-    // six 34 KB blocks fit on an SM: one resident wave covers up to 6 tiles per SM
-    const int grid = std::min(device_sm_count() * 6, g.m * g.m);
+    // five blocks (34 KB shared memory, 48 registers) are resident per SM: one wave, so a dependent launched
+    // early never holds slots the grid still needs
+    const int grid = std::min(device_sm_count() * 5, g.m * g.m);
     launch_dependent(emu::k_slice, dim3(grid), dim3(256), 0, st, X, leaf, leaf_out, rmax, cmax, sA, sB, g.m,
                      tile_list, tile_count, done);
     note_launch();

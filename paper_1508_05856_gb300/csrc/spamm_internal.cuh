@@ -30,7 +30,7 @@ Geometry make_geometry(int n, int nb);
 // t + (i*m + j)*nb*nb.  tree holds the squared Frobenius norms of every
 // quadtree node.
 // With the tensor-core (SPAMM_EMU64) arithmetic a matrix also carries its
-// BF16 slices in the operand-A and operand-B layouts and the magnitude
+// FP16 digit slices in the operand-A and operand-B layouts and the magnitude
 // maxima (IEEE bits) of its rows and columns.
 struct TileMat {
     double* t = nullptr;
@@ -189,7 +189,7 @@ size_t emu_slice_bytes_per_tile();  // bytes of one tile's slices in one operand
 // Row/column magnitude maxima of a packed matrix (arrays must be zeroed first).
 void launch_rowcol_max(const double* X, const Geometry& g, unsigned long long* rmax, unsigned long long* cmax,
                        cudaStream_t st);
-// BF16 slices of both operand roles from FP64 tiles and row/column maxima,
+// FP16 digit slices of both operand roles from FP64 tiles and row/column maxima,
 // for the listed tiles (or all tiles when tile_list is null).  With leaf_out
 // null, tiles whose leaf[] norm is zero are skipped; with leaf_out set, every
 // listed tile is sliced and its squared Frobenius norm written to leaf_out.
