@@ -311,8 +311,9 @@ struct EmuArgs {
     unsigned long long* cmaxC;
     const int* counts;
     const int* jlist;
-    const int* tile_list;               // compacted output tiles with work
-    const int* tile_count;
+    const int* tile_list;               // compacted output tiles with work, in `buckets` cost classes
+    const int* tile_count;              // [buckets]
+    int buckets;
     int* sched;                         // [2] tile ticket counter and finished-CTA counter, zero between launches
     double* trace_part;
     const int* done;
@@ -447,7 +448,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
     long long* sBot = sTop + NB * 65;                                             // [64][65]
     const int m = a.m;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ntiles = *a.tile_count;
+    // bucket counts held in registers: a drawn ticket maps to its tile with one load
+    int bcount[kTileBuckets];
+    int ntiles = 0;
+#pragma unroll
+    for (int b = 0; b < kTileBuckets; ++b) {
+        bcount[b] = b < a.buckets ? a.tile_count[b] : 0;
+        ntiles += bcount[b];
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) a.slice_list[m * m] = ntiles;
     if ((int)blockIdx.x >= ntiles) return;
 
@@ -488,7 +496,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
             // the following ticket is in flight while this tile is prepared
             int nxt = 0;
             if (!end && lane == 0) nxt = atomicAdd(a.sched, 1);
-            const int tile = end ? 0 : a.tile_list[idx];
+            int tile = 0;
+            if (!end) {
+                int t = idx, b = 0;
+#pragma unroll
+                for (int q = 0; q < kTileBuckets - 1; ++q)
+                    if (b == q && t >= bcount[q]) {
+                        t -= bcount[q];
+                        b = q + 1;
+                    }
+                tile = a.tile_list[(size_t)b * m * m + t];
+            }
             const int i = tile / m, k = tile - (tile / m) * m;
             // this tile's metadata, fetched before waiting for its slot
             const int cnt = end ? 0 : a.counts[tile];
@@ -772,7 +790,7 @@ void launch_slice(const double* X, const double* leaf, double* leaf_out, const u
 
 void launch_gemm_emu(const Geometry& g, const TileMat& A, const TileMat& B, const TileMat& C, const int* counts,
                      const int* jlist, const int* tile_list, const int* tile_count, EpiMode mode, double* trace_part,
-                     int* sched, const int* done, int* err, double tau, cudaStream_t st) {
+                     int* sched, const int* done, int* err, double tau, cudaStream_t st, int buckets) {
     emu::EmuArgs a;
     a.sliceA = A.sliceA;
     a.sliceB = B.sliceB;
@@ -792,6 +810,7 @@ void launch_gemm_emu(const Geometry& g, const TileMat& A, const TileMat& B, cons
     a.jlist = jlist;
     a.tile_list = tile_list;
     a.tile_count = tile_count;
+    a.buckets = buckets;
     a.sched = sched;
     a.trace_part = trace_part;
     a.done = done;

@@ -24,12 +24,13 @@ __global__ void __launch_bounds__(kThreads) k_gemm_f64(const double* __restrict_
                                                        const double* __restrict__ leafB, double* __restrict__ leafC,
                                                        const int* __restrict__ counts, const int* __restrict__ jlist,
                                                        const int* __restrict__ tile_list,
-                                                       const int* __restrict__ tile_count, int m, int n, int dense,
+                                                       const int* __restrict__ tile_count, int buckets, int m, int n,
+                                                       int dense,
                                                        int mode, double* __restrict__ trace_part,
                                                        const int* __restrict__ done) {
     grid_dependency_wait();
     if (done && *done) return;
-    if (tile_list && (int)blockIdx.x >= *tile_count) return;
+    if (tile_list && (int)blockIdx.x >= listed_total(tile_count, buckets)) return;
     constexpr int TM = NB / 16;  // each thread owns TM x TM outputs
     constexpr int LDS = NB + 1;  // padded row of the staged chunks
     extern __shared__ double smem[];
@@ -37,7 +38,7 @@ __global__ void __launch_bounds__(kThreads) k_gemm_f64(const double* __restrict_
     double* Bs = smem + kKC * LDS;  // [kKC][LDS]  B chunk
     __shared__ double red[8];
 
-    const int tile = tile_list ? tile_list[blockIdx.x] : (int)blockIdx.x;
+    const int tile = tile_list ? listed_tile(tile_list, tile_count, buckets, m * m, (int)blockIdx.x) : (int)blockIdx.x;
     const int i = tile / m, k = tile - (tile / m) * m;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int nt = dense ? m : counts[tile];
@@ -123,10 +124,11 @@ __global__ void __launch_bounds__(kThreads) k_gemm_f64(const double* __restrict_
 template <int NB>
 void launch_nb(const Geometry& g, const double* A, const double* B, double* C, const double* leafA,
                const double* leafB, double* treeC, const int* counts, const int* jlist, const int* tile_list,
-               const int* tile_count, int dense, EpiMode mode, double* trace_part, const int* done, cudaStream_t st) {
+               const int* tile_count, int dense, EpiMode mode, double* trace_part, const int* done, cudaStream_t st,
+               int buckets) {
     const size_t smem = 2 * (size_t)kKC * (NB + 1) * sizeof(double);
     launch_dependent(k_gemm_f64<NB>, dim3(g.m * g.m), dim3(kThreads), smem, st, A, B, C, leafA, leafB, treeC, counts,
-                     jlist, tile_list, tile_count, g.m, g.n, dense, (int)mode, trace_part, done);
+                     jlist, tile_list, tile_count, buckets, g.m, g.n, dense, (int)mode, trace_part, done);
     note_launch();
 }
 
@@ -147,19 +149,19 @@ void f64_kernel_attributes() {
 void launch_gemm_f64(const Geometry& g, const double* A, const double* B, double* C, const double* leafA,
                      const double* leafB, double* treeC, const int* counts, const int* jlist, const int* tile_list,
                      const int* tile_count, int dense, EpiMode mode, double* trace_part, const int* done,
-                     cudaStream_t st) {
+                     cudaStream_t st, int buckets) {
     switch (g.nb) {
         case 32:
             launch_nb<32>(g, A, B, C, leafA, leafB, treeC, counts, jlist, tile_list, tile_count, dense, mode,
-                          trace_part, done, st);
+                          trace_part, done, st, buckets);
             break;
         case 64:
             launch_nb<64>(g, A, B, C, leafA, leafB, treeC, counts, jlist, tile_list, tile_count, dense, mode,
-                          trace_part, done, st);
+                          trace_part, done, st, buckets);
             break;
         case 128:
             launch_nb<128>(g, A, B, C, leafA, leafB, treeC, counts, jlist, tile_list, tile_count, dense, mode,
-                           trace_part, done, st);
+                           trace_part, done, st, buckets);
             break;
         default: break;
     }

@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(1024) k_tree(TreeDev td, double* __restrict__ 
             nxt = t;
         }
     }
-    if (ex.zero_int && threadIdx.x == 0) *ex.zero_int = 0;
+    if (ex.zero_int && threadIdx.x < ex.zero_n) ex.zero_int[threadIdx.x] = 0;
     if (ex.trace_part && threadIdx.x < 32)
         trace_error(ex.trace_part, ex.n, td.m, ex.k, ex.tol_t, ex.t_hist, ex.done, ex.iters);
 }
@@ -323,6 +323,7 @@ __global__ void __launch_bounds__(256) k_cull(TreeDev td, const double* __restri
     if (done && *done) return;
     __shared__ int red[8];
     __shared__ int lst[8];
+    __shared__ int bkt[8];
     for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < co.zero_n; q += (long)gridDim.x * blockDim.x)
         co.zero_u64[q] = 0ull;
     const int m = td.m;
@@ -360,17 +361,21 @@ __global__ void __launch_bounds__(256) k_cull(TreeDev td, const double* __restri
         }
     }
     if (co.tile_list) {
-        // one atomic per block appends the block's listed output tiles
-        if (lane == 0) lst[threadIdx.x >> 5] = listed ? wid : -1;
+        // one atomic per block and bucket appends the block's listed output tiles
+        if (lane == 0) {
+            lst[threadIdx.x >> 5] = listed ? wid : -1;
+            bkt[threadIdx.x >> 5] = co.buckets > 1 ? tile_bucket(cnt) : 0;
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
-            int c = 0;
-            for (int w = 0; w < 8; ++w) c += lst[w] >= 0;
-            if (c) {
-                int q = atomicAdd(co.tile_count, c);
-                for (int w = 0; w < 8; ++w)
-                    if (lst[w] >= 0) co.tile_list[q++] = lst[w];
-            }
+            int c[kTileBuckets] = {0, 0, 0, 0, 0};
+            for (int w = 0; w < 8; ++w)
+                if (lst[w] >= 0) ++c[bkt[w]];
+            int q[kTileBuckets];
+            for (int b = 0; b < kTileBuckets; ++b) q[b] = c[b] ? atomicAdd(co.tile_count + b, c[b]) : 0;
+            const size_t mm = (size_t)m * m;
+            for (int w = 0; w < 8; ++w)
+                if (lst[w] >= 0) co.tile_list[bkt[w] * mm + q[bkt[w]]++] = lst[w];
         }
     }
     if (thr_out && wid == 0 && lane == 0) *thr_out = thr;

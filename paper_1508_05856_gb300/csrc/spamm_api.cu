@@ -105,13 +105,15 @@ struct GraphKey {
 };
 
 // Scratch of one problem size on one device.
+constexpr int kFlagInts = 32;
+
 struct Plan {
     int device = 0;
     Geometry g;
     TileMat buf[6];
     int* counts = nullptr;
     int* jlist = nullptr;
-    int* tile_list = nullptr;                // [m*m] compacted output tiles of one product
+    int* tile_list = nullptr;                // [kTileBuckets*m*m] compacted output tiles of one product
     // second product scratch and stream: the iteration's two independent
     // products (Y and Z updates) run on two branches
     int* counts2 = nullptr;
@@ -130,8 +132,8 @@ struct Plan {
     double* trace_part = nullptr;  // [m]
     double* scal = nullptr;        // c0, mu, c, sqrt c, thr, resid, spare...
     double* rowsum = nullptr;      // [n]
-    int* flags = nullptr;          // done, iters, device error, output-tile counts of the two branches,
-                                   // [8..11] tile tickets of the tensor-core kernel per branch
+    int* flags = nullptr;          // [0] done, [1] iters, [2] device error, [8..11] tile tickets of the
+                                   // tensor-core kernel per branch, [16 + 8 b ..] output-tile bucket counts
     double* partial = nullptr;     // [m*m]
     double* stage[3] = {nullptr, nullptr, nullptr};  // n*n row-major staging
     // profiling: event pairs around each leaf-product kernel of a call
@@ -222,17 +224,17 @@ static int alloc_plan(Plan* p, int n, int nb) {
     }
     CKA(dev_alloc(&p->counts, (size_t)g.m * g.m * sizeof(int)));
     CKA(dev_alloc(&p->jlist, (size_t)g.m * g.m * g.m * sizeof(int)));
-    CKA(dev_alloc(&p->tile_list, (size_t)g.m * g.m * sizeof(int)));
+    CKA(dev_alloc(&p->tile_list, (size_t)kTileBuckets * g.m * g.m * sizeof(int)));
     CKA(dev_alloc(&p->counts2, (size_t)g.m * g.m * sizeof(int)));
     CKA(dev_alloc(&p->jlist2, (size_t)g.m * g.m * g.m * sizeof(int)));
-    CKA(dev_alloc(&p->tile_list2, (size_t)g.m * g.m * sizeof(int)));
+    CKA(dev_alloc(&p->tile_list2, (size_t)kTileBuckets * g.m * g.m * sizeof(int)));
     CKA(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
     CKA(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
     CKA(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
     CKA(dev_alloc(&p->trace_part, (size_t)g.m * sizeof(double)));
     CKA(dev_alloc(&p->scal, 16 * sizeof(double)));
     CKA(dev_alloc(&p->rowsum, (size_t)n * sizeof(double)));
-    CKA(dev_alloc(&p->flags, 16 * sizeof(int)));
+    CKA(dev_alloc(&p->flags, kFlagInts * sizeof(int)));
     CKA(dev_alloc(&p->partial, (size_t)g.m * g.m * sizeof(double)));
     return SPAMM_OK;
 }
@@ -283,7 +285,8 @@ size_t plan_footprint(int n, int nb, int precision, bool host_io) {
     if (nb == 0) nb = precision == SPAMM_EMU64 ? 64 : 32;
     const Geometry g = make_geometry(n, nb);
     size_t b = 6 * (g.elems() + (size_t)g.tree_size) * sizeof(double);
-    b += 2 * ((size_t)g.m * g.m * (g.m + 2)) * sizeof(int) + (size_t)g.m * sizeof(double) + (size_t)n * sizeof(double) +
+    b += 2 * ((size_t)g.m * g.m * (g.m + 1 + kTileBuckets)) * sizeof(int) + (size_t)g.m * sizeof(double) +
+         (size_t)n * sizeof(double) +
          (size_t)g.m * g.m * sizeof(double) + 4096;
     if (precision == SPAMM_EMU64)
         b += 6 * (2 * emu_slice_bytes_per_tile() * (size_t)g.m * g.m + 2 * (size_t)g.m * g.nb * 8 +
@@ -480,17 +483,18 @@ static void mark_sliced(Plan* p, const TileMat& M, cudaStream_t st) {
         }
 }
 
-// The output-tile counter (flags[3]) is zero on entry (the call's flag reset,
-// then the tree pass of the previous product); the tree pass may also carry
-// the iteration's trace error (tk).
+// The output-tile bucket counters are zero on entry (the call's flag reset,
+// then the tree pass of the previous product on the branch); the tree pass
+// may also carry the iteration's trace error (tk).
 static void product(Plan* p, const TileMat& A, const TileMat& B, TileMat& C, double tau, EpiMode mode,
                     unsigned long long* ctr, cudaStream_t st, const TreeExtra* tk = nullptr, int slot = 0) {
     const Geometry& g = p->g;
     int* counts = slot ? p->counts2 : p->counts;
     int* jlist = slot ? p->jlist2 : p->jlist;
     int* tile_list = slot ? p->tile_list2 : p->tile_list;
-    int* tile_count = p->flags + 3 + slot;
+    int* tile_count = p->flags + 16 + 8 * slot;  // kTileBuckets counts
     CullOut co{counts, jlist, tile_list, tile_count, C.tree, mode == EPI_NS_X ? 1 : 0};
+    co.buckets = kTileBuckets;
     if (p->emu) {
         co.zero_u64 = C.rmax;  // rmax and cmax, contiguous
         co.zero_n = 2 * (long)g.m * g.nb;
@@ -510,10 +514,10 @@ static void product(Plan* p, const TileMat& A, const TileMat& B, TileMat& C, dou
     }
     if (p->emu) {
         launch_gemm_emu(g, A, B, C, counts, jlist, tile_list, tile_count, mode, p->trace_part,
-                        p->flags + 8 + 2 * slot, p->flags, p->flags + 2, tau, st);
+                        p->flags + 8 + 2 * slot, p->flags, p->flags + 2, tau, st, kTileBuckets);
     } else {
         launch_gemm_f64(g, A.t, B.t, C.t, A.tree, B.tree, C.tree, counts, jlist, tile_list, tile_count, 0,
-                        mode, p->trace_part, p->flags, st);
+                        mode, p->trace_part, p->flags, st, kTileBuckets);
     }
     if (e0 && e1) cudaEventRecordWithFlags(e1, st, cudaEventRecordExternal);
     p->gemm_launches++;
@@ -533,6 +537,7 @@ static void product(Plan* p, const TileMat& A, const TileMat& B, TileMat& C, dou
     }
     TreeExtra ex = tk ? *tk : TreeExtra();
     ex.zero_int = tile_count;
+    ex.zero_n = kTileBuckets;
     launch_tree(g, C.tree, p->flags, st, ex);
 }
 
@@ -570,7 +575,7 @@ static int multiply_core(const double* A, const double* B, double* C, int n, dou
     if ((e = out_target(p, 2, C, &dC))) return e;
     begin_call(p, o.profile != 0, o.precision == SPAMM_EMU64);
     if (p->emu && (e = ensure_emu(p))) return e;
-    CK(cudaMemsetAsync(p->flags, 0, 16 * sizeof(int), st));
+    CK(cudaMemsetAsync(p->flags, 0, kFlagInts * sizeof(int), st));
     CK(cudaMemsetAsync(p->task_ctr, 0, 4 * sizeof(unsigned long long), st));
     launch_pack(dA, n, g, nullptr, nullptr, p->buf[0], st);
     launch_tree(g, p->buf[0].tree, nullptr, st);
@@ -702,7 +707,7 @@ static int residual_impl(Plan* p, const double* dS, const double* dZ, double* ou
 static int enqueue_solve(Plan* p, const double* dS, double* dY, double* dZ, int n, double tau, double tau_s,
                          int maxit, const spamm_opts& o, cudaStream_t st, int* iters) {
     const Geometry& g = p->g;
-    CK(cudaMemsetAsync(p->flags, 0, 16 * sizeof(int), st));
+    CK(cudaMemsetAsync(p->flags, 0, kFlagInts * sizeof(int), st));
     CK(cudaMemsetAsync(p->task_ctr, 0, (3 * (size_t)p->maxit_cap + 4) * sizeof(unsigned long long), st));
     CK(cudaMemsetAsync(p->t_hist, 0, (size_t)p->maxit_cap * sizeof(double), st));
 

@@ -118,7 +118,8 @@ void launch_identity(const Geometry& g, TileMat Z, cudaStream_t st);
 // trace_part set, the iteration's trace error t_k = (n - sum trace_part)/n
 // into t_hist[k], *iters = k + 1, and *done = 1 once |t_k| <= tol_t > 0.
 struct TreeExtra {
-    int* zero_int = nullptr;
+    int* zero_int = nullptr;  // zero_n ints
+    int zero_n = 1;
     const double* trace_part = nullptr;
     int n = 0, k = 0;
     double tol_t = 0.0;
@@ -137,6 +138,9 @@ void launch_tree(const Geometry& g, double* tree, const int* done, cudaStream_t 
 // tile is exactly zero and its data are not written (readers check nu == 0).
 // zero_u64[0 .. zero_n) is cleared on the way (the output's row/column
 // maxima, which the leaf products accumulate with atomics).
+// With buckets > 1 the listed tiles are sorted coarsely by cost: a tile with
+// cnt tasks goes to bucket tile_bucket(cnt), whose ids sit at
+// tile_list[b*m*m ...] with count tile_count[b] (all counts zero on entry).
 struct CullOut {
     int* counts;
     int* jlist;
@@ -146,7 +150,32 @@ struct CullOut {
     int force_diag;
     unsigned long long* zero_u64 = nullptr;
     long zero_n = 0;
+    int buckets = 1;
 };
+
+// Buckets of listed output tiles by task count, most expensive first: the
+// persistent leaf-product kernels draw tiles in this order, so the cheap
+// tiles fill the end of a launch (longest-first scheduling).
+constexpr int kTileBuckets = 5;
+__host__ __device__ inline int tile_bucket(int cnt) {
+    return cnt >= 16 ? 0 : cnt >= 8 ? 1 : cnt >= 4 ? 2 : cnt >= 2 ? 3 : 4;
+}
+#ifdef __CUDACC__
+// Number of listed tiles, and the id of the t-th one (buckets in order).
+__device__ __forceinline__ int listed_total(const int* tile_count, int buckets) {
+    int n = 0;
+    for (int b = 0; b < buckets; ++b) n += tile_count[b];
+    return n;
+}
+__device__ __forceinline__ int listed_tile(const int* tile_list, const int* tile_count, int buckets, int mm, int t) {
+    for (int b = 0; b < buckets; ++b) {
+        const int c = tile_count[b];
+        if (t < c) return tile_list[(size_t)b * mm + t];
+        t -= c;
+    }
+    return -1;
+}
+#endif
 void launch_cull(const Geometry& g, const double* treeA, const double* treeB, double tau, const CullOut& out,
                  unsigned long long* total, double* thr_out, const int* done, cudaStream_t st);
 // Tile-major -> row-major with out = in * (*mul) or in / (*div) (one of them
@@ -168,7 +197,7 @@ void launch_resid_norm(const double* R, const Geometry& g, double* partial, doub
 void launch_gemm_f64(const Geometry& g, const double* A, const double* B, double* C, const double* leafA,
                      const double* leafB, double* treeC, const int* counts, const int* jlist, const int* tile_list,
                      const int* tile_count, int dense, EpiMode mode, double* trace_part, const int* done,
-                     cudaStream_t st);
+                     cudaStream_t st, int buckets = 1);
 
 // ---- spamm_api.cu, for the request server --------------------------------
 }  // namespace spamm
@@ -203,6 +232,6 @@ void launch_slice(const double* X, const double* leaf, double* leaf_out, const u
 // sched: two ints, zero before the first launch; the kernel leaves them zero.
 void launch_gemm_emu(const Geometry& g, const TileMat& A, const TileMat& B, const TileMat& C, const int* counts,
                      const int* jlist, const int* tile_list, const int* tile_count, EpiMode mode, double* trace_part,
-                     int* sched, const int* done, int* err, double tau, cudaStream_t st);
+                     int* sched, const int* done, int* err, double tau, cudaStream_t st, int buckets = 1);
 
 }  // namespace spamm
