@@ -35,8 +35,8 @@ STATUS = {0: "SPAMM_OK", -1: "SPAMM_ERR_ARG", -2: "SPAMM_ERR_NOMEM", -3: "SPAMM_
           -8: "SPAMM_ERR_UNSUPPORTED", -9: "SPAMM_ERR_NOTFOUND"}
 
 # every extern "C" function declared in include/spamm.h
-HEADER_SYMBOLS = ["spamm_opts_init", "spamm_multiply", "spamm_sqrt_invsqrt", "spamm_sqrt_invsqrt_batched",
-                  "spamm_norm_tree", "spamm_cull", "spamm_last_error", "spamm_strerror", "spamm_release",
+HEADER_SYMBOLS = ["spamm_opts_init", "spamm_autotune_leaf", "spamm_multiply", "spamm_sqrt_invsqrt",
+                  "spamm_sqrt_invsqrt_batched", "spamm_norm_tree", "spamm_cull", "spamm_last_error", "spamm_strerror", "spamm_release",
                   "spamm_kernel_launches", "spamm_version", "spamm_multiply_noalloc", "spamm_server_create",
                   "spamm_server_submit", "spamm_server_poll", "spamm_server_wait", "spamm_server_destroy"]
 
@@ -88,6 +88,8 @@ def lib(build_if_missing: bool = True):
         vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int
         L.spamm_opts_init.argtypes = [ctypes.POINTER(Opts)]
         L.spamm_opts_init.restype = None
+        L.spamm_autotune_leaf.argtypes = [vp, ip, ctypes.c_double, ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_int)]
+        L.spamm_autotune_leaf.restype = ip
         L.spamm_multiply.argtypes = [vp, vp, vp, ip, ctypes.c_double, ctypes.POINTER(Opts), ctypes.POINTER(Stats)]
         L.spamm_multiply.restype = ip
         L.spamm_sqrt_invsqrt.argtypes = [vp, ip, ctypes.c_double, ip, vp, vp, ctypes.POINTER(Opts),
@@ -218,6 +220,16 @@ def multiply(A, B, tau: float, leaf: int = 64, precision: int = FP64, out=None, 
     o = _opts(leaf=leaf, precision=precision, stream=_stream_of(a, stream))
     _check(lib().spamm_multiply(pa, pb, _ptr(C), n, float(tau), ctypes.byref(o), ctypes.byref(st)))
     return C, _stats_dict(st)
+
+
+def autotune_leaf(S, tau: float, precision: int = FP64, stream=None) -> int:
+    """Fastest leaf size for problems like S (spamm_autotune_leaf); cached per device, n, arithmetic and
+    decade of tau.  Calls given leaf=0 use the same choice."""
+    s, ps, n, _ = _prep(S)
+    o = _opts(leaf=0, precision=precision, stream=_stream_of(s, stream))
+    leaf = ctypes.c_int(0)
+    _check(lib().spamm_autotune_leaf(ps, n, float(tau), ctypes.byref(o), ctypes.byref(leaf)))
+    return leaf.value
 
 
 def sqrt_invsqrt(S, tau: float, maxit: int, leaf: int = 64, precision: int = FP64, tau_s=None, mu_rel=0.0,
