@@ -9,7 +9,8 @@ arrays.  It shares no code with the CUDA path.
 Paper references (Challacombe, Haut & Bock, "A N-Body Solver for Square Root
 Iteration"): the quadtree and its Frobenius-norm recursion (Sec. 1), the
 stable SpAMM occlusion cull, Eq. (newspamm), the dual-channel square-root
-iteration, Eq. (cannonical), and the trace error t_k (Sec. 4.2).
+iteration, Eq. (cannonical), the trace error t_k and the damped, stabilised
+NS map (Sec. 4.2).
 """
 from __future__ import annotations
 
@@ -64,7 +65,9 @@ def lib():
             L.or_gershgorin.argtypes = [dp, ctypes.c_int, ctypes.c_double]
             L.or_gershgorin.restype = ctypes.c_double
             L.or_ns.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                ctypes.c_int, ctypes.c_int, ctypes.c_double, dp, dp, dp, lp, dp]
+                                ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, dp, dp, dp, lp, dp]
+            L.or_map_params.argtypes = [ctypes.c_int, ctypes.c_double, dp, dp]
+            L.or_map_params.restype = None
             L.or_ns.restype = ctypes.c_int
             L.or_residual.argtypes = [dp, dp, ctypes.c_int]
             L.or_residual.restype = ctypes.c_double
@@ -176,8 +179,20 @@ def gershgorin(S, mu: float = 0.0) -> float:
     return lib().or_gershgorin(_d(S), S.shape[0], mu)
 
 
+MAP_NS = 0      # alpha = 1, eps = 0: T = 1.5 I - 0.5 X
+MAP_SCALED = 1  # sigmoidal alpha(t), eps(t) of Sec. 4.2 "Mapping"
+
+
+def map_params(t: float, map: int = MAP_SCALED) -> tuple[float, float]:
+    """(alpha, eps) of the NS map for relative trace error t."""
+    a = np.zeros(1)
+    e = np.zeros(1)
+    lib().or_map_params(int(map), float(t), _d(a), _d(e))
+    return float(a[0]), float(e[0])
+
+
 def sqrt_invsqrt(S, nb: int, tau: float, maxit: int, tau_s: float | None = None, mu_rel: float = 0.0,
-                 order: int = 0, tol_t: float = 0.0) -> dict:
+                 order: int = 0, tol_t: float = 0.0, map: int = MAP_NS) -> dict:
     """Dual-channel NS iteration; returns Y ~ S^{1/2}, Z ~ S^{-1/2} and the per-iteration history."""
     S = _mat(S)
     n = S.shape[0]
@@ -188,7 +203,8 @@ def sqrt_invsqrt(S, nb: int, tau: float, maxit: int, tau_s: float | None = None,
     th = np.zeros(max(maxit, 1))
     kh = np.zeros((max(maxit, 1), 3), dtype=np.int64)
     c = np.zeros(1)
-    it = lib().or_ns(_d(S), n, nb, tau, tau_s, mu_rel, maxit, order, tol_t, _d(Y), _d(Z), _d(th), _l(kh), _d(c))
+    it = lib().or_ns(_d(S), n, nb, tau, tau_s, mu_rel, maxit, order, tol_t, int(map), _d(Y), _d(Z), _d(th), _l(kh),
+                     _d(c))
     if it < 0:
         raise RuntimeError(f"oracle NS failed ({it})")
     return {"Y": Y, "Z": Z, "iters": it, "t_hist": th[:it].copy(), "task_hist": kh[:it].copy(),

@@ -23,9 +23,13 @@
  *      c10 = a10 b00 + a11 b10, c11 = a10 b01 + a11 b11);
  *   - leaf products are triple loops, accumulated per output tile with the
  *     surviving j in ascending order and the inner index ascending;
- *   - the square-root iteration is Eq. (cannonical) with alpha = 1, i.e.
- *     T = 1.5 I - 0.5 X, started from X0 = Y0 = S / c, Z0 = I, where c is the
- *     Gershgorin bound of the largest eigenvalue (Sec. 3.2).
+ *   - the square-root iteration is Eq. (cannonical), started from
+ *     X0 = Y0 = S / c, Z0 = I, where c is the Gershgorin bound of the
+ *     largest eigenvalue (Sec. 3.2), with T = h_alpha[U] the NS logistic of
+ *     Sec. 4.2 "Mapping" applied to the stabilised U = eps I + (1-2 eps) X:
+ *     map 0 is alpha = 1, eps = 0 (T = 1.5 I - 0.5 X); map 1 takes alpha
+ *     and eps from the sigmoidal damping functions of the trace error t of
+ *     the X being mapped.
  *
  * Parity-pinned by tests/test_oracle_pins.py (tau = 0 dense product, the
  * tile-level closed form of the lemma, recursive == brute-force cull sets,
@@ -319,21 +323,67 @@ double or_gershgorin(const double* S, int n, double mu) {
 }
 
 /*
+ * Damping of the NS map, Sec. 4.2 "Mapping": with the relative trace error t
+ * of the matrix being mapped, the logistic scale is
+ *   alpha(t) = 1 + 1.85 / (1 + exp(-50 (t - 0.35)))
+ * and the stabiliser width
+ *   eps(t)   = 0.1 / (1 + exp(-75 (t - 0.30))),
+ * so that both are switched off (alpha -> 1, eps -> 0) as t -> 0.
+ * map 0 is the plain map: alpha = 1, eps = 0 for every t.
+ */
+void or_map_params(int map, double t, double* alpha, double* eps) {
+    if (map == 0) {
+        *alpha = 1.0;
+        *eps = 0.0;
+        return;
+    }
+    *alpha = 1.0 + 1.85 / (1.0 + exp(-50.0 * (t - 0.35)));
+    *eps = 0.1 / (1.0 + exp(-75.0 * (t - 0.30)));
+}
+
+/*
+ * T = h_alpha[U] = (sqrt(alpha)/2) (3 I - alpha U) with U = eps I + (1 - 2 eps) X,
+ * the stabilising shift-and-scale of [0,1] onto [eps, 1-eps] followed by the
+ * NS logistic (Sec. 4.2 "Mapping"); alpha and eps from t (or_map_params).
+ */
+static void or_apply_map(const double* X, double* T, int n, int map, double t) {
+    double alpha, eps;
+    or_map_params(map, t, &alpha, &eps);
+    const double half_root = 0.5 * sqrt(alpha);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            const double x = X[(long)i * n + j];
+            const double u = (i == j) ? eps + (1.0 - 2.0 * eps) * x : (1.0 - 2.0 * eps) * x;
+            T[(long)i * n + j] = half_root * ((i == j ? 3.0 : 0.0) - alpha * u);
+        }
+}
+
+/* t = (n - tr X) / n, the relative trace error (Sec. 4.2). */
+static double or_trace_error(const double* X, int n) {
+    double tr = 0.0;
+    for (int i = 0; i < n; ++i) tr += X[(long)i * n + i];
+    return ((double)n - tr) / (double)n;
+}
+
+/*
  * Y -> S^{1/2}, Z -> S^{-1/2} by the dual channel iteration with
- * T = h[X] = 1.5 I - 0.5 X (the NS map with alpha = 1):
+ * T = h_alpha[eps I + (1 - 2 eps) X] (or_apply_map; map 0: T = 1.5 I - 0.5 X):
  *   order 0 (as printed):  Y <- T (x)_{tau_s} Y,  Z <- Z (x)_tau T
  *   order 1 (transposed):  Y <- Y (x)_{tau_s} T,  Z <- T (x)_tau Z
  *   then X <- Y (x)_tau Z (order 0) or X <- Z (x)_tau Y (order 1), and
  *   t_k = (n - tr X) / n (Sec. 4.2).
  * mu_rel > 0 regularises with S + mu I, mu = mu_rel * (Gershgorin bound of S)
- * (Sec. 6).  The iteration stops after maxit steps or once |t_k| <= tol_t
- * (tol_t > 0).  t_hist (maxit) and task_hist (3*maxit: y, z, x products) may
- * be NULL.  Returns the number of iterations run; *scale_c receives c.
+ * (Sec. 6).  The map applied to X_k takes alpha and eps from t_k of that same
+ * X_k (t_0 from X0 = S / c).  The iteration stops after maxit steps or once
+ * |t_k| <= tol_t (tol_t > 0).  t_hist (maxit) and task_hist (3*maxit: y, z,
+ * x products) may be NULL.  Returns the number of iterations run; *scale_c
+ * receives c.
  */
 int or_ns(const double* S, int n, int nb, double tau, double tau_s, double mu_rel, int maxit,
-          int order, double tol_t, double* Y, double* Z, double* t_hist, long* task_hist,
+          int order, double tol_t, int map, double* Y, double* Z, double* t_hist, long* task_hist,
           double* scale_c) {
-    if (n <= 0 || nb <= 0 || maxit < 0 || !(tau >= 0.0) || !(tau_s >= 0.0)) return OR_ERR_ARG;
+    if (n <= 0 || nb <= 0 || maxit < 0 || !(tau >= 0.0) || !(tau_s >= 0.0) || map < 0 || map > 1)
+        return OR_ERR_ARG;
     size_t nn = (size_t)n * n;
     double* X = (double*)malloc(sizeof(double) * nn);
     double* T = (double*)malloc(sizeof(double) * nn);
@@ -351,11 +401,11 @@ int or_ns(const double* S, int n, int nb, double tau, double tau_s, double mu_re
             Z[(long)i * n + j] = (i == j) ? 1.0 : 0.0;
         }
     memcpy(X, Y, sizeof(double) * nn);
+    double t_cur = or_trace_error(X, n);
 
     int it = 0;
     for (int k = 0; k < maxit; ++k) {
-        for (size_t q = 0; q < nn; ++q) T[q] = -0.5 * X[q];
-        for (int i = 0; i < n; ++i) T[(long)i * n + i] = 1.5 - 0.5 * X[(long)i * n + i];
+        or_apply_map(X, T, n, map, t_cur);
         long ty, tz, tx;
         if (order == 0) {
             ty = or_spamm(T, Y, W, n, nb, tau_s, NULL, 0);
@@ -374,9 +424,8 @@ int or_ns(const double* S, int n, int nb, double tau, double tau_s, double mu_re
         if (order == 0) tx = or_spamm(Y, Z, X, n, nb, tau, NULL, 0);
         else tx = or_spamm(Z, Y, X, n, nb, tau, NULL, 0);
         if (ty < 0 || tz < 0 || tx < 0) { free(X); free(T); free(W); return OR_ERR_NOMEM; }
-        double tr = 0.0;
-        for (int i = 0; i < n; ++i) tr += X[(long)i * n + i];
-        double tk = ((double)n - tr) / (double)n;
+        const double tk = or_trace_error(X, n);
+        t_cur = tk;
         if (t_hist) t_hist[k] = tk;
         if (task_hist) { task_hist[3 * k] = ty; task_hist[3 * k + 1] = tz; task_hist[3 * k + 2] = tx; }
         it = k + 1;

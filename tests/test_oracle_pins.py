@@ -328,3 +328,91 @@ def test_tol_stop_and_regularisation():
     lam, Q = np.linalg.eigh(Smu)
     assert np.linalg.norm(r2["Z"] - (Q / np.sqrt(lam)) @ Q.T) <= 1e-12 * np.linalg.norm(r2["Z"]) * 10
     assert r2["scale_c"] == pytest.approx(c0 + mu_rel * c0, rel=1e-15)
+
+
+# --------------------------------------------------------------------------- the damped, stabilised NS map (Sec. 4.2)
+
+
+def test_map_sigmoid_landmarks():
+    """alpha(t) and eps(t) against the landmarks of their definitions: the plain map, the asymptotes, the
+    midpoints (where the logistic factor is exactly 1/2) and the slopes there (amplitude * rate / 4)."""
+    assert oracle.map_params(0.7, oracle.MAP_NS) == (1.0, 0.0)
+    a, e = oracle.map_params(0.35)
+    assert a == pytest.approx(1.0 + 1.85 / 2, rel=1e-15)
+    a, e = oracle.map_params(0.30)
+    assert e == pytest.approx(0.1 / 2, rel=1e-15)
+    assert oracle.map_params(20.0) == (pytest.approx(2.85, rel=1e-15), pytest.approx(0.1, rel=1e-15))
+    a, e = oracle.map_params(-20.0)
+    assert a == 1.0 and 0.0 <= e < 1e-300
+    h = 1e-6
+    da = (oracle.map_params(0.35 + h)[0] - oracle.map_params(0.35 - h)[0]) / (2 * h)
+    de = (oracle.map_params(0.30 + h)[1] - oracle.map_params(0.30 - h)[1]) / (2 * h)
+    assert da == pytest.approx(1.85 * 50 / 4, rel=1e-7)
+    assert de == pytest.approx(0.1 * 75 / 4, rel=1e-7)
+    # both damp monotonically towards the plain map as t -> 0
+    ts = np.linspace(-0.2, 1.0, 61)
+    al = [oracle.map_params(t)[0] for t in ts]
+    ep = [oracle.map_params(t)[1] for t in ts]
+    assert all(np.diff(al) >= 0) and all(np.diff(ep) >= 0)
+
+
+def _scalar_scaled_ns(lam, iters, order=0):
+    """The scaled, stabilised map acting on the eigenvalues: for symmetric S = Q diag(lam) Q^T every iterate is
+    Q f(lam) Q^T, and t = (n - tr X)/n = 1 - mean(x) couples the eigenvalues only through alpha and eps."""
+    y = lam.copy()
+    z = np.ones_like(lam)
+    x = lam.copy()
+    for _ in range(iters):
+        a, e = oracle.map_params(1.0 - x.mean())
+        u = e + (1.0 - 2.0 * e) * x
+        t = 0.5 * math.sqrt(a) * (3.0 - a * u)
+        y = t * y
+        z = z * t
+        x = y * z
+    return y, z
+
+
+@pytest.mark.parametrize("iters", [1, 3, 8])
+def test_scaled_map_matches_eigen_recursion(iters):
+    n, nb = 40, 8
+    S = synth.gaussian_lattice(n, sigma=0.9, seed=0)
+    c = np.abs(S).sum(1).max()
+    lam, Q = np.linalg.eigh(S / c)
+    y, z = _scalar_scaled_ns(lam, iters)
+    for order in (0, 1):
+        r = oracle.sqrt_invsqrt(S, nb, 0.0, iters, order=order, map=oracle.MAP_SCALED)
+        Yk = (Q * (y * math.sqrt(c))) @ Q.T
+        Zk = (Q * (z / math.sqrt(c))) @ Q.T
+        assert np.linalg.norm(r["Y"] - Yk) <= 1e-12 * np.linalg.norm(Yk)
+        assert np.linalg.norm(r["Z"] - Zk) <= 1e-11 * np.linalg.norm(Zk)
+
+
+def test_scaled_map_fixed_point():
+    """At convergence h_alpha[u] = 1 with u = eps + (1 - 2 eps) x, i.e. u* = (3 - 2/sqrt(alpha))/alpha and
+    x* = (u* - eps)/(1 - 2 eps), with alpha and eps taken at t* = 1 - x* (solved here by fixed-point
+    iteration of that scalar equation).  The stabiliser leaves the trace error at t* ~ -eps(0), not 0."""
+    xs = 1.0
+    for _ in range(60):
+        a, e = oracle.map_params(1.0 - xs)
+        us = (3.0 - 2.0 / math.sqrt(a)) / a
+        xs = (us - e) / (1.0 - 2.0 * e)
+    t_star = 1.0 - xs
+    assert -1.8e-11 < t_star < -1.6e-11
+    S = synth.kms(128, 0.9)
+    r = oracle.sqrt_invsqrt(S, 16, 0.0, 40, map=oracle.MAP_SCALED)
+    assert abs(r["t_hist"][-1] - t_star) <= 2e-14
+    # ZSZ = x* I at the fixed point
+    assert oracle.residual(S, r["Z"]) == pytest.approx(abs(t_star) * math.sqrt(128), rel=2e-3)
+
+
+@pytest.mark.parametrize("kind", ["kms", "gauss"])
+def test_scaled_map_accelerates(kind):
+    """The scaled map needs fewer iterations than alpha = 1 on ill-conditioned inputs (Sec. 4.2)."""
+    S = synth.kms(200, 0.99) if kind == "kms" else synth.gaussian_lattice(125, 0.9, seed=0)
+
+    def iters_to(mp):
+        r = oracle.sqrt_invsqrt(S, 16, 0.0, 60, map=mp, tol_t=1e-9)
+        assert abs(r["t_hist"][-1]) <= 1e-9
+        return r["iters"]
+
+    assert iters_to(oracle.MAP_SCALED) + 3 <= iters_to(oracle.MAP_NS)
