@@ -32,6 +32,8 @@ N = 4096
 RHO = 0.9
 LEAF = 64
 MAXIT = 30
+MAP = 0  # 0: NS map with alpha = 1; 1: damped, stabilised h_alpha (--map scaled)
+TOL = 0.0  # > 0: a solve stops once |t_k| <= TOL (at most MAXIT iterations), on the device
 TAU_HEADLINE = 1e-14
 TAU_SWEEP = (1e-4, 1e-6, 1e-8)
 GATE = 1e-8
@@ -40,7 +42,9 @@ UNIT = "solves/s"
 
 
 def workload_name(tau: float, precision: str) -> str:
-    return (f"KMS rho={RHO} N={N} N_b={LEAF} tau={tau:g} tau_s={0.01 * tau:g} {MAXIT} dual-channel NS iterations, "
+    mp = ", damped stabilised map h_alpha" if MAP else ""
+    steps = f"{MAXIT}" if TOL <= 0 else f"until |t_k| <= {TOL:g} (at most {MAXIT})"
+    return (f"KMS rho={RHO} N={N} N_b={LEAF} tau={tau:g} tau_s={0.01 * tau:g} {steps} dual-channel NS iterations{mp}, "
             f"{precision} leaf products")
 
 
@@ -135,7 +139,7 @@ def oracle_solve_rate(S, tau: float, budget_s: float, min_solves: int = 1) -> tu
     t0 = time.perf_counter()
     cnt = 0
     while True:
-        oracle.sqrt_invsqrt(S, LEAF, tau, MAXIT)
+        oracle.sqrt_invsqrt(S, LEAF, tau, MAXIT, map=MAP, tol_t=TOL)
         cnt += 1
         el = time.perf_counter() - t0
         if cnt >= min_solves and el >= budget_s:
@@ -155,11 +159,11 @@ def run_reference(args, ws, rank):
     S = synth.kms(N, RHO)
     tau = args.tau
     for _ in range(args.warmup):
-        oracle.sqrt_invsqrt(S, LEAF, tau, MAXIT)
+        oracle.sqrt_invsqrt(S, LEAF, tau, MAXIT, map=MAP, tol_t=TOL)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.sqrt_invsqrt(S, LEAF, tau, MAXIT)
+        oracle.sqrt_invsqrt(S, LEAF, tau, MAXIT, map=MAP, tol_t=TOL)
         times.append(time.perf_counter() - t0)
     tot = sum(times)
     v = len(times) / tot
@@ -168,7 +172,7 @@ def run_reference(args, ws, rank):
             "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(tau, "FP64 CPU oracle"), "n": N, "leaf": LEAF, "tau": tau,
-                       "maxit": MAXIT},
+                       "maxit": MAXIT, "tol_t": TOL, "map": args.map},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{len(times)} full solves of the workload on {cores} OpenMP threads"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -241,8 +245,8 @@ def run_gpu(args, ws, rank, local):
     stream = torch.cuda.current_stream(dev)
 
     def solve(t, profile=False, residual=False):
-        return sp.sqrt_invsqrt(Sd, t, MAXIT, leaf=LEAF, precision=prec, Y=Yd, Z=Zd, profile=profile,
-                               residual=residual)
+        return sp.sqrt_invsqrt(Sd, t, MAXIT, leaf=LEAF, precision=prec, Y=Yd, Z=Zd, profile=profile, map=MAP,
+                               tol_t=TOL, residual=residual)
 
     # verification solve (untimed): residual against the gate, FP64 dense
     _, _, vst = solve(tau, residual=True)
@@ -297,27 +301,28 @@ def run_gpu(args, ws, rank, local):
     Sh = torch.from_numpy(S).pin_memory()
     Yh = torch.empty((N, N), dtype=torch.float64).pin_memory()
     Zh = torch.empty((N, N), dtype=torch.float64).pin_memory()
-    sp.sqrt_invsqrt(Sh, tau, MAXIT, leaf=LEAF, precision=prec, Y=Yh, Z=Zh)
+    sp.sqrt_invsqrt(Sh, tau, MAXIT, leaf=LEAF, precision=prec, Y=Yh, Z=Zh, map=MAP, tol_t=TOL)
     e2e_t = []
     for _ in range(args.steps):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        sp.sqrt_invsqrt(Sh, tau, MAXIT, leaf=LEAF, precision=prec, Y=Yh, Z=Zh)
+        sp.sqrt_invsqrt(Sh, tau, MAXIT, leaf=LEAF, precision=prec, Y=Yh, Z=Zh, map=MAP, tol_t=TOL)
         e2e_t.append(time.perf_counter() - t0)
     e2e_tot = max_over_ranks(sum(e2e_t), ws, dev)
 
     # the plain FP64-pipe method on the same workload, for comparison with the tensor-core path
     fp64_path = None
     if prec == sp.EMU64 and not args.no_fp64_path:
-        _, _, fst = sp.sqrt_invsqrt(Sd, tau, MAXIT, leaf=LEAF, precision=sp.FP64, Y=Yd, Z=Zd, residual=True)
+        _, _, fst = sp.sqrt_invsqrt(Sd, tau, MAXIT, leaf=LEAF, precision=sp.FP64, Y=Yd, Z=Zd, residual=True,
+                                         map=MAP, tol_t=TOL)
         ft = []
         for _ in range(3):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            sp.sqrt_invsqrt(Sd, tau, MAXIT, leaf=LEAF, precision=sp.FP64, Y=Yd, Z=Zd)
+            sp.sqrt_invsqrt(Sd, tau, MAXIT, leaf=LEAF, precision=sp.FP64, Y=Yd, Z=Zd, map=MAP, tol_t=TOL)
             e1.record(stream)
             e1.synchronize()
             ft.append(e0.elapsed_time(e1) / 1e3)
@@ -391,13 +396,14 @@ def run_gpu(args, ws, rank, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == sp.FP64 else "f16-split",
             "data": "synthetic",
             "config": {"workload": workload_name(tau, args.precision.upper()), "n": N, "leaf": LEAF, "tau": tau,
-                       "tau_s": 0.01 * tau, "maxit": MAXIT, "precision": args.precision,
+                       "tau_s": 0.01 * tau, "maxit": MAXIT, "tol_t": TOL, "precision": args.precision,
+                       "map": args.map,
                        "l2": "flushed by a 256 MB write before every timed solve",
                        "parallelism": f"replicas x{ws}"},
             "latency_ms": {"p50": p50, "p99": p99},
             "resid_F": vst["resid_F"], "gate": GATE, "gate_met": bool(vst["resid_F"] <= GATE),
             "tasks_per_solve": vst["tasks_total"], "volume_pct": 100.0 * vst["tasks_total"] / vst["tasks_dense"],
-            "t_final": vst["t_final"],
+            "t_final": vst["t_final"], "iters": vst["iters"],
             "roofline": roof,
             "fp64_path": fp64_path,
             "cpu_baseline": cpu,
@@ -434,7 +440,7 @@ def run_batched(args, local):
     t_batch = time.perf_counter() - t0
     t0 = time.perf_counter()
     for S, t in zip(Ss, taus):
-        sp.sqrt_invsqrt(S, t, MAXIT, leaf=LEAF, precision=prec)
+        sp.sqrt_invsqrt(S, t, MAXIT, leaf=LEAF, precision=prec, map=MAP, tol_t=TOL)
     torch.cuda.synchronize()
     t_seq = time.perf_counter() - t0
     line = {"metric": "batched NS solves/s (mixed KMS / 3D Gaussian, N in [128, 2048])", "value": len(Ss) / t_batch,
@@ -442,7 +448,7 @@ def run_batched(args, local):
             "data": "synthetic",
             "config": {"workload": f"{len(Ss)} matrices, sizes log-uniform in [128, 2048] (multiples of 32), "
                                    f"50% KMS rho~U(0.5,0.95), 50% Gaussian sigma~U(0.6,0.9), tau={args.batch_tau:g}, "
-                                   f"{MAXIT} iterations", "precision": args.precision},
+                                   f"{MAXIT} iterations", "precision": args.precision, "map": args.map},
             "one_call_per_matrix": {"value": len(Ss) / t_seq, "unit": UNIT},
             "tasks": int(sum(st["tasks_total"] for st in sts))}
     print(json.dumps(line), flush=True)
@@ -485,7 +491,8 @@ def run_serve(args, local):
     seq_status = []
     for S, r in zip(mats, trace):
         a = time.perf_counter()
-        _, _, st = sp.sqrt_invsqrt(S, r["tau"], MAXIT, leaf=LEAF, precision=prec, raise_on=False)
+        _, _, st = sp.sqrt_invsqrt(S, r["tau"], MAXIT, leaf=LEAF, precision=prec, raise_on=False, map=MAP,
+                                   tol_t=TOL)
         seq_lat.append(time.perf_counter() - a)
         seq_status.append(st["status"])
     t_seq = time.perf_counter() - t0
@@ -496,7 +503,7 @@ def run_serve(args, local):
             "config": {"workload": f"{len(ids)} requests, Poisson arrivals at {args.rate:g}/s, N log-uniform in "
                                    f"[256, {args.serve_max_n}] (multiples of 32), 3D Gaussian decay, tau in "
                                    "{1e-4, 1e-6, 1e-8}", "max_active": args.max_active, "budget_gb": args.budget_gb,
-                       "precision": args.precision},
+                       "precision": args.precision, "map": args.map},
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
             "requests": {"ok": int(sum(1 for x in statuses if x == 0)),
                          "diverged": int(sum(1 for x in statuses if x == -3)),
@@ -527,7 +534,7 @@ def run_c3(args, local):
     stream = torch.cuda.current_stream(dev)
     rows = []
     for tau in args.c3_tau:
-        kw = dict(leaf=LEAF, precision=prec, Y=Yd, Z=Zd, mu_rel=args.c3_mu)
+        kw = dict(leaf=LEAF, precision=prec, Y=Yd, Z=Zd, mu_rel=args.c3_mu, map=MAP, tol_t=TOL, raise_on=False)
         _, _, vst = sp.sqrt_invsqrt(Sd, tau, MAXIT, residual=True, **kw)
         sp.sqrt_invsqrt(Sd, tau, MAXIT, **kw)
         ts = []
@@ -542,7 +549,8 @@ def run_c3(args, local):
             ts.append(e0.elapsed_time(e1) / 1e3)
         rows.append({"tau": tau, "solves_per_s": len(ts) / sum(ts), "ms_per_solve": 1e3 * sum(ts) / len(ts),
                      "resid_F": vst["resid_F"], "gate_met": bool(vst["resid_F"] <= GATE),
-                     "tasks": vst["tasks_total"], "volume_pct": 100.0 * vst["tasks_total"] / vst["tasks_dense"]})
+                     "tasks": vst["tasks_total"], "volume_pct": 100.0 * vst["tasks_total"] / vst["tasks_dense"],
+                     "iters": vst["iters"], "t_final": vst["t_final"], "status": vst["status"]})
     cpu = None
     if args.c3_oracle:
         import oracle
@@ -558,15 +566,17 @@ def run_c3(args, local):
             "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
             "dtype": "f64" if prec == sp.FP64 else "f16-split", "data": "synthetic",
             "config": {"workload": f"3D Gaussian decay sigma={args.c3_sigma} on {args.c3_n} jittered Morton-ordered "
-                                   f"lattice points, N_b={LEAF}, {MAXIT} iterations, mu_rel={args.c3_mu}",
-                       "precision": args.precision, "tau_best": best["tau"]},
+                                   f"lattice points, N_b={LEAF}, "
+                                   + (f"{MAXIT} iterations" if TOL <= 0 else f"until |t_k| <= {TOL:g} (at most {MAXIT})")
+                                   + f", mu_rel={args.c3_mu}",
+                       "precision": args.precision, "map": args.map, "tau_best": best["tau"]},
             "per_tau": rows, "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
     return 0
 
 
 def main():
-    global N, MAXIT
+    global N, MAXIT, MAP, TOL
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -598,10 +608,16 @@ def main():
     ap.add_argument("--serve-max-n", type=int, default=8192)
     ap.add_argument("--max-active", type=int, default=8)
     ap.add_argument("--budget-gb", type=float, default=64.0)
+    ap.add_argument("--map", choices=["ns", "scaled"], default="ns",
+                    help="NS map: alpha = 1, or the damped, stabilised h_alpha of Sec. 4.2")
+    ap.add_argument("--tol-t", type=float, default=0.0,
+                    help="stop a solve once |t_k| <= tol (Sec. 4.2 trace error); 0 runs exactly --maxit steps")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     N, MAXIT = args.size, args.maxit
+    MAP = 1 if args.map == "scaled" else 0
+    TOL = args.tol_t
     ws, rank, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, ws, rank)

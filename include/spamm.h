@@ -8,7 +8,8 @@
  *     ||a^i|| ||b^i|| < tau ||A|| ||B|| (relative criterion, root norms of the
  *     whole operands), and only the surviving leaf-tile products are formed.
  *   - Dual-channel Newton-Schulz iteration, Eq. (cannonical), with the NS map
- *     h[x] = (3 - x)/2 (alpha = 1, Sec. 4.2): from S scaled into (0,1],
+ *     h[x] = (3 - x)/2 (alpha = 1, Sec. 4.2; opts->map selects the damped,
+ *     stabilised h_alpha of Sec. 4.2 "Mapping"): from S scaled into (0,1],
  *     X0 = Y0 = S, Z0 = I;  T = h[X];  Y <- T (x)_{tau_s} Y;  Z <- Z (x)_tau T;
  *     X <- Y (x)_tau Z;  Y -> S^{1/2}, Z -> S^{-1/2}.  tau_s is the tighter
  *     threshold of the "sensitive" y channel (Sec. 4.1, tau_s ~ 0.01 tau).
@@ -63,6 +64,19 @@ extern "C" {
                           the tensor cores with exact FP32 partial sums and
                           64-bit accumulation (FP64-class result)              */
 
+/* ---- NS map T = h_alpha[eps I + (1 - 2 eps) X] (Sec. 4.2 "Mapping") ----- */
+#define SPAMM_MAP_NS 0      /* alpha = 1, eps = 0: T = (3 I - X) / 2             */
+#define SPAMM_MAP_SCALED 1  /* the logistic h_alpha[u] = (sqrt(alpha)/2)(3 - alpha u)
+                               after the stabilising shift-and-scale
+                               u = eps + (1 - 2 eps) x of [0,1] onto [eps, 1-eps],
+                               with alpha(t) = 1 + 1.85/(1 + exp(-50 (t - .35)))
+                               and eps(t) = .1/(1 + exp(-75 (t - .30))) taken
+                               from the trace error t of the X being mapped
+                               (t_0 from S / c): scaling for the early steps,
+                               switched off towards convergence.  The
+                               stabiliser leaves a fixed point with
+                               t ~ -eps(0) ~ -1.7e-11 (ZSZ ~ (1 + 1.7e-11) I). */
+
 /* ---- order of the two channel products --------------------------------- */
 #define SPAMM_ORDER_PAPER 0       /* Y <- T Y, Z <- Z T, X <- Y Z (as printed)  */
 #define SPAMM_ORDER_TRANSPOSED 1  /* Y <- Y T, Z <- T Z, X <- Z Y: the exact
@@ -81,6 +95,7 @@ typedef struct spamm_opts {
     int profile;       /* nonzero: time every leaf-product kernel with CUDA
                           events on the call's stream (stats->gemm_ms)         */
     void* stream;      /* cudaStream_t; NULL = legacy default stream            */
+    int map;           /* SPAMM_MAP_NS or SPAMM_MAP_SCALED                      */
 } spamm_opts;
 
 typedef struct spamm_stats {
@@ -100,7 +115,8 @@ typedef struct spamm_stats {
 } spamm_stats;
 
 /* Fill *opts with defaults: leaf 64, SPAMM_FP64, tau_s = 0.01 tau, no shift,
- * fixed iteration count, paper order, no residual, default stream. */
+ * fixed iteration count, paper order, no residual, default stream,
+ * SPAMM_MAP_NS. */
 void spamm_opts_init(spamm_opts* opts);
 
 /*

@@ -695,13 +695,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
             const int eBc = eB_sh[slot][c];
             double* outt = a.C + (size_t)tile * NB * NB;
             const bool nsx = a.mode == EPI_NS_X;
+            const bool with_tr = a.mode != EPI_PLAIN;
             // T = 1.5 I - 0.5 X: off the diagonal -x/2 is the conversion of -t64 one binade lower; the one
-            // thread per column that owns the diagonal entry computes it up front
-            const int rd = (nsx && i == k && (c & 7) == r0 && gj < a.n) ? c : -1;
+            // thread per column that owns the diagonal entry computes it up front (and its trace share)
+            const int rd = (with_tr && i == k && (c & 7) == r0 && gj < a.n) ? c : -1;
             double xd = 0.0, vd = 0.0;
             if (rd >= 0) {
                 xd = fixed_to_double(sTop[c * 65 + c] + sBot[c * 65 + c], eA_sh[slot][c] + eBc - 48);
-                vd = 1.5 - 0.5 * xd;
+                vd = nsx ? 1.5 - 0.5 * xd : xd;
             }
             const int sc = eBc - 48 - (nsx ? 1 : 0);
             unsigned long long cmx = 0;
@@ -723,11 +724,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
                     if (lane == q0 + u) rowm = rm;
                 }
             }
-            if (cmx) atomicMax(a.cmaxC + gj, cmx);
-            if (lane < 8 && rowm) atomicMax(a.rmaxC + i * NB + r0 + 8 * lane, (unsigned long long)rowm << 32);
+            // X itself (EPI_X) is not sliced: the maxima are those of the map's output, taken by k_map
+            if (a.mode != EPI_X) {
+                if (cmx) atomicMax(a.cmaxC + gj, cmx);
+                if (lane < 8 && rowm) atomicMax(a.rmaxC + i * NB + r0 + 8 * lane, (unsigned long long)rowm << 32);
+            }
             for (int o = 16; o > 0; o >>= 1) nup = df_add(nup, df_shfl_xor(nup, o));
             if (lane == 0) nu_sh[ew] = nup;
-            const bool diag_tile = nsx && i == k;
+            const bool diag_tile = with_tr && i == k;
             if (diag_tile) {
                 double tr = rd >= 0 ? xd : 0.0;
                 for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);

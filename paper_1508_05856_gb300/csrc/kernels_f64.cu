@@ -91,10 +91,10 @@ __global__ void __launch_bounds__(kThreads) k_gemm_f64(const double* __restrict_
             const int r = ty + 16 * p, c = tx + 16 * q;
             const int gi = i * NB + r, gj = k * NB + c;
             double v = acc[p][q];
-            if (mode == EPI_NS_X) {
+            if (mode != EPI_PLAIN) {
                 const bool diag = (gi == gj) && (gi < n);
                 if (diag) tr += v;
-                v = diag ? 1.5 - 0.5 * v : -0.5 * v;
+                if (mode == EPI_NS_X) v = diag ? 1.5 - 0.5 * v : -0.5 * v;
             }
             Ct[(size_t)r * NB + c] = v;
             nu = fma(v, v, nu);
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(kThreads) k_gemm_f64(const double* __restrict_
         for (int w = 0; w < 8; ++w) s += red[w];
         leafC[tile] = s;
     }
-    if (mode == EPI_NS_X && i == k) {
+    if (mode != EPI_PLAIN && i == k) {
         __syncthreads();
         for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
         if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = tr;

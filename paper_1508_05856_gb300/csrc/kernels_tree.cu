@@ -165,30 +165,119 @@ void launch_pack(const double* src, int n, const Geometry& g, const double* mu, 
     note_launch();
 }
 
-// T = 1.5 I - 0.5 X on the logical diagonal, -0.5 X elsewhere (Sec. 4.2 map, alpha = 1).
-__global__ void __launch_bounds__(256) k_hmap(const double* __restrict__ X, int n, int m, int nb,
-                                              double* __restrict__ T, double* __restrict__ leaf) {
-    __shared__ double red[8];
-    const int tile = blockIdx.x;
-    const int i = tile / m, j = tile % m;
-    const int ne = nb * nb;
-    const double* x = X + (size_t)tile * ne;
-    double* t = T + (size_t)tile * ne;
-    double acc = 0.0;
-    for (int idx = threadIdx.x; idx < ne; idx += 256) {
-        const int r = idx / nb, cc = idx - r * nb;
-        const int gi = i * nb + r, gj = j * nb + cc;
-        const double xv = x[idx];
-        const double v = (gi == gj && gi < n) ? 1.5 - 0.5 * xv : -0.5 * xv;
-        t[idx] = v;
-        acc = fma(v, v, acc);
-    }
-    const double s = block_sum_256(acc, red);
-    if (threadIdx.x == 0) leaf[tile] = s;
+// ---------------------------------------------------------------- the NS map
+// Sum of the diagonal-tile trace partials, fixed order (lane-strided, then a
+// butterfly): the same value in every warp that calls it.  Warp-wide.
+__device__ __forceinline__ double trace_sum_warp(const double* __restrict__ trace_part, int m) {
+    double tr = 0.0;
+    for (int i = (int)(threadIdx.x & 31); i < m; i += 32) tr += trace_part[i];
+    for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+    return tr;
 }
 
-void launch_hmap(const double* X, const Geometry& g, TileMat T, cudaStream_t st) {
-    k_hmap<<<g.m * g.m, 256, 0, st>>>(X, g.n, g.m, g.nb, T.t, T.tree);
+// trace_part[i] = sum of the logical diagonal of tile (i, i), one warp per tile.
+__global__ void __launch_bounds__(32) k_trace_parts(const double* __restrict__ X, int n, int m, int nb,
+                                                    double* __restrict__ trace_part) {
+    const int i = blockIdx.x;
+    const double* x = X + ((size_t)i * m + i) * nb * nb;
+    const int cnt = min(nb, n - i * nb);
+    double s = 0.0;
+    for (int r = threadIdx.x; r < cnt; r += 32) s += x[(size_t)r * nb + r];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) trace_part[i] = s;
+}
+
+void launch_trace_parts(const double* X, const Geometry& g, double* trace_part, cudaStream_t st) {
+    k_trace_parts<<<g.m, 32, 0, st>>>(X, g.n, g.m, g.nb, trace_part);
+    note_launch();
+}
+
+// T = h_alpha[U], U = eps I + (1 - 2 eps) X, the NS logistic after the
+// stabilising shift-and-scale (Sec. 4.2 "Mapping"), written as T = c0 I + c1 X
+// with c0 = (sqrt(alpha)/2)(3 - alpha eps), c1 = -(sqrt(alpha)/2) alpha (1 - 2 eps).
+// SPAMM_MAP_SCALED takes alpha and eps from the sigmoidal damping functions of
+// t = (n - tr X)/n; SPAMM_MAP_NS is alpha = 1, eps = 0 (c0 = 1.5, c1 = -0.5,
+// both exact).  Grid-stride over tiles; a tile whose X is exactly zero (leaf
+// norm 0, data unwritten) off the diagonal stays zero.  Writes T's leaf
+// norms and, when rmax is set (64 x 64 tiles), T's row/column magnitude maxima.
+__global__ void __launch_bounds__(256, 4) k_map(const double* X, double* T, const double* leafX, double* leafT,
+                                                int n, int m, int nb, int map, const double* __restrict__ trace_part,
+                                                unsigned long long* __restrict__ rmax,
+                                                unsigned long long* __restrict__ cmax, const int* __restrict__ done) {
+    grid_dependency_wait();
+    if (done && *done) return;
+    __shared__ double red[8];
+    __shared__ double coef[2];
+    __shared__ unsigned long long cm_sh[4][64];
+    if (threadIdx.x < 32) {
+        double alpha = 1.0, eps = 0.0;
+        if (map == SPAMM_MAP_SCALED) {
+            const double t = ((double)n - trace_sum_warp(trace_part, m)) / (double)n;
+            alpha = 1.0 + 1.85 / (1.0 + exp(-50.0 * (t - 0.35)));
+            eps = 0.1 / (1.0 + exp(-75.0 * (t - 0.30)));
+        }
+        if (threadIdx.x == 0) {
+            const double hr = 0.5 * sqrt(alpha);
+            coef[0] = hr * (3.0 - alpha * eps);
+            coef[1] = -(hr * alpha) * (1.0 - 2.0 * eps);
+        }
+    }
+    __syncthreads();
+    const double c0 = coef[0], c1 = coef[1];
+    const int ne = nb * nb;
+    const int lane = threadIdx.x & 31;
+    for (int tile = blockIdx.x; tile < m * m; tile += gridDim.x) {
+        const int i = tile / m, j = tile - (tile / m) * m;
+        const double* x = X + (size_t)tile * ne;
+        double* t = T + (size_t)tile * ne;
+        const double nu_x = leafX[tile];
+        __syncthreads();  // every thread has read leafX[tile] before thread 0 may overwrite it (in place)
+        if (nu_x == 0.0 && i != j) {
+            if (T != X)
+                for (int idx = threadIdx.x; idx < ne; idx += 256) t[idx] = 0.0;
+            if (threadIdx.x == 0) leafT[tile] = 0.0;
+            continue;
+        }
+        double acc = 0.0;
+        unsigned long long cmx = 0;
+        for (int idx = threadIdx.x; idx < ne; idx += 256) {
+            const int r = idx / nb, cc = idx - r * nb;
+            const int gi = i * nb + r, gj = j * nb + cc;
+            const double xv = x[idx];
+            const double v = (gi == gj && gi < n) ? fma(c1, xv, c0) : c1 * xv;
+            t[idx] = v;
+            acc = fma(v, v, acc);
+            if (rmax) {
+                // 64-wide tiles: this thread keeps column threadIdx.x & 63, and the row's 64 entries sit in
+                // two consecutive warps; the maxima feed only the slicing exponents, so the upper 32 bits
+                // (sign cleared) carry what is needed
+                const unsigned long long vb = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+                cmx = max(cmx, vb);
+                const unsigned rm = __reduce_max_sync(0xffffffffu, (unsigned)(vb >> 32));
+                if (lane == 0 && rm) atomicMax(rmax + (size_t)i * nb + r, (unsigned long long)rm << 32);
+            }
+        }
+        if (rmax) {
+            cm_sh[threadIdx.x >> 6][threadIdx.x & 63] = cmx;
+            __syncthreads();
+            if (threadIdx.x < 64) {
+                const unsigned long long mx =
+                    max(max(cm_sh[0][threadIdx.x], cm_sh[1][threadIdx.x]), max(cm_sh[2][threadIdx.x], cm_sh[3][threadIdx.x]));
+                if (mx) atomicMax(cmax + (size_t)j * nb + threadIdx.x, mx);
+            }
+        }
+        const double s = block_sum_256(acc, red);
+        if (threadIdx.x == 0) leafT[tile] = s;
+    }
+}
+
+void launch_map(const double* X, const double* leafX, TileMat T, const Geometry& g, int map, const double* trace_part,
+                bool maxima, const int* done, cudaStream_t st) {
+    // one resident wave (four 256-thread blocks per SM), so a dependent launch never waits on a later wave
+    const int grid = std::min(device_sm_count() * 4, g.m * g.m);
+    launch_dependent(k_map, dim3(grid), dim3(256), 0, st, X, T.t, leafX, T.tree, g.n, g.m, g.nb, map, trace_part,
+                     maxima ? T.rmax : (unsigned long long*)nullptr, maxima ? T.cmax : (unsigned long long*)nullptr,
+                     done);
     note_launch();
 }
 
@@ -226,18 +315,20 @@ __device__ __forceinline__ double child_sum(const double* ch, int dc, int I, int
 }
 
 // t_k = (n - tr X)/n from the diagonal-tile trace partials (fixed-order warp
-// reduction), t_hist[k], iteration count and the tolerance stop.
-__device__ __forceinline__ void trace_error(const double* __restrict__ trace_part, int n, int m, int k, double tol_t,
-                                            double* __restrict__ t_hist, int* __restrict__ done,
-                                            int* __restrict__ iters) {
-    double tr = 0.0;
-    for (int i = threadIdx.x; i < m; i += 32) tr += trace_part[i];
-    for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+// reduction) into t_hist[k], k = *iters the iterations done so far; then the
+// count and the stop (tolerance reached, or the last of maxit iterations),
+// which also ends a graph's conditional loop.
+__device__ __forceinline__ void trace_error(const double* __restrict__ trace_part, int n, int m, const TreeExtra& ex) {
+    const double tr = trace_sum_warp(trace_part, m);
     if (threadIdx.x != 0) return;
+    const int k = *ex.iters;
     const double t = ((double)n - tr) / (double)n;
-    t_hist[k] = t;
-    *iters = k + 1;
-    if (tol_t > 0.0 && fabs(t) <= tol_t) *done = 1;
+    ex.t_hist[k] = t;
+    *ex.iters = k + 1;
+    if ((ex.tol_t > 0.0 && fabs(t) <= ex.tol_t) || k + 1 >= ex.maxit) {
+        *ex.done = 1;
+        if (ex.has_cond) cudaGraphSetConditional(ex.cond, 0u);
+    }
 }
 
 // Levels whose children exceed 64 x 64 go through global memory; from there
@@ -299,7 +390,7 @@ __global__ void __launch_bounds__(1024) k_tree(TreeDev td, double* __restrict__ 
     }
     if (ex.zero_int && threadIdx.x < ex.zero_n) ex.zero_int[threadIdx.x] = 0;
     if (ex.trace_part && threadIdx.x < 32)
-        trace_error(ex.trace_part, ex.n, td.m, ex.k, ex.tol_t, ex.t_hist, ex.done, ex.iters);
+        trace_error(ex.trace_part, ex.n, td.m, ex);
 }
 
 void launch_tree(const Geometry& g, double* tree, const int* done, cudaStream_t st, const TreeExtra& ex) {
@@ -385,7 +476,7 @@ __global__ void __launch_bounds__(256) k_cull(TreeDev td, const double* __restri
         if (threadIdx.x == 0) {
             int sacc = 0;
             for (int w = 0; w < 8; ++w) sacc += red[w];
-            if (sacc) atomicAdd(total, (unsigned long long)sacc);
+            if (sacc) atomicAdd(co.iter ? total + 3 * (size_t)*co.iter : total, (unsigned long long)sacc);
         }
     }
 }
@@ -401,10 +492,16 @@ void launch_cull(const Geometry& g, const double* treeA, const double* treeB, do
 // ---------------------------------------------------------------- unpack
 __global__ void __launch_bounds__(256) k_unpack(const double* __restrict__ src, const double* __restrict__ leaf,
                                                 int n, int m, int nb, double* __restrict__ dst,
-                                                const double* __restrict__ mul, const double* __restrict__ div) {
+                                                const double* __restrict__ mul, const double* __restrict__ div,
+                                                const double* __restrict__ src_alt, const double* __restrict__ leaf_alt,
+                                                const int* __restrict__ iters, int iters_src) {
     const int tile = blockIdx.x;
     const int i = tile / m, j = tile % m;
     const int ne = nb * nb;
+    if (iters && ((*iters - iters_src) & 1)) {
+        src = src_alt;
+        leaf = leaf_alt;
+    }
     const double* s = src + (size_t)tile * ne;
     const double fm = mul ? *mul : 1.0;
     const double fd = div ? *div : 1.0;
@@ -422,8 +519,10 @@ __global__ void __launch_bounds__(256) k_unpack(const double* __restrict__ src, 
 }
 
 void launch_unpack(const double* src, const double* leaf, const Geometry& g, double* dst, const double* mul,
-                   const double* div, cudaStream_t st) {
-    k_unpack<<<g.m * g.m, 256, 0, st>>>(src, leaf, g.n, g.m, g.nb, dst, mul, div);
+                   const double* div, cudaStream_t st, const double* src_alt, const double* leaf_alt,
+                   const int* iters, int iters_src) {
+    k_unpack<<<g.m * g.m, 256, 0, st>>>(src, leaf, g.n, g.m, g.nb, dst, mul, div, src_alt, leaf_alt, iters,
+                                         iters_src);
     note_launch();
 }
 

@@ -25,7 +25,12 @@
 namespace spamm {
 
 static std::atomic<long long> g_launches{0};
-void note_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+// this thread's launches: what a capture on this thread enqueued (other threads may launch meanwhile)
+static thread_local long long t_launches = 0;
+void note_launch(int k) {
+    g_launches.fetch_add(k, std::memory_order_relaxed);
+    t_launches += k;
+}
 
 static std::mutex g_attr_mu;
 static bool g_attr_done[64] = {};
@@ -95,12 +100,12 @@ struct GraphKey {
     const double* S = nullptr;
     double* Y = nullptr;
     double* Z = nullptr;
-    int n = 0, leaf = 0, precision = 0, order = 0, maxit = 0, profile = 0;
-    double tau = 0.0, tau_s = 0.0, mu_rel = 0.0;
+    int n = 0, leaf = 0, precision = 0, order = 0, maxit = 0, profile = 0, map = 0;
+    double tau = 0.0, tau_s = 0.0, mu_rel = 0.0, tol_t = 0.0;
     bool operator==(const GraphKey& o) const {
         return S == o.S && Y == o.Y && Z == o.Z && n == o.n && leaf == o.leaf && precision == o.precision &&
-               order == o.order && maxit == o.maxit && profile == o.profile && tau == o.tau && tau_s == o.tau_s &&
-               mu_rel == o.mu_rel;
+               order == o.order && maxit == o.maxit && profile == o.profile && map == o.map && tau == o.tau &&
+               tau_s == o.tau_s && mu_rel == o.mu_rel && tol_t == o.tol_t;
     }
 };
 
@@ -147,10 +152,13 @@ struct Plan {
     // CUDA graph of the last fixed-iteration solve and what it was captured for
     cudaGraphExec_t gexec = nullptr;
     GraphKey gkey;
-    long long graph_kernels = 0;
+    long long graph_kernels = 0;       // kernels of one replay (a loop graph: without its body)
+    long long graph_body_kernels = 0;  // kernels of one loop body (two iterations)
+    bool graph_loop = false;           // the iteration is a WHILE conditional node
     int graph_events = 0;       // profiling events recorded inside the graph
     long long graph_gemm = 0;   // leaf-product launches inside the graph
     cudaStream_t gstream = nullptr;
+    cudaStream_t bstream = nullptr;    // captures the loop body
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 };
 
@@ -191,6 +199,7 @@ static void free_plan(Plan* p) {
     for (auto e : p->ev) cudaEventDestroy(e);
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     if (p->gstream) cudaStreamDestroy(p->gstream);
+    if (p->bstream) cudaStreamDestroy(p->bstream);
     if (p->ev_in) cudaEventDestroy(p->ev_in);
     if (p->ev_out) cudaEventDestroy(p->ev_out);
     cudaSetDevice(cur);
@@ -473,6 +482,12 @@ static double profiled_ms(Plan* p) {
     return ms;
 }
 
+static bool slicing_pending(const Plan* p, const TileMat& M) {
+    for (int q = 0; q < 6; ++q)
+        if (p->buf[q].t == M.t) return (p->sliced_mask >> q) & 1u;
+    return false;
+}
+
 // One SpAMM product of two packed operands into dst (tree leaves + levels).
 // Records that M's slices are complete once `st` reaches this point.
 static void mark_sliced(Plan* p, const TileMat& M, cudaStream_t st) {
@@ -487,13 +502,15 @@ static void mark_sliced(Plan* p, const TileMat& M, cudaStream_t st) {
 // then the tree pass of the previous product on the branch); the tree pass
 // may also carry the iteration's trace error (tk).
 static void product(Plan* p, const TileMat& A, const TileMat& B, TileMat& C, double tau, EpiMode mode,
-                    unsigned long long* ctr, cudaStream_t st, const TreeExtra* tk = nullptr, int slot = 0) {
+                    unsigned long long* ctr, cudaStream_t st, const TreeExtra* tk = nullptr, int slot = 0,
+                    int map = SPAMM_MAP_NS) {
     const Geometry& g = p->g;
     int* counts = slot ? p->counts2 : p->counts;
     int* jlist = slot ? p->jlist2 : p->jlist;
     int* tile_list = slot ? p->tile_list2 : p->tile_list;
     int* tile_count = p->flags + 16 + 8 * slot;  // kTileBuckets counts
-    CullOut co{counts, jlist, tile_list, tile_count, C.tree, mode == EPI_NS_X ? 1 : 0};
+    CullOut co{counts, jlist, tile_list, tile_count, C.tree, mode != EPI_PLAIN ? 1 : 0};
+    co.iter = p->flags + 1;  // the task counter of iteration k is ctr[3 k]
     co.buckets = kTileBuckets;
     if (p->emu) {
         co.zero_u64 = C.rmax;  // rmax and cmax, contiguous
@@ -501,9 +518,10 @@ static void product(Plan* p, const TileMat& A, const TileMat& B, TileMat& C, dou
     }
     launch_cull(g, A.tree, B.tree, tau, co, ctr, nullptr, p->flags, st);
     if (p->emu) {
-        // the operands' slices may still be in flight on a slicing stream
-        cudaStreamWaitEvent(st, A.sliced, 0);
-        if (B.sliced != A.sliced) cudaStreamWaitEvent(st, B.sliced, 0);
+        // the operands' slices may still be in flight on a slicing stream (only slicing enqueued since the
+        // last join is waited on: a captured loop body depends on nothing recorded outside it)
+        if (slicing_pending(p, A)) cudaStreamWaitEvent(st, A.sliced, 0);
+        if (B.sliced != A.sliced && slicing_pending(p, B)) cudaStreamWaitEvent(st, B.sliced, 0);
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (p->profile) {
@@ -521,6 +539,8 @@ static void product(Plan* p, const TileMat& A, const TileMat& B, TileMat& C, dou
     }
     if (e0 && e1) cudaEventRecordWithFlags(e1, st, cudaEventRecordExternal);
     p->gemm_launches++;
+    // X's map whose coefficients need the finished tr X: in place, with T's leaf norms (and maxima)
+    if (mode == EPI_X) launch_map(C.t, C.tree, C, g, map, p->trace_part, p->emu, p->flags, st);
     if (p->emu) {
         // tensor-core path: the leaf-product kernel wrote the output's leaf norms (all the tree and the next
         // culls need); its slices follow on the branch's slicing stream, beside the tree and the next culls.
@@ -700,18 +720,19 @@ static int residual_impl(Plan* p, const double* dS, const double* dZ, double* ou
     return SPAMM_OK;
 }
 
-// Enqueue the device work of one solve on st: scaling, packing, the NS loop
-// and unpacking (a1-a7).  With tol_t > 0 the host reads the stop flag after
-// every iteration; otherwise nothing here synchronises (so it can be captured
-// in a CUDA graph).  *iters gets the number of iterations enqueued.
-static int enqueue_solve(Plan* p, const double* dS, double* dY, double* dZ, int n, double tau, double tau_s,
-                         int maxit, const spamm_opts& o, cudaStream_t st, int* iters) {
+// The buffers of one solve: Y, Z and their successors (swapped every iteration) and T.
+struct SolveBufs {
+    TileMat Yb, Zb, Tb, Y2, Z2;
+};
+
+// a1-a2: flags and histories cleared, Gershgorin bound (plus the Tikhonov shift of Sec. 6) and scaling,
+// X0 = Y0 = S / c packed with leaf norms, T0 = h[X0], Z0 = I (and their slices on the tensor-core path).
+static int enqueue_prologue(Plan* p, const double* dS, int n, const spamm_opts& o, cudaStream_t st, SolveBufs* sb) {
     const Geometry& g = p->g;
     CK(cudaMemsetAsync(p->flags, 0, kFlagInts * sizeof(int), st));
     CK(cudaMemsetAsync(p->task_ctr, 0, (3 * (size_t)p->maxit_cap + 4) * sizeof(unsigned long long), st));
     CK(cudaMemsetAsync(p->t_hist, 0, (size_t)p->maxit_cap * sizeof(double), st));
 
-    // a1: Gershgorin bound (plus the Tikhonov shift of Sec. 6) and scaling
     double* c0 = p->scal + 0;
     double* mu = p->scal + 1;
     double* c = p->scal + 2;
@@ -725,78 +746,153 @@ static int enqueue_solve(Plan* p, const double* dS, double* dY, double* dZ, int 
     launch_gershgorin(dS, n, mu_ptr, p->rowsum, c, st);
     launch_sqrt_scalar(c, sqc, st);
 
-    // a2: X0 = Y0 = S / c (packed with leaf norms), T0 = h[X0], Z0 = I
-    TileMat Yb = p->buf[0], Zb = p->buf[1], Tb = p->buf[2], Y2 = p->buf[3], Z2 = p->buf[4];
-    launch_pack(dS, n, g, mu_ptr, c, Yb, st);
-    launch_tree(g, Yb.tree, nullptr, st);
-    launch_hmap(Yb.t, g, Tb, st);
-    launch_tree(g, Tb.tree, nullptr, st);
-    launch_identity(g, Zb, st);
-    launch_tree(g, Zb.tree, nullptr, st);
+    *sb = SolveBufs{p->buf[0], p->buf[1], p->buf[2], p->buf[3], p->buf[4]};
+    launch_pack(dS, n, g, mu_ptr, c, sb->Yb, st);
+    launch_tree(g, sb->Yb.tree, nullptr, st);
+    if (o.map == SPAMM_MAP_SCALED) launch_trace_parts(sb->Yb.t, g, p->trace_part, st);
+    launch_map(sb->Yb.t, sb->Yb.tree, sb->Tb, g, o.map, p->trace_part, false, nullptr, st);
+    launch_tree(g, sb->Tb.tree, nullptr, st);
+    launch_identity(g, sb->Zb, st);
+    launch_tree(g, sb->Zb.tree, nullptr, st);
     if (p->emu) {
-        prepare_emu(p, Yb, st);
-        prepare_emu(p, Tb, st);
-        prepare_emu(p, Zb, st);
+        prepare_emu(p, sb->Yb, st);
+        prepare_emu(p, sb->Tb, st);
+        prepare_emu(p, sb->Zb, st);
     }
     CK(cudaGetLastError());
+    return SPAMM_OK;
+}
 
-    // a3-a6: the iteration
-    int it_host = 0;
+// One iteration (a3-a6).  Its index k lives on the device (the iteration counter flags[1], advanced by the
+// X product's tree pass together with t_k), so the same launches serve every iteration of a loop; once the
+// stop flag is set (|t_k| <= tol_t, or maxit steps) every kernel returns at once.  cond (may be null) is the
+// graph conditional that the stopping tree pass clears.
+static int enqueue_iteration(Plan* p, SolveBufs& sb, double tau, double tau_s, int maxit, const spamm_opts& o,
+                             cudaStream_t st, const cudaGraphConditionalHandle* cond) {
+    const Geometry& g = p->g;
+    TreeExtra tk;
+    tk.trace_part = p->trace_part;
+    tk.n = g.n;
+    tk.maxit = maxit;
+    tk.tol_t = o.tol_t;
+    tk.t_hist = p->t_hist;
+    tk.done = p->flags;
+    tk.iters = p->flags + 1;
+    if (cond) {
+        tk.cond = *cond;
+        tk.has_cond = 1;
+    }
+    unsigned long long* ctr = p->task_ctr;  // + 3 k on the device
+    // the Y and Z updates are independent: the Z update runs on the side branch (a profiled call keeps them
+    // in order, so that each leaf-product timing is that kernel's own)
+    cudaStream_t zs = p->profile ? st : p->side;
+    if (zs != st) {
+        CK(cudaEventRecord(p->ev_fork, st));
+        CK(cudaStreamWaitEvent(zs, p->ev_fork, 0));
+    }
+    if (o.order == SPAMM_ORDER_PAPER) {
+        product(p, sb.Tb, sb.Yb, sb.Y2, tau_s, EPI_PLAIN, ctr + 0, st);           // Y <- T (x)_{tau_s} Y
+        product(p, sb.Zb, sb.Tb, sb.Z2, tau, EPI_PLAIN, ctr + 1, zs, nullptr, 1);  // Z <- Z (x)_tau T
+    } else {
+        product(p, sb.Yb, sb.Tb, sb.Y2, tau_s, EPI_PLAIN, ctr + 0, st);           // Y <- Y (x)_{tau_s} T
+        product(p, sb.Tb, sb.Zb, sb.Z2, tau, EPI_PLAIN, ctr + 1, zs, nullptr, 1);  // Z <- T (x)_tau Z
+    }
+    if (zs != st) {
+        CK(cudaEventRecord(p->ev_join, zs));
+        CK(cudaStreamWaitEvent(st, p->ev_join, 0));
+    }
+    // alpha = 1: T = h[X] fused into the X product's epilogue; the damped map needs tr X first
+    const EpiMode xmode = o.map == SPAMM_MAP_NS ? EPI_NS_X : EPI_X;
+    std::swap(sb.Yb, sb.Y2);
+    std::swap(sb.Zb, sb.Z2);
+    if (o.order == SPAMM_ORDER_PAPER)
+        product(p, sb.Yb, sb.Zb, sb.Tb, tau, xmode, ctr + 2, st, &tk, 0, o.map);  // X <- Y (x)_tau Z, T = h[X]
+    else
+        product(p, sb.Zb, sb.Yb, sb.Tb, tau, xmode, ctr + 2, st, &tk, 0, o.map);  // X <- Z (x)_tau Y, T = h[X]
+    CK(cudaGetLastError());
+    return SPAMM_OK;
+}
+
+// a7: unscale and unpack.  The iterates alternate between two buffers; `swaps` is the number of iterations
+// enqueued since sb was set up, and the unpack picks the buffer of the last iteration that ran.
+static int enqueue_epilogue(Plan* p, const SolveBufs& sb, double* dY, double* dZ, int swaps, cudaStream_t st) {
+    const Geometry& g = p->g;
+    const double* sqc = p->scal + 3;
+    join_slicing(p, st);
+    launch_unpack(sb.Yb.t, sb.Yb.tree, g, dY, sqc, nullptr, st, sb.Y2.t, sb.Y2.tree, p->flags + 1, swaps);
+    launch_unpack(sb.Zb.t, sb.Zb.tree, g, dZ, nullptr, sqc, st, sb.Z2.t, sb.Z2.tree, p->flags + 1, swaps);
+    CK(cudaGetLastError());
+    return SPAMM_OK;
+}
+
+// The whole solve on st, one launch sequence per iteration.  Nothing here synchronises unless host_poll is
+// set with tol_t > 0: then the host reads the stop flag after every iteration and stops enqueueing.
+static int enqueue_solve(Plan* p, const double* dS, double* dY, double* dZ, int n, double tau, double tau_s,
+                         int maxit, const spamm_opts& o, cudaStream_t st, bool host_poll) {
+    SolveBufs sb;
+    int e = enqueue_prologue(p, dS, n, o, st, &sb);
+    if (e) return e;
+    int swaps = 0;
     for (int k = 0; k < maxit; ++k) {
-        unsigned long long* ctr = p->task_ctr + 3 * (size_t)k;
-        // t_k rides on the X product's tree pass
-        TreeExtra tk;
-        tk.trace_part = p->trace_part;
-        tk.n = g.n;
-        tk.k = k;
-        tk.tol_t = o.tol_t;
-        tk.t_hist = p->t_hist;
-        tk.done = p->flags;
-        tk.iters = p->flags + 1;
-        // the Y and Z updates are independent: the Z update runs on the side branch (a profiled call
-        // keeps them in order, so that each leaf-product timing is that kernel's own)
-        cudaStream_t zs = p->profile ? st : p->side;
-        if (zs != st) {
-            CK(cudaEventRecord(p->ev_fork, st));
-            CK(cudaStreamWaitEvent(zs, p->ev_fork, 0));
-        }
-        if (o.order == SPAMM_ORDER_PAPER) {
-            product(p, Tb, Yb, Y2, tau_s, EPI_PLAIN, ctr + 0, st);           // Y <- T (x)_{tau_s} Y
-            product(p, Zb, Tb, Z2, tau, EPI_PLAIN, ctr + 1, zs, nullptr, 1);  // Z <- Z (x)_tau T
-        } else {
-            product(p, Yb, Tb, Y2, tau_s, EPI_PLAIN, ctr + 0, st);           // Y <- Y (x)_{tau_s} T
-            product(p, Tb, Zb, Z2, tau, EPI_PLAIN, ctr + 1, zs, nullptr, 1);  // Z <- T (x)_tau Z
-        }
-        if (zs != st) {
-            CK(cudaEventRecord(p->ev_join, zs));
-            CK(cudaStreamWaitEvent(st, p->ev_join, 0));
-        }
-        if (o.order == SPAMM_ORDER_PAPER) {
-            std::swap(Yb, Y2);
-            std::swap(Zb, Z2);
-            product(p, Yb, Zb, Tb, tau, EPI_NS_X, ctr + 2, st, &tk);  // X <- Y (x)_tau Z, T = h[X]
-        } else {
-            std::swap(Yb, Y2);
-            std::swap(Zb, Z2);
-            product(p, Zb, Yb, Tb, tau, EPI_NS_X, ctr + 2, st, &tk);  // X <- Z (x)_tau Y, T = h[X]
-        }
-        CK(cudaGetLastError());
-        it_host = k + 1;
-        if (o.tol_t > 0.0) {
+        if ((e = enqueue_iteration(p, sb, tau, tau_s, maxit, o, st, nullptr))) return e;
+        swaps = k + 1;
+        if (host_poll && o.tol_t > 0.0) {
             int done = 0;
             CK(cudaMemcpyAsync(&done, p->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
             if (done) break;
         }
     }
+    return enqueue_epilogue(p, sb, dY, dZ, swaps, st);
+}
 
-    // a7: unscale and unpack
-    join_slicing(p, st);
-    launch_unpack(Yb.t, Yb.tree, g, dY, sqc, nullptr, st);
-    launch_unpack(Zb.t, Zb.tree, g, dZ, nullptr, sqc, st);
-    CK(cudaGetLastError());
-    *iters = it_host;
-    return SPAMM_OK;
+// The solve captured with its iteration as a WHILE conditional node: the body holds two iterations (so the
+// alternating buffers are back in place after it) and runs until the stopping tree pass clears the
+// condition.  Only the iterations that run are launched.  Called while gstream is capturing.
+static int enqueue_solve_loop(Plan* p, const double* dS, double* dY, double* dZ, int n, double tau, double tau_s,
+                              int maxit, const spamm_opts& o, cudaStream_t st) {
+    SolveBufs sb;
+    int e = enqueue_prologue(p, dS, n, o, st, &sb);
+    if (e) return e;
+    join_slicing(p, st);  // the body waits on nothing recorded outside it
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t graph = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edata = nullptr;
+    size_t ndeps = 0;
+    CK(cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph, &deps, &edata, &ndeps));
+    if (cs != cudaStreamCaptureStatusActive) return SPAMM_ERR_CUDA;
+    cudaGraphConditionalHandle cond;
+    CK(cudaGraphConditionalHandleCreate(&cond, graph, maxit > 0 ? 1u : 0u, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, graph, deps, edata, ndeps, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    CK(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    CK(cudaStreamBeginCaptureToGraph(p->bstream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    const long long l0 = t_launches;
+    int eb = enqueue_iteration(p, sb, tau, tau_s, maxit, o, p->bstream, &cond);
+    if (!eb) eb = enqueue_iteration(p, sb, tau, tau_s, maxit, o, p->bstream, &cond);
+    if (!eb) join_slicing(p, p->bstream);
+    p->graph_body_kernels = t_launches - l0;
+    cudaGraph_t bg = nullptr;
+    const cudaError_t be = cudaStreamEndCapture(p->bstream, &bg);
+    if (eb) return eb;
+    CK(be);
+    return enqueue_epilogue(p, sb, dY, dZ, 0, st);
+}
+
+// SPAMM_NO_LOOP_GRAPH=1 captures one launch sequence per iteration instead of the conditional loop.
+static bool loop_graphs_enabled() {
+    static const bool on = [] {
+        const char* v = getenv("SPAMM_NO_LOOP_GRAPH");
+        return !(v && v[0] && v[0] != '0');
+    }();
+    return on;
 }
 
 static bool graphs_enabled() {
@@ -807,16 +903,46 @@ static bool graphs_enabled() {
     return on;
 }
 
-// Replay (or capture, then replay) the whole fixed-iteration solve as one
-// CUDA graph on the plan's own stream, ordered after and before `st`.
+// Replay (or capture, then replay) the whole solve as one CUDA graph on the plan's own stream, ordered after
+// and before `st`.  The iteration is a WHILE conditional node (only the iterations that run are launched);
+// a profiled solve, whose event records cannot sit in a conditional body, and a device or driver that
+// rejects the conditional graph get one launch sequence per iteration instead.
+static std::atomic<bool> g_loop_graph_ok{true};
+
+static int capture_solve(Plan* p, const double* dS, double* dY, double* dZ, int n, double tau, double tau_s,
+                         int maxit, const spamm_opts& o, bool loop, cudaGraphExec_t* exec) {
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(p->gstream, cudaStreamCaptureModeThreadLocal));
+    const int e = loop ? enqueue_solve_loop(p, dS, dY, dZ, n, tau, tau_s, maxit, o, p->gstream)
+                       : enqueue_solve(p, dS, dY, dZ, n, tau, tau_s, maxit, o, p->gstream, false);
+    const cudaError_t ce = cudaStreamEndCapture(p->gstream, &graph);
+    if (e || ce != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        if (!e) {
+            g_last_error = std::string("graph capture: ") + cudaGetErrorString(ce);
+            return SPAMM_ERR_CUDA;
+        }
+        return e;
+    }
+    const cudaError_t ie = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+        g_last_error = std::string("graph instantiate: ") + cudaGetErrorString(ie);
+        return SPAMM_ERR_CUDA;
+    }
+    return SPAMM_OK;
+}
+
 static int solve_graph(Plan* p, const double* dS, double* dY, double* dZ, int n, double tau, double tau_s, int maxit,
                        const spamm_opts& o, cudaStream_t st) {
     if (!p->gstream) {
         CK(cudaStreamCreateWithFlags(&p->gstream, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&p->bstream, cudaStreamNonBlocking));
         CK(cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&p->ev_out, cudaEventDisableTiming));
     }
-    const GraphKey key{dS, dY, dZ, n, o.leaf, o.precision, o.order, maxit, o.profile ? 1 : 0, tau, tau_s, o.mu_rel};
+    const GraphKey key{dS, dY, dZ, n, o.leaf, o.precision, o.order, maxit, o.profile ? 1 : 0, o.map, tau, tau_s,
+                       o.mu_rel, o.tol_t};
     CK(cudaEventRecord(p->ev_in, st));
     CK(cudaStreamWaitEvent(p->gstream, p->ev_in, 0));
     if (!p->gexec || !(p->gkey == key)) {
@@ -824,23 +950,29 @@ static int solve_graph(Plan* p, const double* dS, double* dY, double* dZ, int n,
             cudaGraphExecDestroy(p->gexec);
             p->gexec = nullptr;
         }
-        const long long l0 = g_launches.load();
-        cudaGraph_t graph = nullptr;
-        CK(cudaStreamBeginCapture(p->gstream, cudaStreamCaptureModeThreadLocal));
-        int iters = 0;
-        const int e = enqueue_solve(p, dS, dY, dZ, n, tau, tau_s, maxit, o, p->gstream, &iters);
-        const cudaError_t ce = cudaStreamEndCapture(p->gstream, &graph);
-        if (e) {
-            if (graph) cudaGraphDestroy(graph);
-            return e;
+        const long long l0 = t_launches;
+        const int ev0 = p->ev_used;
+        const bool loop = g_loop_graph_ok && !p->profile && loop_graphs_enabled();
+        int e = capture_solve(p, dS, dY, dZ, n, tau, tau_s, maxit, o, loop, &p->gexec);
+        if (e == SPAMM_ERR_CUDA && loop) {
+            // conditional graphs unavailable here: fall back to one launch sequence per iteration
+            cudaGetLastError();
+            g_loop_graph_ok = false;
+            p->gexec = nullptr;
+            p->sliced_mask = 0;
+            p->ev_used = ev0;
+            p->gemm_launches = 0;
+            g_launches.fetch_sub(t_launches - l0);
+            t_launches = l0;
+            e = capture_solve(p, dS, dY, dZ, n, tau, tau_s, maxit, o, false, &p->gexec);
         }
-        CK(ce);
-        const cudaError_t ie = cudaGraphInstantiate(&p->gexec, graph, 0);
-        cudaGraphDestroy(graph);
-        CK(ie);
+        if (e) return e;
         p->gkey = key;
-        p->graph_kernels = g_launches.load() - l0;
+        p->graph_loop = loop && g_loop_graph_ok;
+        p->graph_kernels = t_launches - l0;
         g_launches.fetch_sub(p->graph_kernels);  // counted again when the graph runs
+        t_launches = l0;
+        if (p->graph_loop) p->graph_kernels -= p->graph_body_kernels;
         p->graph_events = p->ev_used;
         p->graph_gemm = p->gemm_launches;
     }
@@ -848,7 +980,9 @@ static int solve_graph(Plan* p, const double* dS, double* dY, double* dZ, int n,
     p->ev_used = p->graph_events;
     p->gemm_launches = p->graph_gemm;
     CK(cudaGraphLaunch(p->gexec, p->gstream));
-    note_launch((int)p->graph_kernels);
+    // a loop graph launches its body once per two iterations run: counted after the call from the iteration
+    // count (graph_kernels then covers the prologue, one body and the epilogue)
+    if (!p->graph_loop) note_launch((int)p->graph_kernels);
     CK(cudaEventRecord(p->ev_out, p->gstream));
     CK(cudaStreamWaitEvent(st, p->ev_out, 0));
     return SPAMM_OK;
@@ -878,12 +1012,12 @@ static int sqrt_impl(const double* S, int n, double tau, int maxit, double* Y, d
     begin_call(p, o.profile != 0, o.precision == SPAMM_EMU64);
     if (p->emu && (e = ensure_emu(p))) return e;
 
-    int it_host = 0;
-    if (o.tol_t == 0.0 && graphs_enabled()) {
+    const int it_host = maxit;  // at most; the device counts the iterations that ran
+    const bool graph = graphs_enabled();
+    if (graph) {
         if ((e = solve_graph(p, dS, dY, dZ, n, tau, tau_s, maxit, o, st))) return e;
-        it_host = maxit;
     } else {
-        if ((e = enqueue_solve(p, dS, dY, dZ, n, tau, tau_s, maxit, o, st, &it_host))) return e;
+        if ((e = enqueue_solve(p, dS, dY, dZ, n, tau, tau_s, maxit, o, st, true))) return e;
     }
     double* c = p->scal + 2;
     double resid = -1.0;
@@ -910,7 +1044,9 @@ static int sqrt_impl(const double* S, int n, double tau, int maxit, double* Y, d
         return SPAMM_ERR_TIMEOUT;
     }
 
-    const int iters = it_host;
+    // iterations run on the device (fewer than enqueued once |t_k| <= tol_t)
+    const int iters = std::min(it_host, flags_h[1]);
+    if (graph && p->graph_loop) note_launch((int)(p->graph_kernels + (long long)((iters + 1) / 2) * p->graph_body_kernels));
     long long total = 0;
     for (int q = 0; q < 3 * iters; ++q) total += (long long)kc[q];
     const double t_final = iters > 0 ? th[iters - 1] : 0.0;
@@ -962,6 +1098,10 @@ static int check_common(int n, double tau, const spamm_opts& o) {
         g_last_error = "unknown order";
         return SPAMM_ERR_ARG;
     }
+    if (o.map != SPAMM_MAP_NS && o.map != SPAMM_MAP_SCALED) {
+        g_last_error = "unknown map";
+        return SPAMM_ERR_ARG;
+    }
     if (std::isnan(o.tau_s) || std::isnan(o.mu_rel) || o.mu_rel < 0.0 || std::isnan(o.tol_t) || o.tol_t < 0.0) {
         g_last_error = "tau_s, mu_rel, tol_t must be numbers (mu_rel, tol_t >= 0)";
         return SPAMM_ERR_ARG;
@@ -1011,6 +1151,7 @@ void spamm_opts_init(spamm_opts* o) {
     o->order = SPAMM_ORDER_PAPER;
     o->residual = 0;
     o->stream = nullptr;
+    o->map = SPAMM_MAP_NS;
 }
 
 int spamm_autotune_leaf(const double* S, int n, double tau, const spamm_opts* opts, int* leaf) {

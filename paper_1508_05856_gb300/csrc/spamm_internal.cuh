@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <cstddef>
 
+#include "spamm.h"
+
 namespace spamm {
 
 constexpr int kMaxLevels = 24;
@@ -54,7 +56,11 @@ struct TreeDev {
 };
 TreeDev tree_dev(const Geometry& g);
 
-enum EpiMode { EPI_PLAIN = 0, EPI_NS_X = 1 };
+// Leaf-product epilogues: the plain product; X with T = 1.5 I - 0.5 X fused
+// (the alpha = 1 map) plus the trace partials; X itself plus the trace
+// partials (for a map whose coefficients depend on tr X, applied by k_map
+// once the whole product is done).
+enum EpiMode { EPI_PLAIN = 0, EPI_NS_X = 1, EPI_X = 2 };
 
 // Counts kernel launches (spamm_kernel_launches); every launcher calls it.
 void note_launch(int k = 1);
@@ -109,23 +115,34 @@ void launch_scale_mu(const double* c0, double mu_rel, double* mu_out, cudaStream
 // dst = (src + mu delta) / c.  Edge padding is zero.
 void launch_pack(const double* src, int n, const Geometry& g, const double* mu, const double* scale_c,
                  TileMat dst, cudaStream_t st);
-// T = 1.5 I_n - 0.5 X elementwise on tiles (logical identity), with leaf norms.
-void launch_hmap(const double* X, const Geometry& g, TileMat T, cudaStream_t st);
+// trace_part[i] = logical trace of diagonal tile (i, i) of a packed matrix.
+void launch_trace_parts(const double* X, const Geometry& g, double* trace_part, cudaStream_t st);
+// T = h_alpha[eps I + (1 - 2 eps) X] elementwise on tiles (logical identity):
+// map SPAMM_MAP_NS (alpha = 1, eps = 0) or SPAMM_MAP_SCALED (alpha, eps from
+// t = (n - sum trace_part)/n).  X may be T.t (in place; leafX then T.tree).
+// Writes T's leaf norms and, with `maxima`, accumulates T's row/column
+// maxima into T.rmax/T.cmax (which must be zero).  Skipped once *done is set.
+void launch_map(const double* X, const double* leafX, TileMat T, const Geometry& g, int map, const double* trace_part,
+                bool maxima, const int* done, cudaStream_t st);
 // Z = I_n in tile-major form, with leaf norms.
 void launch_identity(const Geometry& g, TileMat Z, cudaStream_t st);
 // Work fused into the quadtree pass, all optional.  After the levels:
 // *zero_int = 0 (the output-tile counter, ready for the next cull); with
 // trace_part set, the iteration's trace error t_k = (n - sum trace_part)/n
-// into t_hist[k], *iters = k + 1, and *done = 1 once |t_k| <= tol_t > 0.
+// into t_hist[k] with k = *iters, then *iters = k + 1, and the stop:
+// *done = 1 (and the graph conditional `cond` cleared, if has_cond) once
+// |t_k| <= tol_t > 0 or k + 1 == maxit.
 struct TreeExtra {
     int* zero_int = nullptr;  // zero_n ints
     int zero_n = 1;
     const double* trace_part = nullptr;
-    int n = 0, k = 0;
+    int n = 0, maxit = 0;
     double tol_t = 0.0;
     double* t_hist = nullptr;
     int* done = nullptr;
     int* iters = nullptr;
+    cudaGraphConditionalHandle cond = 0;
+    int has_cond = 0;
 };
 // Upper quadtree levels from the leaf level (skipped when *done is set).
 void launch_tree(const Geometry& g, double* tree, const int* done, cudaStream_t st,
@@ -151,6 +168,7 @@ struct CullOut {
     unsigned long long* zero_u64 = nullptr;
     long zero_n = 0;
     int buckets = 1;
+    const int* iter = nullptr;  // set: the task count goes to total[3 * *iter]
 };
 
 // Buckets of listed output tiles by task count, most expensive first: the
@@ -180,8 +198,13 @@ void launch_cull(const Geometry& g, const double* treeA, const double* treeB, do
                  unsigned long long* total, double* thr_out, const int* done, cudaStream_t st);
 // Tile-major -> row-major with out = in * (*mul) or in / (*div) (one of them
 // null or both null).  Tiles whose leaf norm is 0 are written as zeros.
+// With `iters` set, the source is src/leaf when *iters - iters_src is even and
+// src_alt/leaf_alt when it is odd: the iterates alternate between two buffers,
+// and a solve that stopped on the device (|t_k| <= tol_t) ran *iters of the
+// iters_src iterations its launch sequence holds.
 void launch_unpack(const double* src, const double* leaf, const Geometry& g, double* dst, const double* mul,
-                   const double* div, cudaStream_t st);
+                   const double* div, cudaStream_t st, const double* src_alt = nullptr,
+                   const double* leaf_alt = nullptr, const int* iters = nullptr, int iters_src = 0);
 // sqrt of device scalar: out = sqrt(*c)
 void launch_sqrt_scalar(const double* c, double* out, cudaStream_t st);
 // sum over logical entries of (R - I)^2 -> *out (deterministic)

@@ -75,7 +75,7 @@ def test_emu_multiply_kms_scales():
 
 def _emu_ns(S, tau, maxit, **kw):
     Y, Z, st = sp.sqrt_invsqrt(dev(S), tau, maxit, leaf=64, precision=sp.EMU64, **kw)
-    ref = oracle.sqrt_invsqrt(S, 64, tau, maxit, **{k: v for k, v in kw.items() if k in ("order", "mu_rel")})
+    ref = oracle.sqrt_invsqrt(S, 64, tau, maxit, **{k: v for k, v in kw.items() if k in ("order", "mu_rel", "map")})
     ez = np.linalg.norm(Z.cpu().numpy() - ref["Z"]) / np.linalg.norm(ref["Z"])
     ey = np.linalg.norm(Y.cpu().numpy() - ref["Y"]) / np.linalg.norm(ref["Y"])
     return ez, ey, st, ref
@@ -137,3 +137,13 @@ def test_emu_output_tile_with_more_than_256_tasks():
     Co = oracle.leaf_products(A, B, nb, tasks)[:nb, :nb]
     As, Bs = A[:nb, :], B[:, :nb]
     assert (np.abs(C00 - Co) <= _tol(As, Bs, n)).all()
+
+
+@pytest.mark.parametrize("n,tau,order", [(256, 1e-8, 0), (700, 1e-10, 1)])
+def test_emu_ns_scaled_map(n, tau, order):
+    """Damped, stabilised map on the tensor-core path: X is written plain, the map kernel forms T in place
+    with its leaf norms and row/column maxima, then T is sliced."""
+    S = synth.gaussian_lattice(n, 0.9, seed=1)
+    ez, ey, st, ref = _emu_ns(S, tau, 20, order=order, map=sp.MAP_SCALED)
+    assert ez <= 1e-9 and ey <= 1e-9, (ez, ey)
+    np.testing.assert_allclose(st["t_hist"], ref["t_hist"], rtol=0, atol=1e-11)

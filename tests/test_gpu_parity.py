@@ -121,7 +121,7 @@ def test_host_and_device_pointers_agree():
 def _ns_compare(S, nb, tau, maxit, **kw):
     Y, Z, st = sp.sqrt_invsqrt(dev(S), tau, maxit, leaf=nb, **kw)
     Y, Z = host(Y), host(Z)
-    kw2 = {k: v for k, v in kw.items() if k in ("tau_s", "mu_rel", "order", "tol_t")}
+    kw2 = {k: v for k, v in kw.items() if k in ("tau_s", "mu_rel", "order", "tol_t", "map")}
     ref = oracle.sqrt_invsqrt(S, nb, tau, maxit, **kw2)
     assert st["iters"] == ref["iters"]
     ez = np.linalg.norm(Z - ref["Z"]) / np.linalg.norm(ref["Z"])
@@ -218,3 +218,72 @@ def test_leaf_autotuner():
     Y1, Z1, _ = sp.sqrt_invsqrt(S, 1e-8, 12, leaf=leaf)
     assert torch.equal(Y0, Y1) and torch.equal(Z0, Z1)
     assert sp.autotune_leaf(S, 1e-8, precision=sp.EMU64) == 64
+
+
+# ------------------------------------------------------------------------------------------ damped, stabilised map
+
+
+@pytest.mark.parametrize("n,nb,tau,order", [(200, 32, 1e-6, 0), (333, 64, 1e-8, 1), (96, 128, 0.0, 0),
+                                            (129, 32, 1e-10, 1)])
+def test_ns_scaled_map(n, nb, tau, order):
+    """alpha(t), eps(t) of Sec. 4.2 "Mapping" on an ill-conditioned Gaussian decay (sigma 0.9): the map runs
+    after the X product (it needs tr X), in place, with T's leaf norms."""
+    S = synth.gaussian_lattice(n, 0.9, seed=n)
+    Y, Z, st, ref = _ns_compare(S, nb, tau, 20, order=order, map=sp.MAP_SCALED)
+    assert st["t_hist"][0] > 0.35          # the first steps run with alpha well above 1
+
+
+def test_ns_scaled_map_converges_sooner():
+    S = synth.kms(300, 0.99)
+    # tau 1e-12 keeps the SpAMM error floor of t_k below the tolerance for both maps (17 vs 11 steps)
+    _, _, s1, _ = _ns_compare(S, 32, 1e-12, 40, tol_t=1e-9, map=sp.MAP_SCALED)
+    _, _, s0, _ = _ns_compare(S, 32, 1e-12, 40, tol_t=1e-9)
+    assert s1["iters"] + 3 <= s0["iters"]
+
+
+def test_ns_plain_map_is_default():
+    S = synth.gaussian_lattice(150, 0.7, seed=3)
+    a = sp.sqrt_invsqrt(dev(S), 1e-7, 10, leaf=32)
+    b = sp.sqrt_invsqrt(dev(S), 1e-7, 10, leaf=32, map=sp.MAP_NS)
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+
+
+def test_ns_scaled_map_batched_equals_single():
+    Ss = [synth.gaussian_lattice(n, 0.9, seed=n) for n in (120, 257)]
+    Ys, Zs, _ = sp.sqrt_invsqrt_batched([dev(S) for S in Ss], [1e-8, 1e-8], 15, leaf=32, map=sp.MAP_SCALED)
+    for S, Yb, Zb in zip(Ss, Ys, Zs):
+        Y1, Z1, _ = sp.sqrt_invsqrt(dev(S), 1e-8, 15, leaf=32, map=sp.MAP_SCALED)
+        assert torch.equal(Yb, Y1) and torch.equal(Zb, Z1)
+
+
+@pytest.mark.parametrize("tol,mp", [(1e-2, 0), (1e-3, 0), (1e-3, 1), (1e-4, 1)])
+def test_ns_tolerance_stop_in_graph(tol, mp):
+    """A solve that stops on |t_k| <= tol_t runs as one captured graph: the kernels after the stop return on
+    the device flag and the unpack takes the buffer of the last executed iteration (odd and even counts)."""
+    S = synth.kms(320, 0.9)
+    Y, Z, st, ref = _ns_compare(S, 32, 1e-10, 40, tol_t=tol, map=mp)
+    assert st["iters"] == ref["iters"] < 40
+    assert (st["task_hist"][st["iters"]:] == 0).all() if len(st["task_hist"]) > st["iters"] else True
+    # a second call replays the same graph
+    Y2, Z2, st2 = sp.sqrt_invsqrt(dev(S), 1e-10, 40, leaf=32, tol_t=tol, map=mp)
+    assert st2["iters"] == st["iters"] and np.array_equal(host(Y2), Y) and np.array_equal(host(Z2), Z)
+
+
+def test_loop_graph_launches_only_the_iterations_run():
+    """The iteration is a WHILE conditional node of the solve's graph: a solve stopped by tol_t launches the
+    kernels of the iterations it ran (rounded up to the two-iteration body), not those of maxit."""
+    S = synth.kms(256, 0.9)
+    kw = dict(leaf=32)
+
+    def launches(**extra):
+        sp.sqrt_invsqrt(dev(S), 1e-10, 30, **kw, **extra)          # captures the graph
+        torch.cuda.synchronize()
+        l0 = sp.kernel_launches()
+        _, _, st = sp.sqrt_invsqrt(dev(S), 1e-10, 30, **kw, **extra)
+        return sp.kernel_launches() - l0, st["iters"]
+
+    fixed, it_fixed = launches()
+    stopped, it_stop = launches(tol_t=1e-3)
+    assert it_fixed == 30 and it_stop < 12
+    per_iter = fixed / 30.0
+    assert stopped <= per_iter * (it_stop + 1) + 20, (stopped, fixed, it_stop)
