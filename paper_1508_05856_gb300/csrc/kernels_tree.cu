@@ -318,6 +318,7 @@ __device__ __forceinline__ double child_sum(const double* ch, int dc, int I, int
 // reduction) into t_hist[k], k = *iters the iterations done so far; then the
 // count and the stop (tolerance reached, or the last of maxit iterations),
 // which also ends a graph's conditional loop.
+template <bool kLoop>
 __device__ __forceinline__ void trace_error(const double* __restrict__ trace_part, int n, int m, const TreeExtra& ex) {
     const double tr = trace_sum_warp(trace_part, m);
     if (threadIdx.x != 0) return;
@@ -327,13 +328,16 @@ __device__ __forceinline__ void trace_error(const double* __restrict__ trace_par
     *ex.iters = k + 1;
     if ((ex.tol_t > 0.0 && fabs(t) <= ex.tol_t) || k + 1 >= ex.maxit) {
         *ex.done = 1;
-        if (ex.has_cond) cudaGraphSetConditional(ex.cond, 0u);
+        if constexpr (kLoop) cudaGraphSetConditional(ex.cond, 0u);
     }
 }
 
 // Levels whose children exceed 64 x 64 go through global memory; from there
 // on the children are held in shared memory (each level is still written
 // out), so the top levels cost shared-memory latency instead of global.
+// kLoop: the instance in a graph's conditional loop body, the only one that calls the device runtime
+// (profilers skip kernels that do, so every other launch uses the plain instance).
+template <bool kLoop>
 __global__ void __launch_bounds__(1024) k_tree(TreeDev td, double* __restrict__ tree, const int* __restrict__ done,
                                                TreeExtra ex) {
     grid_dependency_wait();
@@ -390,11 +394,14 @@ __global__ void __launch_bounds__(1024) k_tree(TreeDev td, double* __restrict__ 
     }
     if (ex.zero_int && threadIdx.x < ex.zero_n) ex.zero_int[threadIdx.x] = 0;
     if (ex.trace_part && threadIdx.x < 32)
-        trace_error(ex.trace_part, ex.n, td.m, ex);
+        trace_error<kLoop>(ex.trace_part, ex.n, td.m, ex);
 }
 
 void launch_tree(const Geometry& g, double* tree, const int* done, cudaStream_t st, const TreeExtra& ex) {
-    launch_dependent(k_tree, dim3(1), dim3(1024), 0, st, tree_dev(g), tree, done, ex);
+    if (ex.has_cond)
+        launch_dependent(k_tree<true>, dim3(1), dim3(1024), 0, st, tree_dev(g), tree, done, ex);
+    else
+        launch_dependent(k_tree<false>, dim3(1), dim3(1024), 0, st, tree_dev(g), tree, done, ex);
     note_launch();
 }
 
