@@ -65,7 +65,8 @@ def lib():
             L.or_gershgorin.argtypes = [dp, ctypes.c_int, ctypes.c_double]
             L.or_gershgorin.restype = ctypes.c_double
             L.or_ns.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, dp, dp, dp, lp, dp]
+                                ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, dp, dp, dp, lp,
+                                dp]
             L.or_map_params.argtypes = [ctypes.c_int, ctypes.c_double, dp, dp]
             L.or_map_params.restype = None
             L.or_ns.restype = ctypes.c_int
@@ -191,9 +192,14 @@ def map_params(t: float, map: int = MAP_SCALED) -> tuple[float, float]:
     return float(a[0]), float(e[0])
 
 
+CHANNEL_DUAL = 0    # Eq. (cannonical)
+CHANNEL_SINGLE = 1  # Eq. (single): z <- z h[x], x = z^T s z
+
+
 def sqrt_invsqrt(S, nb: int, tau: float, maxit: int, tau_s: float | None = None, mu_rel: float = 0.0,
-                 order: int = 0, tol_t: float = 0.0, map: int = MAP_NS) -> dict:
-    """Dual-channel NS iteration; returns Y ~ S^{1/2}, Z ~ S^{-1/2} and the per-iteration history."""
+                 order: int = 0, tol_t: float = 0.0, map: int = MAP_NS, channel: int = CHANNEL_DUAL) -> dict:
+    """NS square-root iteration (dual or single channel); returns Y ~ S^{1/2}, Z ~ S^{-1/2} and the
+    per-iteration history."""
     S = _mat(S)
     n = S.shape[0]
     if tau_s is None:
@@ -203,8 +209,8 @@ def sqrt_invsqrt(S, nb: int, tau: float, maxit: int, tau_s: float | None = None,
     th = np.zeros(max(maxit, 1))
     kh = np.zeros((max(maxit, 1), 3), dtype=np.int64)
     c = np.zeros(1)
-    it = lib().or_ns(_d(S), n, nb, tau, tau_s, mu_rel, maxit, order, tol_t, int(map), _d(Y), _d(Z), _d(th), _l(kh),
-                     _d(c))
+    it = lib().or_ns(_d(S), n, nb, tau, tau_s, mu_rel, maxit, order, tol_t, int(map), int(channel), _d(Y), _d(Z),
+                     _d(th), _l(kh), _d(c))
     if it < 0:
         raise RuntimeError(f"oracle NS failed ({it})")
     return {"Y": Y, "Z": Z, "iters": it, "t_hist": th[:it].copy(), "task_hist": kh[:it].copy(),

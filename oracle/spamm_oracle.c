@@ -23,7 +23,8 @@
  *      c10 = a10 b00 + a11 b10, c11 = a10 b01 + a11 b11);
  *   - leaf products are triple loops, accumulated per output tile with the
  *     surviving j in ascending order and the inner index ascending;
- *   - the square-root iteration is Eq. (cannonical), started from
+ *   - the square-root iteration is Eq. (cannonical) (or Eq. (single), the
+ *     single channel instance), started from
  *     X0 = Y0 = S / c, Z0 = I, where c is the Gershgorin bound of the
  *     largest eigenvalue (Sec. 3.2), with T = h_alpha[U] the NS logistic of
  *     Sec. 4.2 "Mapping" applied to the stabilised U = eps I + (1-2 eps) X:
@@ -365,6 +366,12 @@ static double or_trace_error(const double* X, int n) {
     return ((double)n - tr) / (double)n;
 }
 
+/* T = A^T (n x n). */
+static void or_transpose(const double* A, double* T, int n) {
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) T[(long)j * n + i] = A[(long)i * n + j];
+}
+
 /*
  * Y -> S^{1/2}, Z -> S^{-1/2} by the dual channel iteration with
  * T = h_alpha[eps I + (1 - 2 eps) X] (or_apply_map; map 0: T = 1.5 I - 0.5 X):
@@ -374,21 +381,35 @@ static double or_trace_error(const double* X, int n) {
  *   t_k = (n - tr X) / n (Sec. 4.2).
  * mu_rel > 0 regularises with S + mu I, mu = mu_rel * (Gershgorin bound of S)
  * (Sec. 6).  The map applied to X_k takes alpha and eps from t_k of that same
- * X_k (t_0 from X0 = S / c).  The iteration stops after maxit steps or once
- * |t_k| <= tol_t (tol_t > 0).  t_hist (maxit) and task_hist (3*maxit: y, z,
- * x products) may be NULL.  Returns the number of iterations run; *scale_c
- * receives c.
+ * X_k (t_0 from X0 = S / c).
+ *
+ * channel 1 is the single channel instance, Eq. (single), from X0 = s = S / c
+ * and Z0 = I, every product at tau:
+ *   Z <- Z (x)_tau T,   W <- s (x)_tau Z,   X <- Z^T (x)_tau W,
+ * i.e. x_k = z_k^T s z_k with the inner product s z_k taken first; Y = W
+ * (s z -> s^{1/2}).  Only the printed order (order 0) is defined for it.
+ *
+ * The iteration stops after maxit steps or once |t_k| <= tol_t (tol_t > 0).
+ * t_hist (maxit) and task_hist (3*maxit: the y, z, x products of the dual
+ * channel; z, s z, x of the single channel) may be NULL.  Returns the number
+ * of iterations run; *scale_c receives c.
  */
 int or_ns(const double* S, int n, int nb, double tau, double tau_s, double mu_rel, int maxit,
-          int order, double tol_t, int map, double* Y, double* Z, double* t_hist, long* task_hist,
-          double* scale_c) {
-    if (n <= 0 || nb <= 0 || maxit < 0 || !(tau >= 0.0) || !(tau_s >= 0.0) || map < 0 || map > 1)
+          int order, double tol_t, int map, int channel, double* Y, double* Z, double* t_hist,
+          long* task_hist, double* scale_c) {
+    if (n <= 0 || nb <= 0 || maxit < 0 || !(tau >= 0.0) || !(tau_s >= 0.0) || map < 0 || map > 1 ||
+        channel < 0 || channel > 1 || (channel == 1 && order != 0))
         return OR_ERR_ARG;
     size_t nn = (size_t)n * n;
     double* X = (double*)malloc(sizeof(double) * nn);
     double* T = (double*)malloc(sizeof(double) * nn);
     double* W = (double*)malloc(sizeof(double) * nn);
-    if (!X || !T || !W) { free(X); free(T); free(W); return OR_ERR_NOMEM; }
+    double* s1 = channel == 1 ? (double*)malloc(sizeof(double) * nn) : NULL;
+    double* Zt = channel == 1 ? (double*)malloc(sizeof(double) * nn) : NULL;
+    if (!X || !T || !W || (channel == 1 && (!s1 || !Zt))) {
+        free(X); free(T); free(W); free(s1); free(Zt);
+        return OR_ERR_NOMEM;
+    }
 
     double mu = 0.0;
     if (mu_rel > 0.0) mu = mu_rel * or_gershgorin(S, n, 0.0);
@@ -401,12 +422,29 @@ int or_ns(const double* S, int n, int nb, double tau, double tau_s, double mu_re
             Z[(long)i * n + j] = (i == j) ? 1.0 : 0.0;
         }
     memcpy(X, Y, sizeof(double) * nn);
+    if (channel == 1) memcpy(s1, Y, sizeof(double) * nn);
     double t_cur = or_trace_error(X, n);
 
     int it = 0;
     for (int k = 0; k < maxit; ++k) {
         or_apply_map(X, T, n, map, t_cur);
         long ty, tz, tx;
+        if (channel == 1) {
+            /* Eq. (single): z_k = z_{k-1} h[x_{k-1}], x_k = z_k^T s z_k */
+            tz = or_spamm(Z, T, W, n, nb, tau, NULL, 0);
+            memcpy(Z, W, sizeof(double) * nn);
+            ty = or_spamm(s1, Z, Y, n, nb, tau, NULL, 0);
+            or_transpose(Z, Zt, n);
+            tx = or_spamm(Zt, Y, X, n, nb, tau, NULL, 0);
+            if (ty < 0 || tz < 0 || tx < 0) { free(X); free(T); free(W); free(s1); free(Zt); return OR_ERR_NOMEM; }
+            const double tk = or_trace_error(X, n);
+            t_cur = tk;
+            if (t_hist) t_hist[k] = tk;
+            if (task_hist) { task_hist[3 * k] = tz; task_hist[3 * k + 1] = ty; task_hist[3 * k + 2] = tx; }
+            it = k + 1;
+            if (tol_t > 0.0 && fabs(tk) <= tol_t) break;
+            continue;
+        }
         if (order == 0) {
             ty = or_spamm(T, Y, W, n, nb, tau_s, NULL, 0);
             memcpy(Y, W, sizeof(double) * nn);
@@ -423,7 +461,7 @@ int or_ns(const double* S, int n, int nb, double tau, double tau_s, double mu_re
          * Y T / T Z with X = Y Z is unstable near the fixed point. */
         if (order == 0) tx = or_spamm(Y, Z, X, n, nb, tau, NULL, 0);
         else tx = or_spamm(Z, Y, X, n, nb, tau, NULL, 0);
-        if (ty < 0 || tz < 0 || tx < 0) { free(X); free(T); free(W); return OR_ERR_NOMEM; }
+        if (ty < 0 || tz < 0 || tx < 0) { free(X); free(T); free(W); free(s1); free(Zt); return OR_ERR_NOMEM; }
         const double tk = or_trace_error(X, n);
         t_cur = tk;
         if (t_hist) t_hist[k] = tk;
@@ -431,10 +469,11 @@ int or_ns(const double* S, int n, int nb, double tau, double tau_s, double mu_re
         it = k + 1;
         if (tol_t > 0.0 && fabs(tk) <= tol_t) break;
     }
+    /* single channel with no iteration: Y = s Z0 = s, already in Y */
     double sc = sqrt(c);
     for (size_t q = 0; q < nn; ++q) { Y[q] = Y[q] * sc; Z[q] = Z[q] / sc; }
     if (scale_c) *scale_c = c;
-    free(X); free(T); free(W);
+    free(X); free(T); free(W); free(s1); free(Zt);
     return it;
 }
 

@@ -416,3 +416,75 @@ def test_scaled_map_accelerates(kind):
         return r["iters"]
 
     assert iters_to(oracle.MAP_SCALED) + 3 <= iters_to(oracle.MAP_NS)
+
+
+# --------------------------------------------------------------------------- the single channel instance, Eq. (single)
+
+
+def test_single_channel_worked_2x2():
+    g = json.load(open(os.path.join(GOLD, "single_channel_2x2.json")))
+    S = np.array(g["S"])
+    r = oracle.sqrt_invsqrt(S, 1, 0.0, 1, channel=oracle.CHANNEL_SINGLE)
+    assert r["scale_c"] == g["scale_c"]
+    assert r["t_hist"][0] == g["t1"]
+    sc = math.sqrt(g["scale_c"])
+    np.testing.assert_array_equal(r["Y"], np.array(g["w1"]) * sc)
+    np.testing.assert_array_equal(r["Z"], np.array(g["z1"]) / sc)
+
+
+def _scalar_single(lam, iters, scaled=False):
+    """Eq. (single) on the eigenvalues: z <- z h[x], x = z^2 lam (z^T s z for commuting symmetric factors)."""
+    z = np.ones_like(lam)
+    x = lam.copy()
+    for _ in range(iters):
+        a, e = oracle.map_params(1.0 - x.mean(), oracle.MAP_SCALED if scaled else oracle.MAP_NS)
+        t = 0.5 * math.sqrt(a) * (3.0 - a * (e + (1.0 - 2.0 * e) * x))
+        z = z * t
+        x = z * z * lam
+    return lam * z, z
+
+
+@pytest.mark.parametrize("iters,scaled", [(1, False), (4, False), (12, False), (3, True), (9, True)])
+def test_single_channel_matches_eigen_recursion(iters, scaled):
+    n, nb = 40, 8
+    S = synth.gaussian_lattice(n, sigma=0.8, seed=1)
+    c = np.abs(S).sum(1).max()
+    lam, Q = np.linalg.eigh(S / c)
+    y, z = _scalar_single(lam, iters, scaled)
+    r = oracle.sqrt_invsqrt(S, nb, 0.0, iters, channel=oracle.CHANNEL_SINGLE,
+                            map=oracle.MAP_SCALED if scaled else oracle.MAP_NS)
+    Yk = (Q * (y * math.sqrt(c))) @ Q.T
+    Zk = (Q * (z / math.sqrt(c))) @ Q.T
+    assert np.linalg.norm(r["Y"] - Yk) <= 1e-12 * np.linalg.norm(Yk)
+    assert np.linalg.norm(r["Z"] - Zk) <= 1e-11 * np.linalg.norm(Zk)
+
+
+def test_single_channel_diagonal_is_scalar_recursion_bitwise():
+    d = np.array([0.9, 0.05, 0.3, 1.7, 0.011, 0.6, 2.0, 0.25, 0.125, 1.0, 0.75, 0.4])
+    c = d.max()
+    r = oracle.sqrt_invsqrt(np.diag(d), 4, 0.0, 9, channel=oracle.CHANNEL_SINGLE)
+    lam = d / c
+    z = np.ones_like(lam)
+    x = lam.copy()
+    for _ in range(9):
+        z = z * (1.5 - 0.5 * x)
+        w = lam * z
+        x = z * w
+    np.testing.assert_array_equal(np.diag(r["Z"]), z / math.sqrt(c))
+    np.testing.assert_array_equal(np.diag(r["Y"]), w * math.sqrt(c))
+
+
+@pytest.mark.parametrize("iters", [2, 7, 20])
+def test_single_and_dual_channels_agree_at_tau0(iters):
+    """In exact arithmetic y_k = s z_k, so x_k = y_k z_k = z_k^T s z_k: both instances give the same iterates."""
+    S = synth.kms(96, 0.9)
+    a = oracle.sqrt_invsqrt(S, 16, 0.0, iters)
+    b = oracle.sqrt_invsqrt(S, 16, 0.0, iters, channel=oracle.CHANNEL_SINGLE)
+    assert np.linalg.norm(a["Z"] - b["Z"]) <= 1e-12 * np.linalg.norm(a["Z"])
+    assert np.linalg.norm(a["Y"] - b["Y"]) <= 1e-12 * np.linalg.norm(a["Y"])
+    np.testing.assert_allclose(a["t_hist"], b["t_hist"], rtol=0, atol=1e-13)
+
+
+def test_single_channel_rejects_transposed_order():
+    with pytest.raises(RuntimeError):
+        oracle.sqrt_invsqrt(synth.kms(16, 0.5), 4, 0.0, 2, order=1, channel=oracle.CHANNEL_SINGLE)
