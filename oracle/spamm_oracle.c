@@ -384,10 +384,12 @@ static void or_transpose(const double* A, double* T, int n) {
  * X_k (t_0 from X0 = S / c).
  *
  * channel 1 is the single channel instance, Eq. (single), from X0 = s = S / c
- * and Z0 = I, every product at tau:
- *   Z <- Z (x)_tau T,   W <- s (x)_tau Z,   X <- Z^T (x)_tau W,
- * i.e. x_k = z_k^T s z_k with the inner product s z_k taken first; Y = W
- * (s z -> s^{1/2}).  Only the printed order (order 0) is defined for it.
+ * and Z0 = I:
+ *   Z <- Z (x)_tau T,   W <- s (x)_{tau_s} Z,   X <- Z^T (x)_tau W,
+ * i.e. x_k = z_k^T s z_k with the inner product s z_k taken first, at the
+ * sensitive threshold tau_s as in the volume plots of the single instance
+ * (Sec. 5.3); Y = W (s z -> s^{1/2}).  Only the printed order (order 0) is
+ * defined for it.
  *
  * The iteration stops after maxit steps or once |t_k| <= tol_t (tol_t > 0).
  * t_hist (maxit) and task_hist (3*maxit: the y, z, x products of the dual
@@ -433,7 +435,7 @@ int or_ns(const double* S, int n, int nb, double tau, double tau_s, double mu_re
             /* Eq. (single): z_k = z_{k-1} h[x_{k-1}], x_k = z_k^T s z_k */
             tz = or_spamm(Z, T, W, n, nb, tau, NULL, 0);
             memcpy(Z, W, sizeof(double) * nn);
-            ty = or_spamm(s1, Z, Y, n, nb, tau, NULL, 0);
+            ty = or_spamm(s1, Z, Y, n, nb, tau_s, NULL, 0);
             or_transpose(Z, Zt, n);
             tx = or_spamm(Zt, Y, X, n, nb, tau, NULL, 0);
             if (ty < 0 || tz < 0 || tx < 0) { free(X); free(T); free(W); free(s1); free(Zt); return OR_ERR_NOMEM; }

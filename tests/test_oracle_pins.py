@@ -488,3 +488,18 @@ def test_single_and_dual_channels_agree_at_tau0(iters):
 def test_single_channel_rejects_transposed_order():
     with pytest.raises(RuntimeError):
         oracle.sqrt_invsqrt(synth.kms(16, 0.5), 4, 0.0, 2, order=1, channel=oracle.CHANNEL_SINGLE)
+
+
+def test_single_channel_s_product_threshold_is_tau_s():
+    """W = s (x)_{tau_s} z (the single instance's sensitive product): after one step its task count is the
+    brute-force count of the leaf test at tau_s, which differs here from the count at tau."""
+    n, nb, tau = 96, 8, 2e-3
+    S = synth.gaussian_lattice(n, 0.6, seed=5)
+    r = oracle.sqrt_invsqrt(S, nb, tau, 1, tau_s=0.01 * tau, channel=oracle.CHANNEL_SINGLE)
+    c = r["scale_c"]
+    s = S / c
+    z1 = r["Z"] * math.sqrt(c)
+    n_tau_s = len(oracle.cull_flat(s, z1, nb, 0.01 * tau))
+    n_tau = len(oracle.cull_flat(s, z1, nb, tau))
+    assert n_tau_s != n_tau
+    assert r["task_hist"][0][1] == n_tau_s
