@@ -34,6 +34,7 @@ LEAF = 64
 MAXIT = 30
 MAP = 0  # 0: NS map with alpha = 1; 1: damped, stabilised h_alpha (--map scaled)
 TOL = 0.0  # > 0: a solve stops once |t_k| <= TOL (at most MAXIT iterations), on the device
+CHANNEL = 0  # 0: dual channel, Eq. (cannonical); 1: single channel, Eq. (single)
 TAU_HEADLINE = 1e-14
 TAU_SWEEP = (1e-4, 1e-6, 1e-8)
 GATE = 1e-8
@@ -42,9 +43,9 @@ UNIT = "solves/s"
 
 
 def workload_name(tau: float, precision: str) -> str:
-    mp = ", damped stabilised map h_alpha" if MAP else ""
+    mp = (", damped stabilised map h_alpha" if MAP else "") + (", single channel" if CHANNEL else "")
     steps = f"{MAXIT}" if TOL <= 0 else f"until |t_k| <= {TOL:g} (at most {MAXIT})"
-    return (f"KMS rho={RHO} N={N} N_b={LEAF} tau={tau:g} tau_s={0.01 * tau:g} {steps} dual-channel NS iterations{mp}, "
+    return (f"KMS rho={RHO} N={N} N_b={LEAF} tau={tau:g} tau_s={0.01 * tau:g} {steps} NS iterations{mp}, "
             f"{precision} leaf products")
 
 
@@ -139,7 +140,7 @@ def oracle_solve_rate(S, tau: float, budget_s: float, min_solves: int = 1) -> tu
     t0 = time.perf_counter()
     cnt = 0
     while True:
-        oracle.sqrt_invsqrt(S, LEAF, tau, MAXIT, map=MAP, tol_t=TOL)
+        oracle.sqrt_invsqrt(S, LEAF, tau, MAXIT, map=MAP, tol_t=TOL, channel=CHANNEL)
         cnt += 1
         el = time.perf_counter() - t0
         if cnt >= min_solves and el >= budget_s:
@@ -159,11 +160,11 @@ def run_reference(args, ws, rank):
     S = synth.kms(N, RHO)
     tau = args.tau
     for _ in range(args.warmup):
-        oracle.sqrt_invsqrt(S, LEAF, tau, MAXIT, map=MAP, tol_t=TOL)
+        oracle.sqrt_invsqrt(S, LEAF, tau, MAXIT, map=MAP, tol_t=TOL, channel=CHANNEL)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.sqrt_invsqrt(S, LEAF, tau, MAXIT, map=MAP, tol_t=TOL)
+        oracle.sqrt_invsqrt(S, LEAF, tau, MAXIT, map=MAP, tol_t=TOL, channel=CHANNEL)
         times.append(time.perf_counter() - t0)
     tot = sum(times)
     v = len(times) / tot
@@ -172,7 +173,7 @@ def run_reference(args, ws, rank):
             "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(tau, "FP64 CPU oracle"), "n": N, "leaf": LEAF, "tau": tau,
-                       "maxit": MAXIT, "tol_t": TOL, "map": args.map},
+                       "maxit": MAXIT, "tol_t": TOL, "map": args.map, "channel": args.channel},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{len(times)} full solves of the workload on {cores} OpenMP threads"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -246,7 +247,7 @@ def run_gpu(args, ws, rank, local):
 
     def solve(t, profile=False, residual=False):
         return sp.sqrt_invsqrt(Sd, t, MAXIT, leaf=LEAF, precision=prec, Y=Yd, Z=Zd, profile=profile, map=MAP,
-                               tol_t=TOL, residual=residual)
+                               tol_t=TOL, residual=residual, channel=CHANNEL)
 
     # verification solve (untimed): residual against the gate, FP64 dense
     _, _, vst = solve(tau, residual=True)
@@ -301,13 +302,13 @@ def run_gpu(args, ws, rank, local):
     Sh = torch.from_numpy(S).pin_memory()
     Yh = torch.empty((N, N), dtype=torch.float64).pin_memory()
     Zh = torch.empty((N, N), dtype=torch.float64).pin_memory()
-    sp.sqrt_invsqrt(Sh, tau, MAXIT, leaf=LEAF, precision=prec, Y=Yh, Z=Zh, map=MAP, tol_t=TOL)
+    sp.sqrt_invsqrt(Sh, tau, MAXIT, leaf=LEAF, precision=prec, Y=Yh, Z=Zh, map=MAP, tol_t=TOL, channel=CHANNEL)
     e2e_t = []
     for _ in range(args.steps):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        sp.sqrt_invsqrt(Sh, tau, MAXIT, leaf=LEAF, precision=prec, Y=Yh, Z=Zh, map=MAP, tol_t=TOL)
+        sp.sqrt_invsqrt(Sh, tau, MAXIT, leaf=LEAF, precision=prec, Y=Yh, Z=Zh, map=MAP, tol_t=TOL, channel=CHANNEL)
         e2e_t.append(time.perf_counter() - t0)
     e2e_tot = max_over_ranks(sum(e2e_t), ws, dev)
 
@@ -317,7 +318,7 @@ def run_gpu(args, ws, rank, local):
     to_tol = None
     if TOL <= 0 and args.tol_report > 0:
         _, _, tst = sp.sqrt_invsqrt(Sd, tau, MAXIT, leaf=LEAF, precision=prec, Y=Yd, Z=Zd, map=MAP,
-                                    tol_t=args.tol_report, residual=True, raise_on=False)
+                                    tol_t=args.tol_report, residual=True, raise_on=False, channel=CHANNEL)
         tt = []
         for _ in range(args.steps):
             flush.zero_()
@@ -325,7 +326,7 @@ def run_gpu(args, ws, rank, local):
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             sp.sqrt_invsqrt(Sd, tau, MAXIT, leaf=LEAF, precision=prec, Y=Yd, Z=Zd, map=MAP, tol_t=args.tol_report,
-                            raise_on=False)
+                            raise_on=False, channel=CHANNEL)
             e1.record(stream)
             e1.synchronize()
             tt.append(e0.elapsed_time(e1) / 1e3)
@@ -337,14 +338,15 @@ def run_gpu(args, ws, rank, local):
     fp64_path = None
     if prec == sp.EMU64 and not args.no_fp64_path:
         _, _, fst = sp.sqrt_invsqrt(Sd, tau, MAXIT, leaf=LEAF, precision=sp.FP64, Y=Yd, Z=Zd, residual=True,
-                                         map=MAP, tol_t=TOL)
+                                         map=MAP, tol_t=TOL, channel=CHANNEL)
         ft = []
         for _ in range(3):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            sp.sqrt_invsqrt(Sd, tau, MAXIT, leaf=LEAF, precision=sp.FP64, Y=Yd, Z=Zd, map=MAP, tol_t=TOL)
+            sp.sqrt_invsqrt(Sd, tau, MAXIT, leaf=LEAF, precision=sp.FP64, Y=Yd, Z=Zd, map=MAP, tol_t=TOL,
+                            channel=CHANNEL)
             e1.record(stream)
             e1.synchronize()
             ft.append(e0.elapsed_time(e1) / 1e3)
@@ -419,7 +421,7 @@ def run_gpu(args, ws, rank, local):
             "data": "synthetic",
             "config": {"workload": workload_name(tau, args.precision.upper()), "n": N, "leaf": LEAF, "tau": tau,
                        "tau_s": 0.01 * tau, "maxit": MAXIT, "tol_t": TOL, "precision": args.precision,
-                       "map": args.map,
+                       "map": args.map, "channel": args.channel,
                        "l2": "flushed by a 256 MB write before every timed solve",
                        "parallelism": f"replicas x{ws}"},
             "latency_ms": {"p50": p50, "p99": p99},
@@ -463,7 +465,7 @@ def run_batched(args, local):
     t_batch = time.perf_counter() - t0
     t0 = time.perf_counter()
     for S, t in zip(Ss, taus):
-        sp.sqrt_invsqrt(S, t, MAXIT, leaf=LEAF, precision=prec, map=MAP, tol_t=TOL)
+        sp.sqrt_invsqrt(S, t, MAXIT, leaf=LEAF, precision=prec, map=MAP, tol_t=TOL, channel=CHANNEL)
     torch.cuda.synchronize()
     t_seq = time.perf_counter() - t0
     line = {"metric": "batched NS solves/s (mixed KMS / 3D Gaussian, N in [128, 2048])", "value": len(Ss) / t_batch,
@@ -515,7 +517,7 @@ def run_serve(args, local):
     for S, r in zip(mats, trace):
         a = time.perf_counter()
         _, _, st = sp.sqrt_invsqrt(S, r["tau"], MAXIT, leaf=LEAF, precision=prec, raise_on=False, map=MAP,
-                                   tol_t=TOL)
+                                   tol_t=TOL, channel=CHANNEL)
         seq_lat.append(time.perf_counter() - a)
         seq_status.append(st["status"])
     t_seq = time.perf_counter() - t0
@@ -557,7 +559,8 @@ def run_c3(args, local):
     stream = torch.cuda.current_stream(dev)
     rows = []
     for tau in args.c3_tau:
-        kw = dict(leaf=LEAF, precision=prec, Y=Yd, Z=Zd, mu_rel=args.c3_mu, map=MAP, tol_t=TOL, raise_on=False)
+        kw = dict(leaf=LEAF, precision=prec, Y=Yd, Z=Zd, mu_rel=args.c3_mu, map=MAP, tol_t=TOL, channel=CHANNEL,
+                  raise_on=False)
         _, _, vst = sp.sqrt_invsqrt(Sd, tau, MAXIT, residual=True, **kw)
         sp.sqrt_invsqrt(Sd, tau, MAXIT, **kw)
         ts = []
@@ -590,16 +593,18 @@ def run_c3(args, local):
             "dtype": "f64" if prec == sp.FP64 else "f16-split", "data": "synthetic",
             "config": {"workload": f"3D Gaussian decay sigma={args.c3_sigma} on {args.c3_n} jittered Morton-ordered "
                                    f"lattice points, N_b={LEAF}, "
-                                   + (f"{MAXIT} iterations" if TOL <= 0 else f"until |t_k| <= {TOL:g} (at most {MAXIT})")
+                                   + (f"{MAXIT} iterations" if TOL <= 0
+                                      else f"until |t_k| <= {TOL:g} (at most {MAXIT})")
                                    + f", mu_rel={args.c3_mu}",
-                       "precision": args.precision, "map": args.map, "tau_best": best["tau"]},
+                       "precision": args.precision, "map": args.map, "channel": args.channel,
+                       "tau_best": best["tau"]},
             "per_tau": rows, "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
     return 0
 
 
 def main():
-    global N, MAXIT, MAP, TOL
+    global N, MAXIT, MAP, TOL, CHANNEL
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -635,6 +640,8 @@ def main():
                     help="NS map: alpha = 1, or the damped, stabilised h_alpha of Sec. 4.2")
     ap.add_argument("--tol-t", type=float, default=0.0,
                     help="stop a solve once |t_k| <= tol (Sec. 4.2 trace error); 0 runs exactly --maxit steps")
+    ap.add_argument("--channel", choices=["dual", "single"], default="dual",
+                    help="instance of the iteration: dual channel, Eq. (cannonical), or single, Eq. (single)")
     ap.add_argument("--tol-report", type=float, default=1e-12,
                     help="with fixed-step solves, also time solves stopped at |t_k| <= this (0: skip)")
     args = ap.parse_args()
@@ -643,6 +650,7 @@ def main():
     N, MAXIT = args.size, args.maxit
     MAP = 1 if args.map == "scaled" else 0
     TOL = args.tol_t
+    CHANNEL = 1 if args.channel == "single" else 0
     ws, rank, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, ws, rank)

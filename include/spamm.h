@@ -77,6 +77,13 @@ extern "C" {
                                stabiliser leaves a fixed point with
                                t ~ -eps(0) ~ -1.7e-11 (ZSZ ~ (1 + 1.7e-11) I). */
 
+/* ---- instance of the square-root iteration ------------------------------ */
+#define SPAMM_CHANNEL_DUAL 0    /* Eq. (cannonical): Y and Z channels, X = Y Z      */
+#define SPAMM_CHANNEL_SINGLE 1  /* Eq. (single): Z <- Z (x)_tau h[X],
+                                   W = s (x)_{tau_s} Z, X <- Z^T (x)_tau W
+                                   (Y = W unscaled, which tends to S^{1/2});
+                                   paper order only                            */
+
 /* ---- order of the two channel products --------------------------------- */
 #define SPAMM_ORDER_PAPER 0       /* Y <- T Y, Z <- Z T, X <- Y Z (as printed)  */
 #define SPAMM_ORDER_TRANSPOSED 1  /* Y <- Y T, Z <- T Z, X <- Z Y: the exact
@@ -96,6 +103,7 @@ typedef struct spamm_opts {
                           events on the call's stream (stats->gemm_ms)         */
     void* stream;      /* cudaStream_t; NULL = legacy default stream            */
     int map;           /* SPAMM_MAP_NS or SPAMM_MAP_SCALED                      */
+    int channel;       /* SPAMM_CHANNEL_DUAL or SPAMM_CHANNEL_SINGLE            */
 } spamm_opts;
 
 typedef struct spamm_stats {
@@ -116,7 +124,7 @@ typedef struct spamm_stats {
 
 /* Fill *opts with defaults: leaf 64, SPAMM_FP64, tau_s = 0.01 tau, no shift,
  * fixed iteration count, paper order, no residual, default stream,
- * SPAMM_MAP_NS. */
+ * SPAMM_MAP_NS, SPAMM_CHANNEL_DUAL. */
 void spamm_opts_init(spamm_opts* opts);
 
 /*
@@ -144,7 +152,10 @@ int spamm_multiply(const double* A, const double* B, double* C, int n, double ta
 
 /*
  * Y ~ S^{1/2} and Z ~ S^{-1/2} for symmetric positive definite S by the
- * dual-channel iteration of Eq. (cannonical) (see the top of this file).
+ * dual-channel iteration of Eq. (cannonical) (see the top of this file), or
+ * with opts->channel = SPAMM_CHANNEL_SINGLE the single channel of
+ * Eq. (single); SPAMM_ERR_ARG for the single channel with
+ * SPAMM_ORDER_TRANSPOSED.
  * S is scaled by its Gershgorin bound c (plus mu, Sec. 6) into (0,1]; the
  * results are unscaled as Y * sqrt(c), Z / sqrt(c).  Runs maxit iterations,
  * or fewer when opts->tol_t > 0.  Y and Z are written even when the status

@@ -31,6 +31,8 @@ ORDER_PAPER = 0
 ORDER_TRANSPOSED = 1
 MAP_NS = 0       # T = (3I - X)/2 (alpha = 1)
 MAP_SCALED = 1   # damped, stabilised h_alpha (Sec. 4.2 "Mapping")
+CHANNEL_DUAL = 0    # Eq. (cannonical)
+CHANNEL_SINGLE = 1  # Eq. (single): Z <- Z h[X], X = Z^T s Z
 
 STATUS = {0: "SPAMM_OK", -1: "SPAMM_ERR_ARG", -2: "SPAMM_ERR_NOMEM", -3: "SPAMM_ERR_DIVERGED",
           -4: "SPAMM_ERR_NOTCONVERGED", -5: "SPAMM_ERR_TIMEOUT", -6: "SPAMM_ERR_ADMIT", -7: "SPAMM_ERR_CUDA",
@@ -54,7 +56,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("leaf", ctypes.c_int), ("precision", ctypes.c_int), ("tau_s", ctypes.c_double),
                 ("mu_rel", ctypes.c_double), ("tol_t", ctypes.c_double), ("order", ctypes.c_int),
                 ("residual", ctypes.c_int), ("profile", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("map", ctypes.c_int)]
+                ("map", ctypes.c_int), ("channel", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -184,7 +186,7 @@ def _stream_of(ref, stream):
 
 
 def _opts(leaf=64, precision=FP64, tau_s=None, mu_rel=0.0, tol_t=0.0, order=ORDER_PAPER, residual=False,
-          stream=None, profile=False, map=MAP_NS) -> Opts:
+          stream=None, profile=False, map=MAP_NS, channel=CHANNEL_DUAL) -> Opts:
     o = Opts()
     lib().spamm_opts_init(ctypes.byref(o))
     o.leaf = int(leaf)
@@ -197,6 +199,7 @@ def _opts(leaf=64, precision=FP64, tau_s=None, mu_rel=0.0, tol_t=0.0, order=ORDE
     o.profile = 1 if profile else 0
     o.stream = stream
     o.map = int(map)
+    o.channel = int(channel)
     return o
 
 
@@ -239,7 +242,7 @@ def autotune_leaf(S, tau: float, precision: int = FP64, stream=None) -> int:
 
 def sqrt_invsqrt(S, tau: float, maxit: int, leaf: int = 64, precision: int = FP64, tau_s=None, mu_rel=0.0,
                  tol_t=0.0, order=ORDER_PAPER, residual=False, Y=None, Z=None, stream=None, raise_on=True,
-                 profile=False, map=None):
+                 profile=False, map=None, channel=None):
     """Y ~ S^{1/2}, Z ~ S^{-1/2} by dual-channel Newton-Schulz on SpAMM products; returns (Y, Z, stats)."""
     s, ps, n, _ = _prep(S)
     Y = Y if Y is not None else _like(s, n)
@@ -250,7 +253,7 @@ def sqrt_invsqrt(S, tau: float, maxit: int, leaf: int = 64, precision: int = FP6
     st.t_hist = th.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     st.task_hist = kh.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong))
     o = _opts(leaf, precision, tau_s, mu_rel, tol_t, order, residual, _stream_of(s, stream), profile,
-              MAP_NS if map is None else map)
+              MAP_NS if map is None else map, CHANNEL_DUAL if channel is None else channel)
     status = lib().spamm_sqrt_invsqrt(ps, n, float(tau), int(maxit), _ptr(Y), _ptr(Z), ctypes.byref(o),
                                       ctypes.byref(st))
     d = _stats_dict(st, th, kh)
@@ -261,7 +264,7 @@ def sqrt_invsqrt(S, tau: float, maxit: int, leaf: int = 64, precision: int = FP6
 
 
 def sqrt_invsqrt_batched(Ss, taus, maxit: int, leaf: int = 64, precision: int = FP64, tau_s=None, mu_rel=0.0,
-                         tol_t=0.0, order=ORDER_PAPER, residual=False, stream=None, map=None):
+                         tol_t=0.0, order=ORDER_PAPER, residual=False, stream=None, map=None, channel=None):
     """Many independent solves in one call; returns (list of Y, list of Z, list of stats)."""
     cnt = len(Ss)
     keep = [_prep(S) for S in Ss]
@@ -275,7 +278,7 @@ def sqrt_invsqrt_batched(Ss, taus, maxit: int, leaf: int = 64, precision: int = 
     ts = (ctypes.c_double * cnt)(*[float(t) for t in taus])
     stats = (Stats * cnt)()
     o = _opts(leaf, precision, tau_s, mu_rel, tol_t, order, residual, _stream_of(keep[0][0], stream) if cnt else None,
-              map=MAP_NS if map is None else map)
+              map=MAP_NS if map is None else map, channel=CHANNEL_DUAL if channel is None else channel)
     _check(lib().spamm_sqrt_invsqrt_batched(cnt, sp, ns, ts, int(maxit), yp, zp, ctypes.byref(o), stats))
     return Ys, Zs, [_stats_dict(stats[q]) for q in range(cnt)]
 
@@ -318,9 +321,10 @@ class Server:
     memory budget; admitted requests run concurrently on separate CUDA streams."""
 
     def __init__(self, bytes_budget: int, max_active: int = 4, leaf: int = 64, precision: int = FP64, tau_s=None,
-                 mu_rel=0.0, tol_t=0.0, order=ORDER_PAPER, map=None):
+                 mu_rel=0.0, tol_t=0.0, order=ORDER_PAPER, map=None, channel=None):
         self._h = ctypes.c_void_p(0)
-        o = _opts(leaf, precision, tau_s, mu_rel, tol_t, order, False, None, map=MAP_NS if map is None else map)
+        o = _opts(leaf, precision, tau_s, mu_rel, tol_t, order, False, None, map=MAP_NS if map is None else map,
+                  channel=CHANNEL_DUAL if channel is None else channel)
         _check(lib().spamm_server_create(int(bytes_budget), int(max_active), ctypes.byref(o), ctypes.byref(self._h)))
         self._keep = {}
 

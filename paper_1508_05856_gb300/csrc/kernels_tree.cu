@@ -281,6 +281,49 @@ void launch_map(const double* X, const double* leafX, TileMat T, const Geometry&
     note_launch();
 }
 
+// T = A^T on the tile grid: tile (i,j) of T is tile (j,i) of A transposed, moved through shared memory in
+// 32 x 32 blocks (coalesced reads along A's rows, writes along T's rows).  T's leaf norms are A's, transposed
+// (a tile's Frobenius norm does not depend on the order of its entries).  Tiles of norm 0 are not written:
+// every reader goes by the norm.  Grid-stride over output tiles; skipped once *done is set.
+__global__ void __launch_bounds__(256) k_transpose(const double* __restrict__ A, const double* __restrict__ leafA,
+                                                   double* __restrict__ T, double* __restrict__ leafT, int m, int nb,
+                                                   const int* __restrict__ done) {
+    grid_dependency_wait();
+    if (done && *done) return;
+    __shared__ double sm[32][33];
+    const size_t ne = (size_t)nb * nb;
+    for (int tile = blockIdx.x; tile < m * m; tile += gridDim.x) {
+        const int i = tile / m, j = tile - (tile / m) * m;
+        const int src = j * m + i;
+        const double nu = leafA[src];
+        if (threadIdx.x == 0) leafT[tile] = nu;
+        if (nu == 0.0) continue;
+        const double* a = A + (size_t)src * ne;
+        double* t = T + (size_t)tile * ne;
+        for (int r0 = 0; r0 < nb; r0 += 32)
+            for (int c0 = 0; c0 < nb; c0 += 32) {
+                __syncthreads();
+                for (int q = threadIdx.x; q < 1024; q += 256) {
+                    const int c = q >> 5, r = q & 31;
+                    sm[c][r] = a[(size_t)(c0 + c) * nb + r0 + r];  // A's row c0 + c, column r0 + r
+                }
+                __syncthreads();
+                for (int q = threadIdx.x; q < 1024; q += 256) {
+                    const int r = q >> 5, c = q & 31;
+                    t[(size_t)(r0 + r) * nb + c0 + c] = sm[c][r];  // T's row r0 + r, column c0 + c
+                }
+            }
+    }
+}
+
+void launch_transpose(const TileMat& A, TileMat T, const Geometry& g, const int* done, cudaStream_t st) {
+    // one resident wave (34 KB of shared memory and 256 threads per block leave room for 4 per SM)
+    const int grid = std::min(device_sm_count() * 4, g.m * g.m);
+    launch_dependent(k_transpose, dim3(grid), dim3(256), 0, st, (const double*)A.t, (const double*)A.tree, T.t,
+                     T.tree, g.m, g.nb, done);
+    note_launch();
+}
+
 __global__ void __launch_bounds__(256) k_identity(int n, int m, int nb, double* __restrict__ Z,
                                                   double* __restrict__ leaf) {
     const int tile = blockIdx.x;

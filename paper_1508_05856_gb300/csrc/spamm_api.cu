@@ -100,11 +100,12 @@ struct GraphKey {
     const double* S = nullptr;
     double* Y = nullptr;
     double* Z = nullptr;
-    int n = 0, leaf = 0, precision = 0, order = 0, maxit = 0, profile = 0, map = 0;
+    int n = 0, leaf = 0, precision = 0, order = 0, maxit = 0, profile = 0, map = 0, channel = 0;
     double tau = 0.0, tau_s = 0.0, mu_rel = 0.0, tol_t = 0.0;
     bool operator==(const GraphKey& o) const {
         return S == o.S && Y == o.Y && Z == o.Z && n == o.n && leaf == o.leaf && precision == o.precision &&
-               order == o.order && maxit == o.maxit && profile == o.profile && map == o.map && tau == o.tau &&
+               order == o.order && maxit == o.maxit && profile == o.profile && map == o.map &&
+               channel == o.channel && tau == o.tau &&
                tau_s == o.tau_s && mu_rel == o.mu_rel && tol_t == o.tol_t;
     }
 };
@@ -720,9 +721,10 @@ static int residual_impl(Plan* p, const double* dS, const double* dZ, double* ou
     return SPAMM_OK;
 }
 
-// The buffers of one solve: Y, Z and their successors (swapped every iteration) and T.
+// The buffers of one solve: Y, Z and their successors (swapped every iteration) and T.  The single channel
+// keeps s packed (Sb), writes W = s Z into Yb (= Y2, not swapped) and Z^T into Ztb.
 struct SolveBufs {
-    TileMat Yb, Zb, Tb, Y2, Z2;
+    TileMat Yb, Zb, Tb, Y2, Z2, Sb, Ztb;
 };
 
 // a1-a2: flags and histories cleared, Gershgorin bound (plus the Tikhonov shift of Sec. 6) and scaling,
@@ -746,18 +748,28 @@ static int enqueue_prologue(Plan* p, const double* dS, int n, const spamm_opts& 
     launch_gershgorin(dS, n, mu_ptr, p->rowsum, c, st);
     launch_sqrt_scalar(c, sqc, st);
 
-    *sb = SolveBufs{p->buf[0], p->buf[1], p->buf[2], p->buf[3], p->buf[4]};
-    launch_pack(dS, n, g, mu_ptr, c, sb->Yb, st);
-    launch_tree(g, sb->Yb.tree, nullptr, st);
-    if (o.map == SPAMM_MAP_SCALED) launch_trace_parts(sb->Yb.t, g, p->trace_part, st);
-    launch_map(sb->Yb.t, sb->Yb.tree, sb->Tb, g, o.map, p->trace_part, false, nullptr, st);
+    // X0 = s in buf 0: Y0 of the dual channel, the constant s of the single channel
+    const TileMat X0 = p->buf[0];
+    if (o.channel == SPAMM_CHANNEL_SINGLE)
+        *sb = SolveBufs{p->buf[3], p->buf[1], p->buf[2], p->buf[3], p->buf[4], X0, p->buf[5]};
+    else
+        *sb = SolveBufs{X0, p->buf[1], p->buf[2], p->buf[3], p->buf[4], TileMat(), TileMat()};
+    launch_pack(dS, n, g, mu_ptr, c, X0, st);
+    launch_tree(g, X0.tree, nullptr, st);
+    if (o.map == SPAMM_MAP_SCALED) launch_trace_parts(X0.t, g, p->trace_part, st);
+    launch_map(X0.t, X0.tree, sb->Tb, g, o.map, p->trace_part, false, nullptr, st);
     launch_tree(g, sb->Tb.tree, nullptr, st);
     launch_identity(g, sb->Zb, st);
     launch_tree(g, sb->Zb.tree, nullptr, st);
     if (p->emu) {
-        prepare_emu(p, sb->Yb, st);
+        prepare_emu(p, X0, st);
         prepare_emu(p, sb->Tb, st);
         prepare_emu(p, sb->Zb, st);
+    }
+    if (o.channel == SPAMM_CHANNEL_SINGLE) {
+        // W = s Z0 = s: the Y output of a solve with no iteration
+        CK(cudaMemcpyAsync(sb->Yb.t, X0.t, g.elems() * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(sb->Yb.tree, X0.tree, (size_t)g.tree_size * sizeof(double), cudaMemcpyDeviceToDevice, st));
     }
     CK(cudaGetLastError());
     return SPAMM_OK;
@@ -783,6 +795,37 @@ static int enqueue_iteration(Plan* p, SolveBufs& sb, double tau, double tau_s, i
         tk.has_cond = 1;
     }
     unsigned long long* ctr = p->task_ctr;  // + 3 k on the device
+    const EpiMode xmode = o.map == SPAMM_MAP_NS ? EPI_NS_X : EPI_X;
+    if (o.channel == SPAMM_CHANNEL_SINGLE) {
+        // Eq. (single): Z <- Z (x) T, then Z^T (tile transpose, its quadtree and slices) on the side branch
+        // beside W = s (x)_{tau_s} Z (the sensitive product, as in the paper's single-instance volumes), then
+        // X = Z^T (x) W with T = h[X] and t_k
+        product(p, sb.Zb, sb.Tb, sb.Z2, tau, EPI_PLAIN, ctr + 0, st);  // Z <- Z (x)_tau T
+        std::swap(sb.Zb, sb.Z2);
+        cudaStream_t zs = p->profile ? st : p->side;
+        if (zs != st) {
+            CK(cudaEventRecord(p->ev_fork, st));
+            CK(cudaStreamWaitEvent(zs, p->ev_fork, 0));
+        }
+        TileMat Zt = sb.Ztb;  // its row maxima are Z's column maxima and vice versa
+        Zt.rmax = sb.Zb.cmax;
+        Zt.cmax = sb.Zb.rmax;
+        launch_transpose(sb.Zb, Zt, g, p->flags, zs);
+        launch_tree(g, Zt.tree, p->flags, zs);
+        if (p->emu) {
+            launch_slice(Zt.t, Zt.tree, nullptr, Zt.rmax, Zt.cmax, Zt.sliceA, Zt.sliceB, g, nullptr, nullptr,
+                         p->flags, zs);
+            mark_sliced(p, Zt, zs);
+        }
+        product(p, sb.Sb, sb.Zb, sb.Yb, tau_s, EPI_PLAIN, ctr + 1, st);  // W <- s (x)_{tau_s} Z
+        if (zs != st) {
+            CK(cudaEventRecord(p->ev_join, zs));
+            CK(cudaStreamWaitEvent(st, p->ev_join, 0));
+        }
+        product(p, Zt, sb.Yb, sb.Tb, tau, xmode, ctr + 2, st, &tk, 0, o.map);  // X <- Z^T (x)_tau W, T = h[X]
+        CK(cudaGetLastError());
+        return SPAMM_OK;
+    }
     // the Y and Z updates are independent: the Z update runs on the side branch (a profiled call keeps them
     // in order, so that each leaf-product timing is that kernel's own)
     cudaStream_t zs = p->profile ? st : p->side;
@@ -802,7 +845,6 @@ static int enqueue_iteration(Plan* p, SolveBufs& sb, double tau, double tau_s, i
         CK(cudaStreamWaitEvent(st, p->ev_join, 0));
     }
     // alpha = 1: T = h[X] fused into the X product's epilogue; the damped map needs tr X first
-    const EpiMode xmode = o.map == SPAMM_MAP_NS ? EPI_NS_X : EPI_X;
     std::swap(sb.Yb, sb.Y2);
     std::swap(sb.Zb, sb.Z2);
     if (o.order == SPAMM_ORDER_PAPER)
@@ -941,8 +983,8 @@ static int solve_graph(Plan* p, const double* dS, double* dY, double* dZ, int n,
         CK(cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&p->ev_out, cudaEventDisableTiming));
     }
-    const GraphKey key{dS, dY, dZ, n, o.leaf, o.precision, o.order, maxit, o.profile ? 1 : 0, o.map, tau, tau_s,
-                       o.mu_rel, o.tol_t};
+    const GraphKey key{dS, dY, dZ, n, o.leaf, o.precision, o.order, maxit, o.profile ? 1 : 0, o.map, o.channel,
+                       tau, tau_s, o.mu_rel, o.tol_t};
     CK(cudaEventRecord(p->ev_in, st));
     CK(cudaStreamWaitEvent(p->gstream, p->ev_in, 0));
     if (!p->gexec || !(p->gkey == key)) {
@@ -1102,6 +1144,14 @@ static int check_common(int n, double tau, const spamm_opts& o) {
         g_last_error = "unknown map";
         return SPAMM_ERR_ARG;
     }
+    if (o.channel != SPAMM_CHANNEL_DUAL && o.channel != SPAMM_CHANNEL_SINGLE) {
+        g_last_error = "unknown channel";
+        return SPAMM_ERR_ARG;
+    }
+    if (o.channel == SPAMM_CHANNEL_SINGLE && o.order != SPAMM_ORDER_PAPER) {
+        g_last_error = "the single channel is defined in the paper order only";
+        return SPAMM_ERR_ARG;
+    }
     if (std::isnan(o.tau_s) || std::isnan(o.mu_rel) || o.mu_rel < 0.0 || std::isnan(o.tol_t) || o.tol_t < 0.0) {
         g_last_error = "tau_s, mu_rel, tol_t must be numbers (mu_rel, tol_t >= 0)";
         return SPAMM_ERR_ARG;
@@ -1152,6 +1202,7 @@ void spamm_opts_init(spamm_opts* o) {
     o->residual = 0;
     o->stream = nullptr;
     o->map = SPAMM_MAP_NS;
+    o->channel = SPAMM_CHANNEL_DUAL;
 }
 
 int spamm_autotune_leaf(const double* S, int n, double tau, const spamm_opts* opts, int* leaf) {

@@ -124,6 +124,9 @@ void launch_trace_parts(const double* X, const Geometry& g, double* trace_part, 
 // maxima into T.rmax/T.cmax (which must be zero).  Skipped once *done is set.
 void launch_map(const double* X, const double* leafX, TileMat T, const Geometry& g, int map, const double* trace_part,
                 bool maxima, const int* done, cudaStream_t st);
+// T = A^T on the tile grid (tile (i,j) of T = tile (j,i) of A, transposed) with T's leaf norms; tiles of
+// norm 0 are left unwritten.  Skipped once *done is set.
+void launch_transpose(const TileMat& A, TileMat T, const Geometry& g, const int* done, cudaStream_t st);
 // Z = I_n in tile-major form, with leaf norms.
 void launch_identity(const Geometry& g, TileMat Z, cudaStream_t st);
 // Work fused into the quadtree pass, all optional.  After the levels:

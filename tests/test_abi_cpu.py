@@ -41,7 +41,7 @@ def test_strerror_and_defaults():
     o = sp.Opts()
     L.spamm_opts_init(ctypes.byref(o))
     assert o.leaf == 64 and o.precision == sp.FP64 and o.tau_s < 0 and o.order == sp.ORDER_PAPER
-    assert o.map == sp.MAP_NS
+    assert o.map == sp.MAP_NS and o.channel == sp.CHANNEL_DUAL
 
 
 @pytest.mark.parametrize("n,tau,leaf", [(0, 1e-6, 64), (-5, 1e-6, 64), (64, -1.0, 64), (64, float("nan"), 64),
@@ -70,6 +70,14 @@ def test_bad_option_fields_rejected():
     o.map = 2
     assert L.spamm_sqrt_invsqrt(buf, 4, 0.0, 5, buf, buf, ctypes.byref(o), None) == -1
     assert b"map" in L.spamm_last_error()
+    L.spamm_opts_init(ctypes.byref(o))
+    o.channel = 3
+    assert L.spamm_sqrt_invsqrt(buf, 4, 0.0, 5, buf, buf, ctypes.byref(o), None) == -1
+    L.spamm_opts_init(ctypes.byref(o))
+    o.channel = sp.CHANNEL_SINGLE
+    o.order = sp.ORDER_TRANSPOSED
+    assert L.spamm_sqrt_invsqrt(buf, 4, 0.0, 5, buf, buf, ctypes.byref(o), None) == -1
+    assert b"single channel" in L.spamm_last_error()
     L.spamm_opts_init(ctypes.byref(o))
     o.mu_rel = -1.0
     assert L.spamm_sqrt_invsqrt(buf, 4, 0.0, 5, buf, buf, ctypes.byref(o), None) == -1

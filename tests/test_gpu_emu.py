@@ -75,7 +75,8 @@ def test_emu_multiply_kms_scales():
 
 def _emu_ns(S, tau, maxit, **kw):
     Y, Z, st = sp.sqrt_invsqrt(dev(S), tau, maxit, leaf=64, precision=sp.EMU64, **kw)
-    ref = oracle.sqrt_invsqrt(S, 64, tau, maxit, **{k: v for k, v in kw.items() if k in ("order", "mu_rel", "map")})
+    ref = oracle.sqrt_invsqrt(S, 64, tau, maxit,
+                              **{k: v for k, v in kw.items() if k in ("order", "mu_rel", "map", "channel")})
     ez = np.linalg.norm(Z.cpu().numpy() - ref["Z"]) / np.linalg.norm(ref["Z"])
     ey = np.linalg.norm(Y.cpu().numpy() - ref["Y"]) / np.linalg.norm(ref["Y"])
     return ez, ey, st, ref
@@ -145,5 +146,15 @@ def test_emu_ns_scaled_map(n, tau, order):
     with its leaf norms and row/column maxima, then T is sliced."""
     S = synth.gaussian_lattice(n, 0.9, seed=1)
     ez, ey, st, ref = _emu_ns(S, tau, 20, order=order, map=sp.MAP_SCALED)
+    assert ez <= 1e-9 and ey <= 1e-9, (ez, ey)
+    np.testing.assert_allclose(st["t_hist"], ref["t_hist"], rtol=0, atol=1e-11)
+
+
+@pytest.mark.parametrize("n,tau,mp", [(256, 1e-9, 0), (700, 1e-12, 0), (320, 1e-10, 1)])
+def test_emu_ns_single_channel(n, tau, mp):
+    """Eq. (single) on the tensor-core path: Z^T's slices come from the tile transpose with Z's column maxima
+    as its row maxima."""
+    S = synth.gaussian_lattice(n, 0.7, seed=2)
+    ez, ey, st, ref = _emu_ns(S, tau, 20, channel=sp.CHANNEL_SINGLE, map=mp)
     assert ez <= 1e-9 and ey <= 1e-9, (ez, ey)
     np.testing.assert_allclose(st["t_hist"], ref["t_hist"], rtol=0, atol=1e-11)

@@ -121,7 +121,7 @@ def test_host_and_device_pointers_agree():
 def _ns_compare(S, nb, tau, maxit, **kw):
     Y, Z, st = sp.sqrt_invsqrt(dev(S), tau, maxit, leaf=nb, **kw)
     Y, Z = host(Y), host(Z)
-    kw2 = {k: v for k, v in kw.items() if k in ("tau_s", "mu_rel", "order", "tol_t", "map")}
+    kw2 = {k: v for k, v in kw.items() if k in ("tau_s", "mu_rel", "order", "tol_t", "map", "channel")}
     ref = oracle.sqrt_invsqrt(S, nb, tau, maxit, **kw2)
     assert st["iters"] == ref["iters"]
     ez = np.linalg.norm(Z - ref["Z"]) / np.linalg.norm(ref["Z"])
@@ -287,3 +287,36 @@ def test_loop_graph_launches_only_the_iterations_run():
     assert it_fixed == 30 and it_stop < 12
     per_iter = fixed / 30.0
     assert stopped <= per_iter * (it_stop + 1) + 20, (stopped, fixed, it_stop)
+
+
+# ------------------------------------------------------------------------------------------ single channel
+
+
+def test_ns_single_channel_gaussian_256_leaf32():
+    """Eq. (single) on the small Gaussian configuration: per-iteration task counts of the z, s z and x
+    products equal the oracle's."""
+    S = synth.gaussian_lattice(256, 0.6, seed=0)
+    Y, Z, st, ref = _ns_compare(S, 32, 1e-6, 30, channel=sp.CHANNEL_SINGLE)
+    np.testing.assert_array_equal(st["task_hist"], ref["task_hist"])
+
+
+@pytest.mark.parametrize("n,nb,tau,mp", [(333, 64, 1e-8, 0), (200, 128, 0.0, 0), (300, 32, 1e-9, 1),
+                                         (129, 64, 1e-10, 1)])
+def test_ns_single_channel(n, nb, tau, mp):
+    S = synth.gaussian_lattice(n, 0.8, seed=n)
+    _ns_compare(S, nb, tau, 20, channel=sp.CHANNEL_SINGLE, map=mp)
+
+
+def test_ns_single_channel_tolerance_stop():
+    S = synth.kms(320, 0.9)
+    Y, Z, st, ref = _ns_compare(S, 32, 1e-10, 40, tol_t=1e-3, channel=sp.CHANNEL_SINGLE)
+    assert st["iters"] == ref["iters"] < 40
+
+
+def test_ns_single_channel_batched_equals_single():
+    Ss = [synth.gaussian_lattice(n, 0.7, seed=n) for n in (96, 200)]
+    Ys, Zs, _ = sp.sqrt_invsqrt_batched([dev(S) for S in Ss], [1e-8, 1e-8], 12, leaf=32,
+                                        channel=sp.CHANNEL_SINGLE)
+    for S, Yb, Zb in zip(Ss, Ys, Zs):
+        Y1, Z1, _ = sp.sqrt_invsqrt(dev(S), 1e-8, 12, leaf=32, channel=sp.CHANNEL_SINGLE)
+        assert torch.equal(Yb, Y1) and torch.equal(Zb, Z1)
