@@ -66,7 +66,9 @@ def lib():
             L.or_gershgorin.restype = ctypes.c_double
             L.or_ns.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                 ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, dp, dp, dp, lp,
-                                dp]
+                                lp, ctypes.c_int, dp]
+            L.or_lens_hist.argtypes = [ip, ctypes.c_long, ctypes.c_int, lp]
+            L.or_lens_hist.restype = None
             L.or_map_params.argtypes = [ctypes.c_int, ctypes.c_double, dp, dp]
             L.or_map_params.restype = None
             L.or_ns.restype = ctypes.c_int
@@ -196,10 +198,20 @@ CHANNEL_DUAL = 0    # Eq. (cannonical)
 CHANNEL_SINGLE = 1  # Eq. (single): z <- z h[x], x = z^T s z
 
 
+def lens_hist(tasks, bins: int) -> np.ndarray:
+    """Plane-diagonal profile of a task list: [3, bins] counts of |i-j|, |j-k|, |i-k| (last bin: >= bins-1)."""
+    tasks = np.ascontiguousarray(tasks, dtype=np.int32).reshape(-1, 3)
+    h = np.zeros((3, bins), dtype=np.int64)
+    lib().or_lens_hist(_i(tasks), tasks.shape[0], int(bins), _l(h))
+    return h
+
+
 def sqrt_invsqrt(S, nb: int, tau: float, maxit: int, tau_s: float | None = None, mu_rel: float = 0.0,
-                 order: int = 0, tol_t: float = 0.0, map: int = MAP_NS, channel: int = CHANNEL_DUAL) -> dict:
+                 order: int = 0, tol_t: float = 0.0, map: int = MAP_NS, channel: int = CHANNEL_DUAL,
+                 lens_bins: int = 0) -> dict:
     """NS square-root iteration (dual or single channel); returns Y ~ S^{1/2}, Z ~ S^{-1/2} and the
-    per-iteration history."""
+    per-iteration history (with lens_bins > 0 also the plane-diagonal profile of every product,
+    [iters, 3 products, 3 planes, lens_bins])."""
     S = _mat(S)
     n = S.shape[0]
     if tau_s is None:
@@ -209,12 +221,16 @@ def sqrt_invsqrt(S, nb: int, tau: float, maxit: int, tau_s: float | None = None,
     th = np.zeros(max(maxit, 1))
     kh = np.zeros((max(maxit, 1), 3), dtype=np.int64)
     c = np.zeros(1)
+    lh = np.zeros((max(maxit, 1), 3, 3, max(lens_bins, 1)), dtype=np.int64)
     it = lib().or_ns(_d(S), n, nb, tau, tau_s, mu_rel, maxit, order, tol_t, int(map), int(channel), _d(Y), _d(Z),
-                     _d(th), _l(kh), _d(c))
+                     _d(th), _l(kh), _l(lh) if lens_bins > 0 else None, int(lens_bins), _d(c))
     if it < 0:
         raise RuntimeError(f"oracle NS failed ({it})")
-    return {"Y": Y, "Z": Z, "iters": it, "t_hist": th[:it].copy(), "task_hist": kh[:it].copy(),
-            "scale_c": float(c[0])}
+    out = {"Y": Y, "Z": Z, "iters": it, "t_hist": th[:it].copy(), "task_hist": kh[:it].copy(),
+           "scale_c": float(c[0])}
+    if lens_bins > 0:
+        out["lens_hist"] = lh[:it].copy()
+    return out
 
 
 def residual(S, Z) -> float:

@@ -366,6 +366,22 @@ static double or_trace_error(const double* X, int n) {
     return ((double)n - tr) / (double)n;
 }
 
+/*
+ * Plane-diagonal profile of a task list (the "lensing" of Sec. 7.2: the
+ * culled volume collapsing onto the plane diagonals of the ijk cube).
+ * hist[q * bins + d] += number of surviving triples (i, j, k) whose distance
+ * d from plane q is that many tiles: q = 0 |i - j| (plane i = j, the left
+ * operand's diagonal), q = 1 |j - k| (the right operand's), q = 2 |i - k|
+ * (the product's); d >= bins counts in the last bin.
+ */
+void or_lens_hist(const int* tasks, long cnt, int bins, long* hist) {
+    for (long t = 0; t < cnt; ++t) {
+        const int i = tasks[3 * t], j = tasks[3 * t + 1], k = tasks[3 * t + 2];
+        const int d[3] = {abs(i - j), abs(j - k), abs(i - k)};
+        for (int q = 0; q < 3; ++q) hist[q * bins + (d[q] < bins ? d[q] : bins - 1)] += 1;
+    }
+}
+
 /* T = A^T (n x n). */
 static void or_transpose(const double* A, double* T, int n) {
     for (int i = 0; i < n; ++i)
@@ -393,25 +409,33 @@ static void or_transpose(const double* A, double* T, int n) {
  *
  * The iteration stops after maxit steps or once |t_k| <= tol_t (tol_t > 0).
  * t_hist (maxit) and task_hist (3*maxit: the y, z, x products of the dual
- * channel; z, s z, x of the single channel) may be NULL.  Returns the number
- * of iterations run; *scale_c receives c.
+ * channel; z, s z, x of the single channel) may be NULL.  lens_hist may be
+ * NULL or hold maxit * 3 * 3 * lens_bins counts: the plane-diagonal profile
+ * (or_lens_hist) of product p of iteration k at ((k * 3 + p) * 3) * lens_bins.
+ * Returns the number of iterations run; *scale_c receives c.
  */
 int or_ns(const double* S, int n, int nb, double tau, double tau_s, double mu_rel, int maxit,
           int order, double tol_t, int map, int channel, double* Y, double* Z, double* t_hist,
-          long* task_hist, double* scale_c) {
+          long* task_hist, long* lens_hist, int lens_bins, double* scale_c) {
     if (n <= 0 || nb <= 0 || maxit < 0 || !(tau >= 0.0) || !(tau_s >= 0.0) || map < 0 || map > 1 ||
-        channel < 0 || channel > 1 || (channel == 1 && order != 0))
+        channel < 0 || channel > 1 || (channel == 1 && order != 0) || (lens_hist && lens_bins <= 0))
         return OR_ERR_ARG;
+    const int m = or_tiles_per_side(n, nb);
+    const long full = (long)m * m * m;
     size_t nn = (size_t)n * n;
     double* X = (double*)malloc(sizeof(double) * nn);
     double* T = (double*)malloc(sizeof(double) * nn);
     double* W = (double*)malloc(sizeof(double) * nn);
     double* s1 = channel == 1 ? (double*)malloc(sizeof(double) * nn) : NULL;
     double* Zt = channel == 1 ? (double*)malloc(sizeof(double) * nn) : NULL;
-    if (!X || !T || !W || (channel == 1 && (!s1 || !Zt))) {
-        free(X); free(T); free(W); free(s1); free(Zt);
+    int* tl = lens_hist ? (int*)malloc(sizeof(int) * 3 * (size_t)full) : NULL;
+    if (!X || !T || !W || (channel == 1 && (!s1 || !Zt)) || (lens_hist && !tl)) {
+        free(X); free(T); free(W); free(s1); free(Zt); free(tl);
         return OR_ERR_NOMEM;
     }
+    const long cap = tl ? full : 0;
+#define OR_LENS(p, cnt) \
+    if (tl && (cnt) >= 0) or_lens_hist(tl, (cnt), lens_bins, lens_hist + ((long)k * 3 + (p)) * 3 * lens_bins)
 
     double mu = 0.0;
     if (mu_rel > 0.0) mu = mu_rel * or_gershgorin(S, n, 0.0);
@@ -433,12 +457,18 @@ int or_ns(const double* S, int n, int nb, double tau, double tau_s, double mu_re
         long ty, tz, tx;
         if (channel == 1) {
             /* Eq. (single): z_k = z_{k-1} h[x_{k-1}], x_k = z_k^T s z_k */
-            tz = or_spamm(Z, T, W, n, nb, tau, NULL, 0);
+            tz = or_spamm(Z, T, W, n, nb, tau, tl, cap);
+            OR_LENS(0, tz);
             memcpy(Z, W, sizeof(double) * nn);
-            ty = or_spamm(s1, Z, Y, n, nb, tau_s, NULL, 0);
+            ty = or_spamm(s1, Z, Y, n, nb, tau_s, tl, cap);
+            OR_LENS(1, ty);
             or_transpose(Z, Zt, n);
-            tx = or_spamm(Zt, Y, X, n, nb, tau, NULL, 0);
-            if (ty < 0 || tz < 0 || tx < 0) { free(X); free(T); free(W); free(s1); free(Zt); return OR_ERR_NOMEM; }
+            tx = or_spamm(Zt, Y, X, n, nb, tau, tl, cap);
+            OR_LENS(2, tx);
+            if (ty < 0 || tz < 0 || tx < 0) {
+                free(X); free(T); free(W); free(s1); free(Zt); free(tl);
+                return OR_ERR_NOMEM;
+            }
             const double tk = or_trace_error(X, n);
             t_cur = tk;
             if (t_hist) t_hist[k] = tk;
@@ -448,22 +478,30 @@ int or_ns(const double* S, int n, int nb, double tau, double tau_s, double mu_re
             continue;
         }
         if (order == 0) {
-            ty = or_spamm(T, Y, W, n, nb, tau_s, NULL, 0);
+            ty = or_spamm(T, Y, W, n, nb, tau_s, tl, cap);
+            OR_LENS(0, ty);
             memcpy(Y, W, sizeof(double) * nn);
-            tz = or_spamm(Z, T, W, n, nb, tau, NULL, 0);
+            tz = or_spamm(Z, T, W, n, nb, tau, tl, cap);
+            OR_LENS(1, tz);
             memcpy(Z, W, sizeof(double) * nn);
         } else {
-            ty = or_spamm(Y, T, W, n, nb, tau_s, NULL, 0);
+            ty = or_spamm(Y, T, W, n, nb, tau_s, tl, cap);
+            OR_LENS(0, ty);
             memcpy(Y, W, sizeof(double) * nn);
-            tz = or_spamm(T, Z, W, n, nb, tau, NULL, 0);
+            tz = or_spamm(T, Z, W, n, nb, tau, tl, cap);
+            OR_LENS(1, tz);
             memcpy(Z, W, sizeof(double) * nn);
         }
         /* X = Y Z as printed; the transposed variant needs X = Z Y (the exact
          * transpose of the printed iteration for symmetric iterates).  Pairing
          * Y T / T Z with X = Y Z is unstable near the fixed point. */
-        if (order == 0) tx = or_spamm(Y, Z, X, n, nb, tau, NULL, 0);
-        else tx = or_spamm(Z, Y, X, n, nb, tau, NULL, 0);
-        if (ty < 0 || tz < 0 || tx < 0) { free(X); free(T); free(W); free(s1); free(Zt); return OR_ERR_NOMEM; }
+        if (order == 0) tx = or_spamm(Y, Z, X, n, nb, tau, tl, cap);
+        else tx = or_spamm(Z, Y, X, n, nb, tau, tl, cap);
+        OR_LENS(2, tx);
+        if (ty < 0 || tz < 0 || tx < 0) {
+            free(X); free(T); free(W); free(s1); free(Zt); free(tl);
+            return OR_ERR_NOMEM;
+        }
         const double tk = or_trace_error(X, n);
         t_cur = tk;
         if (t_hist) t_hist[k] = tk;
@@ -475,7 +513,8 @@ int or_ns(const double* S, int n, int nb, double tau, double tau_s, double mu_re
     double sc = sqrt(c);
     for (size_t q = 0; q < nn; ++q) { Y[q] = Y[q] * sc; Z[q] = Z[q] / sc; }
     if (scale_c) *scale_c = c;
-    free(X); free(T); free(W); free(s1); free(Zt);
+#undef OR_LENS
+    free(X); free(T); free(W); free(s1); free(Zt); free(tl);
     return it;
 }
 

@@ -503,3 +503,48 @@ def test_single_channel_s_product_threshold_is_tau_s():
     n_tau = len(oracle.cull_flat(s, z1, nb, tau))
     assert n_tau_s != n_tau
     assert r["task_hist"][0][1] == n_tau_s
+
+
+# --------------------------------------------------------------------------- plane-diagonal profile ("lensing", Sec. 7.2)
+
+
+def test_lens_profile_dense_closed_form():
+    """At tau = 0 every (i, j, k) survives: for each plane, distance 0 holds m^2 triples and distance d > 0
+    holds m * 2 (m - d); the task counts of every product are m^3."""
+    n, nb = 70, 10  # m = 7
+    m = 7
+    S = synth.kms(n, 0.9)
+    r = oracle.sqrt_invsqrt(S, nb, 0.0, 2, lens_bins=m)
+    want = np.array([m * m] + [m * 2 * (m - d) for d in range(1, m)])
+    for k in range(2):
+        for p in range(3):
+            assert r["task_hist"][k][p] == m ** 3
+            for q in range(3):
+                np.testing.assert_array_equal(r["lens_hist"][k, p, q], want)
+
+
+def test_lens_profile_identity_operand_lies_on_its_plane():
+    """With Z0 = I the first z product Z0 (x) T0 has a left operand supported on tile diagonal only, so its
+    whole volume lies on the plane i = j; the counts agree with the task count; a narrow last bin collects
+    every distance beyond it."""
+    n, nb = 96, 8
+    S = synth.gaussian_lattice(n, 0.6, seed=3)
+    r = oracle.sqrt_invsqrt(S, nb, 1e-6, 3, lens_bins=4)
+    h = r["lens_hist"]
+    z0 = h[0, 1]
+    assert z0[0, 0] == r["task_hist"][0][1] and z0[0, 1:].sum() == 0
+    assert (h.sum(axis=3) == r["task_hist"][:, :, None]).all()
+    tasks, _ = oracle.cull(S, S, nb, 1e-3)
+    full = oracle.lens_hist(tasks, 12)  # m = 12: every distance has its own bin
+    narrow = oracle.lens_hist(tasks, 4)
+    np.testing.assert_array_equal(narrow[:, :3], full[:, :3])
+    np.testing.assert_array_equal(narrow[:, 3], full[:, 3:].sum(axis=1))
+
+
+def test_lens_profile_hand_triples():
+    # (i, j, k) = (0, 1, 3): 1 tile from plane i = j, 2 from j = k, 3 from i = k; (5, 5, 0): 0, 5 -> last bin, 5
+    h = oracle.lens_hist(np.array([[0, 1, 3], [5, 5, 0]]), 5)
+    want = np.zeros((3, 5), dtype=np.int64)
+    want[0, 1] += 1; want[1, 2] += 1; want[2, 3] += 1
+    want[0, 0] += 1; want[1, 4] += 1; want[2, 4] += 1
+    np.testing.assert_array_equal(h, want)
