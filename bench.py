@@ -205,6 +205,23 @@ def measure_dgemm_tflops(torch, dev) -> float:
     return 2.0 * n ** 3 / best / 1e12
 
 
+def lens_summary(h, bins: int, channel: int) -> dict:
+    """Share (%) of each product's surviving tile triples lying on each plane diagonal (distance 0) and within
+    one tile of it, at the first and the last iteration: the collapse of the volume the paper calls lensing."""
+    names = ("z", "s z", "x") if channel else ("y", "z", "x")
+    planes = ("i=j", "j=k", "i=k")
+    out = {"bins": bins, "iterations": int(h.shape[0])}
+    for label, k in (("first", 0), ("last", h.shape[0] - 1)):
+        rec = {}
+        for p, nm in enumerate(names):
+            tot = float(h[k, p, 0].sum())
+            rec[nm] = {pl: {"on": round(100.0 * h[k, p, q, 0] / tot, 2) if tot else None,
+                            "within_1": round(100.0 * h[k, p, q, :2].sum() / tot, 2) if tot else None}
+                       for q, pl in enumerate(planes)}
+        out[label] = rec
+    return out
+
+
 def captured_traffic(kernel: str, tasks_per_launch: float):
     """DRAM bytes (read + write) per launch from the committed ncu capture of `kernel`, scaled by tasks
     to this run's mean launch; None when the kernel source changed since the capture."""
@@ -251,6 +268,15 @@ def run_gpu(args, ws, rank, local):
 
     # verification solve (untimed): residual against the gate, FP64 dense
     _, _, vst = solve(tau, residual=True)
+    lensing = None
+    if args.lens_bins > 0:
+        # plane-diagonal profile of every product (untimed): volume share on each plane diagonal per iteration
+        _, _, lst = sp.sqrt_invsqrt(Sd, tau, MAXIT, leaf=LEAF, precision=prec, Y=Yd, Z=Zd, map=MAP, tol_t=TOL,
+                                    channel=CHANNEL, lens_bins=args.lens_bins)
+        lensing = lens_summary(lst["lens_hist"], args.lens_bins, CHANNEL)
+        if args.lens_npz:
+            np.savez(args.lens_npz, lens_hist=lst["lens_hist"], task_hist=lst["task_hist"], t_hist=lst["t_hist"])
+            lensing["npz"] = args.lens_npz
     for _ in range(max(args.warmup, 3)):
         solve(tau)
     torch.cuda.synchronize()
@@ -431,6 +457,7 @@ def run_gpu(args, ws, rank, local):
             "roofline": roof,
             "fp64_path": fp64_path,
             "to_tolerance": to_tol,
+            "lensing": lensing,
             "cpu_baseline": cpu,
             "e2e": {"value": job_rate(ws, args.steps, e2e_tot), "unit": UNIT, "h2d_bytes_per_step": nbytes,
                     "d2h_bytes_per_step": 2 * nbytes},
@@ -642,6 +669,9 @@ def main():
                     help="stop a solve once |t_k| <= tol (Sec. 4.2 trace error); 0 runs exactly --maxit steps")
     ap.add_argument("--channel", choices=["dual", "single"], default="dual",
                     help="instance of the iteration: dual channel, Eq. (cannonical), or single, Eq. (single)")
+    ap.add_argument("--lens-bins", type=int, default=0,
+                    help="also profile the products' volumes about the plane diagonals (Sec. 7.2), this many bins")
+    ap.add_argument("--lens-npz", default="", help="write the full plane-diagonal profile to this .npz")
     ap.add_argument("--tol-report", type=float, default=1e-12,
                     help="with fixed-step solves, also time solves stopped at |t_k| <= this (0: skip)")
     args = ap.parse_args()

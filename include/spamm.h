@@ -120,6 +120,17 @@ typedef struct spamm_stats {
     double gemm_ms;            /* opts->profile: summed duration of the
                                   leaf-product kernels (CUDA events), else 0    */
     long long gemm_launches;   /* leaf-product kernel launches of the call       */
+    long long* lens_hist;      /* in: NULL, or a caller array of
+                                  maxit * 3 * 3 * lens_bins counts: the plane-
+                                  diagonal profile ("lensing", Sec. 7.2) of
+                                  every product's surviving tile triples
+                                  (i, j, k).  Entry ((k * 3 + p) * 3 + q) *
+                                  lens_bins + d counts the triples of product p
+                                  (task_hist order) of iteration k at distance d
+                                  tiles from plane q: q = 0 |i - j|, 1 |j - k|,
+                                  2 |i - k|; the last bin takes every d >=
+                                  lens_bins - 1.  Filled for the iterations run */
+    int lens_bins;             /* in: bins per plane, 1 .. 4096 (with lens_hist) */
 } spamm_stats;
 
 /* Fill *opts with defaults: leaf 64, SPAMM_FP64, tau_s = 0.01 tau, no shift,

@@ -64,7 +64,8 @@ class Stats(ctypes.Structure):
                 ("scale_c", ctypes.c_double), ("tasks_total", ctypes.c_longlong),
                 ("tasks_dense", ctypes.c_longlong), ("flops", ctypes.c_double),
                 ("t_hist", ctypes.POINTER(ctypes.c_double)), ("task_hist", ctypes.POINTER(ctypes.c_longlong)),
-                ("gemm_ms", ctypes.c_double), ("gemm_launches", ctypes.c_longlong)]
+                ("gemm_ms", ctypes.c_double), ("gemm_launches", ctypes.c_longlong),
+                ("lens_hist", ctypes.POINTER(ctypes.c_longlong)), ("lens_bins", ctypes.c_int)]
 
 
 _lock = threading.Lock()
@@ -242,8 +243,10 @@ def autotune_leaf(S, tau: float, precision: int = FP64, stream=None) -> int:
 
 def sqrt_invsqrt(S, tau: float, maxit: int, leaf: int = 64, precision: int = FP64, tau_s=None, mu_rel=0.0,
                  tol_t=0.0, order=ORDER_PAPER, residual=False, Y=None, Z=None, stream=None, raise_on=True,
-                 profile=False, map=None, channel=None):
-    """Y ~ S^{1/2}, Z ~ S^{-1/2} by dual-channel Newton-Schulz on SpAMM products; returns (Y, Z, stats)."""
+                 profile=False, map=None, channel=None, lens_bins=0):
+    """Y ~ S^{1/2}, Z ~ S^{-1/2} by dual-channel Newton-Schulz on SpAMM products; returns (Y, Z, stats).
+    With lens_bins > 0, stats["lens_hist"] holds the plane-diagonal profile of every product's surviving tile
+    triples, [iters, 3 products, 3 planes (|i-j|, |j-k|, |i-k|), lens_bins]."""
     s, ps, n, _ = _prep(S)
     Y = Y if Y is not None else _like(s, n)
     Z = Z if Z is not None else _like(s, n)
@@ -252,11 +255,18 @@ def sqrt_invsqrt(S, tau: float, maxit: int, leaf: int = 64, precision: int = FP6
     st = Stats()
     st.t_hist = th.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     st.task_hist = kh.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong))
+    lh = None
+    if lens_bins > 0:
+        lh = np.zeros((max(1, maxit), 3, 3, int(lens_bins)), dtype=np.int64)
+        st.lens_hist = lh.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong))
+        st.lens_bins = int(lens_bins)
     o = _opts(leaf, precision, tau_s, mu_rel, tol_t, order, residual, _stream_of(s, stream), profile,
               MAP_NS if map is None else map, CHANNEL_DUAL if channel is None else channel)
     status = lib().spamm_sqrt_invsqrt(ps, n, float(tau), int(maxit), _ptr(Y), _ptr(Z), ctypes.byref(o),
                                       ctypes.byref(st))
     d = _stats_dict(st, th, kh)
+    if lh is not None:
+        d["lens_hist"] = lh[:st.iters].copy()
     d["status"] = status
     if raise_on:
         _check(status)

@@ -281,6 +281,41 @@ void launch_map(const double* X, const double* leafX, TileMat T, const Geometry&
     note_launch();
 }
 
+// Plane-diagonal profile (Sec. 7.2 "lensing") of a product's task lists: a warp per output tile (i, k)
+// walks its surviving j; block histograms in shared memory, then one atomic per non-empty bin.  Launched
+// in stream order after the cull (not as a programmatic dependent: its grid may take several waves).
+__global__ void __launch_bounds__(256) k_lens(const int* __restrict__ counts, const int* __restrict__ jlist, int m,
+                                              int bins, const int* __restrict__ iter, int which,
+                                              unsigned long long* __restrict__ lens, const int* __restrict__ done) {
+    if (done && *done) return;
+    extern __shared__ unsigned hist[];  // [3][bins]
+    for (int q = threadIdx.x; q < 3 * bins; q += blockDim.x) hist[q] = 0u;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (int wid = blockIdx.x * 8 + (threadIdx.x >> 5); wid < m * m; wid += gridDim.x * 8) {
+        const int i = wid / m, k = wid - (wid / m) * m;
+        const int cnt = counts[wid];
+        const int* js = jlist + (size_t)wid * m;
+        for (int t = lane; t < cnt; t += 32) {
+            const int j = js[t];
+            atomicAdd(&hist[min(abs(i - j), bins - 1)], 1u);
+            atomicAdd(&hist[bins + min(abs(j - k), bins - 1)], 1u);
+        }
+        if (lane == 0 && cnt) atomicAdd(&hist[2 * bins + min(abs(i - k), bins - 1)], (unsigned)cnt);
+    }
+    __syncthreads();
+    unsigned long long* out = lens + ((size_t)*iter * 3 + which) * 3 * bins;
+    for (int q = threadIdx.x; q < 3 * bins; q += blockDim.x)
+        if (hist[q]) atomicAdd(out + q, (unsigned long long)hist[q]);
+}
+
+void launch_lens(const int* counts, const int* jlist, const Geometry& g, int bins, const int* iter, int which,
+                 unsigned long long* lens, const int* done, cudaStream_t st) {
+    const int blocks = std::min((g.m * g.m + 7) / 8, device_sm_count() * 4);
+    k_lens<<<blocks, 256, 3 * (size_t)bins * sizeof(unsigned), st>>>(counts, jlist, g.m, bins, iter, which, lens, done);
+    note_launch();
+}
+
 // T = A^T on the tile grid: tile (i,j) of T is tile (j,i) of A transposed, moved through shared memory in
 // 32 x 32 blocks (coalesced reads along A's rows, writes along T's rows).  T's leaf norms are A's, transposed
 // (a tile's Frobenius norm does not depend on the order of its entries).  Tiles of norm 0 are not written:

@@ -100,12 +100,12 @@ struct GraphKey {
     const double* S = nullptr;
     double* Y = nullptr;
     double* Z = nullptr;
-    int n = 0, leaf = 0, precision = 0, order = 0, maxit = 0, profile = 0, map = 0, channel = 0;
+    int n = 0, leaf = 0, precision = 0, order = 0, maxit = 0, profile = 0, map = 0, channel = 0, lens_bins = 0;
     double tau = 0.0, tau_s = 0.0, mu_rel = 0.0, tol_t = 0.0;
     bool operator==(const GraphKey& o) const {
         return S == o.S && Y == o.Y && Z == o.Z && n == o.n && leaf == o.leaf && precision == o.precision &&
                order == o.order && maxit == o.maxit && profile == o.profile && map == o.map &&
-               channel == o.channel && tau == o.tau &&
+               channel == o.channel && lens_bins == o.lens_bins && tau == o.tau &&
                tau_s == o.tau_s && mu_rel == o.mu_rel && tol_t == o.tol_t;
     }
 };
@@ -125,6 +125,10 @@ struct Plan {
     int* counts2 = nullptr;
     int* jlist2 = nullptr;
     int* tile_list2 = nullptr;
+    // plane-diagonal profiles of the products (stats->lens_hist): lens_bins > 0 for this call
+    unsigned long long* lens = nullptr;
+    size_t lens_elems = 0;
+    int lens_bins = 0;
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // tensor-core path: the slicing of a product output runs on its own stream per branch, beside the
@@ -192,6 +196,7 @@ static void free_plan(Plan* p) {
     cudaFree(p->task_ctr);
     cudaFree(p->t_hist);
     cudaFree(p->trace_part);
+    cudaFree(p->lens);
     cudaFree(p->scal);
     cudaFree(p->rowsum);
     cudaFree(p->flags);
@@ -246,6 +251,18 @@ static int alloc_plan(Plan* p, int n, int nb) {
     CKA(dev_alloc(&p->rowsum, (size_t)n * sizeof(double)));
     CKA(dev_alloc(&p->flags, kFlagInts * sizeof(int)));
     CKA(dev_alloc(&p->partial, (size_t)g.m * g.m * sizeof(double)));
+    return SPAMM_OK;
+}
+
+// Device histograms of the plane-diagonal profile: maxit_cap iterations x 3 products x 3 planes x bins.
+static int ensure_lens(Plan* p, int bins) {
+    const size_t need = (size_t)p->maxit_cap * 9 * bins;
+    if (need <= p->lens_elems) return SPAMM_OK;
+    cudaFree(p->lens);
+    p->lens = nullptr;
+    p->lens_elems = 0;
+    CKA(dev_alloc(&p->lens, need * sizeof(unsigned long long)));
+    p->lens_elems = need;
     return SPAMM_OK;
 }
 
@@ -456,6 +473,7 @@ static int stage_out(Plan* p, int which, double* dst, const double* dev, cudaStr
 }
 
 static void begin_call(Plan* p, bool profile, bool emu) {
+    p->lens_bins = 0;
     p->profile = profile;
     p->emu = emu;
     p->ev_used = 0;
@@ -518,6 +536,8 @@ static void product(Plan* p, const TileMat& A, const TileMat& B, TileMat& C, dou
         co.zero_n = 2 * (long)g.m * g.nb;
     }
     launch_cull(g, A.tree, B.tree, tau, co, ctr, nullptr, p->flags, st);
+    if (p->lens_bins > 0)
+        launch_lens(counts, jlist, g, p->lens_bins, p->flags + 1, (int)(ctr - p->task_ctr), p->lens, p->flags, st);
     if (p->emu) {
         // the operands' slices may still be in flight on a slicing stream (only slicing enqueued since the
         // last join is waited on: a captured loop body depends on nothing recorded outside it)
@@ -734,6 +754,8 @@ static int enqueue_prologue(Plan* p, const double* dS, int n, const spamm_opts& 
     CK(cudaMemsetAsync(p->flags, 0, kFlagInts * sizeof(int), st));
     CK(cudaMemsetAsync(p->task_ctr, 0, (3 * (size_t)p->maxit_cap + 4) * sizeof(unsigned long long), st));
     CK(cudaMemsetAsync(p->t_hist, 0, (size_t)p->maxit_cap * sizeof(double), st));
+    if (p->lens_bins > 0)
+        CK(cudaMemsetAsync(p->lens, 0, (size_t)p->maxit_cap * 9 * p->lens_bins * sizeof(unsigned long long), st));
 
     double* c0 = p->scal + 0;
     double* mu = p->scal + 1;
@@ -984,7 +1006,7 @@ static int solve_graph(Plan* p, const double* dS, double* dY, double* dZ, int n,
         CK(cudaEventCreateWithFlags(&p->ev_out, cudaEventDisableTiming));
     }
     const GraphKey key{dS, dY, dZ, n, o.leaf, o.precision, o.order, maxit, o.profile ? 1 : 0, o.map, o.channel,
-                       tau, tau_s, o.mu_rel, o.tol_t};
+                       p->lens_bins, tau, tau_s, o.mu_rel, o.tol_t};
     CK(cudaEventRecord(p->ev_in, st));
     CK(cudaStreamWaitEvent(p->gstream, p->ev_in, 0));
     if (!p->gexec || !(p->gkey == key)) {
@@ -1053,6 +1075,14 @@ static int sqrt_impl(const double* S, int n, double tau, int maxit, double* Y, d
     if ((e = out_target(p, 2, Z, &dZ))) return e;
     begin_call(p, o.profile != 0, o.precision == SPAMM_EMU64);
     if (p->emu && (e = ensure_emu(p))) return e;
+    if (stats && stats->lens_hist && maxit > 0) {
+        if (stats->lens_bins < 1 || stats->lens_bins > 4096) {
+            g_last_error = "lens_bins must be 1 .. 4096";
+            return SPAMM_ERR_ARG;
+        }
+        if ((e = ensure_lens(p, stats->lens_bins))) return e;
+        p->lens_bins = stats->lens_bins;
+    }
 
     const int it_host = maxit;  // at most; the device counts the iterations that ran
     const bool graph = graphs_enabled();
@@ -1104,6 +1134,10 @@ static int sqrt_impl(const double* S, int n, double tau, int maxit, double* Y, d
             for (int q = 0; q < iters; ++q) stats->t_hist[q] = th[q];
         if (stats->task_hist)
             for (int q = 0; q < 3 * iters; ++q) stats->task_hist[q] = (long long)kc[q];
+        if (p->lens_bins > 0 && iters > 0) {
+            const size_t cnt = (size_t)iters * 9 * p->lens_bins;
+            CK(cudaMemcpy(stats->lens_hist, p->lens, cnt * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+        }
         stats->gemm_ms = p->profile ? profiled_ms(p) : 0.0;
         stats->gemm_launches = p->gemm_launches;
     }

@@ -124,6 +124,12 @@ void launch_trace_parts(const double* X, const Geometry& g, double* trace_part, 
 // maxima into T.rmax/T.cmax (which must be zero).  Skipped once *done is set.
 void launch_map(const double* X, const double* leafX, TileMat T, const Geometry& g, int map, const double* trace_part,
                 bool maxima, const int* done, cudaStream_t st);
+// Plane-diagonal profile of one product's task lists (counts, jlist): adds
+// to lens[(*iter * 3 + which) * 3 * bins + q * bins + d] the triples (i,j,k)
+// at distance d from plane q (|i-j|, |j-k|, |i-k|; d clamped to bins-1).
+// Skipped once *done is set.
+void launch_lens(const int* counts, const int* jlist, const Geometry& g, int bins, const int* iter, int which,
+                 unsigned long long* lens, const int* done, cudaStream_t st);
 // T = A^T on the tile grid (tile (i,j) of T = tile (j,i) of A, transposed) with T's leaf norms; tiles of
 // norm 0 are left unwritten.  Skipped once *done is set.
 void launch_transpose(const TileMat& A, TileMat T, const Geometry& g, const int* done, cudaStream_t st);

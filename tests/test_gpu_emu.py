@@ -158,3 +158,14 @@ def test_emu_ns_single_channel(n, tau, mp):
     ez, ey, st, ref = _emu_ns(S, tau, 20, channel=sp.CHANNEL_SINGLE, map=mp)
     assert ez <= 1e-9 and ey <= 1e-9, (ez, ey)
     np.testing.assert_allclose(st["t_hist"], ref["t_hist"], rtol=0, atol=1e-11)
+
+
+def test_emu_lens_profile_counts():
+    """The plane-diagonal profile on the tensor-core path: every product's histogram sums to its task count,
+    and the first z product (Z0 = I on the left) lies on the plane i = j."""
+    S = synth.kms(512, 0.9)
+    Y, Z, st = sp.sqrt_invsqrt(dev(S), 1e-10, 10, leaf=64, precision=sp.EMU64, lens_bins=8)
+    h = st["lens_hist"]
+    assert h.shape == (10, 3, 3, 8)
+    assert (h.sum(axis=3) == st["task_hist"][:, :, None]).all()
+    assert h[0, 1, 0, 0] == st["task_hist"][0][1] and h[0, 1, 0, 1:].sum() == 0

@@ -320,3 +320,21 @@ def test_ns_single_channel_batched_equals_single():
     for S, Yb, Zb in zip(Ss, Ys, Zs):
         Y1, Z1, _ = sp.sqrt_invsqrt(dev(S), 1e-8, 12, leaf=32, channel=sp.CHANNEL_SINGLE)
         assert torch.equal(Yb, Y1) and torch.equal(Zb, Z1)
+
+
+# ------------------------------------------------------------------------------------------ plane-diagonal profile
+
+
+@pytest.mark.parametrize("channel,tol", [(0, 0.0), (1, 0.0), (0, 1e-3)])
+def test_lens_profile_matches_oracle(channel, tol):
+    """Per-iteration |i-j|, |j-k|, |i-k| histograms of every product's surviving triples (Sec. 7.2 lensing):
+    identical to the oracle's where the task lists are (the Gaussian 256 / N_b 32 case)."""
+    S = synth.gaussian_lattice(256, 0.6, seed=0)
+    Y, Z, st = sp.sqrt_invsqrt(dev(S), 1e-6, 16, leaf=32, channel=channel, tol_t=tol, lens_bins=5)
+    ref = oracle.sqrt_invsqrt(S, 32, 1e-6, 16, channel=channel, tol_t=tol, lens_bins=5)
+    assert st["iters"] == ref["iters"]
+    np.testing.assert_array_equal(st["task_hist"], ref["task_hist"])
+    np.testing.assert_array_equal(st["lens_hist"], ref["lens_hist"])
+    # the profile changes the results in no way
+    Y0, Z0, _ = sp.sqrt_invsqrt(dev(S), 1e-6, 16, leaf=32, channel=channel, tol_t=tol)
+    assert torch.equal(Y, Y0) and torch.equal(Z, Z0)
