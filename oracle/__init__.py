@@ -67,6 +67,9 @@ def lib():
             L.or_ns.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                 ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, dp, dp, dp, lp,
                                 lp, ctypes.c_int, dp]
+            L.or_invsqrt_product.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_int, ctypes.c_double, dp, ip]
+            L.or_invsqrt_product.restype = ctypes.c_int
             L.or_lens_hist.argtypes = [ip, ctypes.c_long, ctypes.c_int, lp]
             L.or_lens_hist.restype = None
             L.or_map_params.argtypes = [ctypes.c_int, ctypes.c_double, dp, dp]
@@ -231,6 +234,21 @@ def sqrt_invsqrt(S, nb: int, tau: float, maxit: int, tau_s: float | None = None,
     if lens_bins > 0:
         out["lens_hist"] = lh[:it].copy()
     return out
+
+
+def invsqrt_product(S, nb: int, mus, tau0: float, tau1: float, maxit: int, tol_t: float = 0.0) -> dict:
+    """Product representation of the regularised inverse factor: slice z_0 = (S + mu_0 c0 I)^{-1/2}, then per
+    level the residual Z^T (S + mu_l c0 I) Z, its inverse square root z_l and Z <- Z z_l.  Returns Z (with
+    Z^T (S + mu_last c0 I) Z -> I) and the NS iterations of every level."""
+    S = _mat(S)
+    n = S.shape[0]
+    mus = np.ascontiguousarray(mus, dtype=np.float64)
+    Z = np.zeros_like(S)
+    its = np.zeros(len(mus), dtype=np.int32)
+    rc = lib().or_invsqrt_product(_d(S), n, nb, len(mus), _d(mus), tau0, tau1, maxit, tol_t, _d(Z), _i(its))
+    if rc != 0:
+        raise RuntimeError(f"oracle product representation failed ({rc})")
+    return {"Z": Z, "iters": its.copy(), "scale_c0": gershgorin(S)}
 
 
 def residual(S, Z) -> float:

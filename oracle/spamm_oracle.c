@@ -518,6 +518,58 @@ int or_ns(const double* S, int n, int nb, double tau, double tau_s, double mu_re
     return it;
 }
 
+/*
+ * Product representation of the regularised inverse factor (Sec. 6,
+ * Eq. (spammsandwich), with the iterative regularisation of Eq. (product_rep)):
+ *   z_0 = (S + mu_0 c0 I)^{-1/2} by or_ns at tau0 (dual channel, map 0,
+ *         mu_rel = mu_0; the most-approximate-yet-effective slice),
+ *   Z = z_0, and for l = 1 .. levels-1:
+ *     R_l = Z^T (x)_{tau1} ((S + mu_l c0 I) (x)_{tau1} Z)   (the residual),
+ *     z_l = R_l^{-1/2} by or_ns at tau0 (no shift),
+ *     Z  <- Z (x)_{tau1} z_l,
+ * so that Z^T (S + mu_{levels-1} c0 I) Z -> I.  c0 is the Gershgorin bound of
+ * S (shifts relative to it, like mu_rel).  Each or_ns runs maxit iterations,
+ * or fewer with tol_t > 0.  iters (levels) may be NULL.  Returns 0 or an
+ * OR_ERR code.
+ */
+int or_invsqrt_product(const double* S, int n, int nb, int levels, const double* mu, double tau0, double tau1,
+                       int maxit, double tol_t, double* Zout, int* iters) {
+    if (n <= 0 || nb <= 0 || levels < 1 || maxit < 0 || !(tau0 >= 0.0) || !(tau1 >= 0.0)) return OR_ERR_ARG;
+    for (int l = 0; l < levels; ++l)
+        if (!(mu[l] >= 0.0)) return OR_ERR_ARG;
+    const size_t nn = (size_t)n * n;
+    double* Y = (double*)malloc(sizeof(double) * nn);
+    double* z = (double*)malloc(sizeof(double) * nn);
+    double* Sm = (double*)malloc(sizeof(double) * nn);
+    double* W = (double*)malloc(sizeof(double) * nn);
+    double* Zt = (double*)malloc(sizeof(double) * nn);
+    double* R = (double*)malloc(sizeof(double) * nn);
+    int rc = OR_OK;
+    if (!Y || !z || !Sm || !W || !Zt || !R) { rc = OR_ERR_NOMEM; goto done; }
+    {
+        const double c0 = or_gershgorin(S, n, 0.0);
+        int it = or_ns(S, n, nb, tau0, 0.01 * tau0, mu[0], maxit, 0, tol_t, 0, 0, Y, Zout, NULL, NULL, NULL, 0,
+                       NULL);
+        if (it < 0) { rc = it; goto done; }
+        if (iters) iters[0] = it;
+        for (int l = 1; l < levels; ++l) {
+            memcpy(Sm, S, sizeof(double) * nn);
+            for (int i = 0; i < n; ++i) Sm[(long)i * n + i] += mu[l] * c0;
+            if (or_spamm(Sm, Zout, W, n, nb, tau1, NULL, 0) < 0) { rc = OR_ERR_NOMEM; goto done; }
+            or_transpose(Zout, Zt, n);
+            if (or_spamm(Zt, W, R, n, nb, tau1, NULL, 0) < 0) { rc = OR_ERR_NOMEM; goto done; }
+            it = or_ns(R, n, nb, tau0, 0.01 * tau0, 0.0, maxit, 0, tol_t, 0, 0, Y, z, NULL, NULL, NULL, 0, NULL);
+            if (it < 0) { rc = it; goto done; }
+            if (iters) iters[l] = it;
+            if (or_spamm(Zout, z, W, n, nb, tau1, NULL, 0) < 0) { rc = OR_ERR_NOMEM; goto done; }
+            memcpy(Zout, W, sizeof(double) * nn);
+        }
+    }
+done:
+    free(Y); free(z); free(Sm); free(W); free(Zt); free(R);
+    return rc;
+}
+
 /* ||Z S Z - I||_F with plain triple loops (verification of a finished solve). */
 double or_residual(const double* S, const double* Z, int n) {
     size_t nn = (size_t)n * n;
