@@ -188,6 +188,30 @@ int spamm_sqrt_invsqrt_batched(int count, const double* const* S, const int* n, 
                                spamm_stats* stats);
 
 /*
+ * Product representation of the regularised inverse factor, Sec. 6
+ * (Eq. (spammsandwich) with the iterative regularisation of
+ * Eq. (product_rep)): a telescoping product of SpAMM "slices".
+ *   z_0 = (S + mu[0] c0 I)^{-1/2} by spamm_sqrt_invsqrt at tau0 (the
+ *         most-approximate-yet-effective slice), Z = z_0; then for
+ *   l = 1 .. levels-1:
+ *     R_l = Z^T (x)_{tau1} ((S + mu[l] c0 I) (x)_{tau1} Z)   (the residual)
+ *     z_l = R_l^{-1/2} by spamm_sqrt_invsqrt at tau0 (no shift)
+ *     Z  <- Z (x)_{tau1} z_l
+ * so that Z^T (S + mu[levels-1] c0 I) Z ~ I.  c0 is the Gershgorin bound
+ * of S; the shifts mu[] (levels of them, >= 0, typically decreasing) are
+ * relative to it like opts->mu_rel.  Every slice runs maxit iterations (or
+ * stops at opts->tol_t) with opts' leaf, precision, map, channel, order
+ * and tau_s rule (opts->mu_rel is ignored).  S, Z: n x n row-major, host or
+ * device.  iters: NULL or `levels` ints, the NS iterations of each slice.
+ * Device scratch: six n x n matrices for the call, plus the cached plans.
+ * Returns SPAMM_OK, an argument or resource error, or the first non-OK
+ * status of a slice's solve (SPAMM_ERR_DIVERGED, SPAMM_ERR_NOTCONVERGED:
+ * Z is still written).
+ */
+int spamm_invsqrt_product(const double* S, int n, int levels, const double* mu, double tau0, double tau1,
+                          int maxit, double* Z, int* iters, const spamm_opts* opts);
+
+/*
  * Norm tree of A for parity checks: nu_leaf[i*m + j] = ||A_ij||_F^2 for the
  * m x m leaf tiles (m = ceil(n/leaf)), accumulated in FP64, and *root =
  * ||A||_F^2 summed up the quadtree (Sec. 1, norm recursion).

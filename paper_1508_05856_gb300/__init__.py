@@ -22,8 +22,9 @@ import numpy as np
 
 from . import _build_lib
 
-__all__ = ["FP64", "EMU64", "ORDER_PAPER", "ORDER_TRANSPOSED", "SpammError", "lib", "build", "multiply",
-           "sqrt_invsqrt", "sqrt_invsqrt_batched", "norm_tree", "cull", "release", "version", "HEADER_SYMBOLS"]
+__all__ = ["FP64", "EMU64", "ORDER_PAPER", "ORDER_TRANSPOSED", "MAP_NS", "MAP_SCALED", "CHANNEL_DUAL",
+           "CHANNEL_SINGLE", "SpammError", "lib", "build", "multiply", "sqrt_invsqrt", "sqrt_invsqrt_batched",
+           "invsqrt_product", "autotune_leaf", "norm_tree", "cull", "release", "version", "HEADER_SYMBOLS", "Server"]
 
 FP64 = 0
 EMU64 = 1
@@ -40,6 +41,7 @@ STATUS = {0: "SPAMM_OK", -1: "SPAMM_ERR_ARG", -2: "SPAMM_ERR_NOMEM", -3: "SPAMM_
 
 # every extern "C" function declared in include/spamm.h
 HEADER_SYMBOLS = ["spamm_opts_init", "spamm_autotune_leaf", "spamm_multiply", "spamm_sqrt_invsqrt",
+                  "spamm_invsqrt_product",
                   "spamm_sqrt_invsqrt_batched", "spamm_norm_tree", "spamm_cull", "spamm_last_error", "spamm_strerror",
                   "spamm_release",
                   "spamm_kernel_launches", "spamm_version", "spamm_multiply_noalloc", "spamm_server_create",
@@ -98,6 +100,9 @@ def lib(build_if_missing: bool = True):
         L.spamm_autotune_leaf.argtypes = [vp, ip, ctypes.c_double, ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_int)]
         L.spamm_autotune_leaf.restype = ip
         L.spamm_multiply.argtypes = [vp, vp, vp, ip, ctypes.c_double, ctypes.POINTER(Opts), ctypes.POINTER(Stats)]
+        L.spamm_invsqrt_product.argtypes = [vp, ip, ip, ctypes.POINTER(ctypes.c_double), ctypes.c_double,
+                                            ctypes.c_double, ip, vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(Opts)]
+        L.spamm_invsqrt_product.restype = ip
         L.spamm_multiply.restype = ip
         L.spamm_sqrt_invsqrt.argtypes = [vp, ip, ctypes.c_double, ip, vp, vp, ctypes.POINTER(Opts),
                                          ctypes.POINTER(Stats)]
@@ -229,6 +234,25 @@ def multiply(A, B, tau: float, leaf: int = 64, precision: int = FP64, out=None, 
     o = _opts(leaf=leaf, precision=precision, stream=_stream_of(a, stream))
     _check(lib().spamm_multiply(pa, pb, _ptr(C), n, float(tau), ctypes.byref(o), ctypes.byref(st)))
     return C, _stats_dict(st)
+
+
+def invsqrt_product(S, mus, tau0: float, tau1: float, maxit: int, leaf: int = 64, precision: int = FP64,
+                    tau_s=None, tol_t=0.0, map=None, channel=None, Z=None, stream=None, raise_on=True):
+    """Product representation of the regularised inverse factor (Sec. 6, spamm_invsqrt_product): slice
+    z_0 = (S + mus[0] c0 I)^{-1/2} at tau0, then per level the residual Z^T (S + mus[l] c0 I) Z at tau1, its
+    inverse square root z_l at tau0 and Z <- Z (x)_tau1 z_l.  Returns (Z, {"iters": [...], "status": s}),
+    with Z^T (S + mus[-1] c0 I) Z ~ I."""
+    s, ps, n, _ = _prep(S)
+    Z = Z if Z is not None else _like(s, n)
+    mu = (ctypes.c_double * len(mus))(*[float(x) for x in mus])
+    its = (ctypes.c_int * len(mus))()
+    o = _opts(leaf, precision, tau_s, 0.0, tol_t, ORDER_PAPER, False, _stream_of(s, stream), False,
+              MAP_NS if map is None else map, CHANNEL_DUAL if channel is None else channel)
+    status = lib().spamm_invsqrt_product(ps, n, len(mus), mu, float(tau0), float(tau1), int(maxit), _ptr(Z), its,
+                                         ctypes.byref(o))
+    if raise_on:
+        _check(status)
+    return Z, {"iters": list(its), "status": status}
 
 
 def autotune_leaf(S, tau: float, precision: int = FP64, stream=None) -> int:

@@ -116,6 +116,50 @@ void launch_gershgorin(const double* S, int n, const double* mu_dev, double* row
 
 __global__ void k_scale_mu(const double* c0, double mu_rel, double* mu_out) { *mu_out = mu_rel * (*c0); }
 
+// Row-major D = S + (mu_rel * *c0) I (the level shift of Sec. 6, relative to a device-side bound c0).
+__global__ void __launch_bounds__(256) k_shift_copy(const double* __restrict__ S, double* __restrict__ D, int n,
+                                                    double mu_rel, const double* __restrict__ c0) {
+    const double mu = mu_rel * *c0;
+    const size_t nn = (size_t)n * n;
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < nn; q += (size_t)gridDim.x * blockDim.x) {
+        const size_t i = q / n, j = q - i * n;
+        D[q] = i == j ? S[q] + mu : S[q];
+    }
+}
+
+void launch_shift_copy(const double* S, double* D, int n, double mu_rel, const double* c0, cudaStream_t st) {
+    const size_t nn = (size_t)n * n;
+    const int blocks = (int)std::min<size_t>((nn + 255) / 256, (size_t)device_sm_count() * 8);
+    k_shift_copy<<<blocks, 256, 0, st>>>(S, D, n, mu_rel, c0);
+    note_launch();
+}
+
+// Row-major T = A^T in 32 x 32 blocks through shared memory (coalesced on both sides).
+__global__ void __launch_bounds__(256) k_transpose_rm(const double* __restrict__ A, double* __restrict__ T, int n) {
+    __shared__ double sm[32][33];
+    const int nbk = (n + 31) / 32;
+    for (int b = blockIdx.x; b < nbk * nbk; b += gridDim.x) {
+        const int r0 = (b / nbk) * 32, c0 = (b - (b / nbk) * nbk) * 32;  // block of A at rows r0, columns c0
+        __syncthreads();
+        for (int q = threadIdx.x; q < 1024; q += 256) {
+            const int r = q >> 5, c = q & 31;
+            if (r0 + r < n && c0 + c < n) sm[r][c] = A[(size_t)(r0 + r) * n + c0 + c];
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < 1024; q += 256) {
+            const int r = q >> 5, c = q & 31;  // T's row c0 + r, column r0 + c
+            if (c0 + r < n && r0 + c < n) T[(size_t)(c0 + r) * n + r0 + c] = sm[c][r];
+        }
+    }
+}
+
+void launch_transpose_rm(const double* A, double* T, int n, cudaStream_t st) {
+    const int nbk = (n + 31) / 32;
+    const int blocks = std::min(nbk * nbk, device_sm_count() * 8);
+    k_transpose_rm<<<blocks, 256, 0, st>>>(A, T, n);
+    note_launch();
+}
+
 void launch_scale_mu(const double* c0, double mu_rel, double* mu_out, cudaStream_t st) {
     k_scale_mu<<<1, 1, 0, st>>>(c0, mu_rel, mu_out);
     note_launch();

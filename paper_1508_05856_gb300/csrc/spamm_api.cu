@@ -1203,6 +1203,78 @@ static int check_common(int n, double tau, const spamm_opts& o) {
     return SPAMM_OK;
 }
 
+// Device scratch of one call, freed when the call returns.
+struct CallScratch {
+    std::vector<void*> ptrs;
+    ~CallScratch() {
+        for (void* q : ptrs) cudaFree(q);
+    }
+    template <typename T>
+    cudaError_t get(T** out, size_t bytes) {
+        void* q = nullptr;
+        const cudaError_t e = dev_alloc(&q, bytes);
+        if (e == cudaSuccess) ptrs.push_back(q);
+        *out = static_cast<T*>(q);
+        return e;
+    }
+};
+
+// Sec. 6 product representation: slice z_0 of S + mu_0 c0 I, then per level the residual
+// Z^T (S + mu_l c0 I) Z, its inverse square root z_l and Z <- Z (x) z_l (see spamm.h).
+static int invsqrt_product_impl(const double* S, int n, int levels, const double* mu, double tau0, double tau1,
+                                int maxit, double* Z, int* iters, const spamm_opts& o_in) {
+    cudaStream_t st = (cudaStream_t)o_in.stream;
+    init_device_attributes();
+    const size_t bytes = (size_t)n * n * sizeof(double);
+    CallScratch cs;
+    double *dZa, *dW, *dR, *dz, *dY, *dT, *rowsum, *c0;
+    CKA(cs.get(&dZa, bytes));
+    CKA(cs.get(&dW, bytes));
+    CKA(cs.get(&dR, bytes));
+    CKA(cs.get(&dz, bytes));
+    CKA(cs.get(&dY, bytes));
+    CKA(cs.get(&dT, bytes));
+    CKA(cs.get(&rowsum, (size_t)n * sizeof(double)));
+    CKA(cs.get(&c0, sizeof(double)));
+    const double* dS = S;
+    if (!is_device_ptr(S)) {
+        double* st_S;
+        CKA(cs.get(&st_S, bytes));
+        CK(cudaMemcpyAsync(st_S, S, bytes, cudaMemcpyHostToDevice, st));
+        dS = st_S;
+    }
+    launch_gershgorin(dS, n, nullptr, rowsum, c0, st);
+    spamm_opts o = o_in;
+    o.residual = 0;
+    o.profile = 0;
+    int status = SPAMM_OK;
+    auto solve = [&](const double* M, double mu_rel, double* out, int level) -> int {
+        spamm_opts os = o;
+        os.mu_rel = mu_rel;
+        spamm_stats sst;
+        std::memset(&sst, 0, sizeof(sst));
+        const int e = sqrt_impl(M, n, tau0, maxit, dY, out, os, &sst);
+        if (e && e != SPAMM_ERR_DIVERGED && e != SPAMM_ERR_NOTCONVERGED) return e;
+        if (e && !status) status = e;
+        if (iters) iters[level] = sst.iters;
+        return SPAMM_OK;
+    };
+    int e = solve(dS, mu[0], dZa, 0);
+    if (e) return e;
+    for (int l = 1; l < levels; ++l) {
+        launch_shift_copy(dS, dT, n, mu[l], c0, st);                   // S + mu_l c0 I
+        if ((e = multiply_impl(dT, dZa, dW, n, tau1, o, nullptr))) return e;  // W = S_mu (x) Z
+        launch_transpose_rm(dZa, dT, n, st);                           // Z^T
+        if ((e = multiply_impl(dT, dW, dR, n, tau1, o, nullptr))) return e;   // R = Z^T (x) W
+        if ((e = solve(dR, 0.0, dz, l))) return e;                     // z_l = R^{-1/2}
+        if ((e = multiply_impl(dZa, dz, dW, n, tau1, o, nullptr))) return e;  // Z (x) z_l
+        std::swap(dZa, dW);
+    }
+    CK(cudaMemcpyAsync(Z, dZa, bytes, cudaMemcpyDefault, st));
+    CK(cudaStreamSynchronize(st));
+    return status;
+}
+
 // Internal entry points used by the request server (spamm_server.cu).
 int run_sqrt(const double* S, int n, double tau, int maxit, double* Y, double* Z, const spamm_opts& o,
              spamm_stats* stats) {
@@ -1287,6 +1359,29 @@ int spamm_sqrt_invsqrt(const double* S, int n, double tau, int maxit, double* Y,
             return SPAMM_ERR_ARG;
         }
         return sqrt_impl(S, n, tau, maxit, Y, Z, o, stats);
+    } catch (...) {
+        g_last_error = "internal exception";
+        return SPAMM_ERR_CUDA;
+    }
+}
+
+int spamm_invsqrt_product(const double* S, int n, int levels, const double* mu, double tau0, double tau1, int maxit,
+                          double* Z, int* iters, const spamm_opts* opts) {
+    try {
+        g_last_error.clear();
+        spamm_opts o = resolve_opts(opts);
+        int e = check_common(n, tau0, o);
+        if (e) return e;
+        if (!S || !Z || !mu || levels < 1 || maxit < 0 || !(tau1 >= 0.0) || std::isinf(tau1)) {
+            g_last_error = "bad product-representation arguments";
+            return SPAMM_ERR_ARG;
+        }
+        for (int l = 0; l < levels; ++l)
+            if (!(mu[l] >= 0.0) || std::isinf(mu[l])) {
+                g_last_error = "shifts must be finite and >= 0";
+                return SPAMM_ERR_ARG;
+            }
+        return invsqrt_product_impl(S, n, levels, mu, tau0, tau1, maxit, Z, iters, o);
     } catch (...) {
         g_last_error = "internal exception";
         return SPAMM_ERR_CUDA;

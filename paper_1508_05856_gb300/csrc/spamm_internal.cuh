@@ -109,6 +109,10 @@ void emu_kernel_attributes();
 // c = max_i sum_j |s_ij + mu delta_ij|; mu read from *mu_dev (may be null = 0).
 void launch_gershgorin(const double* S, int n, const double* mu_dev, double* rowsum, double* out_c,
                        cudaStream_t st);
+// Row-major D = S + (mu_rel * *c0) I.
+void launch_shift_copy(const double* S, double* D, int n, double mu_rel, const double* c0, cudaStream_t st);
+// Row-major T = A^T (n x n).
+void launch_transpose_rm(const double* A, double* T, int n, cudaStream_t st);
 // *mu_out = mu_rel * (*c0)
 void launch_scale_mu(const double* c0, double mu_rel, double* mu_out, cudaStream_t st);
 // Row-major src -> tile-major dst with leaf norms.  When scale_c != null:

@@ -104,3 +104,17 @@ def test_autotune_rejects_bad_arguments_without_device():
     assert L.spamm_autotune_leaf(None, 4, 1e-6, None, ctypes.byref(leaf)) == -1
     assert L.spamm_autotune_leaf(buf, 4, 1e-6, None, None) == -1
     assert leaf.value == -1
+
+
+def test_product_representation_rejects_bad_arguments_without_device():
+    L = sp.lib()
+    o = sp.Opts()
+    L.spamm_opts_init(ctypes.byref(o))
+    buf = (ctypes.c_double * 16)()
+    mu = (ctypes.c_double * 2)(0.1, 0.01)
+    its = (ctypes.c_int * 2)()
+    assert L.spamm_invsqrt_product(buf, 4, 0, mu, 1e-3, 1e-5, 10, buf, its, ctypes.byref(o)) == -1
+    assert L.spamm_invsqrt_product(buf, 4, 2, mu, 1e-3, -1.0, 10, buf, its, ctypes.byref(o)) == -1
+    bad = (ctypes.c_double * 2)(0.1, float("nan"))
+    assert L.spamm_invsqrt_product(buf, 4, 2, bad, 1e-3, 1e-5, 10, buf, its, ctypes.byref(o)) == -1
+    assert L.spamm_invsqrt_product(None, 4, 2, mu, 1e-3, 1e-5, 10, buf, its, ctypes.byref(o)) == -1

@@ -169,3 +169,13 @@ def test_emu_lens_profile_counts():
     assert h.shape == (10, 3, 3, 8)
     assert (h.sum(axis=3) == st["task_hist"][:, :, None]).all()
     assert h[0, 1, 0, 0] == st["task_hist"][0][1] and h[0, 1, 0, 1:].sum() == 0
+
+
+def test_emu_product_representation_matches_oracle():
+    S = synth.gaussian_lattice(256, 0.8, seed=9)
+    mus = [0.05, 0.0005]
+    Z, info = sp.invsqrt_product(dev(S), mus, 1e-8, 1e-10, 25, leaf=64, precision=sp.EMU64)
+    ref = oracle.invsqrt_product(S, 64, mus, 1e-8, 1e-10, 25)
+    assert info["iters"] == list(ref["iters"])
+    Z = Z.cpu().numpy()
+    assert np.linalg.norm(Z - ref["Z"]) <= 1e-8 * np.linalg.norm(ref["Z"])

@@ -338,3 +338,31 @@ def test_lens_profile_matches_oracle(channel, tol):
     # the profile changes the results in no way
     Y0, Z0, _ = sp.sqrt_invsqrt(dev(S), 1e-6, 16, leaf=32, channel=channel, tol_t=tol)
     assert torch.equal(Y, Y0) and torch.equal(Z, Z0)
+
+
+# ------------------------------------------------------------------------------------------ product representation
+
+
+def test_product_representation_matches_oracle():
+    """Sec. 6 product representation on an ill-conditioned Gaussian decay (sigma 0.9): three slices at
+    tau0 = 1e-3 with residual products at tau1 = 1e-5, against the oracle's."""
+    S = synth.gaussian_lattice(200, 0.9, seed=7)
+    mus = [0.1, 0.01, 0.001]
+    Z, info = sp.invsqrt_product(dev(S), mus, 1e-3, 1e-5, 30, leaf=32)
+    ref = oracle.invsqrt_product(S, 32, mus, 1e-3, 1e-5, 30)
+    assert info["iters"] == list(ref["iters"])
+    Z = host(Z)
+    assert np.linalg.norm(Z - ref["Z"]) <= 1e-9 * np.linalg.norm(ref["Z"])
+    # host pointers give the same factor
+    Zh, _ = sp.invsqrt_product(S, mus, 1e-3, 1e-5, 30, leaf=32)
+    np.testing.assert_array_equal(Zh, Z)
+
+
+def test_product_representation_telescopes_at_tau0():
+    S = synth.gaussian_lattice(150, 0.9, seed=8)
+    lam, Q = np.linalg.eigh(S)
+    c0 = np.abs(S).sum(1).max()
+    Z, _ = sp.invsqrt_product(dev(S), [0.1, 0.01, 0.0], 0.0, 0.0, 60, leaf=64)
+    Zw = (Q / np.sqrt(lam)) @ Q.T
+    assert np.linalg.norm(host(Z) - Zw) <= 1e-10 * np.linalg.norm(Zw)
+    assert c0 > 0
