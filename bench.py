@@ -670,13 +670,21 @@ def run_product_rep(args, local):
         M = Z.T @ Smu @ Z
         return float(torch.linalg.norm(M - torch.eye(n, dtype=torch.float64, device=dev)))
 
+    def kappa(M):
+        ev = torch.linalg.eigvalsh(0.5 * (M + M.T))
+        return float(ev.max() / ev.min()) if float(ev.min()) > 0 else float("inf")
+
+    kappa_s = kappa(Smu)
+
     kw = dict(leaf=LEAF, precision=prec, map=MAP, channel=CHANNEL, tol_t=TOL, raise_on=False)
     _, info = sp.invsqrt_product(Sd, mus, tau0, tau1, MAXIT, Z=Zd, **kw)
     r_prod = resid(Zd)
+    k_prod = kappa(Zd.T @ Smu @ Zd)
     ts = timed(lambda: sp.invsqrt_product(Sd, mus, tau0, tau1, MAXIT, Z=Zd, **kw), args.steps)
     # one regularised solve to the last shift at the products' threshold, for comparison
     _, _, st1 = sp.sqrt_invsqrt(Sd, tau1, MAXIT, Y=Yd, Z=Zd, mu_rel=mus[-1], **kw)
     r_one = resid(Zd)
+    k_one = kappa(Zd.T @ Smu @ Zd)
     t1 = timed(lambda: sp.sqrt_invsqrt(Sd, tau1, MAXIT, Y=Yd, Z=Zd, mu_rel=mus[-1], **kw), args.steps)
     line = {"metric": f"product representation of (S + mu I)^-1/2 per second (3D Gaussian N={n})",
             "value": len(ts) / sum(ts), "unit": "factors/s", "n_gpus": 1, "higher_is_better": True,
@@ -686,9 +694,9 @@ def run_product_rep(args, local):
                                    f"bound, residual products at tau1={tau1:g}, {MAXIT} iterations per slice",
                        "precision": args.precision, "levels": len(mus)},
             "ms_per_factor": 1e3 * sum(ts) / len(ts), "slice_iters": info["iters"], "status": info["status"],
-            "resid_F": r_prod,
+            "resid_F": r_prod, "kappa_S_mu": kappa_s, "kappa_ZtSZ": k_prod,
             "single_solve": {"value": len(t1) / sum(t1), "unit": "solves/s", "tau": tau1, "mu_rel": mus[-1],
-                             "resid_F": r_one, "iters": st1["iters"], "status": st1["status"]}}
+                             "resid_F": r_one, "kappa_ZtSZ": k_one, "iters": st1["iters"], "status": st1["status"]}}
     print(json.dumps(line), flush=True)
     return 0
 
