@@ -366,3 +366,31 @@ def test_product_representation_telescopes_at_tau0():
     Zw = (Q / np.sqrt(lam)) @ Q.T
     assert np.linalg.norm(host(Z) - Zw) <= 1e-10 * np.linalg.norm(Zw)
     assert c0 > 0
+
+
+# ------------------------------------------------------------------------------------------ edge cases of the options
+
+
+@pytest.mark.parametrize("n", [1, 2, 33])
+def test_options_on_tiny_and_ragged_sizes(n):
+    """Single channel, damped map and product representation at n = 1, 2 and a ragged 33 (one partial leaf)."""
+    S = synth.kms(n, 0.7) if n > 1 else np.array([[2.5]])
+    for kw in (dict(channel=sp.CHANNEL_SINGLE), dict(map=sp.MAP_SCALED), dict(channel=sp.CHANNEL_SINGLE,
+                                                                             map=sp.MAP_SCALED)):
+        _ns_compare(S, 32, 1e-9, 15, **kw)
+    Z, info = sp.invsqrt_product(dev(S), [0.1, 0.0], 1e-9, 1e-12, 30, leaf=32)
+    ref = oracle.invsqrt_product(S, 32, [0.1, 0.0], 1e-9, 1e-12, 30)
+    assert np.linalg.norm(host(Z) - ref["Z"]) <= 1e-10 * np.linalg.norm(ref["Z"])
+
+
+def test_one_level_product_representation_is_the_regularised_solve():
+    S = synth.gaussian_lattice(150, 0.8, seed=11)
+    Z1, info = sp.invsqrt_product(dev(S), [0.01], 1e-7, 1e-9, 20, leaf=32)
+    _, Z2, st = sp.sqrt_invsqrt(dev(S), 1e-7, 20, leaf=32, mu_rel=0.01)
+    assert torch.equal(Z1, Z2) and info["iters"] == [st["iters"]]
+
+
+def test_lens_single_bin_counts_every_task():
+    S = synth.gaussian_lattice(128, 0.6, seed=12)
+    _, _, st = sp.sqrt_invsqrt(dev(S), 1e-6, 6, leaf=32, lens_bins=1)
+    assert (st["lens_hist"][:, :, :, 0] == st["task_hist"][:, :, None]).all()
