@@ -294,6 +294,7 @@ def run_gpu(args, ws, rank, local):
     gemm_ms = 0.0
     gemm_launches = 0
     gemm_flops = 0.0
+    tensor_units = 0
     for _ in range(args.steps):
         flush.zero_()                       # L2 (129 MB) flushed between timed solves
         e0 = torch.cuda.Event(enable_timing=True)
@@ -320,6 +321,7 @@ def run_gpu(args, ws, rank, local):
         gemm_ms += st["gemm_ms"]
         gemm_launches += st["gemm_launches"]
         gemm_flops += st["flops"]
+        tensor_units += st["tensor_units"]
     tot = sum(step_s)
     tot_max = max_over_ranks(tot, ws, dev)
     value = job_rate(ws, args.steps, tot_max)
@@ -418,13 +420,17 @@ def run_gpu(args, ws, rank, local):
         peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
         peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
         peak = peaks.get("bf16_tflops", 1900.0)
-        # 12 stacked M=128 x N=64 slice pairs over K = 64 per task: 2*128*64*64*12 flop on the FP16 tensor pipe
-        issued = achieved * (2.0 * 128 * 64 * 64 * 12) / (2.0 * LEAF ** 3)
+        # the FP16 tensor work the kernel issued, as it counts it: (stack, slice) units of 2*128*64*64 flop,
+        # 12 per task
+        per_launch = tensor_units * (2.0 * 128 * 64 * 64) / max(1, gemm_launches)
+        issued = per_launch / (avg_ms / 1e3) / 1e12 if avg_ms > 0 else 0.0
         tasks_per_launch = gemm_flops / max(1, gemm_launches) / (2.0 * LEAF ** 3)
         roof = {"bound": "tensor", "achieved": issued, "peak": peak, "unit": "TFLOP/s",
                 "frac": issued / peak if peak else None,
                 "traffic": captured_traffic("k_gemm_emu", tasks_per_launch), "kernel": "spamm::emu::k_gemm_emu",
-                "achieved_counts": "FP16 tensor-pipe flops issued (24x the FP64-equivalent useful flops)",
+                "achieved_counts": "FP16 tensor-pipe flops issued (counted by the kernel: 2*128*64*64 per (stack, "
+                                   "slice) unit, 12 units per task: 24x the FP64-equivalent useful flops)",
+                "units_per_task": tensor_units / max(1.0, tasks_per_launch * gemm_launches),
                 "useful_fp64_equiv_tflops": achieved,
                 "peak_source": ("bf16_tflops of measured x 1.0 (FP16 and BF16 dense rates are equal)" if peaks
                                 else "fallback 1.9 PFLOP/s"),

@@ -131,6 +131,10 @@ typedef struct spamm_stats {
                                   2 |i - k|; the last bin takes every d >=
                                   lens_bins - 1.  Filled for the iterations run */
     int lens_bins;             /* in: bins per plane, 1 .. 4096 (with lens_hist) */
+    long long tensor_units;    /* SPAMM_EMU64: tensor-core work issued, counted
+                                  by the leaf-product kernel in units of one
+                                  128 x 64 x 64 FP16 product (2*128*64*64
+                                  flops): 12 per leaf product                   */
 } spamm_stats;
 
 /* Fill *opts with defaults: leaf 64, SPAMM_FP64, tau_s = 0.01 tau, no shift,

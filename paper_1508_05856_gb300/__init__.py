@@ -67,7 +67,8 @@ class Stats(ctypes.Structure):
                 ("tasks_dense", ctypes.c_longlong), ("flops", ctypes.c_double),
                 ("t_hist", ctypes.POINTER(ctypes.c_double)), ("task_hist", ctypes.POINTER(ctypes.c_longlong)),
                 ("gemm_ms", ctypes.c_double), ("gemm_launches", ctypes.c_longlong),
-                ("lens_hist", ctypes.POINTER(ctypes.c_longlong)), ("lens_bins", ctypes.c_int)]
+                ("lens_hist", ctypes.POINTER(ctypes.c_longlong)), ("lens_bins", ctypes.c_int),
+                ("tensor_units", ctypes.c_longlong)]
 
 
 _lock = threading.Lock()
@@ -212,7 +213,7 @@ def _opts(leaf=64, precision=FP64, tau_s=None, mu_rel=0.0, tol_t=0.0, order=ORDE
 def _stats_dict(s: Stats, th=None, kh=None) -> dict:
     d = {"iters": s.iters, "t_final": s.t_final, "resid_F": s.resid_F, "scale_c": s.scale_c,
          "tasks_total": s.tasks_total, "tasks_dense": s.tasks_dense, "flops": s.flops, "gemm_ms": s.gemm_ms,
-         "gemm_launches": s.gemm_launches}
+         "gemm_launches": s.gemm_launches, "tensor_units": s.tensor_units}
     if th is not None:
         d["t_hist"] = th[:s.iters].copy()
     if kh is not None:

@@ -304,6 +304,7 @@ struct EmuArgs {
     double tau;
     const unsigned long long* rmaxA;    // row maxima of the left operand
     const unsigned long long* cmaxB;    // column maxima of the right operand
+    unsigned long long* units;          // (stack, slice) units issued, summed over the launch (may be null)
     double* C;                          // FP64 output tiles
     double* leafC;                      // output leaf norms (squared Frobenius, double-word FP32 sums)
     int* slice_list;                    // copy of the drawn tiles ([m*m] ids, count at [m*m]) for slicing
@@ -590,6 +591,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
             constexpr uint32_t idesc256 = ptx::idesc_f16_f32(128, 256);
             constexpr uint32_t idesc128 = ptx::idesc_f16_f32(128, 128);
             long long H = 0, C = 0;
+            unsigned long long units = 0;
             int tau = 0;
             bool ok = true;
             for (; ok; ++tau) {
@@ -602,6 +604,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
                 const int T = ntask_sh[slot];
                 for (int t = 0; t < T && ok; ++t) {
                     const bool chunk_start = (t % kChunk) == 0;
+                    units += 12;  // twelve stacked (stack, slice) products per task
                     for (int h = 0; h < 2; ++h, ++H) {
                         const int s = (int)(H % NSTAGE);
                         if (!wait_or_abort(&bar_full[s], (uint32_t)((H / NSTAGE) & 1), abort_flag)) {
@@ -641,6 +644,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
                     }
                 }
             }
+            if (a.units && units) atomicAdd(a.units, units);
         }
         __syncwarp();
     } else {
@@ -794,7 +798,8 @@ void launch_slice(const double* X, const double* leaf, double* leaf_out, const u
 
 void launch_gemm_emu(const Geometry& g, const TileMat& A, const TileMat& B, const TileMat& C, const int* counts,
                      const int* jlist, const int* tile_list, const int* tile_count, EpiMode mode, double* trace_part,
-                     int* sched, const int* done, int* err, double tau, cudaStream_t st, int buckets) {
+                     int* sched, const int* done, int* err, double tau, cudaStream_t st, int buckets,
+                     unsigned long long* units) {
     emu::EmuArgs a;
     a.sliceA = A.sliceA;
     a.sliceB = B.sliceB;
@@ -805,6 +810,7 @@ void launch_gemm_emu(const Geometry& g, const TileMat& A, const TileMat& B, cons
     a.tau = tau;
     a.rmaxA = A.rmax;
     a.cmaxB = B.cmax;
+    a.units = units;
     a.C = C.t;
     a.leafC = C.tree;
     a.slice_list = C.slice_list;

@@ -110,7 +110,9 @@ struct GraphKey {
     }
 };
 
-// Scratch of one problem size on one device.
+// Scratch of one problem size on one device.  Device flags (ints): [0] stop, [1] iterations run, [2] error
+// of a bounded wait, [8..11] leaf-product tile tickets (two branches), [16..20] and [24..28] output-tile
+// bucket counts (two branches), [30..31] tensor-core units issued (64-bit).
 constexpr int kFlagInts = 32;
 
 struct Plan {
@@ -501,6 +503,9 @@ static double profiled_ms(Plan* p) {
     return ms;
 }
 
+// Tensor-core work issued by the call's leaf products (flags[30..31], cleared with the flags).
+static unsigned long long* tensor_units(Plan* p) { return reinterpret_cast<unsigned long long*>(p->flags + 30); }
+
 static bool slicing_pending(const Plan* p, const TileMat& M) {
     for (int q = 0; q < 6; ++q)
         if (p->buf[q].t == M.t) return (p->sliced_mask >> q) & 1u;
@@ -553,7 +558,7 @@ static void product(Plan* p, const TileMat& A, const TileMat& B, TileMat& C, dou
     }
     if (p->emu) {
         launch_gemm_emu(g, A, B, C, counts, jlist, tile_list, tile_count, mode, p->trace_part,
-                        p->flags + 8 + 2 * slot, p->flags, p->flags + 2, tau, st, kTileBuckets);
+                        p->flags + 8 + 2 * slot, p->flags, p->flags + 2, tau, st, kTileBuckets, tensor_units(p));
     } else {
         launch_gemm_f64(g, A.t, B.t, C.t, A.tree, B.tree, C.tree, counts, jlist, tile_list, tile_count, 0,
                         mode, p->trace_part, p->flags, st, kTileBuckets);
@@ -632,9 +637,9 @@ static int multiply_core(const double* A, const double* B, double* C, int n, dou
     CK(cudaGetLastError());
     if ((e = stage_out(p, 2, C, dC, st))) return e;
     unsigned long long tasks = 0;
-    int flags_h[4] = {0, 0, 0, 0};
+    int flags_h[kFlagInts] = {};
     CK(cudaMemcpyAsync(&tasks, p->task_ctr, sizeof(tasks), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(flags_h, p->flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(flags_h, p->flags, kFlagInts * sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (flags_h[2]) {
         g_last_error = "a bounded device-side wait of the tensor-core kernel expired";
@@ -650,6 +655,9 @@ static int multiply_core(const double* A, const double* B, double* C, int n, dou
         stats->flops = 2.0 * (double)g.nb * g.nb * g.nb * (double)tasks;
         stats->gemm_ms = p->profile ? profiled_ms(p) : 0.0;
         stats->gemm_launches = p->gemm_launches;
+        unsigned long long units = 0;
+        std::memcpy(&units, flags_h + 30, sizeof(units));
+        stats->tensor_units = (long long)units;
     }
     return SPAMM_OK;
 }
@@ -1102,14 +1110,14 @@ static int sqrt_impl(const double* S, int n, double tau, int maxit, double* Y, d
     std::vector<double> th((size_t)(it_host > 0 ? it_host : 1), 0.0);
     std::vector<unsigned long long> kc(3 * (size_t)(it_host > 0 ? it_host : 1), 0ull);
     double c_host = 0.0;
-    int flags_h[4] = {0, 0, 0, 0};
+    int flags_h[kFlagInts] = {};
     if (it_host > 0) {
         CK(cudaMemcpyAsync(th.data(), p->t_hist, it_host * sizeof(double), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(kc.data(), p->task_ctr, 3 * (size_t)it_host * sizeof(unsigned long long),
                            cudaMemcpyDeviceToHost, st));
     }
     CK(cudaMemcpyAsync(&c_host, c, sizeof(double), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(flags_h, p->flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(flags_h, p->flags, kFlagInts * sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (flags_h[2]) {
         g_last_error = "a bounded device-side wait of the tensor-core kernel expired";
@@ -1140,6 +1148,9 @@ static int sqrt_impl(const double* S, int n, double tau, int maxit, double* Y, d
         }
         stats->gemm_ms = p->profile ? profiled_ms(p) : 0.0;
         stats->gemm_launches = p->gemm_launches;
+        unsigned long long units = 0;
+        std::memcpy(&units, flags_h + 30, sizeof(units));
+        stats->tensor_units = (long long)units;
     }
     for (int q = 0; q < iters; ++q)
         if (!std::isfinite(th[q]) || std::fabs(th[q]) >= 1.0) {
