@@ -490,15 +490,16 @@ def run_batched(args, local):
     specs = synth.batch_mix(args.batch, lo=128, hi=2048, seed=0)
     Ss = [torch.from_numpy(synth.make(sp_)).to(dev) for sp_ in specs]
     taus = [args.batch_tau] * len(Ss)
-    sp.sqrt_invsqrt_batched(Ss[:16], taus[:16], MAXIT, leaf=LEAF, precision=prec)   # warm-up
+    kw = dict(leaf=LEAF, precision=prec, map=MAP, tol_t=TOL, channel=CHANNEL)
+    sp.sqrt_invsqrt_batched(Ss[:16], taus[:16], MAXIT, raise_on=False, **kw)   # warm-up
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    Ys, Zs, sts = sp.sqrt_invsqrt_batched(Ss, taus, MAXIT, leaf=LEAF, precision=prec)
+    Ys, Zs, sts = sp.sqrt_invsqrt_batched(Ss, taus, MAXIT, raise_on=False, **kw)
     torch.cuda.synchronize()
     t_batch = time.perf_counter() - t0
     t0 = time.perf_counter()
     for S, t in zip(Ss, taus):
-        sp.sqrt_invsqrt(S, t, MAXIT, leaf=LEAF, precision=prec, map=MAP, tol_t=TOL, channel=CHANNEL)
+        sp.sqrt_invsqrt(S, t, MAXIT, raise_on=False, **kw)
     torch.cuda.synchronize()
     t_seq = time.perf_counter() - t0
     line = {"metric": "batched NS solves/s (mixed KMS / 3D Gaussian, N in [128, 2048])", "value": len(Ss) / t_batch,
@@ -506,9 +507,13 @@ def run_batched(args, local):
             "data": "synthetic",
             "config": {"workload": f"{len(Ss)} matrices, sizes log-uniform in [128, 2048] (multiples of 32), "
                                    f"50% KMS rho~U(0.5,0.95), 50% Gaussian sigma~U(0.6,0.9), tau={args.batch_tau:g}, "
-                                   f"{MAXIT} iterations", "precision": args.precision, "map": args.map},
+                                   + (f"{MAXIT} iterations" if TOL <= 0
+                                      else f"until |t_k| <= {TOL:g} (at most {MAXIT})"),
+                       "precision": args.precision, "map": args.map, "channel": args.channel},
             "one_call_per_matrix": {"value": len(Ss) / t_seq, "unit": UNIT},
-            "tasks": int(sum(st["tasks_total"] for st in sts))}
+            "tasks": int(sum(st["tasks_total"] for st in sts)),
+            "iters_mean": float(sum(st["iters"] for st in sts)) / max(1, len(sts)),
+            "call_status": sts[0]["call_status"]}
     print(json.dumps(line), flush=True)
     return 0
 

@@ -299,8 +299,10 @@ def sqrt_invsqrt(S, tau: float, maxit: int, leaf: int = 64, precision: int = FP6
 
 
 def sqrt_invsqrt_batched(Ss, taus, maxit: int, leaf: int = 64, precision: int = FP64, tau_s=None, mu_rel=0.0,
-                         tol_t=0.0, order=ORDER_PAPER, residual=False, stream=None, map=None, channel=None):
-    """Many independent solves in one call; returns (list of Y, list of Z, list of stats)."""
+                         tol_t=0.0, order=ORDER_PAPER, residual=False, stream=None, map=None, channel=None,
+                         raise_on=True):
+    """Many independent solves in one call; returns (list of Y, list of Z, list of stats).  With raise_on
+    False a failed status (the first nonzero one) is returned in every stats dict as "call_status"."""
     cnt = len(Ss)
     keep = [_prep(S) for S in Ss]
     Ys = [_like(k[0], k[2]) for k in keep]
@@ -314,8 +316,13 @@ def sqrt_invsqrt_batched(Ss, taus, maxit: int, leaf: int = 64, precision: int = 
     stats = (Stats * cnt)()
     o = _opts(leaf, precision, tau_s, mu_rel, tol_t, order, residual, _stream_of(keep[0][0], stream) if cnt else None,
               map=MAP_NS if map is None else map, channel=CHANNEL_DUAL if channel is None else channel)
-    _check(lib().spamm_sqrt_invsqrt_batched(cnt, sp, ns, ts, int(maxit), yp, zp, ctypes.byref(o), stats))
-    return Ys, Zs, [_stats_dict(stats[q]) for q in range(cnt)]
+    status = lib().spamm_sqrt_invsqrt_batched(cnt, sp, ns, ts, int(maxit), yp, zp, ctypes.byref(o), stats)
+    if raise_on:
+        _check(status)
+    out = [_stats_dict(stats[q]) for q in range(cnt)]
+    for d in out:
+        d["call_status"] = status
+    return Ys, Zs, out
 
 
 def norm_tree(A, leaf: int = 64, stream=None):
