@@ -224,15 +224,16 @@ def _stats_dict(s: Stats, th=None, kh=None) -> dict:
 # ---------------------------------------------------------------------------- public calls
 
 
-def multiply(A, B, tau: float, leaf: int = 64, precision: int = FP64, out=None, stream=None):
-    """C = A (x)_tau B (Eq. (newspamm)); returns (C, stats)."""
+def multiply(A, B, tau: float, leaf: int = 64, precision: int = FP64, out=None, stream=None, profile=False):
+    """C = A (x)_tau B (Eq. (newspamm)); returns (C, stats).  profile: time the leaf-product kernel with CUDA
+    events (stats["gemm_ms"])."""
     a, pa, n, _ = _prep(A)
     b, pb, nb_, _ = _prep(B)
     if nb_ != n:
         raise ValueError("A and B differ in size")
     C = out if out is not None else _like(a, n)
     st = Stats()
-    o = _opts(leaf=leaf, precision=precision, stream=_stream_of(a, stream))
+    o = _opts(leaf=leaf, precision=precision, stream=_stream_of(a, stream), profile=profile)
     _check(lib().spamm_multiply(pa, pb, _ptr(C), n, float(tau), ctypes.byref(o), ctypes.byref(st)))
     return C, _stats_dict(st)
 

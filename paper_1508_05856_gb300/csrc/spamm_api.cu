@@ -550,11 +550,16 @@ static void product(Plan* p, const TileMat& A, const TileMat& B, TileMat& C, dou
         if (B.sliced != A.sliced && slicing_pending(p, B)) cudaStreamWaitEvent(st, B.sliced, 0);
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
+    unsigned rec_flags = cudaEventRecordDefault;
     if (p->profile) {
         e0 = next_event(p);
         e1 = next_event(p);
-        // "external" records become event-record nodes when the solve is captured into a graph
-        if (e0 && e1) cudaEventRecordWithFlags(e0, st, cudaEventRecordExternal);
+        // "external" records become event-record nodes when the solve is captured into a graph; an
+        // uncaptured call (a single product) records plainly
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+            rec_flags = cudaEventRecordExternal;
+        if (e0 && e1) cudaEventRecordWithFlags(e0, st, rec_flags);
     }
     if (p->emu) {
         launch_gemm_emu(g, A, B, C, counts, jlist, tile_list, tile_count, mode, p->trace_part,
@@ -563,7 +568,7 @@ static void product(Plan* p, const TileMat& A, const TileMat& B, TileMat& C, dou
         launch_gemm_f64(g, A.t, B.t, C.t, A.tree, B.tree, C.tree, counts, jlist, tile_list, tile_count, 0,
                         mode, p->trace_part, p->flags, st, kTileBuckets);
     }
-    if (e0 && e1) cudaEventRecordWithFlags(e1, st, cudaEventRecordExternal);
+    if (e0 && e1) cudaEventRecordWithFlags(e1, st, rec_flags);
     p->gemm_launches++;
     // X's map whose coefficients need the finished tr X: in place, with T's leaf norms (and maxima)
     if (mode == EPI_X) launch_map(C.t, C.tree, C, g, map, p->trace_part, p->emu, p->flags, st);

@@ -394,3 +394,16 @@ def test_lens_single_bin_counts_every_task():
     S = synth.gaussian_lattice(128, 0.6, seed=12)
     _, _, st = sp.sqrt_invsqrt(dev(S), 1e-6, 6, leaf=32, lens_bins=1)
     assert (st["lens_hist"][:, :, :, 0] == st["task_hist"][:, :, None]).all()
+
+
+@pytest.mark.parametrize("precision", [sp.FP64, sp.EMU64])
+def test_profiled_single_product(precision):
+    """opts.profile on an uncaptured call (one product): the leaf-product kernel is timed, the result is the
+    unprofiled one."""
+    A = synth.decay_matrix(512, seed=3, length=20.0)
+    C0, _ = sp.multiply(dev(A), dev(A), 1e-10, leaf=64, precision=precision)
+    C1, st = sp.multiply(dev(A), dev(A), 1e-10, leaf=64, precision=precision, profile=True)
+    assert torch.equal(C0, C1)
+    assert st["gemm_ms"] > 0 and st["gemm_launches"] == 1
+    if precision == sp.EMU64:
+        assert st["tensor_units"] == 12 * st["tasks_total"]
