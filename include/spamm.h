@@ -19,8 +19,9 @@
  *   - Matrices are dense, row-major, n x n, double precision.
  *   - A matrix pointer may address host memory or device memory of the
  *     current CUDA device; the library tells them apart with
- *     cudaPointerGetAttributes and stages host data through its own device
- *     buffers.  The caller owns every pointer it passes; inputs are not
+ *     cudaPointerGetAttributes.  Page-locked host memory is read and written
+ *     in place by the kernels (through its device mapping); pageable host
+ *     data is staged through the library's own device buffers.  The caller owns every pointer it passes; inputs are not
  *     modified; the call returns after the results are written.
  *   - The library owns its scratch space (tile buffers, norm trees, task
  *     lists), cached per problem size and released by spamm_release().

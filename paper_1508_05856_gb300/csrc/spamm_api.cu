@@ -83,15 +83,20 @@ static void set_error(const char* what, cudaError_t e) {
         }                                                      \
     } while (0)
 
-static bool is_device_ptr(const void* p) {
-    if (!p) return false;
+// The address kernels use for a caller matrix they can read and write in place: device or managed memory
+// as it is, and page-locked host memory through its device mapping (on this part the GPU reaches host
+// memory over NVLink-C2C, so the pack and unpack kernels move the data themselves, with no staging copy).
+// Null for pageable host memory, which is staged.
+static void* kernel_view(const void* p) {
+    if (!p) return nullptr;
     cudaPointerAttributes a;
-    cudaError_t e = cudaPointerGetAttributes(&a, p);
-    if (e != cudaSuccess) {
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return nullptr;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return const_cast<void*>(p);
+    if (a.type == cudaMemoryTypeHost && a.devicePointer) return a.devicePointer;
+    return nullptr;
 }
 
 // ----------------------------------------------------------------------------
@@ -443,10 +448,10 @@ static spamm_opts resolve_opts(const spamm_opts* o) {
     return r;  // leaf 0 stays 0: the call resolves it with the autotuner
 }
 
-// Device view of a caller matrix: the pointer itself, or a staged copy.
+// Device view of a caller matrix: the pointer itself (or its device mapping), or a staged copy.
 static int stage_in(Plan* p, int which, const double* src, cudaStream_t st, const double** dev) {
-    if (is_device_ptr(src)) {
-        *dev = src;
+    if (void* v = kernel_view(src)) {
+        *dev = static_cast<const double*>(v);
         return SPAMM_OK;
     }
     int e = ensure_stage(p, which);
@@ -457,8 +462,8 @@ static int stage_in(Plan* p, int which, const double* src, cudaStream_t st, cons
 }
 
 static int out_target(Plan* p, int which, double* dst, double** dev) {
-    if (is_device_ptr(dst)) {
-        *dev = dst;
+    if (void* v = kernel_view(dst)) {
+        *dev = static_cast<double*>(v);
         return SPAMM_OK;
     }
     int e = ensure_stage(p, which);
@@ -467,10 +472,11 @@ static int out_target(Plan* p, int which, double* dst, double** dev) {
     return SPAMM_OK;
 }
 
+// Copies a staged result out; a result the kernels wrote in place (device memory or the mapping of a
+// page-locked host buffer) needs nothing.
 static int stage_out(Plan* p, int which, double* dst, const double* dev, cudaStream_t st) {
-    if (dev == dst) return SPAMM_OK;
+    if (dev != p->stage[which]) return SPAMM_OK;
     CK(cudaMemcpyAsync(dst, dev, (size_t)p->g.n * p->g.n * sizeof(double), cudaMemcpyDeviceToHost, st));
-    (void)which;
     return SPAMM_OK;
 }
 
@@ -1252,8 +1258,8 @@ static int invsqrt_product_impl(const double* S, int n, int levels, const double
     CKA(cs.get(&dT, bytes));
     CKA(cs.get(&rowsum, (size_t)n * sizeof(double)));
     CKA(cs.get(&c0, sizeof(double)));
-    const double* dS = S;
-    if (!is_device_ptr(S)) {
+    const double* dS = static_cast<const double*>(kernel_view(S));
+    if (!dS) {
         double* st_S;
         CKA(cs.get(&st_S, bytes));
         CK(cudaMemcpyAsync(st_S, S, bytes, cudaMemcpyHostToDevice, st));
