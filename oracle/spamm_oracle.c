@@ -440,11 +440,13 @@ int or_ns(const double* S, int n, int nb, double tau, double tau_s, double mu_re
     double mu = 0.0;
     if (mu_rel > 0.0) mu = mu_rel * or_gershgorin(S, n, 0.0);
     double c = or_gershgorin(S, n, mu);
+    /* s <- s / c (Sec. 3.1, rescaling into (0, 1]), applied as a product with the once-rounded 1/c */
+    const double rc = 1.0 / c;
     for (int i = 0; i < n; ++i)
         for (int j = 0; j < n; ++j) {
             double v = S[(long)i * n + j];
             if (i == j) v += mu;
-            Y[(long)i * n + j] = v / c;
+            Y[(long)i * n + j] = v * rc;
             Z[(long)i * n + j] = (i == j) ? 1.0 : 0.0;
         }
     memcpy(X, Y, sizeof(double) * nn);
@@ -510,8 +512,9 @@ int or_ns(const double* S, int n, int nb, double tau, double tau_s, double mu_re
         if (tol_t > 0.0 && fabs(tk) <= tol_t) break;
     }
     /* single channel with no iteration: Y = s Z0 = s, already in Y */
-    double sc = sqrt(c);
-    for (size_t q = 0; q < nn; ++q) { Y[q] = Y[q] * sc; Z[q] = Z[q] / sc; }
+    /* undo the scaling: Y sqrt(c), Z / sqrt(c), the latter as a product with the once-rounded 1/sqrt(c) */
+    const double sc = sqrt(c), rsc = 1.0 / sc;
+    for (size_t q = 0; q < nn; ++q) { Y[q] = Y[q] * sc; Z[q] = Z[q] * rsc; }
     if (scale_c) *scale_c = c;
 #undef OR_LENS
     free(X); free(T); free(W); free(s1); free(Zt); free(tl);

@@ -270,26 +270,41 @@ __device__ __forceinline__ DFloat df_shfl_xor(DFloat x, int o) {
     return DFloat{__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o)};
 }
 
-// Row and column magnitude maxima (as IEEE bits) of a packed FP64 matrix.
+// Row and column magnitude maxima of a packed FP64 matrix, kept as the upper 32 bits of the IEEE pattern
+// (sign cleared), which carry the exponent exactly: the maxima feed only the slicing exponents.  Warp w
+// takes rows 8w .. 8w+7 of a 64 x 64 tile and lane l the columns l and l + 32, sixteen independent loads
+// per thread; rows reduce across the warp, columns across the eight warps in shared memory.
 __global__ void __launch_bounds__(256) k_rowcol_max(const double* __restrict__ X, int m,
                                                     unsigned long long* __restrict__ rmax,
                                                     unsigned long long* __restrict__ cmax) {
-    __shared__ unsigned long long xs[NB][NB + 1];
+    __shared__ unsigned cm_sh[8][NB];
     const int tile = blockIdx.x;
     const int i = tile / m, j = tile - (tile / m) * m;
-    const double* x = X + (size_t)tile * NB * NB;
-    for (int idx = threadIdx.x; idx < NB * NB; idx += 256)
-        xs[idx >> 6][idx & 63] = (unsigned long long)__double_as_longlong(fabs(x[idx]));
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned long long* x = reinterpret_cast<const unsigned long long*>(X + (size_t)tile * NB * NB);
+    unsigned long long a[8], b[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        a[q] = x[(8 * w + q) * NB + lane];
+        b[q] = x[(8 * w + q) * NB + 32 + lane];
+    }
+    unsigned ca = 0, cb = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const unsigned ha = (unsigned)(a[q] >> 32) & 0x7FFFFFFFu, hb = (unsigned)(b[q] >> 32) & 0x7FFFFFFFu;
+        ca = max(ca, ha);
+        cb = max(cb, hb);
+        const unsigned rm = __reduce_max_sync(0xffffffffu, max(ha, hb));
+        if (lane == 0 && rm) atomicMax(rmax + i * NB + 8 * w + q, (unsigned long long)rm << 32);
+    }
+    cm_sh[w][lane] = ca;
+    cm_sh[w][lane + 32] = cb;
     __syncthreads();
     if (threadIdx.x < NB) {
-        unsigned long long mx = 0;
-        for (int c = 0; c < NB; ++c) mx = max(mx, xs[threadIdx.x][c]);
-        if (mx) atomicMax(rmax + i * NB + threadIdx.x, mx);
-    } else if (threadIdx.x < 2 * NB) {
-        const int c = threadIdx.x - NB;
-        unsigned long long mx = 0;
-        for (int r = 0; r < NB; ++r) mx = max(mx, xs[r][c]);
-        if (mx) atomicMax(cmax + j * NB + c, mx);
+        unsigned mx = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) mx = max(mx, cm_sh[q][threadIdx.x]);
+        if (mx) atomicMax(cmax + j * NB + threadIdx.x, (unsigned long long)mx << 32);
     }
 }
 

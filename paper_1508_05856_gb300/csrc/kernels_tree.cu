@@ -71,6 +71,23 @@ __global__ void k_rowsum(const double* __restrict__ S, int n, const double* __re
     // four independent partial sums per lane (FP64 latency is long), fixed order
     double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
     int j = lane;
+    // two of the 128-wide steps below at a time (eight loads in flight), the same additions in the same order
+    for (; j + 224 < n; j += 256) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            v[u] = r[j + 32 * u];
+            if (j + 32 * u == row) v[u] += mu;
+        }
+        p0 += fabs(v[0]);
+        p1 += fabs(v[1]);
+        p2 += fabs(v[2]);
+        p3 += fabs(v[3]);
+        p0 += fabs(v[4]);
+        p1 += fabs(v[5]);
+        p2 += fabs(v[6]);
+        p3 += fabs(v[7]);
+    }
     for (; j + 96 < n; j += 128) {
         double v0 = r[j], v1 = r[j + 32], v2 = r[j + 64], v3 = r[j + 96];
         if (j == row) v0 += mu;
@@ -165,47 +182,77 @@ void launch_scale_mu(const double* c0, double mu_rel, double* mu_out, cudaStream
     note_launch();
 }
 
-__global__ void k_sqrt_scalar(const double* c, double* out) { *out = sqrt(*c); }
 
-void launch_sqrt_scalar(const double* c, double* out, cudaStream_t st) {
-    k_sqrt_scalar<<<1, 1, 0, st>>>(c, out);
+// The scaling constants of a solve, once: sqrt(c) for Y, and the once-rounded reciprocals 1/c (for S) and
+// 1/sqrt(c) (for Z) that the scaling multiplies by.
+__global__ void k_scale_consts(const double* c, double* sqc, double* rc, double* rsqc) {
+    const double s = sqrt(*c);
+    *sqc = s;
+    *rc = 1.0 / *c;
+    *rsqc = 1.0 / s;
+}
+
+void launch_scale_consts(const double* c, double* sqc, double* rc, double* rsqc, cudaStream_t st) {
+    k_scale_consts<<<1, 1, 0, st>>>(c, sqc, rc, rsqc);
     note_launch();
 }
 
 // ---------------------------------------------------------------- pack + leaf norms
-__global__ void __launch_bounds__(256) k_pack(const double* __restrict__ src, int n, int m, int nb,
-                                              const double* __restrict__ mu_dev, const double* __restrict__ c_dev,
+// Entries of a tile handled per thread of a 256-thread block, and how many of them one batch of
+// independent loads covers.
+template <int NB>
+struct TileSplit {
+    static constexpr int kPer = NB * NB / 256;
+    static constexpr int kBatch = kPer < 8 ? kPer : 8;
+};
+
+// One 256-thread block per tile.  Thread t takes the entries t + 256 q (a warp reads 32 consecutive
+// entries of one row), eight independent loads at a time, then scales, stores and squares them in order.
+template <int NB>
+__global__ void __launch_bounds__(256) k_pack(const double* __restrict__ src, int n, int m,
+                                              const double* __restrict__ mu_dev, const double* __restrict__ rc_dev,
                                               double* __restrict__ dst, double* __restrict__ leaf) {
+    using TS = TileSplit<NB>;
     __shared__ double red[8];
     const int tile = blockIdx.x;
-    const int i = tile / m, j = tile % m;
-    const int ne = nb * nb;
+    const int i = tile / m, j = tile - (tile / m) * m;
     const double mu = mu_dev ? *mu_dev : 0.0;
-    const double c = c_dev ? *c_dev : 1.0;
-    const bool scaled = c_dev != nullptr;
-    double* d = dst + (size_t)tile * ne;
+    const double rc = rc_dev ? *rc_dev : 1.0;
+    const bool scaled = rc_dev != nullptr;
+    double* d = dst + (size_t)tile * NB * NB;
     double acc = 0.0;
-    for (int idx = threadIdx.x; idx < ne; idx += 256) {
-        const int r = idx / nb, cc = idx - r * nb;
-        const int gi = i * nb + r, gj = j * nb + cc;
-        double v = 0.0;
-        if (gi < n && gj < n) {
-            v = src[(size_t)gi * n + gj];
-            if (scaled) {
-                if (gi == gj) v += mu;
-                v = v / c;
-            }
+#pragma unroll 1
+    for (int q0 = 0; q0 < TS::kPer; q0 += TS::kBatch) {
+        double v[TS::kBatch];
+#pragma unroll
+        for (int u = 0; u < TS::kBatch; ++u) {
+            const int idx = threadIdx.x + 256 * (q0 + u);
+            const int gi = i * NB + idx / NB, gj = j * NB + idx % NB;
+            v[u] = (gi < n && gj < n) ? src[(size_t)gi * n + gj] : 0.0;
         }
-        d[idx] = v;
-        acc = fma(v, v, acc);
+#pragma unroll
+        for (int u = 0; u < TS::kBatch; ++u) {
+            const int idx = threadIdx.x + 256 * (q0 + u);
+            const int gi = i * NB + idx / NB, gj = j * NB + idx % NB;
+            double x = v[u];
+            if (scaled && gi < n && gj < n) {
+                if (gi == gj) x += mu;
+                x = x * rc;
+            }
+            d[idx] = x;
+            acc = fma(x, x, acc);
+        }
     }
     const double s = block_sum_256(acc, red);
     if (threadIdx.x == 0) leaf[tile] = s;
 }
 
-void launch_pack(const double* src, int n, const Geometry& g, const double* mu, const double* scale_c,
+void launch_pack(const double* src, int n, const Geometry& g, const double* mu, const double* recip_c,
                  TileMat dst, cudaStream_t st) {
-    k_pack<<<g.m * g.m, 256, 0, st>>>(src, n, g.m, g.nb, mu, scale_c, dst.t, dst.tree);
+    const dim3 grid(g.m * g.m), block(256);
+    if (g.nb == 32) k_pack<32><<<grid, block, 0, st>>>(src, n, g.m, mu, recip_c, dst.t, dst.tree);
+    else if (g.nb == 64) k_pack<64><<<grid, block, 0, st>>>(src, n, g.m, mu, recip_c, dst.t, dst.tree);
+    else k_pack<128><<<grid, block, 0, st>>>(src, n, g.m, mu, recip_c, dst.t, dst.tree);
     note_launch();
 }
 
@@ -244,8 +291,9 @@ void launch_trace_parts(const double* X, const Geometry& g, double* trace_part, 
 // both exact).  Grid-stride over tiles; a tile whose X is exactly zero (leaf
 // norm 0, data unwritten) off the diagonal stays zero.  Writes T's leaf
 // norms and, when rmax is set (64 x 64 tiles), T's row/column magnitude maxima.
+template <int NB>
 __global__ void __launch_bounds__(256, 4) k_map(const double* X, double* T, const double* leafX, double* leafT,
-                                                int n, int m, int nb, int map, const double* __restrict__ trace_part,
+                                                int n, int m, int map, const double* __restrict__ trace_part,
                                                 unsigned long long* __restrict__ rmax,
                                                 unsigned long long* __restrict__ cmax, const int* __restrict__ done) {
     grid_dependency_wait();
@@ -268,7 +316,8 @@ __global__ void __launch_bounds__(256, 4) k_map(const double* X, double* T, cons
     }
     __syncthreads();
     const double c0 = coef[0], c1 = coef[1];
-    const int ne = nb * nb;
+    using TS = TileSplit<NB>;
+    constexpr int ne = NB * NB;
     const int lane = threadIdx.x & 31;
     for (int tile = blockIdx.x; tile < m * m; tile += gridDim.x) {
         const int i = tile / m, j = tile - (tile / m) * m;
@@ -284,30 +333,39 @@ __global__ void __launch_bounds__(256, 4) k_map(const double* X, double* T, cons
         }
         double acc = 0.0;
         unsigned long long cmx = 0;
-        for (int idx = threadIdx.x; idx < ne; idx += 256) {
-            const int r = idx / nb, cc = idx - r * nb;
-            const int gi = i * nb + r, gj = j * nb + cc;
-            const double xv = x[idx];
+#pragma unroll 1
+        for (int q0 = 0; q0 < TS::kPer; q0 += TS::kBatch) {
+          // a batch of independent loads first (in place, each thread reads its entries before writing them)
+          double xb[TS::kBatch];
+#pragma unroll
+          for (int u = 0; u < TS::kBatch; ++u) xb[u] = x[threadIdx.x + 256 * (q0 + u)];
+#pragma unroll
+          for (int u = 0; u < TS::kBatch; ++u) {
+            const int idx = threadIdx.x + 256 * (q0 + u);
+            const int r = idx / NB, cc = idx % NB;
+            const int gi = i * NB + r, gj = j * NB + cc;
+            const double xv = xb[u];
             const double v = (gi == gj && gi < n) ? fma(c1, xv, c0) : c1 * xv;
             t[idx] = v;
             acc = fma(v, v, acc);
-            if (rmax) {
+            if (NB == 64 && rmax) {
                 // 64-wide tiles: this thread keeps column threadIdx.x & 63, and the row's 64 entries sit in
                 // two consecutive warps; the maxima feed only the slicing exponents, so the upper 32 bits
                 // (sign cleared) carry what is needed
                 const unsigned long long vb = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
                 cmx = max(cmx, vb);
                 const unsigned rm = __reduce_max_sync(0xffffffffu, (unsigned)(vb >> 32));
-                if (lane == 0 && rm) atomicMax(rmax + (size_t)i * nb + r, (unsigned long long)rm << 32);
+                if (lane == 0 && rm) atomicMax(rmax + (size_t)i * NB + r, (unsigned long long)rm << 32);
             }
+          }
         }
-        if (rmax) {
+        if (NB == 64 && rmax) {
             cm_sh[threadIdx.x >> 6][threadIdx.x & 63] = cmx;
             __syncthreads();
             if (threadIdx.x < 64) {
                 const unsigned long long mx =
                     max(max(cm_sh[0][threadIdx.x], cm_sh[1][threadIdx.x]), max(cm_sh[2][threadIdx.x], cm_sh[3][threadIdx.x]));
-                if (mx) atomicMax(cmax + (size_t)j * nb + threadIdx.x, mx);
+                if (mx) atomicMax(cmax + (size_t)j * NB + threadIdx.x, mx);
             }
         }
         const double s = block_sum_256(acc, red);
@@ -319,9 +377,17 @@ void launch_map(const double* X, const double* leafX, TileMat T, const Geometry&
                 bool maxima, const int* done, cudaStream_t st) {
     // one resident wave (four 256-thread blocks per SM), so a dependent launch never waits on a later wave
     const int grid = std::min(device_sm_count() * 4, g.m * g.m);
-    launch_dependent(k_map, dim3(grid), dim3(256), 0, st, X, T.t, leafX, T.tree, g.n, g.m, g.nb, map, trace_part,
-                     maxima ? T.rmax : (unsigned long long*)nullptr, maxima ? T.cmax : (unsigned long long*)nullptr,
-                     done);
+    unsigned long long* rmax = maxima ? T.rmax : nullptr;
+    unsigned long long* cmax = maxima ? T.cmax : nullptr;
+    if (g.nb == 32)
+        launch_dependent(k_map<32>, dim3(grid), dim3(256), 0, st, X, T.t, leafX, T.tree, g.n, g.m, map, trace_part,
+                         rmax, cmax, done);
+    else if (g.nb == 64)
+        launch_dependent(k_map<64>, dim3(grid), dim3(256), 0, st, X, T.t, leafX, T.tree, g.n, g.m, map, trace_part,
+                         rmax, cmax, done);
+    else
+        launch_dependent(k_map<128>, dim3(grid), dim3(256), 0, st, X, T.t, leafX, T.tree, g.n, g.m, map, trace_part,
+                         rmax, cmax, done);
     note_launch();
 }
 
@@ -619,39 +685,48 @@ void launch_cull(const Geometry& g, const double* treeA, const double* treeB, do
 }
 
 // ---------------------------------------------------------------- unpack
+// One 256-thread block per tile, entries t + 256 q per thread, eight independent loads at a time; an
+// all-zero tile (leaf norm 0) is written as zeros without reading it.
+template <int NB>
 __global__ void __launch_bounds__(256) k_unpack(const double* __restrict__ src, const double* __restrict__ leaf,
-                                                int n, int m, int nb, double* __restrict__ dst,
-                                                const double* __restrict__ mul, const double* __restrict__ div,
+                                                int n, int m, double* __restrict__ dst,
+                                                const double* __restrict__ scale_dev,
                                                 const double* __restrict__ src_alt, const double* __restrict__ leaf_alt,
                                                 const int* __restrict__ iters, int iters_src) {
+    using TS = TileSplit<NB>;
     const int tile = blockIdx.x;
-    const int i = tile / m, j = tile % m;
-    const int ne = nb * nb;
+    const int i = tile / m, j = tile - (tile / m) * m;
     if (iters && ((*iters - iters_src) & 1)) {
         src = src_alt;
         leaf = leaf_alt;
     }
-    const double* s = src + (size_t)tile * ne;
-    const double fm = mul ? *mul : 1.0;
-    const double fd = div ? *div : 1.0;
+    const double* s = src + (size_t)tile * NB * NB;
+    const double f = scale_dev ? *scale_dev : 1.0;
+    const bool scaled = scale_dev != nullptr;
     const bool zero = leaf && leaf[tile] == 0.0;
-    for (int idx = threadIdx.x; idx < ne; idx += 256) {
-        const int r = idx / nb, cc = idx - r * nb;
-        const int gi = i * nb + r, gj = j * nb + cc;
-        if (gi < n && gj < n) {
-            double v = zero ? 0.0 : s[idx];
-            if (mul) v = v * fm;
-            if (div) v = v / fd;
-            dst[(size_t)gi * n + gj] = v;
+#pragma unroll 1
+    for (int q0 = 0; q0 < TS::kPer; q0 += TS::kBatch) {
+        double v[TS::kBatch];
+#pragma unroll
+        for (int u = 0; u < TS::kBatch; ++u) v[u] = zero ? 0.0 : s[threadIdx.x + 256 * (q0 + u)];
+#pragma unroll
+        for (int u = 0; u < TS::kBatch; ++u) {
+            const int idx = threadIdx.x + 256 * (q0 + u);
+            const int gi = i * NB + idx / NB, gj = j * NB + idx % NB;
+            if (gi < n && gj < n) dst[(size_t)gi * n + gj] = scaled ? v[u] * f : v[u];
         }
     }
 }
 
-void launch_unpack(const double* src, const double* leaf, const Geometry& g, double* dst, const double* mul,
-                   const double* div, cudaStream_t st, const double* src_alt, const double* leaf_alt,
-                   const int* iters, int iters_src) {
-    k_unpack<<<g.m * g.m, 256, 0, st>>>(src, leaf, g.n, g.m, g.nb, dst, mul, div, src_alt, leaf_alt, iters,
-                                         iters_src);
+void launch_unpack(const double* src, const double* leaf, const Geometry& g, double* dst, const double* scale,
+                   cudaStream_t st, const double* src_alt, const double* leaf_alt, const int* iters, int iters_src) {
+    const dim3 grid(g.m * g.m), block(256);
+    if (g.nb == 32)
+        k_unpack<32><<<grid, block, 0, st>>>(src, leaf, g.n, g.m, dst, scale, src_alt, leaf_alt, iters, iters_src);
+    else if (g.nb == 64)
+        k_unpack<64><<<grid, block, 0, st>>>(src, leaf, g.n, g.m, dst, scale, src_alt, leaf_alt, iters, iters_src);
+    else
+        k_unpack<128><<<grid, block, 0, st>>>(src, leaf, g.n, g.m, dst, scale, src_alt, leaf_alt, iters, iters_src);
     note_launch();
 }
 

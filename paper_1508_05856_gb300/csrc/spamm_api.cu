@@ -147,7 +147,7 @@ struct Plan {
     double* t_hist = nullptr;                // [maxit_cap]
     int maxit_cap = 0;
     double* trace_part = nullptr;  // [m]
-    double* scal = nullptr;        // c0, mu, c, sqrt c, thr, resid, spare...
+    double* scal = nullptr;        // c0, mu, c, sqrt c, thr, resid, 1/c, 1/sqrt c, spare...
     double* rowsum = nullptr;      // [n]
     int* flags = nullptr;          // [0] done, [1] iters, [2] device error, [8..11] tile tickets of the
                                    // tensor-core kernel per branch, [16 + 8 b ..] output-tile bucket counts
@@ -644,7 +644,7 @@ static int multiply_core(const double* A, const double* B, double* C, int n, dou
     }
     product(p, p->buf[0], p->buf[1], p->buf[2], tau, EPI_PLAIN, p->task_ctr, st);
     join_slicing(p, st);
-    launch_unpack(p->buf[2].t, p->buf[2].tree, g, dC, nullptr, nullptr, st);
+    launch_unpack(p->buf[2].t, p->buf[2].tree, g, dC, nullptr, st);
     CK(cudaGetLastError());
     if ((e = stage_out(p, 2, C, dC, st))) return e;
     unsigned long long tasks = 0;
@@ -780,6 +780,8 @@ static int enqueue_prologue(Plan* p, const double* dS, int n, const spamm_opts& 
     double* mu = p->scal + 1;
     double* c = p->scal + 2;
     double* sqc = p->scal + 3;
+    double* rc = p->scal + 6;
+    double* rsqc = p->scal + 7;
     const double* mu_ptr = nullptr;
     if (o.mu_rel > 0.0) {
         launch_gershgorin(dS, n, nullptr, p->rowsum, c0, st);
@@ -787,7 +789,7 @@ static int enqueue_prologue(Plan* p, const double* dS, int n, const spamm_opts& 
         mu_ptr = mu;
     }
     launch_gershgorin(dS, n, mu_ptr, p->rowsum, c, st);
-    launch_sqrt_scalar(c, sqc, st);
+    launch_scale_consts(c, sqc, rc, rsqc, st);
 
     // X0 = s in buf 0: Y0 of the dual channel, the constant s of the single channel
     const TileMat X0 = p->buf[0];
@@ -795,7 +797,7 @@ static int enqueue_prologue(Plan* p, const double* dS, int n, const spamm_opts& 
         *sb = SolveBufs{p->buf[3], p->buf[1], p->buf[2], p->buf[3], p->buf[4], X0, p->buf[5]};
     else
         *sb = SolveBufs{X0, p->buf[1], p->buf[2], p->buf[3], p->buf[4], TileMat(), TileMat()};
-    launch_pack(dS, n, g, mu_ptr, c, X0, st);
+    launch_pack(dS, n, g, mu_ptr, rc, X0, st);
     launch_tree(g, X0.tree, nullptr, st);
     if (o.map == SPAMM_MAP_SCALED) launch_trace_parts(X0.t, g, p->trace_part, st);
     launch_map(X0.t, X0.tree, sb->Tb, g, o.map, p->trace_part, false, nullptr, st);
@@ -901,9 +903,10 @@ static int enqueue_iteration(Plan* p, SolveBufs& sb, double tau, double tau_s, i
 static int enqueue_epilogue(Plan* p, const SolveBufs& sb, double* dY, double* dZ, int swaps, cudaStream_t st) {
     const Geometry& g = p->g;
     const double* sqc = p->scal + 3;
+    const double* rsqc = p->scal + 7;
     join_slicing(p, st);
-    launch_unpack(sb.Yb.t, sb.Yb.tree, g, dY, sqc, nullptr, st, sb.Y2.t, sb.Y2.tree, p->flags + 1, swaps);
-    launch_unpack(sb.Zb.t, sb.Zb.tree, g, dZ, nullptr, sqc, st, sb.Z2.t, sb.Z2.tree, p->flags + 1, swaps);
+    launch_unpack(sb.Yb.t, sb.Yb.tree, g, dY, sqc, st, sb.Y2.t, sb.Y2.tree, p->flags + 1, swaps);
+    launch_unpack(sb.Zb.t, sb.Zb.tree, g, dZ, rsqc, st, sb.Z2.t, sb.Z2.tree, p->flags + 1, swaps);
     CK(cudaGetLastError());
     return SPAMM_OK;
 }

@@ -115,9 +115,9 @@ void launch_shift_copy(const double* S, double* D, int n, double mu_rel, const d
 void launch_transpose_rm(const double* A, double* T, int n, cudaStream_t st);
 // *mu_out = mu_rel * (*c0)
 void launch_scale_mu(const double* c0, double mu_rel, double* mu_out, cudaStream_t st);
-// Row-major src -> tile-major dst with leaf norms.  When scale_c != null:
-// dst = (src + mu delta) / c.  Edge padding is zero.
-void launch_pack(const double* src, int n, const Geometry& g, const double* mu, const double* scale_c,
+// Row-major src -> tile-major dst with leaf norms.  When recip_c != null:
+// dst = (src + mu delta) * (*recip_c), the scaling by the once-rounded 1/c.  Edge padding is zero.
+void launch_pack(const double* src, int n, const Geometry& g, const double* mu, const double* recip_c,
                  TileMat dst, cudaStream_t st);
 // trace_part[i] = logical trace of diagonal tile (i, i) of a packed matrix.
 void launch_trace_parts(const double* X, const Geometry& g, double* trace_part, cudaStream_t st);
@@ -215,11 +215,12 @@ void launch_cull(const Geometry& g, const double* treeA, const double* treeB, do
 // src_alt/leaf_alt when it is odd: the iterates alternate between two buffers,
 // and a solve that stopped on the device (|t_k| <= tol_t) ran *iters of the
 // iters_src iterations its launch sequence holds.
-void launch_unpack(const double* src, const double* leaf, const Geometry& g, double* dst, const double* mul,
-                   const double* div, cudaStream_t st, const double* src_alt = nullptr,
-                   const double* leaf_alt = nullptr, const int* iters = nullptr, int iters_src = 0);
-// sqrt of device scalar: out = sqrt(*c)
-void launch_sqrt_scalar(const double* c, double* out, cudaStream_t st);
+// dst = src * (*scale) when scale != null, else src.
+void launch_unpack(const double* src, const double* leaf, const Geometry& g, double* dst, const double* scale,
+                   cudaStream_t st, const double* src_alt = nullptr, const double* leaf_alt = nullptr,
+                   const int* iters = nullptr, int iters_src = 0);
+// *sqc = sqrt(*c), *rc = 1 / *c, *rsqc = 1 / sqrt(*c), each rounded once.
+void launch_scale_consts(const double* c, double* sqc, double* rc, double* rsqc, cudaStream_t st);
 // sum over logical entries of (R - I)^2 -> *out (deterministic)
 void launch_resid_norm(const double* R, const Geometry& g, double* partial, double* out, cudaStream_t st);
 

@@ -128,7 +128,7 @@ extern "C" int spamm_multiply_noalloc(const double* A, const double* B, double* 
     launch_cull(g, a.tree, b.tree, tau, co, ctr, nullptr, nullptr, s);
     launch_gemm_f64(g, a.t, b.t, c.t, a.tree, b.tree, c.tree, counts, jlist, tile_list, tile_count, 0, EPI_PLAIN,
                     nullptr, nullptr, s);
-    launch_unpack(c.t, c.tree, g, C, nullptr, nullptr, s);
+    launch_unpack(c.t, c.tree, g, C, nullptr, s);
     e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_error_message((std::string("kernel launch: ") + cudaGetErrorString(e)).c_str());

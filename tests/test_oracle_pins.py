@@ -222,15 +222,18 @@ def test_ns_iterates_match_eigen_recursion(iters):
     assert np.linalg.norm(r["Z"] - Zk) <= 1e-11 * np.linalg.norm(Zk)
 
 
-def test_ns_diagonal_is_scalar_recursion_bitwise():
-    d = np.array([0.9, 0.05, 0.3, 1.7, 0.011, 0.6, 2.0, 0.25, 0.125, 1.0, 0.75, 0.4])
+@pytest.mark.parametrize("scale", [1.0, 0.95])
+def test_ns_diagonal_is_scalar_recursion_bitwise(scale):
+    # scale 0.95 makes c = 1.9, where s * RN(1/c) and s / c differ in 10 of the 12 entries
+    d = np.array([0.9, 0.05, 0.3, 1.7, 0.011, 0.6, 2.0, 0.25, 0.125, 1.0, 0.75, 0.4]) * scale
     S = np.diag(d)
     c = d.max()
     for order in (0, 1):
         r = oracle.sqrt_invsqrt(S, 4, 0.0, 9, order=order)
-        y, z = _scalar_ns(d / c, 9, order)
+        # the scaling is a product with the once-rounded reciprocals 1/c and 1/sqrt(c)
+        y, z = _scalar_ns(d * (1.0 / c), 9, order)
         np.testing.assert_array_equal(np.diag(r["Y"]), y * math.sqrt(c))
-        np.testing.assert_array_equal(np.diag(r["Z"]), z / math.sqrt(c))
+        np.testing.assert_array_equal(np.diag(r["Z"]), z * (1.0 / math.sqrt(c)))
         assert not (r["Y"] - np.diag(np.diag(r["Y"]))).any()
 
 
@@ -429,7 +432,7 @@ def test_single_channel_worked_2x2():
     assert r["t_hist"][0] == g["t1"]
     sc = math.sqrt(g["scale_c"])
     np.testing.assert_array_equal(r["Y"], np.array(g["w1"]) * sc)
-    np.testing.assert_array_equal(r["Z"], np.array(g["z1"]) / sc)
+    np.testing.assert_array_equal(r["Z"], np.array(g["z1"]) * (1.0 / sc))
 
 
 def _scalar_single(lam, iters, scaled=False):
@@ -463,14 +466,14 @@ def test_single_channel_diagonal_is_scalar_recursion_bitwise():
     d = np.array([0.9, 0.05, 0.3, 1.7, 0.011, 0.6, 2.0, 0.25, 0.125, 1.0, 0.75, 0.4])
     c = d.max()
     r = oracle.sqrt_invsqrt(np.diag(d), 4, 0.0, 9, channel=oracle.CHANNEL_SINGLE)
-    lam = d / c
+    lam = d * (1.0 / c)
     z = np.ones_like(lam)
     x = lam.copy()
     for _ in range(9):
         z = z * (1.5 - 0.5 * x)
         w = lam * z
         x = z * w
-    np.testing.assert_array_equal(np.diag(r["Z"]), z / math.sqrt(c))
+    np.testing.assert_array_equal(np.diag(r["Z"]), z * (1.0 / math.sqrt(c)))
     np.testing.assert_array_equal(np.diag(r["Y"]), w * math.sqrt(c))
 
 
@@ -497,7 +500,7 @@ def test_single_channel_s_product_threshold_is_tau_s():
     S = synth.gaussian_lattice(n, 0.6, seed=5)
     r = oracle.sqrt_invsqrt(S, nb, tau, 1, tau_s=0.01 * tau, channel=oracle.CHANNEL_SINGLE)
     c = r["scale_c"]
-    s = S / c
+    s = S * (1.0 / c)
     z1 = r["Z"] * math.sqrt(c)
     n_tau_s = len(oracle.cull_flat(s, z1, nb, 0.01 * tau))
     n_tau = len(oracle.cull_flat(s, z1, nb, tau))
