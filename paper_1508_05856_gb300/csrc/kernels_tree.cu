@@ -61,50 +61,50 @@ __device__ __forceinline__ double block_sum_256(double v, double* red) {
 }
 
 // ---------------------------------------------------------------- Gershgorin
+// sum_j |r_j + mu delta_{j,row}| for one row, by one warp: four independent partial sums per lane (FP64
+// latency is long), partial p adding the entries lane + 32 (4k + p) in increasing k, then (p0 + p1) +
+// (p2 + p3).  Sixteen loads are in flight per lane; kShift = false issues no add for the shift.
+template <bool kShift>
+__device__ __forceinline__ double row_abs_sum(const double* __restrict__ r, int n, int row, int lane, double mu) {
+    double p[4] = {0.0, 0.0, 0.0, 0.0};
+    int j = lane;
+    for (; j + 480 < n; j += 512) {
+        double v[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) v[u] = r[j + 32 * u];
+        if (kShift) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u)
+                if (j + 32 * u == row) v[u] += mu;
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u) p[u & 3] += fabs(v[u]);
+    }
+    for (; j + 96 < n; j += 128) {
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            v[u] = r[j + 32 * u];
+            if (kShift && j + 32 * u == row) v[u] += mu;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) p[u] += fabs(v[u]);
+    }
+    for (; j < n; j += 32) {
+        double v = r[j];
+        if (kShift && j == row) v += mu;
+        p[0] += fabs(v);
+    }
+    return (p[0] + p[1]) + (p[2] + p[3]);
+}
+
 __global__ void k_rowsum(const double* __restrict__ S, int n, const double* __restrict__ mu_dev,
                          double* __restrict__ rowsum) {
     const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (row >= n) return;
-    const double mu = mu_dev ? *mu_dev : 0.0;
     const double* r = S + (size_t)row * n;
-    // four independent partial sums per lane (FP64 latency is long), fixed order
-    double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
-    int j = lane;
-    // two of the 128-wide steps below at a time (eight loads in flight), the same additions in the same order
-    for (; j + 224 < n; j += 256) {
-        double v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            v[u] = r[j + 32 * u];
-            if (j + 32 * u == row) v[u] += mu;
-        }
-        p0 += fabs(v[0]);
-        p1 += fabs(v[1]);
-        p2 += fabs(v[2]);
-        p3 += fabs(v[3]);
-        p0 += fabs(v[4]);
-        p1 += fabs(v[5]);
-        p2 += fabs(v[6]);
-        p3 += fabs(v[7]);
-    }
-    for (; j + 96 < n; j += 128) {
-        double v0 = r[j], v1 = r[j + 32], v2 = r[j + 64], v3 = r[j + 96];
-        if (j == row) v0 += mu;
-        if (j + 32 == row) v1 += mu;
-        if (j + 64 == row) v2 += mu;
-        if (j + 96 == row) v3 += mu;
-        p0 += fabs(v0);
-        p1 += fabs(v1);
-        p2 += fabs(v2);
-        p3 += fabs(v3);
-    }
-    for (; j < n; j += 32) {
-        double v = r[j];
-        if (j == row) v += mu;
-        p0 += fabs(v);
-    }
-    double s = (p0 + p1) + (p2 + p3);
+    double s = mu_dev ? row_abs_sum<true>(r, n, row, lane, *mu_dev) : row_abs_sum<false>(r, n, row, lane, 0.0);
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) rowsum[row] = s;
 }
@@ -200,26 +200,19 @@ void launch_scale_consts(const double* c, double* sqc, double* rc, double* rsqc,
 // ---------------------------------------------------------------- pack + leaf norms
 // Entries of a tile handled per thread of a 256-thread block, and how many of them one batch of
 // independent loads covers.
-template <int NB>
+template <int NB, int kMaxBatch>
 struct TileSplit {
     static constexpr int kPer = NB * NB / 256;
-    static constexpr int kBatch = kPer < 8 ? kPer : 8;
+    static constexpr int kBatch = kPer < kMaxBatch ? kPer : kMaxBatch;
 };
 
 // One 256-thread block per tile.  Thread t takes the entries t + 256 q (a warp reads 32 consecutive
-// entries of one row), eight independent loads at a time, then scales, stores and squares them in order.
-template <int NB>
-__global__ void __launch_bounds__(256) k_pack(const double* __restrict__ src, int n, int m,
-                                              const double* __restrict__ mu_dev, const double* __restrict__ rc_dev,
-                                              double* __restrict__ dst, double* __restrict__ leaf) {
-    using TS = TileSplit<NB>;
-    __shared__ double red[8];
-    const int tile = blockIdx.x;
-    const int i = tile / m, j = tile - (tile / m) * m;
-    const double mu = mu_dev ? *mu_dev : 0.0;
-    const double rc = rc_dev ? *rc_dev : 1.0;
-    const bool scaled = rc_dev != nullptr;
-    double* d = dst + (size_t)tile * NB * NB;
+// entries of one row), sixteen independent loads at a time, then scales, stores and squares them in order.
+// kScale: multiply by rc; kShift (diagonal tiles of a scaled pack): add mu on the logical diagonal first.
+template <int NB, bool kScale, bool kShift>
+__device__ __forceinline__ double pack_tile(const double* __restrict__ src, int n, int i, int j, double mu, double rc,
+                                            double* __restrict__ d) {
+    using TS = TileSplit<NB, 16>;
     double acc = 0.0;
 #pragma unroll 1
     for (int q0 = 0; q0 < TS::kPer; q0 += TS::kBatch) {
@@ -235,14 +228,30 @@ __global__ void __launch_bounds__(256) k_pack(const double* __restrict__ src, in
             const int idx = threadIdx.x + 256 * (q0 + u);
             const int gi = i * NB + idx / NB, gj = j * NB + idx % NB;
             double x = v[u];
-            if (scaled && gi < n && gj < n) {
-                if (gi == gj) x += mu;
+            if (kScale && gi < n && gj < n) {
+                if (kShift && gi == gj) x += mu;
                 x = x * rc;
             }
             d[idx] = x;
             acc = fma(x, x, acc);
         }
     }
+    return acc;
+}
+
+template <int NB>
+__global__ void __launch_bounds__(256) k_pack(const double* __restrict__ src, int n, int m,
+                                              const double* __restrict__ mu_dev, const double* __restrict__ rc_dev,
+                                              double* __restrict__ dst, double* __restrict__ leaf) {
+    __shared__ double red[8];
+    const int tile = blockIdx.x;
+    const int i = tile / m, j = tile - (tile / m) * m;
+    const double mu = mu_dev ? *mu_dev : 0.0;
+    double* d = dst + (size_t)tile * NB * NB;
+    double acc;
+    if (!rc_dev) acc = pack_tile<NB, false, false>(src, n, i, j, 0.0, 1.0, d);
+    else if (i == j) acc = pack_tile<NB, true, true>(src, n, i, j, mu, *rc_dev, d);
+    else acc = pack_tile<NB, true, false>(src, n, i, j, 0.0, *rc_dev, d);
     const double s = block_sum_256(acc, red);
     if (threadIdx.x == 0) leaf[tile] = s;
 }
@@ -316,7 +325,7 @@ __global__ void __launch_bounds__(256, 4) k_map(const double* X, double* T, cons
     }
     __syncthreads();
     const double c0 = coef[0], c1 = coef[1];
-    using TS = TileSplit<NB>;
+    using TS = TileSplit<NB, 8>;
     constexpr int ne = NB * NB;
     const int lane = threadIdx.x & 31;
     for (int tile = blockIdx.x; tile < m * m; tile += gridDim.x) {
@@ -345,7 +354,8 @@ __global__ void __launch_bounds__(256, 4) k_map(const double* X, double* T, cons
             const int r = idx / NB, cc = idx % NB;
             const int gi = i * NB + r, gj = j * NB + cc;
             const double xv = xb[u];
-            const double v = (gi == gj && gi < n) ? fma(c1, xv, c0) : c1 * xv;
+            // off the diagonal tiles no entry takes c0: one multiply
+            const double v = (i == j && gi == gj && gi < n) ? fma(c1, xv, c0) : c1 * xv;
             t[idx] = v;
             acc = fma(v, v, acc);
             if (NB == 64 && rmax) {
@@ -685,25 +695,12 @@ void launch_cull(const Geometry& g, const double* treeA, const double* treeB, do
 }
 
 // ---------------------------------------------------------------- unpack
-// One 256-thread block per tile, entries t + 256 q per thread, eight independent loads at a time; an
+// One 256-thread block per tile, entries t + 256 q per thread, sixteen independent loads at a time; an
 // all-zero tile (leaf norm 0) is written as zeros without reading it.
-template <int NB>
-__global__ void __launch_bounds__(256) k_unpack(const double* __restrict__ src, const double* __restrict__ leaf,
-                                                int n, int m, double* __restrict__ dst,
-                                                const double* __restrict__ scale_dev,
-                                                const double* __restrict__ src_alt, const double* __restrict__ leaf_alt,
-                                                const int* __restrict__ iters, int iters_src) {
-    using TS = TileSplit<NB>;
-    const int tile = blockIdx.x;
-    const int i = tile / m, j = tile - (tile / m) * m;
-    if (iters && ((*iters - iters_src) & 1)) {
-        src = src_alt;
-        leaf = leaf_alt;
-    }
-    const double* s = src + (size_t)tile * NB * NB;
-    const double f = scale_dev ? *scale_dev : 1.0;
-    const bool scaled = scale_dev != nullptr;
-    const bool zero = leaf && leaf[tile] == 0.0;
+template <int NB, bool kScale>
+__device__ __forceinline__ void unpack_tile(const double* __restrict__ s, bool zero, int n, int i, int j, double f,
+                                            double* __restrict__ dst) {
+    using TS = TileSplit<NB, 16>;
 #pragma unroll 1
     for (int q0 = 0; q0 < TS::kPer; q0 += TS::kBatch) {
         double v[TS::kBatch];
@@ -713,9 +710,27 @@ __global__ void __launch_bounds__(256) k_unpack(const double* __restrict__ src, 
         for (int u = 0; u < TS::kBatch; ++u) {
             const int idx = threadIdx.x + 256 * (q0 + u);
             const int gi = i * NB + idx / NB, gj = j * NB + idx % NB;
-            if (gi < n && gj < n) dst[(size_t)gi * n + gj] = scaled ? v[u] * f : v[u];
+            if (gi < n && gj < n) dst[(size_t)gi * n + gj] = kScale ? v[u] * f : v[u];
         }
     }
+}
+
+template <int NB>
+__global__ void __launch_bounds__(256) k_unpack(const double* __restrict__ src, const double* __restrict__ leaf,
+                                                int n, int m, double* __restrict__ dst,
+                                                const double* __restrict__ scale_dev,
+                                                const double* __restrict__ src_alt, const double* __restrict__ leaf_alt,
+                                                const int* __restrict__ iters, int iters_src) {
+    const int tile = blockIdx.x;
+    const int i = tile / m, j = tile - (tile / m) * m;
+    if (iters && ((*iters - iters_src) & 1)) {
+        src = src_alt;
+        leaf = leaf_alt;
+    }
+    const double* s = src + (size_t)tile * NB * NB;
+    const bool zero = leaf && leaf[tile] == 0.0;
+    if (scale_dev) unpack_tile<NB, true>(s, zero, n, i, j, *scale_dev, dst);
+    else unpack_tile<NB, false>(s, zero, n, i, j, 1.0, dst);
 }
 
 void launch_unpack(const double* src, const double* leaf, const Geometry& g, double* dst, const double* scale,
