@@ -222,18 +222,35 @@ def lens_summary(h, bins: int, channel: int) -> dict:
     return out
 
 
+def source_digest(sources) -> str | None:
+    """sha256 over the source text a captured kernel is built from, in order: each entry is a whole file
+    ({"file": path}) or the span of a file from the first occurrence of a start marker up to the next
+    occurrence of an end marker ({"file", "from", "to"}); None when a file or marker is missing."""
+    import hashlib
+    h = hashlib.sha256()
+    for part in sources:
+        path = os.path.join(ROOT, part["file"])
+        if not os.path.exists(path):
+            return None
+        text = open(path, "rb").read()
+        if "from" in part:
+            a = text.find(part["from"].encode())
+            b = text.find(part["to"].encode(), a + 1) if a >= 0 else -1
+            if a < 0 or b < 0:
+                return None
+            text = text[a:b]
+        h.update(text)
+    return h.hexdigest()
+
+
 def captured_traffic(kernel: str, tasks_per_launch: float):
     """DRAM bytes (read + write) per launch from the committed ncu capture of `kernel`, scaled by tasks
-    to this run's mean launch; None when the kernel source changed since the capture."""
-    import hashlib
+    to this run's mean launch; None when the kernel's source changed since the capture."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     rec = json.load(open(path)).get(kernel)
-    if not rec:
-        return None
-    src = os.path.join(ROOT, rec["source"])
-    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["source_sha256"]:
+    if not rec or source_digest(rec["sources"]) != rec["sources_sha256"]:
         return None
     per_task = (rec["dram_read_bytes"] + rec["dram_write_bytes"]) / rec["tasks"]
     return per_task * tasks_per_launch

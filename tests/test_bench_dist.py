@@ -70,3 +70,26 @@ def test_reference_arm_under_torchrun_world2():
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["steps"] == 1
     assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
     assert d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_source_digest_spans(tmp_path, monkeypatch):
+    """The traffic record follows only the hashed spans: an edit outside them keeps the digest, an edit
+    inside changes it, and a missing marker or file gives None."""
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    (tmp_path / "k.cu").write_text("head\n// A\nkernel body\n// B\ntail\n")
+    (tmp_path / "h.cuh").write_text("ptx\n")
+    spec = [{"file": "k.cu", "from": "// A", "to": "// B"}, {"file": "h.cuh"}]
+    d0 = bench.source_digest(spec)
+    assert d0 is not None
+    (tmp_path / "k.cu").write_text("other head\n// A\nkernel body\n// B\nother tail\n")
+    assert bench.source_digest(spec) == d0
+    (tmp_path / "k.cu").write_text("head\n// A\nkernel body changed\n// B\ntail\n")
+    assert bench.source_digest(spec) != d0
+    assert bench.source_digest([{"file": "k.cu", "from": "// A", "to": "// missing"}]) is None
+    assert bench.source_digest([{"file": "absent.cu"}]) is None
+
+
+def test_committed_traffic_record_is_well_formed():
+    rec = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic.json")))["k_gemm_emu"]
+    assert rec["tasks"] > 0 and rec["dram_read_bytes"] > 0
+    assert bench.source_digest(rec["sources"]) is not None
