@@ -597,3 +597,29 @@ def test_product_representation_residual_uses_the_transpose():
     want = z0 @ np.linalg.inv(sl.sqrtm(r1)).real
     r = oracle.invsqrt_product(S, 1, mus, 0.0, 0.0, 80)
     np.testing.assert_allclose(r["Z"], want, rtol=0, atol=1e-13)
+
+
+# --------------------------------------------------------------------------- Gershgorin bound and residual
+
+
+def test_gershgorin_closed_form():
+    """max_i sum_j |s_ij + mu delta_ij| (the rescaling bound of Sec. 3.1): row sums of absolute values with
+    the shift on the diagonal.  Here the row sums are 3.5 and 6.5; column sums (a transposed loop) would give
+    5.5, signed sums (a dropped |.|) -0.5 in both rows, and an ignored shift 7.0."""
+    S = np.array([[1.0, -2.0], [3.0, -4.0]])
+    assert oracle.gershgorin(S, 0.5) == 6.5
+    assert oracle.gershgorin(S) == 7.0
+    assert oracle.gershgorin(S.T, 0.5) == 5.5
+
+
+def test_residual_closed_forms():
+    """||Z S Z - I||_F: zero for an exact inverse square root, sqrt(sum (d_i - 1)^2) for Z = I and diagonal S,
+    and (Z S Z)_{01} = z00 s01 z11 for a triangular Z that a transposed product would get wrong."""
+    S = np.diag([4.0, 16.0, 0.25])
+    assert oracle.residual(S, np.diag([0.5, 0.25, 2.0])) == 0.0
+    d = np.array([2.0, 0.5, 3.0])
+    assert oracle.residual(np.diag(d), np.eye(3)) == pytest.approx(math.sqrt(((d - 1.0) ** 2).sum()), rel=1e-15)
+    Z = np.array([[1.0, 2.0], [0.0, 1.0]])
+    S2 = np.array([[1.0, 0.0], [0.0, 1.0]])
+    # Z S Z = Z^2 = [[1, 4], [0, 1]]: residual 4 (Z S Z^T would give [[5, 2], [2, 1]], residual sqrt(24))
+    assert oracle.residual(S2, Z) == 4.0
