@@ -173,7 +173,9 @@ int spamm_multiply(const double* A, const double* B, double* C, int n, double ta
  * Eq. (single); SPAMM_ERR_ARG for the single channel with
  * SPAMM_ORDER_TRANSPOSED.
  * S is scaled by its Gershgorin bound c (plus mu, Sec. 6) into (0,1]; the
- * results are unscaled as Y * sqrt(c), Z / sqrt(c).  Runs maxit iterations,
+ * results are unscaled as Y * sqrt(c), Z / sqrt(c).  Both divisions are
+ * products with the once-rounded reciprocals 1/c and 1/sqrt(c), computed
+ * once per solve.  Runs maxit iterations,
  * or fewer when opts->tol_t > 0.  Y and Z are written even when the status
  * is SPAMM_ERR_DIVERGED or SPAMM_ERR_NOTCONVERGED.
  */
