@@ -440,7 +440,7 @@ int or_ns(const double* S, int n, int nb, double tau, double tau_s, double mu_re
     double mu = 0.0;
     if (mu_rel > 0.0) mu = mu_rel * or_gershgorin(S, n, 0.0);
     double c = or_gershgorin(S, n, mu);
-    /* s <- s / c (Sec. 3.1, rescaling into (0, 1]), applied as a product with the once-rounded 1/c */
+    /* s <- s / c (Sec. 3.2, rescaling into (0, 1]), applied as a product with the once-rounded 1/c */
     const double rc = 1.0 / c;
     for (int i = 0; i < n; ++i)
         for (int j = 0; j < n; ++j) {

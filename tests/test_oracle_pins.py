@@ -603,7 +603,7 @@ def test_product_representation_residual_uses_the_transpose():
 
 
 def test_gershgorin_closed_form():
-    """max_i sum_j |s_ij + mu delta_ij| (the rescaling bound of Sec. 3.1): row sums of absolute values with
+    """max_i sum_j |s_ij + mu delta_ij| (the rescaling bound of Sec. 3.2): row sums of absolute values with
     the shift on the diagonal.  Here the row sums are 3.5 and 6.5; column sums (a transposed loop) would give
     5.5, signed sums (a dropped |.|) -0.5 in both rows, and an ignored shift 7.0."""
     S = np.array([[1.0, -2.0], [3.0, -4.0]])
