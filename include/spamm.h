@@ -48,7 +48,8 @@ extern "C" {
 #define SPAMM_ERR_ARG (-1)           /* bad size, tau < 0 or NaN, bad option    */
 #define SPAMM_ERR_NOMEM (-2)         /* device allocation failed                 */
 #define SPAMM_ERR_DIVERGED (-3)      /* t_k not finite or |t_k| >= 1: the
-                                        iteration left its basin (Sec. 5.3);
+                                        iteration left its basin of stability
+                                        (Sec. 3, Sec. 5.1);
                                         outputs are still written              */
 #define SPAMM_ERR_NOTCONVERGED (-4)  /* tol_t > 0 and maxit reached with
                                         |t_k| > tol_t; outputs are written      */
