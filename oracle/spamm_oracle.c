@@ -32,10 +32,21 @@
  *     and eps from the sigmoidal damping functions of the trace error t of
  *     the X being mapped.
  *
- * Parity-pinned by tests/test_oracle_pins.py (tau = 0 dense product, the
- * tile-level closed form of the lemma, recursive == brute-force cull sets,
- * the Proposition's bounds, eigen-decomposition iterates, KMS inverse,
- * convergence identities).
+ * Parity-pinned by tests/test_oracle_pins.py, every function:
+ *   - products and culls: the tau = 0 dense product (bitwise), a worked 4x4,
+ *     the tile-level closed form of the lemma, recursive == brute-force cull
+ *     sets, the Proposition's bounds, the norm-tree levels;
+ *   - the iteration: eigen-decomposition iterates, diagonal S against the
+ *     scalar recursion (bitwise), the 2x2 closed form, convergence
+ *     identities, the KMS inverse, padding invariance, the order variants;
+ *   - the damped map: the sigmoid landmarks, eigen iterates, its fixed point;
+ *   - the single channel: a hand-worked 2x2, eigen iterates, diagonal S;
+ *   - lensing histograms: a dense closed form, an identity operand, hand
+ *     triples;
+ *   - the product representation: telescoping at tau = 0, conditioning, the
+ *     transpose;
+ *   - the Gershgorin bound and the residual: closed forms.
+ * No function is left "parity unpinned".
  *
  * Build: gcc -O2 -fopenmp -ffp-contract=off -shared -fPIC (see oracle/__init__.py).
  */
