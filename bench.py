@@ -135,19 +135,36 @@ class ClockSampler:
 # ----------------------------------------------------------------------------- CPU oracle timing
 
 
-def oracle_solve_rate(S, tau: float, budget_s: float, min_solves: int = 1) -> tuple[float, int, float]:
+def oracle_solve_rate(S, tau: float, budget_s: float, min_solves: int = 1) -> tuple[float, int, float, dict]:
+    """Full oracle solves of S for about budget_s seconds: (solves/s, solves, seconds, the last solve)."""
     import oracle
     t0 = time.perf_counter()
     cnt = 0
     while True:
-        oracle.sqrt_invsqrt(S, LEAF, tau, MAXIT, map=MAP, tol_t=TOL, channel=CHANNEL)
+        ref = oracle.sqrt_invsqrt(S, LEAF, tau, MAXIT, map=MAP, tol_t=TOL, channel=CHANNEL)
         cnt += 1
         el = time.perf_counter() - t0
         if cnt >= min_solves and el >= budget_s:
             break
         if el > 0 and cnt >= min_solves and el / cnt * (cnt + 1) > 3 * budget_s:
             break
-    return cnt / el, cnt, el
+    return cnt / el, cnt, el, ref
+
+
+def rel_err(a, b) -> float:
+    import numpy as np
+    nb = float(np.linalg.norm(b))
+    return float(np.linalg.norm(a - b)) / nb if nb > 0 else float(np.linalg.norm(a))
+
+
+def err_vs_oracle(Y, Z, st, ref) -> dict:
+    """Relative Frobenius errors of a GPU solve against the oracle's solve of the same input, and whether the
+    per-iteration task counts of its three products equal the oracle's."""
+    import numpy as np
+    out = {"Z": rel_err(Z, ref["Z"]), "Y": rel_err(Y, ref["Y"]), "iters_equal": bool(st["iters"] == ref["iters"])}
+    if "task_hist" in st:
+        out["task_hist_equal"] = bool(np.array_equal(np.asarray(st["task_hist"]), ref["task_hist"]))
+    return out
 
 
 def run_reference(args, ws, rank):
@@ -279,12 +296,14 @@ def run_gpu(args, ws, rank, local):
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def solve(t, profile=False, residual=False):
+    def solve(t, profile=False, residual=False, raise_on=True):
         return sp.sqrt_invsqrt(Sd, t, MAXIT, leaf=LEAF, precision=prec, Y=Yd, Z=Zd, profile=profile, map=MAP,
-                               tol_t=TOL, residual=residual, channel=CHANNEL)
+                               tol_t=TOL, residual=residual, channel=CHANNEL, raise_on=raise_on)
 
-    # verification solve (untimed): residual against the gate, FP64 dense
+    # verification solve (untimed): residual against the gate, FP64 dense; its Y and Z are compared with the
+    # oracle's solve of the same input on rank 0
     _, _, vst = solve(tau, residual=True)
+    Yv, Zv = (Yd.cpu().numpy(), Zd.cpu().numpy()) if rank == 0 else (None, None)
     lensing = None
     if args.lens_bins > 0:
         # plane-diagonal profile of every product (untimed): volume share on each plane diagonal per iteration
@@ -312,6 +331,8 @@ def run_gpu(args, ws, rank, local):
     gemm_launches = 0
     gemm_flops = 0.0
     tensor_units = 0
+    phase = {k: [0.0, 0] for k in ("cull", "tree", "slice")}
+    n_prof = max(1, min(args.steps, 3))
     for _ in range(args.steps):
         flush.zero_()                       # L2 (129 MB) flushed between timed solves
         e0 = torch.cuda.Event(enable_timing=True)
@@ -326,7 +347,7 @@ def run_gpu(args, ws, rank, local):
     clk = clocks.stop()
     # leaf-product kernel timings: separate solves with per-launch events (not part of the timed steps)
     prof_s = 0.0
-    for _ in range(max(1, min(args.steps, 3))):
+    for _ in range(n_prof):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -339,6 +360,9 @@ def run_gpu(args, ws, rank, local):
         gemm_launches += st["gemm_launches"]
         gemm_flops += st["flops"]
         tensor_units += st["tensor_units"]
+        for k in phase:
+            phase[k][0] += st[f"{k}_ms"]
+            phase[k][1] += st[f"{k}_launches"]
     tot = sum(step_s)
     tot_max = max_over_ranks(tot, ws, dev)
     value = job_rate(ws, args.steps, tot_max)
@@ -396,43 +420,53 @@ def run_gpu(args, ws, rank, local):
             e1.synchronize()
             ft.append(e0.elapsed_time(e1) / 1e3)
         fp64_path = {"value": job_rate(ws, len(ft), max_over_ranks(sum(ft), ws, dev)), "unit": UNIT,
-                     "resid_F": fst["resid_F"], "gate_met": bool(fst["resid_F"] <= GATE)}
+                     "resid_F": fst["resid_F"], "gate_met": bool(fst["resid_F"] <= GATE),
+                     "_out": (Yd.cpu().numpy(), Zd.cpu().numpy(), fst) if rank == 0 else None}
 
     # tau sweep (the configuration's cull-count / error study)
     sweep = []
     if not args.no_sweep:
         for ts in TAU_SWEEP:
-            _, _, rs = solve(ts, residual=True)
+            _, _, rs = solve(ts, residual=True, raise_on=False)
+            out_s = (Yd.cpu().numpy(), Zd.cpu().numpy(), rs) if rank == 0 else None
             tt = []
             for _ in range(3):
                 flush.zero_()
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                solve(ts)
+                solve(ts, raise_on=False)
                 e1.record(stream)
                 e1.synchronize()
                 tt.append(e0.elapsed_time(e1) / 1e3)
             sweep.append({"tau": ts, "solves_per_s": 3 / sum(tt), "resid_F": rs["resid_F"],
                           "tasks": rs["tasks_total"], "volume_pct": 100.0 * rs["tasks_total"] / rs["tasks_dense"],
-                          "gate_met": bool(rs["resid_F"] <= GATE)})
+                          "gate_met": bool(rs["resid_F"] <= GATE), "status": sp.STATUS.get(rs["status"]),
+                          "_out": out_s})
 
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
         return 0
 
-    # roofline of the dominant kernel (the leaf-product kernel)
+    # roofline of the dominant kernel (the leaf-product kernel).  Its per-launch duration comes from profiled
+    # solves (branches serialised, events around each launch); its time per unprofiled solve is that average
+    # times the launches of one solve, next to ms_per_step.  In the unprofiled solve the Y and Z products run
+    # on two branches at once, so the kernel-time sum can exceed the solve's critical path.
+    ms_per_step = 1e3 * tot_max / args.steps
     avg_ms = gemm_ms / max(1, gemm_launches)
     flops_per_launch = gemm_flops / max(1, gemm_launches)
     achieved = flops_per_launch / (avg_ms / 1e3) / 1e12 if avg_ms > 0 else 0.0
+    launches_per_solve = gemm_launches / n_prof
+    kernel_ms_per_solve = avg_ms * launches_per_solve
     if prec == sp.FP64:
         peak = measure_dgemm_tflops(torch, dev)
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if peak else None, "traffic": None,
                 "kernel": f"k_gemm_f64<{LEAF}>",
                 "peak_source": "cuBLAS FP64 GEMM 4096^3 measured in this run (FP64 pipe)",
-                "share_of_step": gemm_ms / 1e3 / prof_s if prof_s else None}
+                "avg_launch_ms": avg_ms, "launches_per_solve": launches_per_solve,
+                "kernel_ms_per_solve": kernel_ms_per_solve, "share_of_step": kernel_ms_per_solve / ms_per_step}
     else:
         peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
         peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
@@ -449,23 +483,65 @@ def run_gpu(args, ws, rank, local):
                                    "slice) unit, 12 units per task: 24x the FP64-equivalent useful flops)",
                 "units_per_task": tensor_units / max(1.0, tasks_per_launch * gemm_launches),
                 "useful_fp64_equiv_tflops": achieved,
+                "useful_frac": achieved / peak if peak else None,
                 "peak_source": ("bf16_tflops of measured x 1.0 (FP16 and BF16 dense rates are equal)" if peaks
                                 else "fallback 1.9 PFLOP/s"),
-                "share_of_step": gemm_ms / 1e3 / prof_s if prof_s else None}
+                "avg_launch_ms": avg_ms, "launches_per_solve": launches_per_solve,
+                "kernel_ms_per_solve": kernel_ms_per_solve, "share_of_step": kernel_ms_per_solve / ms_per_step}
 
+    # the norm-tree, cull and slicing kernels of the products: algorithmic bytes per launch over their mean
+    # duration.  m tiles per side; cull: both operands' leaf norms read (2 * 8 m^2), task counts written
+    # (4 m^2) and 4 bytes per surviving task; tree: the leaf level read (8 m^2) and the upper levels written
+    # (8 m^2 / 3).
+    m = (N + LEAF - 1) // LEAF
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    hbm = (json.load(open(peaks_path)).get("hbm_gbs") if os.path.exists(peaks_path) else None) or 6800.0
+    tasks_per_product = vst["tasks_total"] / max(1, 3 * vst["iters"])
+    setup = {"peak_gbs": hbm, "peak_source": "hbm_gbs of measured" if os.path.exists(peaks_path) else "fallback"}
+    for k, nbytes in (("cull", 20.0 * m * m + 4.0 * tasks_per_product), ("tree", 8.0 * m * m * 4.0 / 3.0),
+                      ("slice", None)):
+        ms_k, cnt_k = phase[k]
+        if cnt_k == 0:
+            continue
+        avg_k = ms_k / cnt_k
+        rec = {"avg_launch_us": 1e3 * avg_k, "launches_per_solve": cnt_k / n_prof,
+               "ms_per_solve": avg_k * cnt_k / n_prof}
+        if nbytes is not None:
+            gbs = nbytes / (avg_k / 1e3) / 1e9
+            rec.update({"bytes_per_launch": nbytes, "achieved_gbs": gbs, "frac": gbs / hbm})
+        setup[k] = rec
+
+    import oracle
+    oracle.build()
     cpu = None
+    ref = None
     if not args.no_cpu_baseline and ws == 1:
-        import oracle
-        oracle.build()
-        rate, cnt, el = oracle_solve_rate(S, tau, budget_s=args.cpu_budget)
+        rate, cnt, el, ref = oracle_solve_rate(S, tau, budget_s=args.cpu_budget)
         cpu = {"value": rate, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                "sample": f"{cnt} full solve(s) of the same workload in {el:.1f} s"}
+    # error of every reported GPU result against the oracle's solve of the same input
+    oracle_err = None
+    if not args.no_oracle_error:
+        if ref is None:
+            ref = oracle.sqrt_invsqrt(S, LEAF, tau, MAXIT, map=MAP, tol_t=TOL, channel=CHANNEL)
+        oracle_err = err_vs_oracle(Yv, Zv, vst, ref)
+        if fp64_path is not None:
+            fy, fz, fst = fp64_path["_out"]
+            fp64_path["err_vs_oracle"] = err_vs_oracle(fy, fz, fst, ref)
+        for row in sweep:
+            sy, sz, sst = row["_out"]
+            row["err_vs_oracle"] = err_vs_oracle(sy, sz, sst, oracle.sqrt_invsqrt(S, LEAF, row["tau"], MAXIT, map=MAP,
+                                                                                   tol_t=TOL, channel=CHANNEL))
+    if fp64_path is not None:
+        fp64_path.pop("_out", None)
+    for row in sweep:
+        row.pop("_out", None)
 
     nbytes = N * N * 8
     p50 = statistics.median(step_s) * 1e3
     p99 = sorted(step_s)[min(len(step_s) - 1, int(math.ceil(0.99 * len(step_s))) - 1)] * 1e3
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * tot_max / args.steps, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == sp.FP64 else "f16-split",
             "data": "synthetic",
             "config": {"workload": workload_name(tau, args.precision.upper()), "n": N, "leaf": LEAF, "tau": tau,
@@ -477,7 +553,10 @@ def run_gpu(args, ws, rank, local):
             "resid_F": vst["resid_F"], "gate": GATE, "gate_met": bool(vst["resid_F"] <= GATE),
             "tasks_per_solve": vst["tasks_total"], "volume_pct": 100.0 * vst["tasks_total"] / vst["tasks_dense"],
             "t_final": vst["t_final"], "iters": vst["iters"],
+            "err_vs_oracle": oracle_err,
+            "err_tolerance": {"Z": 1e-9 if prec == sp.EMU64 else 1e-10, "Y": 1e-9 if prec == sp.EMU64 else 1e-10},
             "roofline": roof,
+            "norm_cull_kernels": setup,
             "fp64_path": fp64_path,
             "to_tolerance": to_tol,
             "lensing": lensing,
@@ -746,6 +825,8 @@ def main():
     ap.add_argument("--size", type=int, default=N, help="matrix size N (a smaller case for profiler captures)")
     ap.add_argument("--maxit", type=int, default=MAXIT, help="iterations per solve (fewer for profiler captures)")
     ap.add_argument("--no-fp64-path", action="store_true", help="skip timing the FP64-pipe solve beside EMU64")
+    ap.add_argument("--no-oracle-error", action="store_true",
+                    help="skip the oracle solves that give every result's error against the oracle")
     ap.add_argument("--c3", action="store_true", help="large 3D Gaussian configuration instead of the headline solve")
     ap.add_argument("--c3-n", type=int, default=16384)
     ap.add_argument("--c3-sigma", type=float, default=0.7)

@@ -19,7 +19,8 @@
  *   - Matrices are dense, row-major, n x n, double precision.
  *   - A matrix pointer may address host memory or device memory of the
  *     current CUDA device; the library tells them apart with
- *     cudaPointerGetAttributes.  Page-locked host memory is read and written
+ *     cudaPointerGetAttributes.  Device memory of another GPU is rejected
+ *     with SPAMM_ERR_ARG.  Page-locked host memory is read and written
  *     in place by the kernels (through its device mapping); pageable host
  *     data is staged through the library's own device buffers.  The caller owns every pointer it passes; inputs are not
  *     modified; the call returns after the results are written.
@@ -49,7 +50,10 @@ extern "C" {
 #define SPAMM_ERR_NOMEM (-2)         /* device allocation failed                 */
 #define SPAMM_ERR_DIVERGED (-3)      /* t_k not finite or |t_k| >= 1: the
                                         iteration left its basin of stability
-                                        (Sec. 3, Sec. 5.1);
+                                        (Sec. 3, Sec. 5.1); or, when the
+                                        residual is computed, ||ZSZ - I||_F >= 1:
+                                        culling errors carried Y and Z off the
+                                        roots (X = YZ can still look converged);
                                         outputs are still written              */
 #define SPAMM_ERR_NOTCONVERGED (-4)  /* tol_t > 0 and maxit reached with
                                         |t_k| > tol_t; outputs are written      */
@@ -101,8 +105,11 @@ typedef struct spamm_opts {
     double tol_t;      /* stop once |t_k| <= tol_t; 0 runs exactly maxit steps  */
     int order;         /* SPAMM_ORDER_PAPER or SPAMM_ORDER_TRANSPOSED           */
     int residual;      /* nonzero: also compute ||Z S Z - I||_F (FP64, dense)   */
-    int profile;       /* nonzero: time every leaf-product kernel with CUDA
-                          events on the call's stream (stats->gemm_ms)         */
+    int profile;       /* nonzero: time every leaf-product, cull, quadtree
+                          and slicing kernel of the products with CUDA events
+                          on the call's stream (stats->gemm_ms, cull_ms,
+                          tree_ms, slice_ms); the two branches of an
+                          iteration then run one after the other            */
     void* stream;      /* cudaStream_t; NULL = legacy default stream            */
     int map;           /* SPAMM_MAP_NS or SPAMM_MAP_SCALED                      */
     int channel;       /* SPAMM_CHANNEL_DUAL or SPAMM_CHANNEL_SINGLE            */
@@ -137,6 +144,15 @@ typedef struct spamm_stats {
                                   by the leaf-product kernel in units of one
                                   128 x 64 x 64 FP16 product (2*128*64*64
                                   flops): 12 per leaf product                   */
+    double cull_ms;            /* opts->profile: summed duration of the cull
+                                  kernels of the products (CUDA events), else 0 */
+    long long cull_launches;   /* opts->profile: cull launches timed            */
+    double tree_ms;            /* opts->profile: summed duration of the products'
+                                  quadtree (upper norm levels) passes           */
+    long long tree_launches;
+    double slice_ms;           /* opts->profile, SPAMM_EMU64: summed duration of
+                                  the products' digit-slicing passes            */
+    long long slice_launches;
 } spamm_stats;
 
 /* Fill *opts with defaults: leaf 64, SPAMM_FP64, tau_s = 0.01 tau, no shift,
@@ -243,14 +259,20 @@ int spamm_cull(const double* A, const double* B, int n, double tau, int leaf, in
  * cudaFree or allocating library routine.  The scratch is one fixed device
  * array of about 6.3 MB, held on every GPU that loads the library until the
  * process exits.
- *   - A, B, C: device pointers (row-major n x n doubles, caller-owned).
- *     Host pointers are rejected with SPAMM_ERR_ARG.
+ *   - A, B, C: device pointers of the current device, or managed memory
+ *     (row-major n x n doubles, caller-owned).  Host pointers and device
+ *     memory of another GPU are rejected with SPAMM_ERR_ARG.
  *   - n <= SPAMM_NOALLOC_MAX_N; larger n returns SPAMM_ERR_UNSUPPORTED.
  *   - leaf: 32, 64 or 128 (0 selects 64).  stream: cudaStream_t or NULL.
  *   - The work is enqueued on `stream` and the call returns without waiting;
  *     synchronise the stream before reading C.
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - CUDA loads device code lazily by default: the array and the kernels
+ *     of each leaf size are placed in device memory by the first call that
+ *     uses them.  So make one call per device, for every leaf size the
+ *     program will use, before it reserves the rest of the device memory;
+ *     after that no call needs device memory beyond what it was given.
  *   - Every call shares the one array.  Calls ordered on one stream are safe;
  *     calls that overlap on the GPU (other streams or threads) race.
  * Same arithmetic and task lists as spamm_multiply with SPAMM_FP64.

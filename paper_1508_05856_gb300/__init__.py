@@ -68,7 +68,10 @@ class Stats(ctypes.Structure):
                 ("t_hist", ctypes.POINTER(ctypes.c_double)), ("task_hist", ctypes.POINTER(ctypes.c_longlong)),
                 ("gemm_ms", ctypes.c_double), ("gemm_launches", ctypes.c_longlong),
                 ("lens_hist", ctypes.POINTER(ctypes.c_longlong)), ("lens_bins", ctypes.c_int),
-                ("tensor_units", ctypes.c_longlong)]
+                ("tensor_units", ctypes.c_longlong), ("cull_ms", ctypes.c_double),
+                ("cull_launches", ctypes.c_longlong), ("tree_ms", ctypes.c_double),
+                ("tree_launches", ctypes.c_longlong), ("slice_ms", ctypes.c_double),
+                ("slice_launches", ctypes.c_longlong)]
 
 
 _lock = threading.Lock()
@@ -213,7 +216,9 @@ def _opts(leaf=64, precision=FP64, tau_s=None, mu_rel=0.0, tol_t=0.0, order=ORDE
 def _stats_dict(s: Stats, th=None, kh=None) -> dict:
     d = {"iters": s.iters, "t_final": s.t_final, "resid_F": s.resid_F, "scale_c": s.scale_c,
          "tasks_total": s.tasks_total, "tasks_dense": s.tasks_dense, "flops": s.flops, "gemm_ms": s.gemm_ms,
-         "gemm_launches": s.gemm_launches, "tensor_units": s.tensor_units}
+         "gemm_launches": s.gemm_launches, "tensor_units": s.tensor_units, "cull_ms": s.cull_ms,
+         "cull_launches": s.cull_launches, "tree_ms": s.tree_ms, "tree_launches": s.tree_launches,
+         "slice_ms": s.slice_ms, "slice_launches": s.slice_launches}
     if th is not None:
         d["t_hist"] = th[:s.iters].copy()
     if kh is not None:

@@ -83,20 +83,40 @@ static void set_error(const char* what, cudaError_t e) {
         }                                                      \
     } while (0)
 
-// The address kernels use for a caller matrix they can read and write in place: device or managed memory
-// as it is, and page-locked host memory through its device mapping (on this part the GPU reaches host
-// memory over NVLink-C2C, so the pack and unpack kernels move the data themselves, with no staging copy).
-// Null for pageable host memory, which is staged.
-static void* kernel_view(const void* p) {
-    if (!p) return nullptr;
+// The address kernels use for a caller matrix they can read and write in place, for work on `device`:
+// device memory of that device or managed memory as it is, and page-locked host memory through its device
+// mapping (on this part the GPU reaches host memory over NVLink-C2C, so the pack and unpack kernels move the
+// data themselves, with no staging copy).  *view is null for pageable host memory, which is staged.  Device
+// memory of another GPU is an argument error: without peer access the kernels cannot reach it.
+int pointer_view(const void* p, int device, void** view) {
+    *view = nullptr;
+    if (!p) return SPAMM_OK;
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
-        return nullptr;
+        return SPAMM_OK;
     }
-    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return const_cast<void*>(p);
-    if (a.type == cudaMemoryTypeHost && a.devicePointer) return a.devicePointer;
-    return nullptr;
+    if (a.type == cudaMemoryTypeManaged) {
+        *view = const_cast<void*>(p);
+    } else if (a.type == cudaMemoryTypeDevice) {
+        if (a.device != device) {
+            char buf[160];
+            snprintf(buf, sizeof(buf), "a matrix is device memory of GPU %d, but the call runs on GPU %d", a.device,
+                     device);
+            g_last_error = buf;
+            return SPAMM_ERR_ARG;
+        }
+        *view = const_cast<void*>(p);
+    } else if (a.type == cudaMemoryTypeHost && a.devicePointer) {
+        *view = a.devicePointer;
+    }
+    return SPAMM_OK;
+}
+
+static int current_view(const void* p, void** view) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    return pointer_view(p, dev, view);
 }
 
 // ----------------------------------------------------------------------------
@@ -153,8 +173,10 @@ struct Plan {
                                    // tensor-core kernel per branch, [16 + 8 b ..] output-tile bucket counts
     double* partial = nullptr;     // [m*m]
     double* stage[3] = {nullptr, nullptr, nullptr};  // n*n row-major staging
-    // profiling: event pairs around each leaf-product kernel of a call
+    // profiling: event pairs around each leaf-product, cull, tree and slicing kernel of a call, and what
+    // each pair times (ProfKind)
     std::vector<cudaEvent_t> ev;
+    std::vector<int> ev_kind;
     int ev_used = 0;
     bool profile = false;
     long long gemm_launches = 0;
@@ -450,11 +472,14 @@ static spamm_opts resolve_opts(const spamm_opts* o) {
 
 // Device view of a caller matrix: the pointer itself (or its device mapping), or a staged copy.
 static int stage_in(Plan* p, int which, const double* src, cudaStream_t st, const double** dev) {
-    if (void* v = kernel_view(src)) {
+    void* v = nullptr;
+    int e = pointer_view(src, p->device, &v);
+    if (e) return e;
+    if (v) {
         *dev = static_cast<const double*>(v);
         return SPAMM_OK;
     }
-    int e = ensure_stage(p, which);
+    e = ensure_stage(p, which);
     if (e) return e;
     CK(cudaMemcpyAsync(p->stage[which], src, (size_t)p->g.n * p->g.n * sizeof(double), cudaMemcpyHostToDevice, st));
     *dev = p->stage[which];
@@ -462,11 +487,14 @@ static int stage_in(Plan* p, int which, const double* src, cudaStream_t st, cons
 }
 
 static int out_target(Plan* p, int which, double* dst, double** dev) {
-    if (void* v = kernel_view(dst)) {
+    void* v = nullptr;
+    int e = pointer_view(dst, p->device, &v);
+    if (e) return e;
+    if (v) {
         *dev = static_cast<double*>(v);
         return SPAMM_OK;
     }
-    int e = ensure_stage(p, which);
+    e = ensure_stage(p, which);
     if (e) return e;
     *dev = p->stage[which];
     return SPAMM_OK;
@@ -489,24 +517,72 @@ static void begin_call(Plan* p, bool profile, bool emu) {
     p->sliced_mask = 0;
 }
 
-static cudaEvent_t next_event(Plan* p) {
+// What a profiled event pair times.
+enum ProfKind { PROF_GEMM = 0, PROF_CULL = 1, PROF_TREE = 2, PROF_SLICE = 3 };
+
+static cudaEvent_t next_event(Plan* p, int kind) {
     if (p->ev_used == (int)p->ev.size()) {
         cudaEvent_t e;
         if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
         p->ev.push_back(e);
+        p->ev_kind.push_back(kind);
     }
+    p->ev_kind[p->ev_used] = kind;
     return p->ev[p->ev_used++];
 }
 
-// Summed duration of the profiled kernels (call after the stream is synchronised).
-static double profiled_ms(Plan* p) {
+// Summed duration of the profiled kernels of one kind, and how many were timed (call after the stream is
+// synchronised).
+static double profiled_ms(Plan* p, int kind, long long* count = nullptr) {
     double ms = 0.0;
+    long long c = 0;
     for (int q = 0; q + 1 < p->ev_used; q += 2) {
+        if (p->ev_kind[q] != kind) continue;
         float t = 0.f;
-        if (cudaEventElapsedTime(&t, p->ev[q], p->ev[q + 1]) == cudaSuccess) ms += t;
-        else cudaGetLastError();  // leave no error behind for the caller
+        if (cudaEventElapsedTime(&t, p->ev[q], p->ev[q + 1]) == cudaSuccess) {
+            ms += t;
+            ++c;
+        } else {
+            cudaGetLastError();  // leave no error behind for the caller
+        }
     }
+    if (count) *count = c;
     return ms;
+}
+
+// Events around the kernels enqueued on `st` while it lives, when the call is profiled.  Under stream capture
+// the records are "external", so that they become event-record nodes of the graph; an uncaptured call (a
+// single product) records plainly.
+struct ProfSpan {
+    cudaEvent_t e1 = nullptr;
+    cudaStream_t st = nullptr;
+    unsigned flags = cudaEventRecordDefault;
+    ProfSpan(Plan* p, cudaStream_t s, int kind) : st(s) {
+        if (!p->profile) return;
+        cudaEvent_t e0 = next_event(p, kind);
+        e1 = next_event(p, kind);
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+            flags = cudaEventRecordExternal;
+        if (e0 && e1) cudaEventRecordWithFlags(e0, st, flags);
+        else e1 = nullptr;
+    }
+    ~ProfSpan() {
+        if (e1) cudaEventRecordWithFlags(e1, st, flags);
+    }
+};
+
+// Profiled kernel times of the call into stats.
+static void profile_stats(Plan* p, spamm_stats* stats) {
+    if (!p->profile) {
+        stats->gemm_ms = stats->cull_ms = stats->tree_ms = stats->slice_ms = 0.0;
+        stats->cull_launches = stats->tree_launches = stats->slice_launches = 0;
+        return;
+    }
+    stats->gemm_ms = profiled_ms(p, PROF_GEMM);
+    stats->cull_ms = profiled_ms(p, PROF_CULL, &stats->cull_launches);
+    stats->tree_ms = profiled_ms(p, PROF_TREE, &stats->tree_launches);
+    stats->slice_ms = profiled_ms(p, PROF_SLICE, &stats->slice_launches);
 }
 
 // Tensor-core work issued by the call's leaf products (flags[30..31], cleared with the flags).
@@ -546,7 +622,10 @@ static void product(Plan* p, const TileMat& A, const TileMat& B, TileMat& C, dou
         co.zero_u64 = C.rmax;  // rmax and cmax, contiguous
         co.zero_n = 2 * (long)g.m * g.nb;
     }
-    launch_cull(g, A.tree, B.tree, tau, co, ctr, nullptr, p->flags, st);
+    {
+        ProfSpan ps(p, st, PROF_CULL);
+        launch_cull(g, A.tree, B.tree, tau, co, ctr, nullptr, p->flags, st);
+    }
     if (p->lens_bins > 0)
         launch_lens(counts, jlist, g, p->lens_bins, p->flags + 1, (int)(ctr - p->task_ctr), p->lens, p->flags, st);
     if (p->emu) {
@@ -555,26 +634,17 @@ static void product(Plan* p, const TileMat& A, const TileMat& B, TileMat& C, dou
         if (slicing_pending(p, A)) cudaStreamWaitEvent(st, A.sliced, 0);
         if (B.sliced != A.sliced && slicing_pending(p, B)) cudaStreamWaitEvent(st, B.sliced, 0);
     }
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    unsigned rec_flags = cudaEventRecordDefault;
-    if (p->profile) {
-        e0 = next_event(p);
-        e1 = next_event(p);
-        // "external" records become event-record nodes when the solve is captured into a graph; an
-        // uncaptured call (a single product) records plainly
-        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-        if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
-            rec_flags = cudaEventRecordExternal;
-        if (e0 && e1) cudaEventRecordWithFlags(e0, st, rec_flags);
+    {
+        ProfSpan ps(p, st, PROF_GEMM);
+        if (p->emu) {
+            launch_gemm_emu(g, A, B, C, counts, jlist, tile_list, tile_count, mode, p->trace_part,
+                            p->flags + 8 + 2 * slot, p->flags, p->flags + 2, tau, st, kTileBuckets,
+                            tensor_units(p));
+        } else {
+            launch_gemm_f64(g, A.t, B.t, C.t, A.tree, B.tree, C.tree, counts, jlist, tile_list, tile_count, 0,
+                            mode, p->trace_part, p->flags, st, kTileBuckets);
+        }
     }
-    if (p->emu) {
-        launch_gemm_emu(g, A, B, C, counts, jlist, tile_list, tile_count, mode, p->trace_part,
-                        p->flags + 8 + 2 * slot, p->flags, p->flags + 2, tau, st, kTileBuckets, tensor_units(p));
-    } else {
-        launch_gemm_f64(g, A.t, B.t, C.t, A.tree, B.tree, C.tree, counts, jlist, tile_list, tile_count, 0,
-                        mode, p->trace_part, p->flags, st, kTileBuckets);
-    }
-    if (e0 && e1) cudaEventRecordWithFlags(e1, st, rec_flags);
     p->gemm_launches++;
     // X's map whose coefficients need the finished tr X: in place, with T's leaf norms (and maxima)
     if (mode == EPI_X) launch_map(C.t, C.tree, C, g, map, p->trace_part, p->emu, p->flags, st);
@@ -588,13 +658,17 @@ static void product(Plan* p, const TileMat& A, const TileMat& B, TileMat& C, dou
             cudaStreamWaitEvent(ss, p->ev_norm[slot], 0);
         }
         const int mm = g.m * g.m;
-        launch_slice(C.t, C.tree, nullptr, C.rmax, C.cmax, C.sliceA, C.sliceB, g, C.slice_list,
-                     C.slice_list + mm, p->flags, ss);
+        {
+            ProfSpan ps(p, ss, PROF_SLICE);
+            launch_slice(C.t, C.tree, nullptr, C.rmax, C.cmax, C.sliceA, C.sliceB, g, C.slice_list,
+                         C.slice_list + mm, p->flags, ss);
+        }
         mark_sliced(p, C, ss);
     }
     TreeExtra ex = tk ? *tk : TreeExtra();
     ex.zero_int = tile_count;
     ex.zero_n = kTileBuckets;
+    ProfSpan ps(p, st, PROF_TREE);
     launch_tree(g, C.tree, p->flags, st, ex);
 }
 
@@ -664,7 +738,7 @@ static int multiply_core(const double* A, const double* B, double* C, int n, dou
         stats->tasks_total = (long long)tasks;
         stats->tasks_dense = (long long)g.m * g.m * g.m;
         stats->flops = 2.0 * (double)g.nb * g.nb * g.nb * (double)tasks;
-        stats->gemm_ms = p->profile ? profiled_ms(p) : 0.0;
+        profile_stats(p, stats);
         stats->gemm_launches = p->gemm_launches;
         unsigned long long units = 0;
         std::memcpy(&units, flags_h + 30, sizeof(units));
@@ -1160,7 +1234,7 @@ static int sqrt_impl(const double* S, int n, double tau, int maxit, double* Y, d
             const size_t cnt = (size_t)iters * 9 * p->lens_bins;
             CK(cudaMemcpy(stats->lens_hist, p->lens, cnt * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
         }
-        stats->gemm_ms = p->profile ? profiled_ms(p) : 0.0;
+        profile_stats(p, stats);
         stats->gemm_launches = p->gemm_launches;
         unsigned long long units = 0;
         std::memcpy(&units, flags_h + 30, sizeof(units));
@@ -1171,6 +1245,13 @@ static int sqrt_impl(const double* S, int n, double tau, int maxit, double* Y, d
             g_last_error = "trace error left [0, 1): the iteration diverged";
             return SPAMM_ERR_DIVERGED;
         }
+    // The trace error follows X = YZ, which stays near I even when culling has moved Y and Z off the
+    // square roots of S.  With the residual computed, ||Z S Z - I||_F >= 1 says so: Z is then outside the
+    // region ||I - Z S Z|| < 1 in which a further Newton-Schulz refinement is guaranteed to converge.
+    if (o.residual && !(resid < 1.0)) {
+        g_last_error = "||Z S Z - I||_F >= 1: Z is no longer an approximate inverse square root of S";
+        return SPAMM_ERR_DIVERGED;
+    }
     if (o.tol_t > 0.0 && !(std::fabs(t_final) <= o.tol_t)) {
         g_last_error = "maxit reached before |t_k| <= tol_t";
         return SPAMM_ERR_NOTCONVERGED;
@@ -1261,7 +1342,12 @@ static int invsqrt_product_impl(const double* S, int n, int levels, const double
     CKA(cs.get(&dT, bytes));
     CKA(cs.get(&rowsum, (size_t)n * sizeof(double)));
     CKA(cs.get(&c0, sizeof(double)));
-    const double* dS = static_cast<const double*>(kernel_view(S));
+    void* vS = nullptr;
+    int ev = current_view(S, &vS);
+    if (ev) return ev;
+    void* vZ = nullptr;
+    if ((ev = current_view(Z, &vZ))) return ev;
+    const double* dS = static_cast<const double*>(vS);
     if (!dS) {
         double* st_S;
         CKA(cs.get(&st_S, bytes));

@@ -242,6 +242,9 @@ struct spamm_opts;
 struct spamm_stats;
 namespace spamm {
 size_t plan_footprint(int n, int nb, int precision, bool host_io);
+// Address the kernels use for caller matrix p in work on `device` (null: pageable host memory, staged);
+// SPAMM_ERR_ARG for device memory of another GPU.
+int pointer_view(const void* p, int device, void** view);
 int run_sqrt(const double* S, int n, double tau, int maxit, double* Y, double* Z, const spamm_opts& o,
              spamm_stats* stats);
 int check_args(int n, double tau, const spamm_opts& o);

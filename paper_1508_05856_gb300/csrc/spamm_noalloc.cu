@@ -67,13 +67,18 @@ int scratch_address(double** out) {
     return SPAMM_OK;
 }
 
+// Device memory of the current device, or managed memory.  Device memory of another GPU is refused: without
+// peer access the kernels could not reach it.
 bool on_device(const void* p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    if (a.type != cudaMemoryTypeDevice) return false;
+    int cur = -1;
+    return cudaGetDevice(&cur) == cudaSuccess && a.device == cur;
 }
 
 }  // namespace
@@ -94,7 +99,7 @@ extern "C" int spamm_multiply_noalloc(const double* A, const double* B, double* 
         return SPAMM_ERR_UNSUPPORTED;
     }
     if (!A || !B || !C || !on_device(A) || !on_device(B) || !on_device(C)) {
-        set_error_message("A, B and C must be device pointers");
+        set_error_message("A, B and C must be device pointers of the current device");
         return SPAMM_ERR_ARG;
     }
     double* base = nullptr;

@@ -44,15 +44,6 @@ struct Request {
     Clock::time_point t_submit, t_done;
 };
 
-bool on_device(const void* p) {
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
 }  // namespace
 }  // namespace spamm
 
@@ -153,7 +144,14 @@ int spamm_server_submit(spamm_server* s, const double* S, int n, double tau, int
     }
     int st = check_args(n, tau, s->opts);
     if (st) return st;
-    const bool host_io = !on_device(S) || !on_device(Y) || !on_device(Z);
+    // device memory of another GPU is refused; host memory (pageable: staged) adds staging to the footprint
+    void* vS = nullptr;
+    void* vY = nullptr;
+    void* vZ = nullptr;
+    if ((st = pointer_view(S, s->device, &vS)) || (st = pointer_view(Y, s->device, &vY)) ||
+        (st = pointer_view(Z, s->device, &vZ)))
+        return st;
+    const bool host_io = !vS || !vY || !vZ;
     const size_t bytes = plan_footprint(n, s->opts.leaf, s->opts.precision, host_io);
     if (bytes > s->budget) {
         set_error_message("the request's device footprint exceeds the server's memory budget");

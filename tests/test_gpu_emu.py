@@ -95,6 +95,24 @@ def test_emu_ns_transposed_order():
     assert ez <= 1e-9 and ey <= 1e-9, (ez, ey)
 
 
+def test_emu_ns_benchmark_configuration():
+    """The configuration the benchmark times, against the oracle at full size: KMS rho 0.9, N 4096, N_b 64,
+    tau 1e-14, tau_s 1e-16, 30 iterations of the dual channel with tensor-core leaf products.  Every
+    per-iteration task count equals the oracle's (no triple of any product lies near enough to its threshold
+    for the two arithmetics to decide it differently), Y and Z agree to the tensor-core path's 1e-9, and the
+    residual meets the 1e-8 gate."""
+    S = synth.kms(4096, 0.9)
+    Y, Z, st = sp.sqrt_invsqrt(dev(S), 1e-14, 30, leaf=64, precision=sp.EMU64, residual=True)
+    ref = oracle.sqrt_invsqrt(S, 64, 1e-14, 30)
+    assert st["iters"] == ref["iters"] == 30
+    np.testing.assert_array_equal(st["task_hist"], ref["task_hist"])
+    ez = np.linalg.norm(Z.cpu().numpy() - ref["Z"]) / np.linalg.norm(ref["Z"])
+    ey = np.linalg.norm(Y.cpu().numpy() - ref["Y"]) / np.linalg.norm(ref["Y"])
+    assert ez <= 1e-9 and ey <= 1e-9, (ez, ey)
+    assert st["resid_F"] <= 1e-8, st["resid_F"]
+    np.testing.assert_allclose(st["t_hist"], ref["t_hist"], rtol=0, atol=1e-12)
+
+
 def test_emu_ns_residual_gate():
     S = synth.kms(1024, 0.9)
     Y, Z, st = sp.sqrt_invsqrt(dev(S), 1e-14, 30, leaf=64, precision=sp.EMU64, residual=True)

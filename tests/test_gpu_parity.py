@@ -195,6 +195,43 @@ def test_ns_kms_4096_full_size():
     _ns_compare(S, 64, 1e-8, 30)
 
 
+def test_ns_kms_4096_benchmark_tau():
+    """The benchmark's configuration on the FP64 path (KMS rho 0.9, N 4096, N_b 64, tau 1e-14, 30
+    iterations): Y and Z within 1e-10 of the oracle, every per-iteration task count equal."""
+    S = synth.kms(4096, 0.9)
+    Y, Z, st, ref = _ns_compare(S, 64, 1e-14, 30)
+    np.testing.assert_array_equal(st["task_hist"], ref["task_hist"])
+
+
+def test_residual_at_least_one_is_reported_as_divergence():
+    """At tau 1e-4 culling carries Y and Z off the roots while X = YZ still looks converged: the residual
+    ||ZSZ - I||_F exceeds 1 and the call reports SPAMM_ERR_DIVERGED (outputs written).  The oracle's solve
+    shows the same residual, so this is the method at that threshold, not the GPU."""
+    S = synth.kms(1024, 0.9)
+    Y, Z, st = sp.sqrt_invsqrt(dev(S), 1e-4, 30, leaf=64, residual=True, raise_on=False)
+    ref = oracle.sqrt_invsqrt(S, 64, 1e-4, 30)
+    r_or = oracle.residual(S, ref["Z"])
+    assert r_or >= 1.0 and abs(ref["t_hist"][-1]) < 1e-12
+    assert st["status"] == -3
+    assert st["resid_F"] == pytest.approx(r_or, rel=1e-6)
+    Y, Z, st = sp.sqrt_invsqrt(dev(S), 1e-12, 30, leaf=64, residual=True, raise_on=False)
+    assert st["status"] == 0 and st["resid_F"] < 1.0
+
+
+@pytest.mark.skipif(not torch.cuda.is_available() or torch.cuda.device_count() < 2,
+                    reason="needs a second GPU to hold memory the current device cannot reach")
+def test_device_memory_of_another_gpu_is_an_argument_error():
+    """Only pointer attributes are read: no kernel sees the other GPU's memory."""
+    other = torch.zeros((64, 64), dtype=torch.float64, device="cuda:1")
+    here = torch.zeros((64, 64), dtype=torch.float64, device="cuda:0")
+    with torch.cuda.device(0):
+        with pytest.raises(sp.SpammError) as ei:
+            sp.multiply(other, here, 0.0, leaf=32, out=here.clone())
+        assert ei.value.status == -1
+        assert sp.lib().spamm_multiply_noalloc(other.data_ptr(), here.data_ptr(), here.data_ptr(), 64, 0.0, 32,
+                                               None) == -1
+
+
 def test_graph_replay_identical_and_profiled():
     """Repeated fixed-iteration solves replay a captured CUDA graph: identical results, kernel timings recorded,
     and no CUDA error left behind for the caller."""
