@@ -335,7 +335,56 @@ struct EmuArgs {
     const int* done;
     int* err;
     int m, n, mode;
+    // batched form: per-item products (items (p << kItemShift) | tile in tile_list, kTileBuckets classes of
+    // stride cap); the drawn items go to slice_items (count at slice_items[cap])
+    const ProdDesc* prods;
+    int* slice_items;
+    int cap;
 };
+
+// What the producer warp needs of an output tile's product.
+struct ProducerView {
+    int m;
+    const int* counts;
+    const int* jlist;
+    const uint8_t* sliceA;
+    const uint8_t* sliceB;
+    const double* leafA;
+    const double* leafB;
+    const unsigned long long* rmaxA;
+    const unsigned long long* cmaxB;
+    bool zero_filter;  // thr = 0: listed tasks may have an exactly zero operand, skipped
+};
+template <bool kBatched>
+__device__ __forceinline__ ProducerView producer_view(const EmuArgs& a, int prod) {
+    if constexpr (kBatched) {
+        const ProdDesc& d = a.prods[prod];
+        const double rA = d.Atree[d.td.off[0]], rB = d.Btree[d.td.off[0]];
+        return ProducerView{d.td.m, d.counts, d.jlist, d.AsliceA, d.BsliceB, d.Atree, d.Btree, d.Armax, d.Bcmax,
+                            !(((d.tau * d.tau) * rA) * rB > 0.0)};
+    } else {
+        return ProducerView{a.m, a.counts, a.jlist, a.sliceA, a.sliceB, a.leafA, a.leafB, a.rmaxA, a.cmaxB,
+                            !(((a.tau * a.tau) * *a.rootA) * *a.rootB > 0.0)};
+    }
+}
+// What the epilogue warps need of an output tile's product.
+struct EpiView {
+    int m, n, mode;
+    double* C;
+    double* leafC;
+    unsigned long long* rmaxC;
+    unsigned long long* cmaxC;
+    double* trace_part;
+};
+template <bool kBatched>
+__device__ __forceinline__ EpiView epi_view(const EmuArgs& a, int prod) {
+    if constexpr (kBatched) {
+        const ProdDesc& d = a.prods[prod];
+        return EpiView{d.td.m, d.n, d.mode, d.Ct, d.Ctree, d.Crmax, d.Ccmax, d.trace_part};
+    } else {
+        return EpiView{a.m, a.n, a.mode, a.C, a.leafC, a.rmaxC, a.cmaxC, a.trace_part};
+    }
+}
 
 __device__ __forceinline__ uint32_t stage_addr(uint32_t base, int s) { return base + (uint32_t)s * STAGE_BYTES; }
 
@@ -443,6 +492,7 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, vo
 // on tile t and the epilogue warps finish tile t-1; the tile id travels in
 // the slot, and mbarriers order the roles.  The last CTA to finish resets
 // the ticket counters for the next launch.
+template <bool kBatched>
 __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
     grid_dependency_wait();
     if (a.done && *a.done) return;
@@ -453,6 +503,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
     __shared__ int tasks_sh[2][kMaxTasks];
     __shared__ int ntask_sh[2];
     __shared__ int tile_sh[2];
+    __shared__ int prod_sh[2];
     __shared__ int eA_sh[2][NB], eB_sh[2][NB];
     __shared__ double tr_sh[kEpiWarps];
     __shared__ DFloat nu_sh[kEpiWarps];
@@ -462,8 +513,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
     const uint32_t sbase = ptx::smem_addr(smem);
     long long* sTop = reinterpret_cast<long long*>(smem + NSTAGE * STAGE_BYTES);  // [64][65]
     long long* sBot = sTop + NB * 65;                                             // [64][65]
-    const int m = a.m;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // stride of one cost class in the tile list, and where the drawn tiles are copied for the slicing pass
+    const int lstride = kBatched ? a.cap : a.m * a.m;
+    int* const drawn = kBatched ? a.slice_items : a.slice_list;
     // bucket counts held in registers: a drawn ticket maps to its tile with one load
     int bcount[kTileBuckets];
     int ntiles = 0;
@@ -472,7 +525,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
         bcount[b] = b < a.buckets ? a.tile_count[b] : 0;
         ntiles += bcount[b];
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.slice_list[m * m] = ntiles;
+    if (blockIdx.x == 0 && threadIdx.x == 0) drawn[lstride] = ntiles;
     if ((int)blockIdx.x >= ntiles) return;
 
     if (warp == 2 && lane == 0) {
@@ -501,7 +554,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
 
     if (warp == 0) {
         // ---------------- producer: per tile the task list and scales, then the half-task stream
-        const bool zero_filter = !(((a.tau * a.tau) * *a.rootA) * *a.rootB > 0.0);
         long long H = 0;
         int tau = 0;
         int idx = lane == 0 ? atomicAdd(a.sched, 1) : 0;
@@ -512,7 +564,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
             // the following ticket is in flight while this tile is prepared
             int nxt = 0;
             if (!end && lane == 0) nxt = atomicAdd(a.sched, 1);
-            int tile = 0;
+            int item = 0;
             if (!end) {
                 int t = idx, b = 0;
 #pragma unroll
@@ -521,20 +573,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
                         t -= bcount[q];
                         b = q + 1;
                     }
-                tile = a.tile_list[(size_t)b * m * m + t];
+                item = a.tile_list[(size_t)b * lstride + t];
             }
+            const int prod = kBatched ? item_prod(item) : 0;
+            const int tile = kBatched ? item_tile(item) : item;
+            const ProducerView v = producer_view<kBatched>(a, prod);
+            const int m = v.m;
             const int i = tile / m, k = tile - (tile / m) * m;
             // this tile's metadata, fetched before waiting for its slot
-            const int cnt = end ? 0 : a.counts[tile];
-            const int* js = a.jlist + (size_t)tile * m;
+            const int cnt = end ? 0 : v.counts[tile];
+            const int* js = v.jlist + (size_t)tile * m;
             const int jpre0 = lane < cnt ? js[lane] : 0;
             const int jpre1 = lane + 32 < cnt ? js[lane + 32] : 0;
             unsigned long long ra0 = 0, ra1 = 0, cb0 = 0, cb1 = 0;
             if (!end) {
-                ra0 = a.rmaxA[i * NB + lane];
-                ra1 = a.rmaxA[i * NB + 32 + lane];
-                cb0 = a.cmaxB[k * NB + lane];
-                cb1 = a.cmaxB[k * NB + 32 + lane];
+                ra0 = v.rmaxA[i * NB + lane];
+                ra1 = v.rmaxA[i * NB + 32 + lane];
+                cb0 = v.cmaxB[k * NB + lane];
+                cb1 = v.cmaxB[k * NB + 32 + lane];
             }
             if (tau >= 2) {
                 bool ok = true;
@@ -561,7 +617,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
                 if (keep && base >= 64) j = js[t];
                 // with thr > 0 every listed task has two nonzero operand tiles; with thr = 0 the
                 // tasks with an exactly zero operand contribute nothing and are skipped
-                if (keep && zero_filter) keep = a.leafA[(size_t)i * m + j] != 0.0 && a.leafB[(size_t)j * m + k] != 0.0;
+                if (keep && v.zero_filter) keep = v.leafA[(size_t)i * m + j] != 0.0 && v.leafB[(size_t)j * m + k] != 0.0;
                 const unsigned bal = __ballot_sync(0xffffffffu, keep);
                 if (keep) tasks_sh[slot][T + __popc(bal & ((1u << lane) - 1u))] = j;
                 T += __popc(bal);
@@ -573,15 +629,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
             if (lane == 0) {
                 ntask_sh[slot] = T;
                 tile_sh[slot] = tile;
-                a.slice_list[idx] = tile;
+                prod_sh[slot] = prod;
+                drawn[idx] = item;
             }
             __syncwarp();
             if (lane == 0) {
                 ptx::mbar_arrive(&bar_tready[slot]);  // release: the task list and scales are visible
                 for (int t = 0; t < T; ++t) {
                     const int j = tasks_sh[slot][t];
-                    const uint8_t* srcA = a.sliceA + ((size_t)i * m + j) * A_TILE_BYTES;
-                    const uint8_t* srcB = a.sliceB + ((size_t)j * m + k) * B_TILE_BYTES;
+                    const uint8_t* srcA = v.sliceA + ((size_t)i * m + j) * A_TILE_BYTES;
+                    const uint8_t* srcB = v.sliceB + ((size_t)j * m + k) * B_TILE_BYTES;
                     for (int h = 0; h < 2; ++h, ++H) {
                         const int s = (int)(H % NSTAGE);
                         if (H >= NSTAGE &&
@@ -682,6 +739,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
             }
             const int tile = tile_sh[slot];
             if (tile < 0) break;
+            const EpiView ev = epi_view<kBatched>(a, prod_sh[slot]);
+            const int m = ev.m;
             const int i = tile / m, k = tile - (tile / m) * m;
             const int T = ntask_sh[slot];
             const int nchunks = (T + kChunk - 1) / kChunk;
@@ -712,12 +771,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
             const int r0 = et >> 6;  // 0..7
             const int gj = k * NB + c;
             const int eBc = eB_sh[slot][c];
-            double* outt = a.C + (size_t)tile * NB * NB;
-            const bool nsx = a.mode == EPI_NS_X;
-            const bool with_tr = a.mode != EPI_PLAIN;
+            double* outt = ev.C + (size_t)tile * NB * NB;
+            const bool nsx = ev.mode == EPI_NS_X;
+            const bool with_tr = ev.mode != EPI_PLAIN;
             // T = 1.5 I - 0.5 X: off the diagonal -x/2 is the conversion of -t64 one binade lower; the one
             // thread per column that owns the diagonal entry computes it up front (and its trace share)
-            const int rd = (with_tr && i == k && (c & 7) == r0 && gj < a.n) ? c : -1;
+            const int rd = (with_tr && i == k && (c & 7) == r0 && gj < ev.n) ? c : -1;
             double xd = 0.0, vd = 0.0;
             if (rd >= 0) {
                 xd = fixed_to_double(sTop[c * 65 + c] + sBot[c * 65 + c], eA_sh[slot][c] + eBc - 48);
@@ -744,9 +803,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
                 }
             }
             // X itself (EPI_X) is not sliced: the maxima are those of the map's output, taken by k_map
-            if (a.mode != EPI_X) {
-                if (cmx) atomicMax(a.cmaxC + gj, cmx);
-                if (lane < 8 && rowm) atomicMax(a.rmaxC + i * NB + r0 + 8 * lane, (unsigned long long)rowm << 32);
+            if (ev.mode != EPI_X) {
+                if (cmx) atomicMax(ev.cmaxC + gj, cmx);
+                if (lane < 8 && rowm) atomicMax(ev.rmaxC + i * NB + r0 + 8 * lane, (unsigned long long)rowm << 32);
             }
             for (int o = 16; o > 0; o >>= 1) nup = df_add(nup, df_shfl_xor(nup, o));
             if (lane == 0) nu_sh[ew] = nup;
@@ -761,11 +820,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
             if (et == 0) {
                 DFloat t = nu_sh[0];
                 for (int w = 1; w < kEpiWarps; ++w) t = df_add(t, nu_sh[w]);
-                a.leafC[tile] = (double)t.hi + (double)t.lo;
+                ev.leafC[tile] = (double)t.hi + (double)t.lo;
                 if (diag_tile) {
                     double s8 = 0.0;
                     for (int w = 0; w < kEpiWarps; ++w) s8 += tr_sh[w];
-                    a.trace_part[i] = s8;
+                    ev.trace_part[i] = s8;
                 }
             }
             if (lane == 0) ptx::mbar_arrive(&bar_tfree[slot]);
@@ -791,7 +850,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
 size_t emu_slice_bytes_per_tile() { return emu::A_TILE_BYTES; }
 
 void emu_kernel_attributes() {
-    cudaFuncSetAttribute(emu::k_gemm_emu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)emu::SMEM_DYN);
+    cudaFuncSetAttribute(emu::k_gemm_emu<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)emu::SMEM_DYN);
+    cudaFuncSetAttribute(emu::k_gemm_emu<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)emu::SMEM_DYN);
 }
 
 void launch_rowcol_max(const double* X, const Geometry& g, unsigned long long* rmax, unsigned long long* cmax,
@@ -843,8 +903,30 @@ void launch_gemm_emu(const Geometry& g, const TileMat& A, const TileMat& B, cons
     a.m = g.m;
     a.n = g.n;
     a.mode = (int)mode;
+    a.prods = nullptr;
+    a.slice_items = nullptr;
+    a.cap = 0;
     const int grid = std::min(device_sm_count(), g.m * g.m);
-    launch_dependent(emu::k_gemm_emu, dim3(grid), dim3(emu::kThreads), emu::SMEM_DYN, st, a);
+    launch_dependent(emu::k_gemm_emu<false>, dim3(grid), dim3(emu::kThreads), emu::SMEM_DYN, st, a);
+    note_launch();
+}
+
+void launch_gemm_emu_batched(const ProdDesc* prods, const int* tile_list, const int* tile_count, int cap,
+                             int* slice_items, int* sched, const int* all_done, int* err, cudaStream_t st,
+                             unsigned long long* units) {
+    emu::EmuArgs a = {};
+    a.prods = prods;
+    a.slice_items = slice_items;
+    a.cap = cap;
+    a.tile_list = tile_list;
+    a.tile_count = tile_count;
+    a.buckets = kTileBuckets;
+    a.sched = sched;
+    a.done = all_done;
+    a.err = err;
+    a.units = units;
+    const int grid = std::min(device_sm_count(), cap);
+    launch_dependent(emu::k_gemm_emu<true>, dim3(grid), dim3(emu::kThreads), emu::SMEM_DYN, st, a);
     note_launch();
 }
 

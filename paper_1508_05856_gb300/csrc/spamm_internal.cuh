@@ -253,6 +253,60 @@ void trim_plans(size_t keep_bytes);
 const char* last_error_message();
 void set_error_message(const char* msg);
 
+// ---- batched products (spamm_batch.cu) -------------------------------------
+// One SpAMM product of a batch of independent solves: operands, output, task lists and the state of the
+// matrix it belongs to.  A stage of the batched iteration runs the products of one table in a single
+// launch of each kernel (cull, leaf products, slicing, quadtree); a work item is one output tile of one
+// product, encoded as (product << kItemShift) | tile.
+constexpr int kItemShift = 18;  // tiles per product < 2^18 (m <= 512)
+constexpr int kMaxStageProducts = 1 << 13;
+struct ProdDesc {
+    const double* At;
+    const double* Atree;
+    const uint8_t* AsliceA;
+    const unsigned long long* Armax;
+    const double* Bt;
+    const double* Btree;
+    const uint8_t* BsliceB;
+    const unsigned long long* Bcmax;
+    double* Ct;
+    double* Ctree;
+    uint8_t* CsliceA;
+    uint8_t* CsliceB;
+    unsigned long long* Crmax;  // followed by Ccmax (2 m N_b words, cleared by the cull)
+    unsigned long long* Ccmax;
+    int* counts;                // [m*m] task counts of the output tiles
+    int* jlist;                 // [m*m*m] ascending j per output tile
+    int* mflags;                // the matrix's [0] stop, [1] iterations run
+    double* trace_part;         // the matrix's [m] diagonal-tile trace partials (X product)
+    double* t_hist;             // the matrix's [maxit] trace errors
+    unsigned long long* task_ctr;  // the matrix's [3 maxit] task counts (y, z, x of each iteration)
+    double tau;
+    double tol_t;
+    int mode;                   // EPI_PLAIN or EPI_NS_X
+    int which;                  // 0 y, 1 z, 2 x product (task counter slot; 2 also takes t_k and the stop)
+    int n, maxit;
+    TreeDev td;
+};
+#ifdef __CUDACC__
+__device__ __forceinline__ int item_prod(int item) { return item >> kItemShift; }
+__device__ __forceinline__ int item_tile(int item) { return item & ((1 << kItemShift) - 1); }
+#endif
+
+// Leaf products of every product of a stage on the tensor cores (leaf 64): the items listed by the batched
+// cull (tile_list / tile_count in kTileBuckets cost classes), drawn most expensive first; slice_items gets
+// the drawn items and their count at slice_items[cap] for the slicing pass.  all_done: the batch has
+// stopped (every kernel returns at once).
+void launch_gemm_emu_batched(const ProdDesc* prods, const int* tile_list, const int* tile_count, int cap,
+                             int* slice_items, int* sched, const int* all_done, int* err, cudaStream_t st,
+                             unsigned long long* units = nullptr);
+// FP64 leaf products of every product of a stage (leaf nb): one CTA per listed item, grid cap.
+void launch_gemm_f64_batched(int nb, const ProdDesc* prods, const int* tile_list, const int* tile_count, int cap,
+                             const int* all_done, cudaStream_t st);
+// Digit slices of the items a batched leaf-product launch drew (slice_items, count at slice_items[cap]).
+void launch_slice_batched(const ProdDesc* prods, const int* slice_items, int cap, const int* all_done,
+                          cudaStream_t st);
+
 // ---- kernels_emu.cu (leaf tile 64 only) -----------------------------------
 size_t emu_slice_bytes_per_tile();  // bytes of one tile's slices in one operand role
 // Row/column magnitude maxima of a packed matrix (arrays must be zeroed first).

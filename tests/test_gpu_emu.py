@@ -97,20 +97,31 @@ def test_emu_ns_transposed_order():
 
 def test_emu_ns_benchmark_configuration():
     """The configuration the benchmark times, against the oracle at full size: KMS rho 0.9, N 4096, N_b 64,
-    tau 1e-14, tau_s 1e-16, 30 iterations of the dual channel with tensor-core leaf products.  Every
-    per-iteration task count equals the oracle's (no triple of any product lies near enough to its threshold
-    for the two arithmetics to decide it differently), Y and Z agree to the tensor-core path's 1e-9, and the
-    residual meets the 1e-8 gate."""
+    tau 1e-14, tau_s 1e-16, 30 iterations of the dual channel with tensor-core leaf products.  Y and Z agree
+    with the oracle to the tensor-core path's 1e-9 and the residual meets the 1e-8 gate.
+
+    The task lists are not compared triple by triple here.  The tensor-core products are FP64-class
+    normwise: an entry carries an absolute error of a few 2^-48 of its row and column scale, whatever its own
+    size.  Far from the diagonal, where the FP64 products are many orders below that level, the tensor-core
+    products hold rounding noise at that level instead, and at tau_s = 1e-16 the y product's threshold sits
+    just below it: those noise tiles pass the cull and add leaf products (measured: 17 % more over the solve,
+    up to 3x in single late products), each contributing below tau_s ||T|| ||Y||.  So the test bounds the
+    solve's task total to [0.95, 1.25] x the oracle's; the FP64 path's lists are compared exactly
+    (test_ns_kms_4096_benchmark_tau)."""
     S = synth.kms(4096, 0.9)
     Y, Z, st = sp.sqrt_invsqrt(dev(S), 1e-14, 30, leaf=64, precision=sp.EMU64, residual=True)
     ref = oracle.sqrt_invsqrt(S, 64, 1e-14, 30)
-    assert st["iters"] == ref["iters"] == 30
-    np.testing.assert_array_equal(st["task_hist"], ref["task_hist"])
     ez = np.linalg.norm(Z.cpu().numpy() - ref["Z"]) / np.linalg.norm(ref["Z"])
     ey = np.linalg.norm(Y.cpu().numpy() - ref["Y"]) / np.linalg.norm(ref["Y"])
+    kg = np.asarray(st["task_hist"], dtype=np.float64)
+    ko = np.asarray(ref["task_hist"], dtype=np.float64)
+    print(f"ez {ez:.3e} ey {ey:.3e} resid {st['resid_F']:.3e} tasks gpu {kg.sum():.0f} oracle {ko.sum():.0f} "
+          f"max per-product rel diff {np.max(np.abs(kg - ko) / np.maximum(ko, 1)):.3f}")
+    assert st["iters"] == ref["iters"] == 30
     assert ez <= 1e-9 and ey <= 1e-9, (ez, ey)
     assert st["resid_F"] <= 1e-8, st["resid_F"]
     np.testing.assert_allclose(st["t_hist"], ref["t_hist"], rtol=0, atol=1e-12)
+    assert 0.95 * ko.sum() <= kg.sum() <= 1.25 * ko.sum()
 
 
 def test_emu_ns_residual_gate():
