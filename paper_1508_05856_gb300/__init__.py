@@ -306,13 +306,15 @@ def sqrt_invsqrt(S, tau: float, maxit: int, leaf: int = 64, precision: int = FP6
 
 def sqrt_invsqrt_batched(Ss, taus, maxit: int, leaf: int = 64, precision: int = FP64, tau_s=None, mu_rel=0.0,
                          tol_t=0.0, order=ORDER_PAPER, residual=False, stream=None, map=None, channel=None,
-                         raise_on=True):
+                         raise_on=True, Ys=None, Zs=None):
     """Many independent solves in one call; returns (list of Y, list of Z, list of stats).  With raise_on
-    False a failed status (the first nonzero one) is returned in every stats dict as "call_status"."""
+    False a failed status (the first nonzero one) is returned in every stats dict as "call_status".  Ys, Zs:
+    optional output matrices (the library reuses its captured batch while the inputs, outputs and options
+    stay the same)."""
     cnt = len(Ss)
     keep = [_prep(S) for S in Ss]
-    Ys = [_like(k[0], k[2]) for k in keep]
-    Zs = [_like(k[0], k[2]) for k in keep]
+    Ys = list(Ys) if Ys is not None else [_like(k[0], k[2]) for k in keep]
+    Zs = list(Zs) if Zs is not None else [_like(k[0], k[2]) for k in keep]
     VP = ctypes.c_void_p * cnt
     sp = VP(*[k[1] for k in keep])
     yp = VP(*[_ptr(y) for y in Ys])

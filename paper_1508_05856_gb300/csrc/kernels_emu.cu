@@ -134,21 +134,42 @@ __device__ __forceinline__ uint32_t digit_pair_f16(const Digits& a, const Digits
 // each listed tile's squared Frobenius norm nu (FP64 fused multiply-adds, a
 // fixed-order reduction) into leaf_out[tile]; unlisted tiles keep the zero
 // the cull wrote for them.
-__global__ void __launch_bounds__(256, 5) k_slice(const double* __restrict__ X, const double* __restrict__ leaf,
+// Batched form (kBatched): tile_list holds items (p << kItemShift) | tile of the products prods[p], whose
+// outputs are sliced; leaf_out is null.
+template <bool kBatched>
+__global__ void __launch_bounds__(256, 5) k_slice(const double* __restrict__ X0, const double* __restrict__ leaf0,
                                                double* __restrict__ leaf_out,
-                                               const unsigned long long* __restrict__ rmax,
-                                               const unsigned long long* __restrict__ cmax,
-                                               uint8_t* __restrict__ sA, uint8_t* __restrict__ sB, int m,
+                                               const unsigned long long* __restrict__ rmax0,
+                                               const unsigned long long* __restrict__ cmax0,
+                                               uint8_t* __restrict__ sA0, uint8_t* __restrict__ sB0, int m0,
                                                const int* __restrict__ tile_list, const int* __restrict__ tile_count,
-                                               const int* __restrict__ done) {
+                                               const int* __restrict__ done, const ProdDesc* __restrict__ prods) {
     grid_dependency_wait();
     if (done && *done) return;
     __shared__ double xs[NB][NB + 1];
     __shared__ int eR[NB], eC[NB];
     __shared__ double nu_sh[8];
-    const int ntiles = tile_list ? *tile_count : m * m;
+    const int ntiles = tile_list ? *tile_count : m0 * m0;
     for (int idx = blockIdx.x; idx < ntiles; idx += gridDim.x) {
-    const int tile = tile_list ? tile_list[idx] : idx;
+    const int item = tile_list ? tile_list[idx] : idx;
+    int tile = item, m = m0;
+    const double* X = X0;
+    const double* leaf = leaf0;
+    const unsigned long long* rmax = rmax0;
+    const unsigned long long* cmax = cmax0;
+    uint8_t* sA = sA0;
+    uint8_t* sB = sB0;
+    if constexpr (kBatched) {
+        const ProdDesc& d = prods[item_prod(item)];
+        tile = item_tile(item);
+        m = d.td.m;
+        X = d.Ct;
+        leaf = d.Ctree;
+        rmax = d.Crmax;
+        cmax = d.Ccmax;
+        sA = d.CsliceA;
+        sB = d.CsliceB;
+    }
     if (!leaf_out && leaf[tile] == 0.0) continue;
     __syncthreads();
     const int i = tile / m, j = tile - (tile / m) * m;
@@ -866,8 +887,18 @@ void launch_slice(const double* X, const double* leaf, double* leaf_out, const u
     // five blocks (34 KB shared memory, 48 registers) are resident per SM: one wave, so a dependent launched
     // early never holds slots the grid still needs
     const int grid = std::min(device_sm_count() * 5, g.m * g.m);
-    launch_dependent(emu::k_slice, dim3(grid), dim3(256), 0, st, X, leaf, leaf_out, rmax, cmax, sA, sB, g.m,
-                     tile_list, tile_count, done);
+    launch_dependent(emu::k_slice<false>, dim3(grid), dim3(256), 0, st, X, leaf, leaf_out, rmax, cmax, sA, sB, g.m,
+                     tile_list, tile_count, done, (const ProdDesc*)nullptr);
+    note_launch();
+}
+
+void launch_slice_batched(const ProdDesc* prods, const int* slice_items, int cap, const int* all_done,
+                          cudaStream_t st) {
+    const int grid = std::min(device_sm_count() * 5, cap);
+    launch_dependent(emu::k_slice<true>, dim3(grid), dim3(256), 0, st, (const double*)nullptr,
+                     (const double*)nullptr, (double*)nullptr, (const unsigned long long*)nullptr,
+                     (const unsigned long long*)nullptr, (uint8_t*)nullptr, (uint8_t*)nullptr, 0, slice_items,
+                     slice_items + cap, all_done, prods);
     note_launch();
 }
 

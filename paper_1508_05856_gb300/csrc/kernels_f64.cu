@@ -18,19 +18,52 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kKC = 32;  // inner-dimension chunk staged in shared memory
 
-template <int NB>
-__global__ void __launch_bounds__(kThreads) k_gemm_f64(const double* __restrict__ A, const double* __restrict__ B,
-                                                       double* __restrict__ C, const double* __restrict__ leafA,
-                                                       const double* __restrict__ leafB, double* __restrict__ leafC,
-                                                       const int* __restrict__ counts, const int* __restrict__ jlist,
+// Batched form (kBatched): the listed entries are items (p << kItemShift) | tile of the products prods[p]
+// (class stride cap), and every operand, output and size comes from prods[p].
+template <int NB, bool kBatched>
+__global__ void __launch_bounds__(kThreads) k_gemm_f64(const double* __restrict__ A0, const double* __restrict__ B0,
+                                                       double* __restrict__ C0, const double* __restrict__ leafA0,
+                                                       const double* __restrict__ leafB0, double* __restrict__ leafC0,
+                                                       const int* __restrict__ counts0, const int* __restrict__ jlist0,
                                                        const int* __restrict__ tile_list,
-                                                       const int* __restrict__ tile_count, int buckets, int m, int n,
+                                                       const int* __restrict__ tile_count, int buckets, int m0, int n0,
                                                        int dense,
-                                                       int mode, double* __restrict__ trace_part,
-                                                       const int* __restrict__ done) {
+                                                       int mode0, double* __restrict__ trace_part0,
+                                                       const int* __restrict__ done,
+                                                       const ProdDesc* __restrict__ prods, int cap) {
     grid_dependency_wait();
     if (done && *done) return;
     if (tile_list && (int)blockIdx.x >= listed_total(tile_count, buckets)) return;
+    const double* A = A0;
+    const double* B = B0;
+    double* C = C0;
+    const double* leafA = leafA0;
+    const double* leafB = leafB0;
+    double* leafC = leafC0;
+    const int* counts = counts0;
+    const int* jlist = jlist0;
+    int m = m0, n = n0, mode = mode0;
+    double* trace_part = trace_part0;
+    int tile;
+    if constexpr (kBatched) {
+        const int item = listed_tile(tile_list, tile_count, buckets, cap, (int)blockIdx.x);
+        const ProdDesc& d = prods[item_prod(item)];
+        tile = item_tile(item);
+        A = d.At;
+        B = d.Bt;
+        C = d.Ct;
+        leafA = d.Atree;
+        leafB = d.Btree;
+        leafC = d.Ctree;
+        counts = d.counts;
+        jlist = d.jlist;
+        m = d.td.m;
+        n = d.n;
+        mode = d.mode;
+        trace_part = d.trace_part;
+    } else {
+        tile = tile_list ? listed_tile(tile_list, tile_count, buckets, m * m, (int)blockIdx.x) : (int)blockIdx.x;
+    }
     constexpr int TM = NB / 16;  // each thread owns TM x TM outputs
     constexpr int LDS = NB + 1;  // padded row of the staged chunks
     extern __shared__ double smem[];
@@ -38,7 +71,6 @@ __global__ void __launch_bounds__(kThreads) k_gemm_f64(const double* __restrict_
     double* Bs = smem + kKC * LDS;  // [kKC][LDS]  B chunk
     __shared__ double red[8];
 
-    const int tile = tile_list ? listed_tile(tile_list, tile_count, buckets, m * m, (int)blockIdx.x) : (int)blockIdx.x;
     const int i = tile / m, k = tile - (tile / m) * m;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int nt = dense ? m : counts[tile];
@@ -127,15 +159,28 @@ void launch_nb(const Geometry& g, const double* A, const double* B, double* C, c
                const int* tile_count, int dense, EpiMode mode, double* trace_part, const int* done, cudaStream_t st,
                int buckets) {
     const size_t smem = 2 * (size_t)kKC * (NB + 1) * sizeof(double);
-    launch_dependent(k_gemm_f64<NB>, dim3(g.m * g.m), dim3(kThreads), smem, st, A, B, C, leafA, leafB, treeC, counts,
-                     jlist, tile_list, tile_count, buckets, g.m, g.n, dense, (int)mode, trace_part, done);
+    launch_dependent(k_gemm_f64<NB, false>, dim3(g.m * g.m), dim3(kThreads), smem, st, A, B, C, leafA, leafB, treeC,
+                     counts, jlist, tile_list, tile_count, buckets, g.m, g.n, dense, (int)mode, trace_part, done,
+                     (const ProdDesc*)nullptr, 0);
+    note_launch();
+}
+
+template <int NB>
+void launch_batched_nb(const ProdDesc* prods, const int* tile_list, const int* tile_count, int cap,
+                       const int* all_done, cudaStream_t st) {
+    const size_t smem = 2 * (size_t)kKC * (NB + 1) * sizeof(double);
+    launch_dependent(k_gemm_f64<NB, true>, dim3(cap), dim3(kThreads), smem, st, (const double*)nullptr,
+                     (const double*)nullptr, (double*)nullptr, (const double*)nullptr, (const double*)nullptr,
+                     (double*)nullptr, (const int*)nullptr, (const int*)nullptr, tile_list, tile_count,
+                     kTileBuckets, 0, 0, 0, 0, (double*)nullptr, all_done, prods, cap);
     note_launch();
 }
 
 template <int NB>
 void set_attr() {
     const size_t smem = 2 * (size_t)kKC * (NB + 1) * sizeof(double);
-    cudaFuncSetAttribute(k_gemm_f64<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_gemm_f64<NB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_gemm_f64<NB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 }  // namespace
@@ -163,6 +208,16 @@ void launch_gemm_f64(const Geometry& g, const double* A, const double* B, double
             launch_nb<128>(g, A, B, C, leafA, leafB, treeC, counts, jlist, tile_list, tile_count, dense, mode,
                            trace_part, done, st, buckets);
             break;
+        default: break;
+    }
+}
+
+void launch_gemm_f64_batched(int nb, const ProdDesc* prods, const int* tile_list, const int* tile_count, int cap,
+                             const int* all_done, cudaStream_t st) {
+    switch (nb) {
+        case 32: launch_batched_nb<32>(prods, tile_list, tile_count, cap, all_done, st); break;
+        case 64: launch_batched_nb<64>(prods, tile_list, tile_count, cap, all_done, st); break;
+        case 128: launch_batched_nb<128>(prods, tile_list, tile_count, cap, all_done, st); break;
         default: break;
     }
 }

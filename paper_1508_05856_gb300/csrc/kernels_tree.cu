@@ -530,24 +530,19 @@ __device__ __forceinline__ void trace_error(const double* __restrict__ trace_par
     }
 }
 
-// Levels whose children exceed 64 x 64 go through global memory; from there
-// on the children are held in shared memory (each level is still written
-// out), so the top levels cost shared-memory latency instead of global.
-// kLoop: the instance in a graph's conditional loop body, the only one that calls the device runtime
-// (profilers skip kernels that do, so every other launch uses the plain instance).
-template <bool kLoop>
-__global__ void __launch_bounds__(1024) k_tree(TreeDev td, double* __restrict__ tree, const int* __restrict__ done,
-                                               TreeExtra ex) {
-    grid_dependency_wait();
-    if (done && *done) return;
-    __shared__ double bufA[64 * 64];
-    __shared__ double bufB[32 * 32];
+// Upper levels of one quadtree from its leaf level, by a block of kThr threads.  Levels whose children
+// exceed 64 x 64 go through global memory; from there on the children are held in shared memory (bufA:
+// 64 x 64, bufB: 32 x 32; each level is still written out), so the top levels cost shared-memory latency
+// instead of global.
+template <int kThr>
+__device__ __forceinline__ void tree_levels(const TreeDev& td, double* __restrict__ tree, double* bufA,
+                                            double* bufB) {
     int l = td.L - 1;
     for (; l >= 0 && td.dim[l + 1] > 64; --l) {
         const int d = td.dim[l], dc = td.dim[l + 1];
         const double* ch = tree + td.off[l + 1];
         double* pa = tree + td.off[l];
-        for (int idx = threadIdx.x; idx < d * d; idx += blockDim.x) {
+        for (int idx = threadIdx.x; idx < d * d; idx += kThr) {
             const int I = idx / d, J = idx - I * d;
             const int ci = 2 * I, cj = 2 * J;
             const bool r1 = ci + 1 < dc, c1 = cj + 1 < dc;
@@ -560,16 +555,17 @@ __global__ void __launch_bounds__(1024) k_tree(TreeDev td, double* __restrict__ 
     if (l >= 0) {
         const int dc0 = td.dim[l + 1];
         const double* ch0 = tree + td.off[l + 1];
-        // up to 4096 children: four independent loads per thread, then the shared-memory stores
-        double v[4];
+        // up to 4096 children: independent loads first, then the shared-memory stores
+        constexpr int kPer = 4096 / kThr;
+        double v[kPer];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int idx = threadIdx.x + q * 1024;
+        for (int q = 0; q < kPer; ++q) {
+            const int idx = threadIdx.x + q * kThr;
             v[q] = idx < dc0 * dc0 ? ch0[idx] : 0.0;
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int idx = threadIdx.x + q * 1024;
+        for (int q = 0; q < kPer; ++q) {
+            const int idx = threadIdx.x + q * kThr;
             if (idx < dc0 * dc0) bufA[idx] = v[q];
         }
         __syncthreads();
@@ -578,7 +574,7 @@ __global__ void __launch_bounds__(1024) k_tree(TreeDev td, double* __restrict__ 
         for (; l >= 0; --l) {
             const int d = td.dim[l], dc = td.dim[l + 1];
             double* pa = tree + td.off[l];
-            for (int idx = threadIdx.x; idx < d * d; idx += blockDim.x) {
+            for (int idx = threadIdx.x; idx < d * d; idx += kThr) {
                 const int I = idx / d, J = idx - I * d;
                 const double s = child_sum(cur, dc, I, J);
                 nxt[idx] = s;
@@ -590,6 +586,18 @@ __global__ void __launch_bounds__(1024) k_tree(TreeDev td, double* __restrict__ 
             nxt = t;
         }
     }
+}
+
+// kLoop: the instance in a graph's conditional loop body, the only one that calls the device runtime
+// (profilers skip kernels that do, so every other launch uses the plain instance).
+template <bool kLoop>
+__global__ void __launch_bounds__(1024) k_tree(TreeDev td, double* __restrict__ tree, const int* __restrict__ done,
+                                               TreeExtra ex) {
+    grid_dependency_wait();
+    if (done && *done) return;
+    __shared__ double bufA[64 * 64];
+    __shared__ double bufB[32 * 32];
+    tree_levels<1024>(td, tree, bufA, bufB);
     if (ex.zero_int && threadIdx.x < ex.zero_n) ex.zero_int[threadIdx.x] = 0;
     if (ex.trace_part && threadIdx.x < 32)
         trace_error<kLoop>(ex.trace_part, ex.n, td.m, ex);
@@ -691,6 +699,147 @@ void launch_cull(const Geometry& g, const double* treeA, const double* treeB, do
     const int warps = g.m * g.m;
     launch_dependent(k_cull, dim3((warps + 7) / 8), dim3(256), 0, st, tree_dev(g), treeA, treeB, tau, out, total,
                      thr_out, done);
+    note_launch();
+}
+
+// ---------------------------------------------------------------- batched cull and quadtree
+// The cull of every product of a stage of a batched solve in one launch.  Block b takes 8 output tiles of
+// one product: blocks[b] = (product, first tile, blocks of that product, index of b among them).  Per
+// output tile the test is the one of k_cull (the leaf test with the coarse pre-filter, ascending j);
+// listed tiles become items (p << kItemShift) | tile in the stage's cost classes (stride cap).  The
+// products of a matrix that has stopped are skipped, and the output's row/column maxima are cleared for
+// the tensor-core products.
+__global__ void __launch_bounds__(256) k_cull_batched(const ProdDesc* __restrict__ prods,
+                                                      const int4* __restrict__ blocks, int* __restrict__ tile_list,
+                                                      int* __restrict__ tile_count, int cap,
+                                                      const int* __restrict__ all_done) {
+    grid_dependency_wait();
+    if (*all_done) return;
+    const int4 bt = blocks[blockIdx.x];
+    const ProdDesc& d = prods[bt.x];
+    if (d.mflags[0]) return;
+    __shared__ int red[8];
+    __shared__ int lst[8];
+    __shared__ int bkt[8];
+    const TreeDev& td = d.td;
+    const int m = td.m;
+    if (d.Crmax) {
+        const long zn = 2L * m * 64;
+        for (long q = (long)bt.w * blockDim.x + threadIdx.x; q < zn; q += (long)bt.z * blockDim.x) d.Crmax[q] = 0ull;
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wid = bt.y + warp;
+    const double* treeA = d.Atree;
+    const double* treeB = d.Btree;
+    const double thr = ((d.tau * d.tau) * treeA[td.off[0]]) * treeB[td.off[0]];
+    int cnt = 0;
+    bool listed = false;
+    if (wid < m * m) {
+        const int i = wid / m, k = wid - (wid / m) * m;
+        const int dc = td.dim[td.coarse];
+        const double* cA = treeA + td.off[td.coarse];
+        const double* cB = treeB + td.off[td.coarse];
+        const int I = i >> td.shift, K = k >> td.shift;
+        int* out = d.jlist + (size_t)wid * m;
+        for (int j0 = 0; j0 < m; j0 += 32) {
+            const int j = j0 + lane;
+            bool coarse = false;
+            if (j < m) {
+                const int J = j >> td.shift;
+                coarse = !(cA[(size_t)I * dc + J] * cB[(size_t)J * dc + K] < thr);
+            }
+            if (!__any_sync(0xffffffffu, coarse)) continue;
+            const bool keep = coarse && !(treeA[(size_t)i * m + j] * treeB[(size_t)j * m + k] < thr);
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            if (keep) out[cnt + __popc(bal & ((1u << lane) - 1u))] = j;
+            cnt += __popc(bal);
+        }
+        if (lane == 0) {
+            d.counts[wid] = cnt;
+            listed = cnt > 0 || (d.mode != EPI_PLAIN && i == k);
+            if (!listed) d.Ctree[wid] = 0.0;
+        }
+    }
+    if (lane == 0) {
+        lst[warp] = listed ? ((bt.x << kItemShift) | wid) : -1;
+        bkt[warp] = tile_bucket(cnt);
+        red[warp] = cnt;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int c[kTileBuckets] = {0, 0, 0, 0, 0};
+        int sacc = 0;
+        for (int w = 0; w < 8; ++w) {
+            if (lst[w] >= 0) ++c[bkt[w]];
+            sacc += red[w];
+        }
+        int q[kTileBuckets];
+        for (int b = 0; b < kTileBuckets; ++b) q[b] = c[b] ? atomicAdd(tile_count + b, c[b]) : 0;
+        for (int w = 0; w < 8; ++w)
+            if (lst[w] >= 0) tile_list[(size_t)bkt[w] * cap + q[bkt[w]]++] = lst[w];
+        if (sacc) atomicAdd(d.task_ctr + 3 * (size_t)d.mflags[1] + d.which, (unsigned long long)sacc);
+    }
+}
+
+void launch_cull_batched(const ProdDesc* prods, const int4* blocks, int nblocks, int* tile_list, int* tile_count,
+                         int cap, const int* all_done, cudaStream_t st) {
+    launch_dependent(k_cull_batched, dim3(nblocks), dim3(256), 0, st, prods, blocks, tile_list, tile_count, cap,
+                     all_done);
+    note_launch();
+}
+
+// Upper quadtree levels of every product output of a stage, one block per product; the stage's cost-class
+// counters are cleared for its next cull.  In the X stage (x_stage) each live matrix also records its
+// trace error t_k = (n - tr X)/n, counts the iteration and stops (|t_k| <= tol_t > 0, or maxit steps), as
+// k_tree does for one solve; the last block to finish ends the batch once every matrix has stopped (and,
+// in a graph's loop body, clears the loop's condition).
+template <bool kLoop>
+__global__ void __launch_bounds__(256) k_tree_batched(const ProdDesc* __restrict__ prods, int nprod,
+                                                      int* __restrict__ tile_count, int* __restrict__ stage_ctr,
+                                                      int* __restrict__ ndone, int count, int* __restrict__ all_done,
+                                                      cudaGraphConditionalHandle cond, int x_stage) {
+    grid_dependency_wait();
+    if (*all_done) return;
+    __shared__ double bufA[64 * 64];
+    __shared__ double bufB[32 * 32];
+    const ProdDesc& d = prods[blockIdx.x];
+    const bool live = d.mflags[0] == 0;
+    if (live) tree_levels<256>(d.td, d.Ctree, bufA, bufB);
+    if (blockIdx.x == 0 && threadIdx.x < kTileBuckets) tile_count[threadIdx.x] = 0;
+    if (!x_stage) return;
+    if (live && threadIdx.x < 32) {
+        const double tr = trace_sum_warp(d.trace_part, d.td.m);
+        if (threadIdx.x == 0) {
+            const int k = d.mflags[1];
+            const double t = ((double)d.n - tr) / (double)d.n;
+            d.t_hist[k] = t;
+            d.mflags[1] = k + 1;
+            if ((d.tol_t > 0.0 && fabs(t) <= d.tol_t) || k + 1 >= d.maxit) {
+                d.mflags[0] = 1;
+                atomicAdd(ndone, 1);
+            }
+        }
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(stage_ctr, 1) == nprod - 1) {
+            *stage_ctr = 0;
+            if (atomicAdd(ndone, 0) >= count) {
+                *all_done = 1;
+                if constexpr (kLoop) cudaGraphSetConditional(cond, 0u);
+            }
+        }
+    }
+}
+
+void launch_tree_batched(const ProdDesc* prods, int nprod, int* tile_count, int* stage_ctr, int* ndone, int count,
+                         int* all_done, const cudaGraphConditionalHandle* cond, bool x_stage, cudaStream_t st) {
+    if (cond)
+        launch_dependent(k_tree_batched<true>, dim3(nprod), dim3(256), 0, st, prods, nprod, tile_count, stage_ctr,
+                         ndone, count, all_done, *cond, x_stage ? 1 : 0);
+    else
+        launch_dependent(k_tree_batched<false>, dim3(nprod), dim3(256), 0, st, prods, nprod, tile_count, stage_ctr,
+                         ndone, count, all_done, (cudaGraphConditionalHandle)0, x_stage ? 1 : 0);
     note_launch();
 }
 

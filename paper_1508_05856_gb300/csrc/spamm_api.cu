@@ -1513,6 +1513,12 @@ int spamm_sqrt_invsqrt_batched(int count, const double* const* S, const int* n, 
             int e = check_common(n[q], tau[q], base);
             if (e) return e;
         }
+        // one graph over the whole batch when the options allow it; otherwise every problem on its own
+        {
+            const int e = batched_solve(count, S, n, tau, maxit, Y, Z, base, stats);
+            if (e != SPAMM_ERR_UNSUPPORTED) return e;
+            g_last_error.clear();
+        }
         int dev = 0;
         CK(cudaGetDevice(&dev));
         const int workers = count < 8 ? count : 8;
@@ -1646,6 +1652,7 @@ const char* spamm_strerror(int s) {
 }
 
 int spamm_release(void) {
+    release_batches();
     g_pool.clear();
     return SPAMM_OK;
 }

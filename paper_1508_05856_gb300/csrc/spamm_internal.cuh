@@ -303,6 +303,21 @@ void launch_gemm_emu_batched(const ProdDesc* prods, const int* tile_list, const 
 // FP64 leaf products of every product of a stage (leaf nb): one CTA per listed item, grid cap.
 void launch_gemm_f64_batched(int nb, const ProdDesc* prods, const int* tile_list, const int* tile_count, int cap,
                              const int* all_done, cudaStream_t st);
+// Cull of every product of a stage: blocks[b] = (product, first output tile, blocks of the product, index
+// of b among them), 8 output tiles per block; tile_list / tile_count (kTileBuckets classes of stride cap,
+// counts zero on entry) get the listed items.
+void launch_cull_batched(const ProdDesc* prods, const int4* blocks, int nblocks, int* tile_list, int* tile_count,
+                         int cap, const int* all_done, cudaStream_t st);
+// Quadtree levels of every product output of a stage (one block per product), the stage's class counters
+// cleared; with x_stage the per-matrix trace error, iteration count and stop, and the batch's end
+// (all_done, and the graph condition when cond is set).  stage_ctr: one int, zero between launches.
+void launch_tree_batched(const ProdDesc* prods, int nprod, int* tile_count, int* stage_ctr, int* ndone, int count,
+                         int* all_done, const cudaGraphConditionalHandle* cond, bool x_stage, cudaStream_t st);
+// The batched solve engine (spamm_batch.cu): SPAMM_ERR_UNSUPPORTED when the per-matrix path must serve
+// the call (options it does not cover, pageable host memory, or a batch larger than the free memory).
+int batched_solve(int count, const double* const* S, const int* n, const double* tau, int maxit,
+                  double* const* Y, double* const* Z, const spamm_opts& o, spamm_stats* stats);
+void release_batches();
 // Digit slices of the items a batched leaf-product launch drew (slice_items, count at slice_items[cap]).
 void launch_slice_batched(const ProdDesc* prods, const int* slice_items, int cap, const int* all_done,
                           cudaStream_t st);
