@@ -566,57 +566,32 @@ def run_gpu(args, ws, rank, local):
             "gpu_launches": launches,
             "clocks": clk,
             "tau_sweep": sweep}
+    if ws == 1 and not args.no_extra:
+        # the other single-GPU configurations, each with its own CPU baseline and errors against the oracle
+        del Sd, Yd, Zd, flush, Sh, Yh, Zh
+        sp.release()
+        torch.cuda.empty_cache()
+        extra = {}
+        for name, fn in (("c3", lambda: c3_config(args, local, taus=[args.c3_tau_default])),
+                         ("c4", lambda: batched_config(args, local)),
+                         ("c5", lambda: serve_config(args, local, seq_requests=args.serve_seq))):
+            t0 = time.perf_counter()
+            extra[name] = fn()
+            extra[name]["bench_seconds"] = time.perf_counter() - t0
+            sp.release()
+            torch.cuda.empty_cache()
+        line["configs"] = extra
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
 
 
-def run_batched(args, local):
-    """Batched configuration: many independent SPD decay matrices of mixed sizes in one call, against the
-    same matrices solved one call at a time."""
-    import torch
-
-    import paper_1508_05856_gb300 as sp
-    import synth
-
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    prec = sp.EMU64 if args.precision == "emu64" else sp.FP64
-    specs = synth.batch_mix(args.batch, lo=128, hi=2048, seed=0)
-    Ss = [torch.from_numpy(synth.make(sp_)).to(dev) for sp_ in specs]
-    taus = [args.batch_tau] * len(Ss)
-    kw = dict(leaf=LEAF, precision=prec, map=MAP, tol_t=TOL, channel=CHANNEL)
-    sp.sqrt_invsqrt_batched(Ss[:16], taus[:16], MAXIT, raise_on=False, **kw)   # warm-up
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    Ys, Zs, sts = sp.sqrt_invsqrt_batched(Ss, taus, MAXIT, raise_on=False, **kw)
-    torch.cuda.synchronize()
-    t_batch = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    for S, t in zip(Ss, taus):
-        sp.sqrt_invsqrt(S, t, MAXIT, raise_on=False, **kw)
-    torch.cuda.synchronize()
-    t_seq = time.perf_counter() - t0
-    line = {"metric": "batched NS solves/s (mixed KMS / 3D Gaussian, N in [128, 2048])", "value": len(Ss) / t_batch,
-            "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": "f64" if prec == sp.FP64 else "f16-split",
-            "data": "synthetic",
-            "config": {"workload": f"{len(Ss)} matrices, sizes log-uniform in [128, 2048] (multiples of 32), "
-                                   f"50% KMS rho~U(0.5,0.95), 50% Gaussian sigma~U(0.6,0.9), tau={args.batch_tau:g}, "
-                                   + (f"{MAXIT} iterations" if TOL <= 0
-                                      else f"until |t_k| <= {TOL:g} (at most {MAXIT})"),
-                       "precision": args.precision, "map": args.map, "channel": args.channel},
-            "one_call_per_matrix": {"value": len(Ss) / t_seq, "unit": UNIT},
-            "tasks": int(sum(st["tasks_total"] for st in sts)),
-            "iters_mean": float(sum(st["iters"] for st in sts)) / max(1, len(sts)),
-            "call_status": sts[0]["call_status"]}
-    print(json.dumps(line), flush=True)
-    return 0
-
-
-def run_serve(args, local):
-    """Serving configuration: Poisson arrivals of square-root requests on 3D Gaussian-decay matrices, served
-    with continuous batching; p50/p99 latency and solves/s, against one request at a time."""
+def batched_config(args, local) -> dict:
+    """Batched configuration: many independent SPD decay matrices of mixed sizes in one call (one graph over
+    the whole batch: every stage of the iteration one launch of each kernel over all matrices), against the
+    same matrices solved one call at a time; errors against the oracle on a sample of the matrices, and the
+    oracle's rate over the same list on the host cores."""
     import numpy as np
     import torch
 
@@ -626,58 +601,108 @@ def run_serve(args, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     prec = sp.EMU64 if args.precision == "emu64" else sp.FP64
-    trace = synth.serving_trace(args.requests, rate=args.rate, lo=256, hi=args.serve_max_n, seed=0)
-    mats = [torch.from_numpy(synth.make(r)).to(dev) for r in trace]
-    with sp.Server(bytes_budget=int(args.budget_gb * (1 << 30)), max_active=args.max_active, leaf=LEAF,
-                   precision=prec) as srv:
-        for S, r in list(zip(mats, trace))[:4]:
-            srv.wait(srv.submit(S, r["tau"], MAXIT), raise_on=False)     # warm-up
+    specs = synth.batch_mix(args.batch, lo=128, hi=2048, seed=0)
+    host = [synth.make(sp_) for sp_ in specs]
+    Ss = [torch.from_numpy(S).to(dev) for S in host]
+    Ys = [torch.empty_like(S) for S in Ss]
+    Zs = [torch.empty_like(S) for S in Ss]
+    taus = [args.batch_tau] * len(Ss)
+    kw = dict(leaf=LEAF, precision=prec, map=MAP, tol_t=TOL, channel=CHANNEL)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    # the first call builds the batch (buffers and graph); the timed calls replay it
+    _, _, sts = sp.sqrt_invsqrt_batched(Ss, taus, MAXIT, raise_on=False, Ys=Ys, Zs=Zs, **kw)
+    torch.cuda.synchronize()
+    l0 = sp.kernel_launches()
+    tb = []
+    for _ in range(args.batch_steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, _, sts = sp.sqrt_invsqrt_batched(Ss, taus, MAXIT, raise_on=False, Ys=Ys, Zs=Zs, **kw)
+        e1.record(stream)
+        e1.synchronize()
+        tb.append(e0.elapsed_time(e1) / 1e3)
+    launches = (sp.kernel_launches() - l0) / max(1, args.batch_steps)
+    # one call per matrix, the same matrices
+    for S, t, Y, Z in list(zip(Ss, taus, Ys, Zs))[:8]:
+        sp.sqrt_invsqrt(S, t, MAXIT, raise_on=False, Y=Y, Z=Z, **kw)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for S, t, Y, Z in zip(Ss, taus, Ys, Zs):
+        sp.sqrt_invsqrt(S, t, MAXIT, raise_on=False, Y=Y, Z=Z, **kw)
+    e1.record(stream)
+    e1.synchronize()
+    t_seq = e0.elapsed_time(e1) / 1e3
+    # errors against the oracle on a sample spread over the sizes, from a fresh batched call
+    _, _, sts = sp.sqrt_invsqrt_batched(Ss, taus, MAXIT, raise_on=False, Ys=Ys, Zs=Zs, **kw)
+    torch.cuda.synchronize()
+    order = np.argsort([S.shape[0] for S in host])
+    sample = [int(order[q]) for q in np.linspace(0, len(order) - 1, args.batch_oracle_sample).astype(int)]
+    errs = None
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        ez, ey, ti = [], [], []
+        for q in sample:
+            ref = oracle.sqrt_invsqrt(host[q], LEAF, taus[q], MAXIT, map=MAP, tol_t=TOL, channel=CHANNEL)
+            ez.append(rel_err(Zs[q].cpu().numpy(), ref["Z"]))
+            ey.append(rel_err(Ys[q].cpu().numpy(), ref["Y"]))
+            ti.append(sts[q]["tasks_total"] == int(ref["task_hist"].sum()))
+        errs = {"matrices": len(sample), "sizes": [int(host[q].shape[0]) for q in sample], "Z_max": max(ez),
+                "Y_max": max(ey), "task_totals_equal": int(sum(ti))}
+        # the oracle over the batch list in order, on the host cores, for about cpu_budget seconds
         t0 = time.perf_counter()
-        ids = []
-        for S, r in zip(mats, trace):
-            delay = r["arrival"] - (time.perf_counter() - t0)
-            if delay > 0:
-                time.sleep(delay)
-            ids.append(srv.submit(S, r["tau"], MAXIT))
-        # a request whose iteration diverges (aggressive tau on an ill-conditioned matrix) is answered with
-        # its status like any other; it is counted, not dropped
-        done = [srv.wait(i, raise_on=False) for i in ids]
-        lats = [d[3] for d in done]
-        statuses = [d[2]["status"] for d in done]
-        t_all = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    seq_lat = []
-    seq_status = []
-    for S, r in zip(mats, trace):
-        a = time.perf_counter()
-        _, _, st = sp.sqrt_invsqrt(S, r["tau"], MAXIT, leaf=LEAF, precision=prec, raise_on=False, map=MAP,
-                                   tol_t=TOL, channel=CHANNEL)
-        seq_lat.append(time.perf_counter() - a)
-        seq_status.append(st["status"])
-    t_seq = time.perf_counter() - t0
-    lat = np.array(lats) * 1e3
-    line = {"metric": "served NS requests: solves/s with p50/p99 latency", "value": len(ids) / t_all, "unit": UNIT,
-            "n_gpus": 1, "higher_is_better": True, "dtype": "f64" if prec == sp.FP64 else "f16-split",
-            "data": "synthetic",
-            "config": {"workload": f"{len(ids)} requests, Poisson arrivals at {args.rate:g}/s, N log-uniform in "
-                                   f"[256, {args.serve_max_n}] (multiples of 32), 3D Gaussian decay, tau in "
-                                   "{1e-4, 1e-6, 1e-8}", "max_active": args.max_active, "budget_gb": args.budget_gb,
-                       "precision": args.precision, "map": args.map},
-            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
-            "requests": {"ok": int(sum(1 for x in statuses if x == 0)),
-                         "diverged": int(sum(1 for x in statuses if x == -3)),
-                         "other_error": int(sum(1 for x in statuses if x not in (0, -3))),
-                         "same_status_as_alone": bool(statuses == seq_status)},
-            "one_request_at_a_time": {"value": len(ids) / t_seq, "unit": UNIT,
-                                      "p50_service_ms": float(np.percentile(np.array(seq_lat) * 1e3, 50))}}
-    print(json.dumps(line), flush=True)
+        done = 0
+        for q in range(len(host)):
+            oracle.sqrt_invsqrt(host[q], LEAF, taus[q], MAXIT, map=MAP, tol_t=TOL, channel=CHANNEL)
+            done += 1
+            if time.perf_counter() - t0 >= args.batch_cpu_budget:
+                break
+        el = time.perf_counter() - t0
+        cpu = {"value": done / el, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"the first {done} matrices of the batch list in {el:.1f} s (list order, sizes as drawn)"}
+    t_batch = sum(tb) / len(tb)
+    out = {"metric": "batched NS solves/s (mixed KMS / 3D Gaussian, N in [128, 2048])", "value": len(Ss) / t_batch,
+           "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": "f64" if prec == sp.FP64 else "f16-split",
+           "data": "synthetic",
+           "config": {"workload": f"{len(Ss)} matrices, sizes log-uniform in [128, 2048] (multiples of 32), "
+                                  f"50% KMS rho~U(0.5,0.95), 50% Gaussian sigma~U(0.6,0.9), tau={args.batch_tau:g}, "
+                                  + (f"{MAXIT} iterations" if TOL <= 0
+                                     else f"until |t_k| <= {TOL:g} (at most {MAXIT})"),
+                      "precision": args.precision, "map": args.map, "channel": args.channel,
+                      "l2": "flushed by a 256 MB write before every timed batch"},
+           "ms_per_batch": 1e3 * t_batch, "timed_batches": len(tb), "gpu_launches_per_batch": launches,
+           "one_call_per_matrix": {"value": len(Ss) / t_seq, "unit": UNIT},
+           "tasks": int(sum(st["tasks_total"] for st in sts)),
+           "iters_mean": float(sum(st["iters"] for st in sts)) / max(1, len(sts)),
+           "call_status": sp.STATUS.get(sts[0]["call_status"]),
+           "err_vs_oracle": errs, "cpu_baseline": cpu}
+    del Ss, Ys, Zs, flush
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_batched(args, local):
+    print(json.dumps(batched_config(args, local)), flush=True)
     return 0
 
 
-def run_c3(args, local):
-    """Large configuration: 3D Gaussian decay on N jittered Morton-ordered lattice points (default N = 16384),
-    N_b = 64, one or more tau, optional Tikhonov shift mu = mu_rel * c.  Solves/s, residual and cull volume per
-    tau; the oracle time of one product, extrapolated to a solve, when asked for."""
+def serve_config(args, local, requests=None, seq_requests=None) -> dict:
+    """Serving configuration: Poisson arrivals of square-root requests on 3D Gaussian-decay matrices, served by
+    the request server (queued device-resident requests are solved together, sharing every launch); p50/p99
+    latency from arrival to completion and solves/s, against the same requests solved one at a time.
+
+    Each request's matrix is built on the device when it arrives, from its own seeded point set (input
+    generation, not part of the solve).  The client keeps at most --serve-outstanding-gb of request matrices
+    (S, Y, Z) alive; a request arriving beyond that waits on the client and its wait counts in its latency."""
+    import collections
+
+    import numpy as np
     import torch
 
     import paper_1508_05856_gb300 as sp
@@ -686,16 +711,159 @@ def run_c3(args, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     prec = sp.EMU64 if args.precision == "emu64" else sp.FP64
+    R = requests or args.requests
+    trace = synth.serving_trace(R, rate=args.rate, lo=256, hi=args.serve_max_n, seed=0)
+
+    def make(r):
+        # S_ij = exp(-|r_i - r_j|^2 / (2 sigma^2)), built in row blocks; finished before the request is
+        # handed to the server, whose workers run on their own streams
+        pts = torch.from_numpy(synth.lattice_points(r["n"], r["seed"])).to(dev)
+        n = r["n"]
+        S = torch.empty((n, n), dtype=torch.float64, device=dev)
+        c = -1.0 / (2.0 * r["sigma"] * r["sigma"])
+        for a in range(0, n, 2048):
+            d = pts[a:a + 2048, None, :] - pts[None, :, :]
+            S[a:a + 2048] = torch.exp((d * d).sum(-1) * c)
+        torch.cuda.current_stream(dev).synchronize()
+        return S
+
+    cap = int(args.serve_outstanding_gb * (1 << 30))
+    nbytes = [3 * r["n"] * r["n"] * 8 for r in trace]
+    lat = [0.0] * R
+    status = [None] * R
+    keep_out = {}
+    sample = {q for q in range(R) if trace[q]["n"] <= 1024 and q < 200}
+    sample = set(sorted(sample)[:args.serve_oracle_sample])
+    with sp.Server(bytes_budget=int(args.budget_gb * (1 << 30)), max_active=args.max_active, leaf=LEAF,
+                   precision=prec) as srv:
+        for r in trace[:4]:
+            srv.wait(srv.submit(make(r), r["tau"], MAXIT), raise_on=False)     # warm-up
+        torch.cuda.synchronize()
+        pending = collections.deque()
+        outstanding = {}
+        out_bytes = 0
+        nxt = 0
+        t0 = time.perf_counter()
+        t_last = t0
+        while nxt < R or pending or outstanding:
+            now = time.perf_counter() - t0
+            while nxt < R and trace[nxt]["arrival"] <= now:
+                pending.append(nxt)
+                nxt += 1
+            busy = False
+            while pending and (out_bytes + nbytes[pending[0]] <= cap or not outstanding):
+                q = pending.popleft()
+                S = make(trace[q])
+                rid = srv.submit(S, trace[q]["tau"], MAXIT)
+                outstanding[rid] = (q, time.perf_counter() - t0, S)
+                out_bytes += nbytes[q]
+                busy = True
+            for rid in list(outstanding):
+                if srv.poll(rid) == 2:
+                    q, t_sub, S = outstanding.pop(rid)
+                    Y, Z, st, l = srv.wait(rid, raise_on=False)
+                    lat[q] = t_sub + l - trace[q]["arrival"]
+                    status[q] = st["status"]
+                    t_last = max(t_last, t0 + t_sub + l)
+                    if q in sample:
+                        keep_out[q] = (S.cpu().numpy(), Y.cpu().numpy(), Z.cpu().numpy())
+                    out_bytes -= nbytes[q]
+                    busy = True
+            if not busy:
+                time.sleep(0.0005)
+        t_all = t_last - (t0 + trace[0]["arrival"])
+    # the same requests one at a time (a prefix of the trace when the run asks for fewer)
+    Rs = min(R, seq_requests or R)
+    seq_status = []
+    seq_lat = []
+    same_out = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for q in range(Rs):
+        a = time.perf_counter()
+        S = make(trace[q])
+        Y, Z, st = sp.sqrt_invsqrt(S, trace[q]["tau"], MAXIT, leaf=LEAF, precision=prec, raise_on=False, map=MAP,
+                                   tol_t=TOL, channel=CHANNEL)
+        torch.cuda.synchronize()
+        seq_lat.append(time.perf_counter() - a)
+        seq_status.append(st["status"])
+        if q in keep_out:
+            same_out += int(np.array_equal(keep_out[q][1], Y.cpu().numpy()) and
+                            np.array_equal(keep_out[q][2], Z.cpu().numpy()))
+        del S, Y, Z
+    t_seq = time.perf_counter() - t0
+    errs = None
+    if keep_out and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        ez = []
+        for q, (S, Y, Z) in sorted(keep_out.items()):
+            ref = oracle.sqrt_invsqrt(S, LEAF, trace[q]["tau"], MAXIT, map=MAP, tol_t=TOL, channel=CHANNEL)
+            ez.append(max(rel_err(Z, ref["Z"]), rel_err(Y, ref["Y"])))
+        errs = {"requests": len(ez), "max_rel_err_YZ": max(ez)}
+    la = np.array(lat) * 1e3
+    out = {"metric": "served NS requests: solves/s with p50/p99 latency", "value": R / t_all, "unit": UNIT,
+           "n_gpus": 1, "higher_is_better": True, "dtype": "f64" if prec == sp.FP64 else "f16-split",
+           "data": "synthetic",
+           "config": {"workload": f"{R} requests, Poisson arrivals at {args.rate:g}/s, N log-uniform in "
+                                  f"[256, {args.serve_max_n}] (multiples of 32), 3D Gaussian decay sigma~U(0.6,0.9) "
+                                  f"on each request's own seeded lattice, tau in {{1e-4, 1e-6, 1e-8}}, {MAXIT} "
+                                  "iterations", "max_active": args.max_active, "budget_gb": args.budget_gb,
+                      "client_outstanding_gb": args.serve_outstanding_gb, "precision": args.precision,
+                      "map": args.map},
+           "latency_ms": {"p50": float(np.percentile(la, 50)), "p99": float(np.percentile(la, 99)),
+                          "from": "arrival to completion"},
+           "requests": {"ok": int(sum(1 for x in status if x == 0)),
+                        "diverged": int(sum(1 for x in status if x == -3)),
+                        "other_error": int(sum(1 for x in status if x not in (0, -3))),
+                        "same_status_as_alone": bool(status[:Rs] == seq_status),
+                        "status_mismatches": [{"q": q, "n": trace[q]["n"], "tau": trace[q]["tau"],
+                                               "served": status[q], "alone": seq_status[q]}
+                                              for q in range(Rs) if status[q] != seq_status[q]][:10],
+                        "bitwise_same_as_alone": f"{same_out} of {len([q for q in keep_out if q < Rs])} sampled"},
+           "one_request_at_a_time": {"value": Rs / t_seq, "unit": UNIT, "requests": Rs,
+                                     "p50_service_ms": float(np.percentile(np.array(seq_lat) * 1e3, 50))},
+           "err_vs_oracle": errs}
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_serve(args, local):
+    print(json.dumps(serve_config(args, local)), flush=True)
+    return 0
+
+
+def c3_config(args, local, taus=None) -> dict:
+    """Large configuration: 3D Gaussian decay on N jittered Morton-ordered lattice points (default N = 16384),
+    N_b = 64, one or more tau, optional Tikhonov shift mu = mu_rel * c.  Solves/s, residual and cull volume per
+    tau.  The oracle cannot solve this size in the time of a run: its rate is the measured time of a random
+    sample of the solve's own leaf products, scaled by the solve's task count (labelled extrapolated), and the
+    GPU result is checked by properties that hold at any size: ||ZSZ - I||_F (FP64, dense) and Y^2 = S on a
+    sample of rows."""
+    import numpy as np
+    import torch
+
+    import paper_1508_05856_gb300 as sp
+    import synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = sp.EMU64 if args.precision == "emu64" else sp.FP64
+    taus = list(taus if taus is not None else args.c3_tau)
     S = synth.gaussian_lattice(args.c3_n, args.c3_sigma, seed=0)
     Sd = torch.from_numpy(S).to(dev)
     Yd, Zd = torch.empty_like(Sd), torch.empty_like(Sd)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-    rows = []
-    for tau in args.c3_tau:
+    rng = np.random.default_rng(0)
+    rows = torch.from_numpy(np.sort(rng.choice(args.c3_n, size=64, replace=False))).to(dev)
+    rows_out = []
+    for tau in taus:
         kw = dict(leaf=LEAF, precision=prec, Y=Yd, Z=Zd, mu_rel=args.c3_mu, map=MAP, tol_t=TOL, channel=CHANNEL,
                   raise_on=False)
         _, _, vst = sp.sqrt_invsqrt(Sd, tau, MAXIT, residual=True, **kw)
+        # Y^2 = S on 64 sampled rows, FP64 (verification only; without a shift)
+        y2 = float(torch.linalg.norm(Yd[rows] @ Yd - Sd[rows]) / torch.linalg.norm(Sd[rows]))
         sp.sqrt_invsqrt(Sd, tau, MAXIT, **kw)
         ts = []
         for _ in range(args.c3_steps):
@@ -707,33 +875,50 @@ def run_c3(args, local):
             e1.record(stream)
             e1.synchronize()
             ts.append(e0.elapsed_time(e1) / 1e3)
-        rows.append({"tau": tau, "solves_per_s": len(ts) / sum(ts), "ms_per_solve": 1e3 * sum(ts) / len(ts),
-                     "resid_F": vst["resid_F"], "gate_met": bool(vst["resid_F"] <= GATE),
-                     "tasks": vst["tasks_total"], "volume_pct": 100.0 * vst["tasks_total"] / vst["tasks_dense"],
-                     "iters": vst["iters"], "t_final": vst["t_final"], "status": vst["status"]})
+        rows_out.append({"tau": tau, "solves_per_s": len(ts) / sum(ts), "ms_per_solve": 1e3 * sum(ts) / len(ts),
+                         "resid_F": vst["resid_F"], "gate_met": bool(vst["resid_F"] <= GATE),
+                         "y2_rows_rel_err": y2 if not args.c3_mu else None,
+                         "tasks": vst["tasks_total"], "volume_pct": 100.0 * vst["tasks_total"] / vst["tasks_dense"],
+                         "iters": vst["iters"], "t_final": vst["t_final"], "status": sp.STATUS.get(vst["status"])})
+    best = max((r for r in rows_out if r["gate_met"]), key=lambda r: r["solves_per_s"], default=rows_out[-1])
     cpu = None
-    if args.c3_oracle:
+    if not args.no_cpu_baseline:
         import oracle
         oracle.build()
+        # a random sample of the leaf products of one product of the solve (X0 X0 at the best tau), timed in
+        # the oracle, per task, times the solve's tasks
+        c = oracle.gershgorin(S)
+        X0 = S * (1.0 / c)
+        X0d = torch.from_numpy(X0).to(dev)
+        tasks, _, ntask = sp.cull(X0d, X0d, best["tau"], LEAF)
+        del X0d
+        pick = tasks[rng.choice(len(tasks), size=min(len(tasks), args.c3_oracle_tasks), replace=False)]
         t0 = time.perf_counter()
-        _, cnt = oracle.spamm(S / oracle.gershgorin(S), S / oracle.gershgorin(S), LEAF, args.c3_tau[-1])
+        oracle.leaf_products(X0, X0, LEAF, pick)
         el = time.perf_counter() - t0
-        cpu = {"value": 1.0 / (el * 3 * MAXIT), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-               "sample": f"one SpAMM product S/c (x) S/c at tau={args.c3_tau[-1]:g} ({cnt} tasks) in {el:.1f} s, "
-                         f"extrapolated to {3 * MAXIT} products per solve"}
-    best = max((r for r in rows if r["gate_met"]), key=lambda r: r["solves_per_s"], default=rows[-1])
-    line = {"metric": f"NS solves/s at ||ZSZ-I||_F<=1e-8 (3D Gaussian N={args.c3_n})", "value": best["solves_per_s"],
-            "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
-            "dtype": "f64" if prec == sp.FP64 else "f16-split", "data": "synthetic",
-            "config": {"workload": f"3D Gaussian decay sigma={args.c3_sigma} on {args.c3_n} jittered Morton-ordered "
-                                   f"lattice points, N_b={LEAF}, "
-                                   + (f"{MAXIT} iterations" if TOL <= 0
-                                      else f"until |t_k| <= {TOL:g} (at most {MAXIT})")
-                                   + f", mu_rel={args.c3_mu}",
-                       "precision": args.precision, "map": args.map, "channel": args.channel,
-                       "tau_best": best["tau"]},
-            "per_tau": rows, "cpu_baseline": cpu}
-    print(json.dumps(line), flush=True)
+        per_task = el / len(pick)
+        cpu = {"value": 1.0 / (per_task * best["tasks"]), "unit": UNIT, "cores": oracle.num_threads(),
+               "kind": "oracle", "extrapolated": True,
+               "sample": f"{len(pick)} leaf products of X0 (x) X0 at tau={best['tau']:g} in {el:.2f} s, scaled to "
+                         f"the solve's {best['tasks']} leaf products (the culls, trees and maps left out)"}
+    out = {"metric": f"NS solves/s at ||ZSZ-I||_F<=1e-8 (3D Gaussian N={args.c3_n})", "value": best["solves_per_s"],
+           "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+           "dtype": "f64" if prec == sp.FP64 else "f16-split", "data": "synthetic",
+           "config": {"workload": f"3D Gaussian decay sigma={args.c3_sigma} on {args.c3_n} jittered Morton-ordered "
+                                  f"lattice points, N_b={LEAF}, "
+                                  + (f"{MAXIT} iterations" if TOL <= 0
+                                     else f"until |t_k| <= {TOL:g} (at most {MAXIT})")
+                                  + f", mu_rel={args.c3_mu}",
+                      "precision": args.precision, "map": args.map, "channel": args.channel,
+                      "tau_best": best["tau"], "l2": "flushed by a 256 MB write before every timed solve"},
+           "per_tau": rows_out, "cpu_baseline": cpu}
+    del Sd, Yd, Zd, flush
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_c3(args, local):
+    print(json.dumps(c3_config(args, local)), flush=True)
     return 0
 
 
@@ -828,20 +1013,33 @@ def main():
     ap.add_argument("--no-oracle-error", action="store_true",
                     help="skip the oracle solves that give every result's error against the oracle")
     ap.add_argument("--c3", action="store_true", help="large 3D Gaussian configuration instead of the headline solve")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="headline only: leave out the large, batched and served configurations")
+    ap.add_argument("--c3-tau-default", type=float, default=1e-15,
+                    help="tau of the large configuration inside the default run (the largest meeting the gate)")
+    ap.add_argument("--serve-seq", type=int, default=500,
+                    help="requests of the trace also solved one at a time inside the default run")
     ap.add_argument("--c3-n", type=int, default=16384)
     ap.add_argument("--c3-sigma", type=float, default=0.7)
     ap.add_argument("--c3-tau", type=float, nargs="+", default=[1e-10, 1e-12, 1e-14])
     ap.add_argument("--c3-mu", type=float, default=0.0)
     ap.add_argument("--c3-steps", type=int, default=2)
-    ap.add_argument("--c3-oracle", action="store_true", help="time one oracle product, extrapolated")
+    ap.add_argument("--c3-oracle-tasks", type=int, default=3000,
+                    help="leaf products the oracle times for the extrapolated CPU rate")
     ap.add_argument("--batched", action="store_true", help="batched configuration instead of the headline solve")
     ap.add_argument("--batch", type=int, default=512)
     ap.add_argument("--batch-tau", type=float, default=1e-6)
+    ap.add_argument("--batch-steps", type=int, default=3, help="timed batched calls")
+    ap.add_argument("--batch-oracle-sample", type=int, default=6, help="matrices compared with the oracle")
+    ap.add_argument("--batch-cpu-budget", type=float, default=8.0, help="seconds of oracle time over the list")
     ap.add_argument("--serve", action="store_true", help="serving configuration instead of the headline solve")
-    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--requests", type=int, default=2000)
+    ap.add_argument("--serve-outstanding-gb", type=float, default=96.0,
+                    help="request matrices (S, Y, Z) the client keeps alive at most")
+    ap.add_argument("--serve-oracle-sample", type=int, default=4, help="small requests compared with the oracle")
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--serve-max-n", type=int, default=8192)
-    ap.add_argument("--max-active", type=int, default=8)
+    ap.add_argument("--max-active", type=int, default=2)
     ap.add_argument("--budget-gb", type=float, default=64.0)
     ap.add_argument("--map", choices=["ns", "scaled"], default="ns",
                     help="NS map: alpha = 1, or the damped, stabilised h_alpha of Sec. 4.2")

@@ -290,8 +290,16 @@ int spamm_multiply_noalloc(const double* A, const double* B, double* C, int n, d
  * own CUDA stream, so admitted requests overlap on the device.  Y and Z of a
  * request are written exactly as spamm_sqrt_invsqrt(S, n, tau, maxit, Y, Z,
  * opts) writes them: a result does not depend on the other requests.  Work
- * runs on the device that is current when the server is created.  The
- * caller keeps S, Y and Z valid until the request is waited for.
+ * runs on the device that is current when the server is created, on the
+ * workers' own streams: S must hold its final values when it is submitted
+ * (finish the work that writes it first).  The caller keeps S, Y and Z
+ * valid until the request is waited for.  When the options are ones the
+ * batched solve covers (dual channel, alpha = 1 map, leaf != 0) and a
+ * request's matrices are device or page-locked memory, a free worker takes
+ * the head of the queue together with the requests queued behind it (same
+ * maxit, at most 64, within budget / max_active of device memory) and
+ * solves them as one batch, sharing every kernel launch of their
+ * iterations; each result is still the one a single call gives.
  */
 typedef struct spamm_server spamm_server;
 

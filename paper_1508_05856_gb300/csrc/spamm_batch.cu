@@ -403,13 +403,19 @@ int capture(Batch* b, double mu_rel) {
     return err;
 }
 
+// (Re)builds b for a new set of problems: sizes, the arena (kept when it is large enough, else replaced;
+// limit > 0 caps its size, limit = 0 allows 70 % of the free device memory), the tables and the graph.
 int build_batch(Batch* b, int count, const double* const* dS, const int* n, const double* tau, int maxit,
-                double* const* dY, double* const* dZ, const spamm_opts& o) {
+                double* const* dY, double* const* dZ, const spamm_opts& o, size_t limit) {
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
     b->count = count;
     b->leaf = o.leaf;
     b->maxit = maxit;
     b->emu = o.precision == SPAMM_EMU64;
-    b->mats.resize(count);
+    b->mats.assign(count, BatchMat());
     long cap0 = 0, cap1 = 0, blk0 = 0, blk1 = 0;
     for (int q = 0; q < count; ++q) {
         BatchMat& M = b->mats[q];
@@ -435,34 +441,44 @@ int build_batch(Batch* b, int count, const double* const* dS, const int* n, cons
     b->cap[1] = (int)cap1;
     b->ncull_blocks[0] = (int)blk0;
     b->ncull_blocks[1] = (int)blk1;
-    // size, then the allocation (when it does not fit next to what the device holds, the caller solves the
-    // matrices one by one instead)
+    // size, then the allocation (when it does not fit, the caller solves the matrices one by one instead)
+    Arena keep = b->arena;
     b->arena = Arena();
     b->arena.size = ~size_t(0) >> 1;
     layout(b);
     const size_t bytes = b->arena.used;
-    size_t fr = 0, tot = 0;
-    BK(cudaMemGetInfo(&fr, &tot));
-    if (bytes > fr / 10 * 7) {
-        set_error_message("batch footprint exceeds the free device memory");
-        return SPAMM_ERR_NOMEM;
+    b->arena = keep;
+    if (!b->arena.base || b->arena.size < bytes) {
+        size_t fr = 0, tot = 0;
+        BK(cudaMemGetInfo(&fr, &tot));
+        if (b->arena.base) fr += b->arena.size;
+        const size_t cap = limit ? limit : fr / 10 * 7;
+        if (bytes > cap) {
+            set_error_message("batch footprint exceeds the memory it may use");
+            return SPAMM_ERR_NOMEM;
+        }
+        cudaFree(b->arena.base);
+        b->arena = Arena();
+        const size_t want = std::min(cap, bytes + bytes / 2);  // headroom for the next, slightly larger batch
+        BK(cudaMalloc(reinterpret_cast<void**>(&b->arena.base), want));
+        b->arena.size = want;
     }
-    b->arena = Arena();
-    BK(cudaMalloc(reinterpret_cast<void**>(&b->arena.base), bytes));
-    b->arena.size = bytes;
+    b->arena.used = 0;
     if (!layout(b)) {
         set_error_message("batch layout overflow");
         return SPAMM_ERR_CUDA;
     }
     int e = upload_tables(b, o.order, o.tol_t);
     if (e) return e;
-    BK(cudaStreamCreateWithFlags(&b->gst, cudaStreamNonBlocking));
-    BK(cudaStreamCreateWithFlags(&b->bst, cudaStreamNonBlocking));
-    BK(cudaStreamCreateWithFlags(&b->sst, cudaStreamNonBlocking));
-    for (auto& f : b->fork) BK(cudaStreamCreateWithFlags(&f, cudaStreamNonBlocking));
-    for (cudaEvent_t* ev : {&b->ev_fork, &b->ev_sliced, &b->ev_in, &b->ev_out})
-        BK(cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
-    for (auto& ev : b->ev_join) BK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    if (!b->gst) {
+        BK(cudaStreamCreateWithFlags(&b->gst, cudaStreamNonBlocking));
+        BK(cudaStreamCreateWithFlags(&b->bst, cudaStreamNonBlocking));
+        BK(cudaStreamCreateWithFlags(&b->sst, cudaStreamNonBlocking));
+        for (auto& f : b->fork) BK(cudaStreamCreateWithFlags(&f, cudaStreamNonBlocking));
+        for (cudaEvent_t* ev : {&b->ev_fork, &b->ev_sliced, &b->ev_in, &b->ev_out})
+            BK(cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
+        for (auto& ev : b->ev_join) BK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    }
     return capture(b, o.mu_rel);
 }
 
@@ -471,7 +487,7 @@ std::mutex g_batch_mu;
 std::unique_ptr<Batch> g_batch[64];
 
 // Statistics and status of every matrix after a run (the caller's stream is synchronised).
-int collect(Batch* b, const spamm_opts& o, cudaStream_t st, spamm_stats* stats) {
+int collect(Batch* b, const spamm_opts& o, cudaStream_t st, spamm_stats* stats, int* statuses = nullptr) {
     const int c = b->count;
     const int mi = std::max(1, b->maxit);
     std::vector<int> mf(4 * (size_t)c);
@@ -536,6 +552,7 @@ int collect(Batch* b, const spamm_opts& o, cudaStream_t st, spamm_stats* stats) 
             status = SPAMM_ERR_NOTCONVERGED;
             msg = "maxit reached before |t_k| <= tol_t";
         }
+        if (statuses) statuses[q] = status;
         if (status && !first) {
             first = status;
             first_msg = msg;
@@ -545,25 +562,27 @@ int collect(Batch* b, const spamm_opts& o, cudaStream_t st, spamm_stats* stats) 
     return first;
 }
 
-}  // namespace
-
-// Batched solve of `count` problems in one graph (see the top of this file); SPAMM_ERR_UNSUPPORTED when the
-// options or pointers call for the per-matrix path (the message is left untouched then).
-int batched_solve(int count, const double* const* S, const int* n, const double* tau, int maxit,
-                  double* const* Y, double* const* Z, const spamm_opts& o, spamm_stats* stats) {
+// Whether the engine serves these options (the rest go through the per-matrix path).
+bool engine_covers(const spamm_opts& o) {
     static const bool off = [] {
         const char* v = getenv("SPAMM_NO_BATCH_ENGINE");
         return v && v[0] && v[0] != '0';
     }();
-    if (off || o.map != SPAMM_MAP_NS || o.channel != SPAMM_CHANNEL_DUAL || o.residual || o.profile || o.leaf == 0 ||
-        count < 1 || 2 * count > kMaxStageProducts)
-        return SPAMM_ERR_UNSUPPORTED;
+    return !off && o.map == SPAMM_MAP_NS && o.channel == SPAMM_CHANNEL_DUAL && !o.residual && !o.profile &&
+           o.leaf != 0;
+}
+
+// The batched solve in a caller-held slot.  SPAMM_ERR_UNSUPPORTED (message untouched) when the per-matrix
+// path must serve the call.
+int solve_in_slot(std::unique_ptr<Batch>& slot, int count, const double* const* S, const int* n, const double* tau,
+                  int maxit, double* const* Y, double* const* Z, const spamm_opts& o, spamm_stats* stats,
+                  size_t limit, int* statuses = nullptr) {
+    if (!engine_covers(o) || count < 1 || 2 * count > kMaxStageProducts) return SPAMM_ERR_UNSUPPORTED;
     if (stats)
         for (int q = 0; q < count; ++q)
             if (stats[q].lens_hist) return SPAMM_ERR_UNSUPPORTED;
     int dev = 0;
     BK(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return SPAMM_ERR_UNSUPPORTED;
     std::vector<const double*> dS(count);
     std::vector<double*> dY(count), dZ(count);
     for (int q = 0; q < count; ++q) {
@@ -596,20 +615,20 @@ int batched_solve(int count, const double* const* S, const int* n, const double*
         key.ptrs.push_back(dZ[q]);
     }
     init_device_attributes();
-    std::lock_guard<std::mutex> lk(g_batch_mu);
-    std::unique_ptr<Batch>& slot = g_batch[dev];
-    if (!slot || !(slot->key == key)) {
-        slot.reset();
-        std::unique_ptr<Batch> b(new Batch);
-        b->device = dev;
-        b->key = key;
-        const int e = build_batch(b.get(), count, dS.data(), n, tau, maxit, dY.data(), dZ.data(), o);
+    if (slot && slot->device != dev) slot.reset();
+    if (!slot || !slot->exec || !(slot->key == key)) {
+        if (!slot) {
+            slot.reset(new Batch);
+            slot->device = dev;
+        }
+        slot->key = BatchKey();
+        const int e = build_batch(slot.get(), count, dS.data(), n, tau, maxit, dY.data(), dZ.data(), o, limit);
         if (e == SPAMM_ERR_NOMEM) {
             cudaGetLastError();
             return SPAMM_ERR_UNSUPPORTED;  // too large to hold at once: solved one by one
         }
         if (e) return e;
-        slot = std::move(b);
+        slot->key = key;
     }
     Batch* b = slot.get();
     cudaStream_t st = static_cast<cudaStream_t>(o.stream);
@@ -618,7 +637,47 @@ int batched_solve(int count, const double* const* S, const int* n, const double*
     BK(cudaGraphLaunch(b->exec, b->gst));
     BK(cudaEventRecord(b->ev_out, b->gst));
     BK(cudaStreamWaitEvent(st, b->ev_out, 0));
-    return collect(b, o, st, stats);
+    return collect(b, o, st, stats, statuses);
+}
+
+}  // namespace
+
+// Batched solve of `count` problems in one graph (see the top of this file), in the batch cached for the
+// current device.
+int batched_solve(int count, const double* const* S, const int* n, const double* tau, int maxit,
+                  double* const* Y, double* const* Z, const spamm_opts& o, spamm_stats* stats) {
+    if (!engine_covers(o)) return SPAMM_ERR_UNSUPPORTED;
+    int dev = 0;
+    BK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return SPAMM_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    return solve_in_slot(g_batch[dev], count, S, n, tau, maxit, Y, Z, o, stats, 0);
+}
+
+// A batch owned by its caller (one per request-server worker): buffers and graph kept between calls.
+struct BatchSlot {
+    std::unique_ptr<Batch> b;
+};
+BatchSlot* batch_slot_create() { return new BatchSlot; }
+void batch_slot_destroy(BatchSlot* s) { delete s; }
+int batched_solve_slot(BatchSlot* s, int count, const double* const* S, const int* n, const double* tau, int maxit,
+                       double* const* Y, double* const* Z, const spamm_opts& o, spamm_stats* stats, size_t limit,
+                       int* statuses) {
+    return solve_in_slot(s->b, count, S, n, tau, maxit, Y, Z, o, stats, limit, statuses);
+}
+bool batch_engine_covers(const spamm_opts& o) { return engine_covers(o); }
+
+// Device bytes one matrix adds to a batch (its five tile buffers with trees, slices and maxima, its two task
+// lists, its stage-list entries and its share of the tables).
+size_t batch_footprint(int n, int nb, int precision, int maxit) {
+    const Geometry g = make_geometry(n, nb);
+    const size_t mm = (size_t)g.m * g.m;
+    size_t b = 5 * (g.elems() + (size_t)g.tree_size) * sizeof(double);
+    if (precision == SPAMM_EMU64) b += 5 * (2 * emu_slice_bytes_per_tile() * mm + 2 * (size_t)g.m * g.nb * 8);
+    b += 2 * (mm + mm * g.m) * sizeof(int) + ((size_t)g.m + 16 + (size_t)n) * sizeof(double);
+    b += 3 * mm * (kTileBuckets + 1) * sizeof(int) + 6 * sizeof(ProdDesc) + 3 * ((mm + 7) / 8) * sizeof(int4);
+    b += 4 * sizeof(int) + 4 * sizeof(double) * (size_t)std::max(1, maxit);  // stop flags, t_k and task counts
+    return b + 32 * 256;                                                      // alignment of the pieces
 }
 
 // Frees the cached batches (no work may be in flight).

@@ -318,6 +318,17 @@ void launch_tree_batched(const ProdDesc* prods, int nprod, int* tile_count, int*
 int batched_solve(int count, const double* const* S, const int* n, const double* tau, int maxit,
                   double* const* Y, double* const* Z, const spamm_opts& o, spamm_stats* stats);
 void release_batches();
+// Caller-owned batches (the request server's workers): the same engine with buffers and graph kept per slot;
+// limit caps the slot's device memory (0: 70 % of the free memory).
+struct BatchSlot;
+BatchSlot* batch_slot_create();
+void batch_slot_destroy(BatchSlot* s);
+// statuses (may be null): every problem's own status.
+int batched_solve_slot(BatchSlot* s, int count, const double* const* S, const int* n, const double* tau, int maxit,
+                       double* const* Y, double* const* Z, const spamm_opts& o, spamm_stats* stats, size_t limit,
+                       int* statuses);
+bool batch_engine_covers(const spamm_opts& o);
+size_t batch_footprint(int n, int nb, int precision, int maxit);
 // Digit slices of the items a batched leaf-product launch drew (slice_items, count at slice_items[cap]).
 void launch_slice_batched(const ProdDesc* prods, const int* slice_items, int cap, const int* all_done,
                           cudaStream_t st);

@@ -70,3 +70,28 @@ def test_plan_cache_stays_bounded_over_many_sizes():
         # idle plans <= total/4, plus the plan in use, plus torch's own tensors of this step
         assert free0 - free <= total // 4 + (4 << 30), (k, free0 - free)
     sp.release()
+
+
+@pytest.mark.parametrize("precision", [sp.FP64, sp.EMU64])
+def test_server_groups_queued_requests_into_shared_launches(precision):
+    """Device-resident requests queued behind a busy worker are solved as one batch: every stage of their
+    iterations is one launch over all of them (far fewer launches than one solve per request), and each
+    result is still bitwise the standalone one."""
+    reqs = _mix(12, seed=5)
+    mats = [dev(S) for S, _ in reqs]
+    alone = [sp.sqrt_invsqrt(S, tau, 16, leaf=64, precision=precision) for S, (_, tau) in zip(mats, reqs)]
+    torch.cuda.synchronize()
+    l0 = sp.kernel_launches()
+    for S, (_, tau) in zip(mats, reqs):
+        sp.sqrt_invsqrt(S, tau, 16, leaf=64, precision=precision)
+    torch.cuda.synchronize()
+    l_alone = sp.kernel_launches() - l0
+    with sp.Server(bytes_budget=16 << 30, max_active=1, leaf=64, precision=precision) as srv:
+        l0 = sp.kernel_launches()
+        ids = [srv.submit(S, tau, 16) for S, (_, tau) in zip(mats, reqs)]
+        outs = [srv.wait(i) for i in ids]
+        l_served = sp.kernel_launches() - l0
+    for (Y1, Z1, st1), (Y, Z, st, lat) in zip(alone, outs):
+        assert torch.equal(Y, Y1) and torch.equal(Z, Z1)
+        assert st["status"] == 0 and st["iters"] == st1["iters"] and st["tasks_total"] == st1["tasks_total"]
+    assert l_served < 0.6 * l_alone, (l_served, l_alone)
