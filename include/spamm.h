@@ -57,7 +57,10 @@ extern "C" {
                                         outputs are still written              */
 #define SPAMM_ERR_NOTCONVERGED (-4)  /* tol_t > 0 and maxit reached with
                                         |t_k| > tol_t; outputs are written      */
-#define SPAMM_ERR_TIMEOUT (-5)       /* a bounded device-side wait expired      */
+#define SPAMM_ERR_TIMEOUT (-5)       /* a bounded device-side wait expired
+                                        (every wait inside the kernels gives
+                                        up after a fixed number of polls; see
+                                        spamm_test_expire_next_wait)           */
 #define SPAMM_ERR_ADMIT (-6)         /* server: request footprint exceeds the
                                         memory budget                          */
 #define SPAMM_ERR_CUDA (-7)          /* a CUDA runtime call failed              */
@@ -332,6 +335,18 @@ int spamm_server_wait(spamm_server* server, long long id, double timeout_s, spam
 
 /* Finish every queued and running request, then free the server. */
 int spamm_server_destroy(spamm_server* server);
+
+/*
+ * Failure-path check of the bounded device waits.  The next spamm_multiply
+ * with SPAMM_EMU64 on the calling thread makes every CTA of its tensor-core
+ * leaf-product kernel first wait on an mbarrier that nothing arrives at, for
+ * at most `polls` polls.  The wait expires, as any internal wait of the kernel
+ * does after its own limit, before the CTA has issued a copy or a product:
+ * the kernel records the error, frees its tensor memory and exits, and the
+ * call returns SPAMM_ERR_TIMEOUT (C is not valid).  Later calls run normally.
+ * polls = 0 clears a pending request.  SPAMM_ERR_ARG for polls < 0.
+ */
+int spamm_test_expire_next_wait(long long polls);
 
 /* Message for the calling thread's last failure ("" if none). */
 const char* spamm_last_error(void);

@@ -361,6 +361,9 @@ struct EmuArgs {
     const ProdDesc* prods;
     int* slice_items;
     int cap;
+    long long poll_limit;   // polls of every internal wait before it expires
+    long long stall_polls;  // > 0: every CTA first waits this long on a barrier nothing arrives at (the
+                            // expired-wait path, taken with nothing in flight)
 };
 
 // What the producer warp needs of an output tile's product.
@@ -496,9 +499,13 @@ __device__ __forceinline__ void flush_groups(uint32_t lane_col_base, int half, l
     }
 }
 
+// Polls of the waits that drain an aborted CTA's copies and products before it exits.
+constexpr long long kDrainPolls = 1ll << 22;
+
 // Bounded wait that also gives up when another role of this CTA aborted.
-__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
-    for (long long it = 0; it < (1ll << 22); ++it) {
+__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                              long long limit) {
+    for (long long it = 0; it < limit; ++it) {
         if (ptx::mbar_try_wait(bar, parity)) return true;
         if ((it & 255) == 255 && *abort_flag) return false;
     }
@@ -520,6 +527,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
     extern __shared__ uint8_t dyn_smem[];
     __shared__ __align__(8) uint64_t bar_full[NSTAGE], bar_empty[NSTAGE], bar_accf, bar_acce;
     __shared__ __align__(8) uint64_t bar_tready[2], bar_tfree[2];
+    __shared__ __align__(8) uint64_t bar_stall, bar_drain;
     __shared__ uint32_t tmem_base_sh;
     __shared__ int tasks_sh[2][kMaxTasks];
     __shared__ int ntask_sh[2];
@@ -556,6 +564,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
         }
         ptx::mbar_init(&bar_accf, 1);
         ptx::mbar_init(&bar_acce, kEpiWarps);
+        ptx::mbar_init(&bar_stall, 1);
+        ptx::mbar_init(&bar_drain, 1);
         for (int q = 0; q < 2; ++q) {
             ptx::mbar_init(&bar_tready[q], 1);
             ptx::mbar_init(&bar_tfree[q], kEpiWarps);
@@ -572,6 +582,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
     ptx::tc_fence_after();
     const uint32_t tmem = tmem_base_sh;
     volatile int* abort_flag = &abort_sh;
+    if (a.stall_polls > 0) {
+        // nothing arrives at bar_stall: the wait expires, the CTA records the error and every role stops
+        // before issuing a copy or a product
+        if (threadIdx.x == 0 && !wait_or_abort(&bar_stall, 0u, abort_flag, a.stall_polls)) atomicExch(a.err, 5);
+        __syncthreads();
+    }
 
     if (warp == 0) {
         // ---------------- producer: per tile the task list and scales, then the half-task stream
@@ -615,7 +631,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
             }
             if (tau >= 2) {
                 bool ok = true;
-                if (lane == 0) ok = wait_or_abort(&bar_tfree[slot], (uint32_t)(((tau >> 1) & 1) ^ 1), abort_flag);
+                if (lane == 0) ok = wait_or_abort(&bar_tfree[slot], (uint32_t)(((tau >> 1) & 1) ^ 1), abort_flag, a.poll_limit);
                 ok = __shfl_sync(0xffffffffu, ok, 0);
                 if (!ok) {
                     if (lane == 0) atomicExch(a.err, 1);
@@ -663,7 +679,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
                     for (int h = 0; h < 2; ++h, ++H) {
                         const int s = (int)(H % NSTAGE);
                         if (H >= NSTAGE &&
-                            !wait_or_abort(&bar_empty[s], (uint32_t)(((H / NSTAGE) - 1) & 1), abort_flag)) {
+                            !wait_or_abort(&bar_empty[s], (uint32_t)(((H / NSTAGE) - 1) & 1), abort_flag, a.poll_limit)) {
                             atomicExch(a.err, 1);
                             break;
                         }
@@ -678,6 +694,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
             __syncwarp();
             idx = __shfl_sync(0xffffffffu, nxt, 0);
         }
+        // an aborted CTA leaves no copy in flight: wait (bounded) for the last copy issued on every stage
+        if (lane == 0 && *abort_flag)
+            for (int s = 0; s < NSTAGE; ++s)
+                if (H > s) {
+                    const long long hl = s + ((H - 1 - s) / NSTAGE) * NSTAGE;
+                    ptx::mbar_wait_bounded(&bar_full[s], (uint32_t)((hl / NSTAGE) & 1), kDrainPolls);
+                }
     } else if (warp == 1) {
         // ---------------- MMA issuer: tasks accumulate in TMEM in chunks of kChunk
         if (lane == 0) {
@@ -689,7 +712,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
             bool ok = true;
             for (; ok; ++tau) {
                 const int slot = tau & 1;
-                if (!wait_or_abort(&bar_tready[slot], (uint32_t)((tau >> 1) & 1), abort_flag)) {
+                if (!wait_or_abort(&bar_tready[slot], (uint32_t)((tau >> 1) & 1), abort_flag, a.poll_limit)) {
                     atomicExch(a.err, 2);
                     break;
                 }
@@ -700,14 +723,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
                     units += 12;  // twelve stacked (stack, slice) products per task
                     for (int h = 0; h < 2; ++h, ++H) {
                         const int s = (int)(H % NSTAGE);
-                        if (!wait_or_abort(&bar_full[s], (uint32_t)((H / NSTAGE) & 1), abort_flag)) {
+                        if (!wait_or_abort(&bar_full[s], (uint32_t)((H / NSTAGE) & 1), abort_flag, a.poll_limit)) {
                             atomicExch(a.err, 2);
                             ok = false;
                             break;
                         }
                         // a new chunk overwrites the accumulators: the epilogue must have read the previous one
                         if (chunk_start && h == 0 && C > 0 &&
-                            !wait_or_abort(&bar_acce, (uint32_t)((C - 1) & 1), abort_flag)) {
+                            !wait_or_abort(&bar_acce, (uint32_t)((C - 1) & 1), abort_flag, a.poll_limit)) {
                             atomicExch(a.err, 3);
                             ok = false;
                             break;
@@ -737,6 +760,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
                     }
                 }
             }
+            // an aborted CTA leaves no product in flight: commit and wait (bounded) for everything issued
+            if (*abort_flag && H > 0) {
+                ptx::mma_commit(&bar_drain);
+                ptx::mbar_wait_bounded(&bar_drain, 0u, kDrainPolls);
+            }
             if (a.units && units) atomicAdd(a.units, units);
         }
         __syncwarp();
@@ -754,7 +782,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
         int tau = 0;
         for (;; ++tau) {
             const int slot = tau & 1;
-            if (!wait_or_abort(&bar_tready[slot], (uint32_t)((tau >> 1) & 1), abort_flag)) {
+            if (!wait_or_abort(&bar_tready[slot], (uint32_t)((tau >> 1) & 1), abort_flag, a.poll_limit)) {
                 atomicExch(a.err, 4);
                 break;
             }
@@ -770,7 +798,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
             for (int c = 0; c < 16; ++c) acc[c] = 0;
             bool ok = true;
             for (int ck = 0; ck < nchunks; ++ck, ++C) {
-                if (!wait_or_abort(&bar_accf, (uint32_t)(C & 1), abort_flag)) {
+                if (!wait_or_abort(&bar_accf, (uint32_t)(C & 1), abort_flag, a.poll_limit)) {
                     atomicExch(a.err, 4);
                     ok = false;
                     break;
@@ -862,6 +890,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
         if (atomicAdd(a.sched + 1, 1) == participants - 1) {
             a.sched[0] = 0;
             a.sched[1] = 0;
+            // after an expired wait the drawn-tile list is incomplete: the slicing pass gets none
+            if (*a.err) drawn[lstride] = 0;
         }
     }
 }
@@ -905,7 +935,7 @@ void launch_slice_batched(const ProdDesc* prods, const int* slice_items, int cap
 void launch_gemm_emu(const Geometry& g, const TileMat& A, const TileMat& B, const TileMat& C, const int* counts,
                      const int* jlist, const int* tile_list, const int* tile_count, EpiMode mode, double* trace_part,
                      int* sched, const int* done, int* err, double tau, cudaStream_t st, int buckets,
-                     unsigned long long* units) {
+                     unsigned long long* units, long long stall_polls) {
     emu::EmuArgs a;
     a.sliceA = A.sliceA;
     a.sliceB = B.sliceB;
@@ -937,6 +967,8 @@ void launch_gemm_emu(const Geometry& g, const TileMat& A, const TileMat& B, cons
     a.prods = nullptr;
     a.slice_items = nullptr;
     a.cap = 0;
+    a.poll_limit = 1ll << 22;
+    a.stall_polls = stall_polls;
     const int grid = std::min(device_sm_count(), g.m * g.m);
     launch_dependent(emu::k_gemm_emu<false>, dim3(grid), dim3(emu::kThreads), emu::SMEM_DYN, st, a);
     note_launch();
@@ -956,6 +988,8 @@ void launch_gemm_emu_batched(const ProdDesc* prods, const int* tile_list, const 
     a.done = all_done;
     a.err = err;
     a.units = units;
+    a.poll_limit = 1ll << 22;
+    a.stall_polls = 0;
     const int grid = std::min(device_sm_count(), cap);
     launch_dependent(emu::k_gemm_emu<true>, dim3(grid), dim3(emu::kThreads), emu::SMEM_DYN, st, a);
     note_launch();

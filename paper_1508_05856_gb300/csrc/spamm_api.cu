@@ -182,6 +182,7 @@ struct Plan {
     long long gemm_launches = 0;
     unsigned long long last_use = 0;  // release order, for evicting the least recently used idle plan
     bool emu = false;        // this call uses the tensor-core (SPAMM_EMU64) leaf products
+    long long stall_polls = 0;  // the next tensor-core leaf-product launch takes its expired-wait path
     bool emu_ready = false;  // slice buffers allocated
     // CUDA graph of the last fixed-iteration solve and what it was captured for
     cudaGraphExec_t gexec = nullptr;
@@ -639,7 +640,8 @@ static void product(Plan* p, const TileMat& A, const TileMat& B, TileMat& C, dou
         if (p->emu) {
             launch_gemm_emu(g, A, B, C, counts, jlist, tile_list, tile_count, mode, p->trace_part,
                             p->flags + 8 + 2 * slot, p->flags, p->flags + 2, tau, st, kTileBuckets,
-                            tensor_units(p));
+                            tensor_units(p), p->stall_polls);
+            p->stall_polls = 0;
         } else {
             launch_gemm_f64(g, A.t, B.t, C.t, A.tree, B.tree, C.tree, counts, jlist, tile_list, tile_count, 0,
                             mode, p->trace_part, p->flags, st, kTileBuckets);
@@ -689,6 +691,10 @@ static void join_slicing(Plan* p, cudaStream_t st) {
     p->sliced_mask = 0;
 }
 
+// Set by spamm_test_expire_next_wait: the next tensor-core product of this thread takes the kernel's
+// expired-wait path.
+static thread_local long long t_stall_next = 0;
+
 static int multiply_core(const double* A, const double* B, double* C, int n, double tau, const spamm_opts& o,
                          spamm_stats* stats) {
     cudaStream_t st = (cudaStream_t)o.stream;
@@ -706,6 +712,10 @@ static int multiply_core(const double* A, const double* B, double* C, int n, dou
     if ((e = out_target(p, 2, C, &dC))) return e;
     begin_call(p, o.profile != 0, o.precision == SPAMM_EMU64);
     if (p->emu && (e = ensure_emu(p))) return e;
+    if (p->emu) {
+        p->stall_polls = t_stall_next;
+        t_stall_next = 0;
+    }
     CK(cudaMemsetAsync(p->flags, 0, kFlagInts * sizeof(int), st));
     CK(cudaMemsetAsync(p->task_ctr, 0, 4 * sizeof(unsigned long long), st));
     launch_pack(dA, n, g, nullptr, nullptr, p->buf[0], st);
@@ -1438,6 +1448,15 @@ int spamm_autotune_leaf(const double* S, int n, double tau, const spamm_opts* op
         g_last_error = "internal exception";
         return SPAMM_ERR_CUDA;
     }
+}
+
+int spamm_test_expire_next_wait(long long polls) {
+    if (polls < 0) {
+        g_last_error = "polls must be >= 0";
+        return SPAMM_ERR_ARG;
+    }
+    t_stall_next = polls;
+    return SPAMM_OK;
 }
 
 int spamm_multiply(const double* A, const double* B, double* C, int n, double tau, const spamm_opts* opts,

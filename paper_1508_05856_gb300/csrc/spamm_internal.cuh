@@ -349,11 +349,14 @@ void launch_slice(const double* X, const double* leaf, double* leaf_out, const u
 // (double-word FP32 sums, about 2^-44 relative), row/column maxima
 // (pre-zeroed), trace partials for EPI_NS_X, and C.slice_list; *err set on a
 // timed-out internal wait.  units (may be null) gets += the (stack, slice)
-// units issued: twelve 128 x 64 x 64 FP16 products per task.
+// units issued: twelve 128 x 64 x 64 FP16 products per task.  stall_polls > 0
+// makes every CTA first wait that many polls on a barrier nothing arrives at:
+// the expired-wait path (error 5 in *err, no copy or product issued, tensor
+// memory freed, no tile handed to the slicing pass).
 // sched: two ints, zero before the first launch; the kernel leaves them zero.
 void launch_gemm_emu(const Geometry& g, const TileMat& A, const TileMat& B, const TileMat& C, const int* counts,
                      const int* jlist, const int* tile_list, const int* tile_count, EpiMode mode, double* trace_part,
                      int* sched, const int* done, int* err, double tau, cudaStream_t st, int buckets = 1,
-                     unsigned long long* units = nullptr);
+                     unsigned long long* units = nullptr, long long stall_polls = 0);
 
 }  // namespace spamm

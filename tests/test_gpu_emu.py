@@ -208,3 +208,25 @@ def test_emu_product_representation_matches_oracle():
     assert info["iters"] == list(ref["iters"])
     Z = Z.cpu().numpy()
     assert np.linalg.norm(Z - ref["Z"]) <= 1e-8 * np.linalg.norm(ref["Z"])
+
+
+def test_expired_device_wait_returns_timeout_and_the_next_call_succeeds():
+    """Every wait inside the tensor-core kernel gives up after a bounded number of polls.  Here one is made to
+    expire (a barrier nothing arrives at, before any copy or product is issued): the call reports
+    SPAMM_ERR_TIMEOUT instead of hanging, the kernel frees its tensor memory, and the next calls (and other
+    work on the device) run normally with the same results as before."""
+    A = dev(synth.decay_matrix(448, seed=21, length=40.0))
+    B = dev(synth.decay_matrix(448, seed=22, length=30.0))
+    C0, _ = sp.multiply(A, B, 1e-9, leaf=64, precision=sp.EMU64)
+    assert sp.lib().spamm_test_expire_next_wait(-1) == -1
+    assert sp.lib().spamm_test_expire_next_wait(64) == 0
+    with pytest.raises(sp.SpammError) as ei:
+        sp.multiply(A, B, 1e-9, leaf=64, precision=sp.EMU64)
+    assert ei.value.status == -5
+    C1, _ = sp.multiply(A, B, 1e-9, leaf=64, precision=sp.EMU64)
+    assert torch.equal(C0, C1)
+    Y, Z, st = sp.sqrt_invsqrt(dev(synth.kms(256, 0.8)), 1e-10, 12, leaf=64, precision=sp.EMU64)
+    assert st["status"] == 0
+    x = torch.arange(1, 1025, device="cuda", dtype=torch.float64).sum()
+    torch.cuda.synchronize()
+    assert float(x) == 1024 * 1025 / 2
