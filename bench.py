@@ -302,7 +302,7 @@ def run_gpu(args, ws, rank, local):
 
     # verification solve (untimed): residual against the gate, FP64 dense; its Y and Z are compared with the
     # oracle's solve of the same input on rank 0
-    _, _, vst = solve(tau, residual=True)
+    _, _, vst = solve(tau, residual=True, raise_on=False)
     Yv, Zv = (Yd.cpu().numpy(), Zd.cpu().numpy()) if rank == 0 else (None, None)
     lensing = None
     if args.lens_bins > 0:
@@ -552,7 +552,7 @@ def run_gpu(args, ws, rank, local):
             "latency_ms": {"p50": p50, "p99": p99},
             "resid_F": vst["resid_F"], "gate": GATE, "gate_met": bool(vst["resid_F"] <= GATE),
             "tasks_per_solve": vst["tasks_total"], "volume_pct": 100.0 * vst["tasks_total"] / vst["tasks_dense"],
-            "t_final": vst["t_final"], "iters": vst["iters"],
+            "t_final": vst["t_final"], "iters": vst["iters"], "status": sp.STATUS.get(vst["status"]),
             "err_vs_oracle": oracle_err,
             "err_tolerance": {"Z": 1e-9 if prec == sp.EMU64 else 1e-10, "Y": 1e-9 if prec == sp.EMU64 else 1e-10},
             "roofline": roof,

@@ -51,9 +51,10 @@ extern "C" {
 #define SPAMM_ERR_DIVERGED (-3)      /* t_k not finite or |t_k| >= 1: the
                                         iteration left its basin of stability
                                         (Sec. 3, Sec. 5.1); or, when the
-                                        residual is computed, ||ZSZ - I||_F >= 1:
-                                        culling errors carried Y and Z off the
-                                        roots (X = YZ can still look converged);
+                                        residual is computed, |t_k| < 1e-8 with
+                                        ||ZSZ - I||_F >= 1: culling errors
+                                        carried Y and Z off the roots while
+                                        X = YZ looks converged;
                                         outputs are still written              */
 #define SPAMM_ERR_NOTCONVERGED (-4)  /* tol_t > 0 and maxit reached with
                                         |t_k| > tol_t; outputs are written      */

@@ -1256,9 +1256,11 @@ static int sqrt_impl(const double* S, int n, double tau, int maxit, double* Y, d
             return SPAMM_ERR_DIVERGED;
         }
     // The trace error follows X = YZ, which stays near I even when culling has moved Y and Z off the
-    // square roots of S.  With the residual computed, ||Z S Z - I||_F >= 1 says so: Z is then outside the
-    // region ||I - Z S Z|| < 1 in which a further Newton-Schulz refinement is guaranteed to converge.
-    if (o.residual && !(resid < 1.0)) {
+    // square roots of S.  With the residual computed, a solve whose trace error says converged
+    // (|t_k| < 1e-8) while ||Z S Z - I||_F >= 1 has reached a wrong fixed point: Z is outside the region
+    // ||I - Z S Z|| < 1 in which a further Newton-Schulz refinement is guaranteed to converge.  (A solve cut
+    // short by maxit, with a large trace error, is not converged, not diverged.)
+    if (o.residual && iters > 0 && std::fabs(t_final) < 1e-8 && !(resid < 1.0)) {
         g_last_error = "||Z S Z - I||_F >= 1: Z is no longer an approximate inverse square root of S";
         return SPAMM_ERR_DIVERGED;
     }
