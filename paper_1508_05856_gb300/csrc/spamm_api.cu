@@ -472,10 +472,25 @@ static spamm_opts resolve_opts(const spamm_opts* o) {
 }
 
 // Device view of a caller matrix: the pointer itself (or its device mapping), or a staged copy.
-static int stage_in(Plan* p, int which, const double* src, cudaStream_t st, const double** dev) {
+// A caller matrix in host memory (page-locked or not).
+static bool host_memory(const void* ptr) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
+}
+
+// read_once: the kernels read the input a single time, so page-locked host memory is read in place through
+// its device mapping; an input read more than once (the solve's S: row sums, then the pack) is copied to
+// the device once instead, by the copy engine, so that the link carries it once.
+static int stage_in(Plan* p, int which, const double* src, cudaStream_t st, const double** dev,
+                    bool read_once = true) {
     void* v = nullptr;
     int e = pointer_view(src, p->device, &v);
     if (e) return e;
+    if (v && !read_once && host_memory(src)) v = nullptr;
     if (v) {
         *dev = static_cast<const double*>(v);
         return SPAMM_OK;
@@ -1176,7 +1191,7 @@ static int sqrt_impl(const double* S, int n, double tau, int maxit, double* Y, d
     if ((e = ensure_hist(p, maxit > 0 ? maxit : 1))) return e;
     const double* dS;
     double *dY, *dZ;
-    if ((e = stage_in(p, 0, S, st, &dS))) return e;
+    if ((e = stage_in(p, 0, S, st, &dS, false))) return e;
     if ((e = out_target(p, 1, Y, &dY))) return e;
     if ((e = out_target(p, 2, Z, &dZ))) return e;
     begin_call(p, o.profile != 0, o.precision == SPAMM_EMU64);
