@@ -239,6 +239,57 @@ __device__ __forceinline__ double pack_tile(const double* __restrict__ src, int 
     return acc;
 }
 
+// Four horizontally adjacent 64 x 64 tiles (i, 4 jb .. 4 jb + 3) per 256-thread block: thread t takes column
+// t of the band in every row, so a row of the band is read as one 2 KB run (the eight warps side by side)
+// and each thread touches a single tile (t / 64); sixteen independent loads at a time.  The leaf norm of a
+// tile is the sum over its two warps of the per-thread sums of squares (rows in order), fixed order.
+template <bool kScale>
+__device__ __forceinline__ void pack_band64(const double* __restrict__ src, int n, int m, int i, int jb, double mu,
+                                            double rc, double* __restrict__ dst, double* __restrict__ leaf,
+                                            double* red) {
+    const int t = threadIdx.x;
+    const int j = 4 * jb + (t >> 6);  // this thread's tile column
+    const int c = t & 63;
+    const int gj = j * 64 + c;
+    const bool colok = j < m && gj < n;
+    double* d = dst + ((size_t)i * m + j) * 4096;
+    double acc = 0.0;
+#pragma unroll 1
+    for (int r0 = 0; r0 < 64; r0 += 16) {
+        double v[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int gi = i * 64 + r0 + u;
+            v[u] = (colok && gi < n) ? src[(size_t)gi * n + gj] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int gi = i * 64 + r0 + u;
+            double x = v[u];
+            if (kScale && colok && gi < n) {
+                if (gi == gj) x += mu;
+                x = x * rc;
+            }
+            if (j < m) d[(r0 + u) * 64 + c] = x;
+            acc = fma(x, x, acc);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((t & 31) == 0) red[t >> 5] = acc;
+    __syncthreads();
+    if (t < 4 && 4 * jb + t < m) leaf[(size_t)i * m + 4 * jb + t] = red[2 * t] + red[2 * t + 1];
+}
+
+__global__ void __launch_bounds__(256) k_pack_band64(const double* __restrict__ src, int n, int m, int bands,
+                                                     const double* __restrict__ mu_dev,
+                                                     const double* __restrict__ rc_dev, double* __restrict__ dst,
+                                                     double* __restrict__ leaf) {
+    __shared__ double red[8];
+    const int i = blockIdx.x / bands, jb = blockIdx.x - (blockIdx.x / bands) * bands;
+    if (rc_dev) pack_band64<true>(src, n, m, i, jb, mu_dev ? *mu_dev : 0.0, *rc_dev, dst, leaf, red);
+    else pack_band64<false>(src, n, m, i, jb, 0.0, 1.0, dst, leaf, red);
+}
+
 template <int NB>
 __global__ void __launch_bounds__(256) k_pack(const double* __restrict__ src, int n, int m,
                                               const double* __restrict__ mu_dev, const double* __restrict__ rc_dev,
@@ -259,9 +310,14 @@ __global__ void __launch_bounds__(256) k_pack(const double* __restrict__ src, in
 void launch_pack(const double* src, int n, const Geometry& g, const double* mu, const double* recip_c,
                  TileMat dst, cudaStream_t st) {
     const dim3 grid(g.m * g.m), block(256);
-    if (g.nb == 32) k_pack<32><<<grid, block, 0, st>>>(src, n, g.m, mu, recip_c, dst.t, dst.tree);
-    else if (g.nb == 64) k_pack<64><<<grid, block, 0, st>>>(src, n, g.m, mu, recip_c, dst.t, dst.tree);
-    else k_pack<128><<<grid, block, 0, st>>>(src, n, g.m, mu, recip_c, dst.t, dst.tree);
+    if (g.nb == 32) {
+        k_pack<32><<<grid, block, 0, st>>>(src, n, g.m, mu, recip_c, dst.t, dst.tree);
+    } else if (g.nb == 64) {
+        const int bands = (g.m + 3) / 4;
+        k_pack_band64<<<dim3(g.m * bands), block, 0, st>>>(src, n, g.m, bands, mu, recip_c, dst.t, dst.tree);
+    } else {
+        k_pack<128><<<grid, block, 0, st>>>(src, n, g.m, mu, recip_c, dst.t, dst.tree);
+    }
     note_launch();
 }
 
