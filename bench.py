@@ -423,6 +423,28 @@ def run_gpu(args, ws, rank, local):
                      "resid_F": fst["resid_F"], "gate_met": bool(fst["resid_F"] <= GATE),
                      "_out": (Yd.cpu().numpy(), Zd.cpu().numpy(), fst) if rank == 0 else None}
 
+    # the other schedule of one solve (the batched engine with one problem: the y and z products share each
+    # launch) and the schedule the autotuner picks for this input
+    schedules = None
+    if TOL <= 0 and MAP == 0 and CHANNEL == 0:
+        sp.sqrt_invsqrt(Sd, tau, MAXIT, leaf=LEAF, precision=prec, Y=Yd, Z=Zd, schedule=sp.SCHED_STAGES)
+        tt = []
+        for _ in range(3):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, _, sst = sp.sqrt_invsqrt(Sd, tau, MAXIT, leaf=LEAF, precision=prec, Y=Yd, Z=Zd,
+                                        schedule=sp.SCHED_STAGES)
+            e1.record(stream)
+            e1.synchronize()
+            tt.append(e0.elapsed_time(e1) / 1e3)
+        _, _, ast = sp.sqrt_invsqrt(Sd, tau, MAXIT, leaf=LEAF, precision=prec, Y=Yd, Z=Zd, schedule=sp.SCHED_AUTO)
+        schedules = {"branches": {"value": value, "unit": UNIT},
+                     "stages": {"value": job_rate(ws, len(tt), max_over_ranks(sum(tt), ws, dev)), "unit": UNIT,
+                                "ran_as": "stages" if sst["schedule"] == sp.SCHED_STAGES else "branches"},
+                     "autotuned": "stages" if ast["schedule"] == sp.SCHED_STAGES else "branches"}
+
     # tau sweep (the configuration's cull-count / error study)
     sweep = []
     if not args.no_sweep:
@@ -558,6 +580,7 @@ def run_gpu(args, ws, rank, local):
             "roofline": roof,
             "norm_cull_kernels": setup,
             "fp64_path": fp64_path,
+            "schedules": schedules,
             "to_tolerance": to_tol,
             "lensing": lensing,
             "cpu_baseline": cpu,

@@ -94,6 +94,20 @@ extern "C" {
                                    (Y = W unscaled, which tends to S^{1/2});
                                    paper order only                            */
 
+/* ---- schedule of one solve's iteration on the device -------------------- */
+#define SPAMM_SCHED_BRANCHES 0  /* the y and z products of an iteration on two
+                                   streams, each product its own cull, leaf-
+                                   product, slicing and quadtree launches      */
+#define SPAMM_SCHED_STAGES 1    /* the batched engine with one problem: the y and
+                                   z products share one launch of each kernel,
+                                   then the x product (dual channel, map
+                                   SPAMM_MAP_NS, device or page-locked S, Y, Z,
+                                   no residual and no profile; otherwise as
+                                   SPAMM_SCHED_BRANCHES)                       */
+#define SPAMM_SCHED_AUTO 2      /* chosen per device, n, arithmetic, leaf and
+                                   decade of tau by timing one solve of the
+                                   call's own input with each (cached)         */
+
 /* ---- order of the two channel products --------------------------------- */
 #define SPAMM_ORDER_PAPER 0       /* Y <- T Y, Z <- Z T, X <- Y Z (as printed)  */
 #define SPAMM_ORDER_TRANSPOSED 1  /* Y <- Y T, Z <- T Z, X <- Z Y: the exact
@@ -117,6 +131,7 @@ typedef struct spamm_opts {
     void* stream;      /* cudaStream_t; NULL = legacy default stream            */
     int map;           /* SPAMM_MAP_NS or SPAMM_MAP_SCALED                      */
     int channel;       /* SPAMM_CHANNEL_DUAL or SPAMM_CHANNEL_SINGLE            */
+    int schedule;      /* SPAMM_SCHED_BRANCHES, _STAGES or _AUTO (solves)       */
 } spamm_opts;
 
 typedef struct spamm_stats {
@@ -157,11 +172,12 @@ typedef struct spamm_stats {
     double slice_ms;           /* opts->profile, SPAMM_EMU64: summed duration of
                                   the products' digit-slicing passes            */
     long long slice_launches;
+    int schedule;              /* the schedule the solve ran with (after AUTO)  */
 } spamm_stats;
 
 /* Fill *opts with defaults: leaf 64, SPAMM_FP64, tau_s = 0.01 tau, no shift,
  * fixed iteration count, paper order, no residual, default stream,
- * SPAMM_MAP_NS, SPAMM_CHANNEL_DUAL. */
+ * SPAMM_MAP_NS, SPAMM_CHANNEL_DUAL, SPAMM_SCHED_BRANCHES. */
 void spamm_opts_init(spamm_opts* opts);
 
 /*

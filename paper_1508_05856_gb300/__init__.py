@@ -23,7 +23,7 @@ import numpy as np
 from . import _build_lib
 
 __all__ = ["FP64", "EMU64", "ORDER_PAPER", "ORDER_TRANSPOSED", "MAP_NS", "MAP_SCALED", "CHANNEL_DUAL",
-           "CHANNEL_SINGLE", "SpammError", "lib", "build", "multiply", "sqrt_invsqrt", "sqrt_invsqrt_batched",
+           "CHANNEL_SINGLE", "SCHED_BRANCHES", "SCHED_STAGES", "SCHED_AUTO", "SpammError", "lib", "build", "multiply", "sqrt_invsqrt", "sqrt_invsqrt_batched",
            "invsqrt_product", "autotune_leaf", "norm_tree", "cull", "release", "version", "HEADER_SYMBOLS", "Server"]
 
 FP64 = 0
@@ -34,6 +34,9 @@ MAP_NS = 0       # T = (3I - X)/2 (alpha = 1)
 MAP_SCALED = 1   # damped, stabilised h_alpha (Sec. 4.2 "Mapping")
 CHANNEL_DUAL = 0    # Eq. (cannonical)
 CHANNEL_SINGLE = 1  # Eq. (single): Z <- Z h[X], X = Z^T s Z
+SCHED_BRANCHES = 0  # y and z products on two streams, launches per product
+SCHED_STAGES = 1    # the batched engine with one problem (the y and z products share launches)
+SCHED_AUTO = 2      # timed on the call's own input, cached
 
 STATUS = {0: "SPAMM_OK", -1: "SPAMM_ERR_ARG", -2: "SPAMM_ERR_NOMEM", -3: "SPAMM_ERR_DIVERGED",
           -4: "SPAMM_ERR_NOTCONVERGED", -5: "SPAMM_ERR_TIMEOUT", -6: "SPAMM_ERR_ADMIT", -7: "SPAMM_ERR_CUDA",
@@ -59,7 +62,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("leaf", ctypes.c_int), ("precision", ctypes.c_int), ("tau_s", ctypes.c_double),
                 ("mu_rel", ctypes.c_double), ("tol_t", ctypes.c_double), ("order", ctypes.c_int),
                 ("residual", ctypes.c_int), ("profile", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("map", ctypes.c_int), ("channel", ctypes.c_int)]
+                ("map", ctypes.c_int), ("channel", ctypes.c_int), ("schedule", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -72,7 +75,7 @@ class Stats(ctypes.Structure):
                 ("tensor_units", ctypes.c_longlong), ("cull_ms", ctypes.c_double),
                 ("cull_launches", ctypes.c_longlong), ("tree_ms", ctypes.c_double),
                 ("tree_launches", ctypes.c_longlong), ("slice_ms", ctypes.c_double),
-                ("slice_launches", ctypes.c_longlong)]
+                ("slice_launches", ctypes.c_longlong), ("schedule", ctypes.c_int)]
 
 
 _lock = threading.Lock()
@@ -199,7 +202,7 @@ def _stream_of(ref, stream):
 
 
 def _opts(leaf=64, precision=FP64, tau_s=None, mu_rel=0.0, tol_t=0.0, order=ORDER_PAPER, residual=False,
-          stream=None, profile=False, map=MAP_NS, channel=CHANNEL_DUAL) -> Opts:
+          stream=None, profile=False, map=MAP_NS, channel=CHANNEL_DUAL, schedule=SCHED_BRANCHES) -> Opts:
     o = Opts()
     lib().spamm_opts_init(ctypes.byref(o))
     o.leaf = int(leaf)
@@ -213,6 +216,7 @@ def _opts(leaf=64, precision=FP64, tau_s=None, mu_rel=0.0, tol_t=0.0, order=ORDE
     o.stream = stream
     o.map = int(map)
     o.channel = int(channel)
+    o.schedule = int(schedule)
     return o
 
 
@@ -221,7 +225,7 @@ def _stats_dict(s: Stats, th=None, kh=None) -> dict:
          "tasks_total": s.tasks_total, "tasks_dense": s.tasks_dense, "flops": s.flops, "gemm_ms": s.gemm_ms,
          "gemm_launches": s.gemm_launches, "tensor_units": s.tensor_units, "cull_ms": s.cull_ms,
          "cull_launches": s.cull_launches, "tree_ms": s.tree_ms, "tree_launches": s.tree_launches,
-         "slice_ms": s.slice_ms, "slice_launches": s.slice_launches}
+         "slice_ms": s.slice_ms, "slice_launches": s.slice_launches, "schedule": s.schedule}
     if th is not None:
         d["t_hist"] = th[:s.iters].copy()
     if kh is not None:
@@ -277,7 +281,7 @@ def autotune_leaf(S, tau: float, precision: int = FP64, stream=None) -> int:
 
 def sqrt_invsqrt(S, tau: float, maxit: int, leaf: int = 64, precision: int = FP64, tau_s=None, mu_rel=0.0,
                  tol_t=0.0, order=ORDER_PAPER, residual=False, Y=None, Z=None, stream=None, raise_on=True,
-                 profile=False, map=None, channel=None, lens_bins=0):
+                 profile=False, map=None, channel=None, lens_bins=0, schedule=SCHED_BRANCHES):
     """Y ~ S^{1/2}, Z ~ S^{-1/2} by dual-channel Newton-Schulz on SpAMM products; returns (Y, Z, stats).
     With lens_bins > 0, stats["lens_hist"] holds the plane-diagonal profile of every product's surviving tile
     triples, [iters, 3 products, 3 planes (|i-j|, |j-k|, |i-k|), lens_bins]."""
@@ -295,7 +299,7 @@ def sqrt_invsqrt(S, tau: float, maxit: int, leaf: int = 64, precision: int = FP6
         st.lens_hist = lh.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong))
         st.lens_bins = int(lens_bins)
     o = _opts(leaf, precision, tau_s, mu_rel, tol_t, order, residual, _stream_of(s, stream), profile,
-              MAP_NS if map is None else map, CHANNEL_DUAL if channel is None else channel)
+              MAP_NS if map is None else map, CHANNEL_DUAL if channel is None else channel, schedule)
     status = lib().spamm_sqrt_invsqrt(ps, n, float(tau), int(maxit), _ptr(Y), _ptr(Z), ctypes.byref(o),
                                       ctypes.byref(st))
     d = _stats_dict(st, th, kh)

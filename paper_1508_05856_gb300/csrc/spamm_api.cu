@@ -1174,12 +1174,94 @@ static int solve_graph(Plan* p, const double* dS, double* dY, double* dZ, int n,
 }
 
 static int sqrt_impl(const double* S, int n, double tau, int maxit, double* Y, double* Z, const spamm_opts& o_in,
+                     spamm_stats* stats);
+
+// ---- schedule autotuner (opts.schedule = SPAMM_SCHED_AUTO) -----------------
+// Times one solve of the call's own input with each schedule (after one untimed solve that captures its
+// graph) and keeps the faster, per device, size, arithmetic, leaf and decade of tau.
+static std::mutex g_sched_mu;
+static std::map<std::tuple<int, int, int, int, int>, int> g_sched;
+
+static int autotune_schedule(const double* S, int n, double tau, int maxit, double* Y, double* Z,
+                             const spamm_opts& o, int* sched) {
+    *sched = SPAMM_SCHED_BRANCHES;
+    spamm_opts t = o;
+    t.schedule = SPAMM_SCHED_STAGES;
+    if (!batch_engine_covers(t) || maxit <= 0) return SPAMM_OK;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    const auto key = std::make_tuple(dev, n, o.precision, o.leaf, tau_decade(tau));
+    {
+        std::lock_guard<std::mutex> lk(g_sched_mu);
+        auto it = g_sched.find(key);
+        if (it != g_sched.end()) {
+            *sched = it->second;
+            return SPAMM_OK;
+        }
+    }
+    cudaStream_t st = (cudaStream_t)o.stream;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 3.4e38f;
+    int choice = SPAMM_SCHED_BRANCHES;
+    int err = SPAMM_OK;
+    for (int sc : {SPAMM_SCHED_BRANCHES, SPAMM_SCHED_STAGES}) {
+        t.schedule = sc;
+        spamm_stats ss;
+        std::memset(&ss, 0, sizeof(ss));
+        int e = sqrt_impl(S, n, tau, maxit, Y, Z, t, &ss);  // captures the schedule's graph
+        if (e && e != SPAMM_ERR_DIVERGED && e != SPAMM_ERR_NOTCONVERGED) {
+            err = e;
+            break;
+        }
+        if (ss.schedule != sc) continue;  // the schedule did not apply to this call
+        cudaEventRecord(e0, st);
+        e = sqrt_impl(S, n, tau, maxit, Y, Z, t, nullptr);
+        cudaEventRecord(e1, st);
+        if (e && e != SPAMM_ERR_DIVERGED && e != SPAMM_ERR_NOTCONVERGED) {
+            err = e;
+            break;
+        }
+        float ms = 0.f;
+        if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best) {
+            best = ms;
+            choice = sc;
+        }
+        cudaGetLastError();
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err) return err;
+    g_last_error.clear();
+    std::lock_guard<std::mutex> lk(g_sched_mu);
+    g_sched[key] = choice;
+    *sched = choice;
+    return SPAMM_OK;
+}
+
+static int sqrt_impl(const double* S, int n, double tau, int maxit, double* Y, double* Z, const spamm_opts& o_in,
                      spamm_stats* stats) {
     spamm_opts o;
     {
         const int e = with_leaf(S, n, tau, o_in, &o);
         if (e) return e;
     }
+    if (o.schedule == SPAMM_SCHED_AUTO) {
+        int sc = SPAMM_SCHED_BRANCHES;
+        const int e = autotune_schedule(S, n, tau, maxit, Y, Z, o, &sc);
+        if (e) return e;
+        o.schedule = sc;
+    }
+    if (o.schedule == SPAMM_SCHED_STAGES) {
+        const int e = stage_solve(S, n, tau, maxit, Y, Z, o, stats);
+        if (e != SPAMM_ERR_UNSUPPORTED) {
+            if (stats) stats->schedule = SPAMM_SCHED_STAGES;
+            return e;
+        }
+        g_last_error.clear();  // not covered: the branch schedule serves the call
+    }
+    if (stats) stats->schedule = SPAMM_SCHED_BRANCHES;
     cudaStream_t st = (cudaStream_t)o.stream;
     const double tau_s = o.tau_s < 0.0 ? 0.01 * tau : o.tau_s;
     init_device_attributes();
@@ -1315,6 +1397,10 @@ static int check_common(int n, double tau, const spamm_opts& o) {
         g_last_error = "unknown channel";
         return SPAMM_ERR_ARG;
     }
+    if (o.schedule != SPAMM_SCHED_BRANCHES && o.schedule != SPAMM_SCHED_STAGES && o.schedule != SPAMM_SCHED_AUTO) {
+        g_last_error = "unknown schedule";
+        return SPAMM_ERR_ARG;
+    }
     if (o.channel == SPAMM_CHANNEL_SINGLE && o.order != SPAMM_ORDER_PAPER) {
         g_last_error = "the single channel is defined in the paper order only";
         return SPAMM_ERR_ARG;
@@ -1447,6 +1533,7 @@ void spamm_opts_init(spamm_opts* o) {
     o->stream = nullptr;
     o->map = SPAMM_MAP_NS;
     o->channel = SPAMM_CHANNEL_DUAL;
+    o->schedule = SPAMM_SCHED_BRANCHES;
 }
 
 int spamm_autotune_leaf(const double* S, int n, double tau, const spamm_opts* opts, int* leaf) {

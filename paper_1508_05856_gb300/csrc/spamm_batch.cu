@@ -654,6 +654,20 @@ int batched_solve(int count, const double* const* S, const int* n, const double*
     return solve_in_slot(g_batch[dev], count, S, n, tau, maxit, Y, Z, o, stats, 0);
 }
 
+// One solve on the batched engine (the stage schedule), in a batch cached per device apart from the batched
+// calls' one, so that the two do not evict each other's graphs.
+std::mutex g_stage_mu;
+std::unique_ptr<Batch> g_stage_batch[64];
+int stage_solve(const double* S, int n, double tau, int maxit, double* Y, double* Z, const spamm_opts& o,
+                spamm_stats* stats) {
+    if (!engine_covers(o)) return SPAMM_ERR_UNSUPPORTED;
+    int dev = 0;
+    BK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return SPAMM_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lk(g_stage_mu);
+    return solve_in_slot(g_stage_batch[dev], 1, &S, &n, &tau, maxit, &Y, &Z, o, stats, 0);
+}
+
 // A batch owned by its caller (one per request-server worker): buffers and graph kept between calls.
 struct BatchSlot {
     std::unique_ptr<Batch> b;
@@ -682,8 +696,12 @@ size_t batch_footprint(int n, int nb, int precision, int maxit) {
 
 // Frees the cached batches (no work may be in flight).
 void release_batches() {
-    std::lock_guard<std::mutex> lk(g_batch_mu);
-    for (auto& b : g_batch) b.reset();
+    {
+        std::lock_guard<std::mutex> lk(g_batch_mu);
+        for (auto& b : g_batch) b.reset();
+    }
+    std::lock_guard<std::mutex> lk(g_stage_mu);
+    for (auto& b : g_stage_batch) b.reset();
 }
 
 }  // namespace spamm

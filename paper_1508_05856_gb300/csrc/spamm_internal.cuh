@@ -318,6 +318,9 @@ void launch_tree_batched(const ProdDesc* prods, int nprod, int* tile_count, int*
 int batched_solve(int count, const double* const* S, const int* n, const double* tau, int maxit,
                   double* const* Y, double* const* Z, const spamm_opts& o, spamm_stats* stats);
 void release_batches();
+// One solve on the batched engine (SPAMM_SCHED_STAGES); SPAMM_ERR_UNSUPPORTED when it does not cover the call.
+int stage_solve(const double* S, int n, double tau, int maxit, double* Y, double* Z, const spamm_opts& o,
+                spamm_stats* stats);
 // Caller-owned batches (the request server's workers): the same engine with buffers and graph kept per slot;
 // limit caps the slot's device memory (0: 70 % of the free memory).
 struct BatchSlot;

@@ -41,7 +41,7 @@ def test_strerror_and_defaults():
     o = sp.Opts()
     L.spamm_opts_init(ctypes.byref(o))
     assert o.leaf == 64 and o.precision == sp.FP64 and o.tau_s < 0 and o.order == sp.ORDER_PAPER
-    assert o.map == sp.MAP_NS and o.channel == sp.CHANNEL_DUAL
+    assert o.map == sp.MAP_NS and o.channel == sp.CHANNEL_DUAL and o.schedule == sp.SCHED_BRANCHES
 
 
 @pytest.mark.parametrize("n,tau,leaf", [(0, 1e-6, 64), (-5, 1e-6, 64), (64, -1.0, 64), (64, float("nan"), 64),
@@ -78,6 +78,10 @@ def test_bad_option_fields_rejected():
     o.order = sp.ORDER_TRANSPOSED
     assert L.spamm_sqrt_invsqrt(buf, 4, 0.0, 5, buf, buf, ctypes.byref(o), None) == -1
     assert b"single channel" in L.spamm_last_error()
+    L.spamm_opts_init(ctypes.byref(o))
+    o.schedule = 3
+    assert L.spamm_sqrt_invsqrt(buf, 4, 0.0, 5, buf, buf, ctypes.byref(o), None) == -1
+    assert b"schedule" in L.spamm_last_error()
     L.spamm_opts_init(ctypes.byref(o))
     o.mu_rel = -1.0
     assert L.spamm_sqrt_invsqrt(buf, 4, 0.0, 5, buf, buf, ctypes.byref(o), None) == -1

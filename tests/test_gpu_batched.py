@@ -94,3 +94,27 @@ def test_batch_repeated_calls_replay_and_stay_identical():
     b = sp.sqrt_invsqrt_batched(Ss, [1e-8, 1e-9], 12, leaf=64, precision=sp.EMU64)
     for x, y in zip(a[0] + a[1], b[0] + b[1]):
         assert torch.equal(x, y)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_stage_schedule_for_one_solve_equals_the_branch_schedule(precision):
+    """SPAMM_SCHED_STAGES runs one solve on the batched engine (the y and z products share each launch):
+    the same result bit for bit; options the engine does not cover (the residual) fall back to branches."""
+    S = dev(synth.gaussian_lattice(448, 0.75, seed=9))
+    Y0, Z0, s0 = sp.sqrt_invsqrt(S, 1e-9, 18, leaf=64, precision=precision)
+    Y1, Z1, s1 = sp.sqrt_invsqrt(S, 1e-9, 18, leaf=64, precision=precision, schedule=sp.SCHED_STAGES)
+    assert s0["schedule"] == sp.SCHED_BRANCHES and s1["schedule"] == sp.SCHED_STAGES
+    assert torch.equal(Y0, Y1) and torch.equal(Z0, Z1)
+    assert np.array_equal(s0["task_hist"], s1["task_hist"]) and np.array_equal(s0["t_hist"], s1["t_hist"])
+    _, _, s2 = sp.sqrt_invsqrt(S, 1e-9, 18, leaf=64, precision=precision, schedule=sp.SCHED_STAGES, residual=True)
+    assert s2["schedule"] == sp.SCHED_BRANCHES and s2["resid_F"] >= 0
+
+
+def test_schedule_autotuner_picks_a_schedule_and_keeps_it():
+    S = dev(synth.kms(1536, 0.9))
+    Y0, Z0, s0 = sp.sqrt_invsqrt(S, 1e-10, 14, leaf=64, precision=sp.EMU64)
+    Y1, Z1, s1 = sp.sqrt_invsqrt(S, 1e-10, 14, leaf=64, precision=sp.EMU64, schedule=sp.SCHED_AUTO)
+    assert s1["schedule"] in (sp.SCHED_BRANCHES, sp.SCHED_STAGES)
+    assert torch.equal(Y0, Y1) and torch.equal(Z0, Z1)
+    _, _, s2 = sp.sqrt_invsqrt(S, 1e-10, 14, leaf=64, precision=sp.EMU64, schedule=sp.SCHED_AUTO)
+    assert s2["schedule"] == s1["schedule"]
