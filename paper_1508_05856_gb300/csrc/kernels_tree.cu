@@ -668,13 +668,84 @@ void launch_tree(const Geometry& g, double* tree, const int* done, cudaStream_t 
 }
 
 // ---------------------------------------------------------------- the cull
-// One warp per output tile (i, k).  Lanes test 32 consecutive j at a time
-// (independent FP64 products, so the long FP64 latency overlaps) and the
-// survivors are compacted with a ballot in ascending j.  A chunk of 32 j is
-// skipped when no coarse block J under it passes the coarse test: parents
-// hold sums of non-negative children, so a coarse pair below the threshold
-// has no surviving leaf pair under it.  The surviving set is exactly the leaf
-// test nuA(i,j) * nuB(j,k) >= thr, i.e. the recursion of Eq. (newspamm).
+// Leaf test of Eq. (newspamm) in squared form: a pair is kept unless fl(nu_a * nu_b) < thr (FP64, strict).
+// Most pairs are decided from the binary exponents alone: with nu_a in [2^ea, 2^(ea+1)) and nu_b in
+// [2^eb, 2^(eb+1)), the product lies in [2^(ea+eb), 2^(ea+eb+2)); for thr in [2^et, 2^(et+1)) it is culled
+// when ea+eb+2 < et and kept when ea+eb >= et+1, and its rounded value falls on the same side (rounding is
+// monotone and powers of two are exact).  Only pairs within a factor of about eight of the threshold, and
+// zero, subnormal or non-finite operands, take the FP64 multiply: the same decision as the multiply, at a
+// fraction of the FP64 work this part's slow FP64 pipe would spend on every candidate.
+__device__ __forceinline__ int biased_exponent(double x) {
+    return (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FFull);
+}
+__device__ __forceinline__ bool keep_pair(double a, double b, double thr, int et) {
+    const int ea = biased_exponent(a), eb = biased_exponent(b);
+    if (ea > 0 && ea < 0x7FF && eb > 0 && eb < 0x7FF && et > 0 && et < 0x7FF) {
+        const int s = ea + eb - 1023;  // biased exponent of 2^(ea'+eb')
+        if (s + 2 < et) return false;
+        if (s >= et + 1) return true;
+    }
+    return !(a * b < thr);
+}
+
+// Task list of output tile (i, k) by one warp: lanes test 32 consecutive j at a time and the survivors are
+// compacted with a ballot in ascending j.  For m <= 128 every candidate's coarse and leaf norms are loaded
+// at once (one round trip); for larger m a chunk of 32 j is skipped when no coarse block J under it passes
+// the coarse test (parents hold sums of non-negative children, so a coarse pair below the threshold has no
+// surviving leaf pair under it).  Either way the surviving set is exactly the leaf test nuA(i,j) * nuB(j,k)
+// >= thr, i.e. the recursion of Eq. (newspamm).  Returns the count (in every lane).
+__device__ __forceinline__ int cull_tile(const TreeDev& td, const double* __restrict__ treeA,
+                                         const double* __restrict__ treeB, double thr, int i, int k, int lane,
+                                         int* __restrict__ out) {
+    const int m = td.m;
+    const int et = biased_exponent(thr);
+    const int dc = td.dim[td.coarse];
+    const double* cA = treeA + td.off[td.coarse];
+    const double* cB = treeB + td.off[td.coarse];
+    const int I = i >> td.shift, K = k >> td.shift;
+    int cnt = 0;
+    if (m <= 128) {
+        double ca[4], cb[4], la[4], lb[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int j = 32 * q + lane;
+            ca[q] = cb[q] = la[q] = lb[q] = 0.0;
+            if (j < m) {
+                const int J = j >> td.shift;
+                ca[q] = cA[(size_t)I * dc + J];
+                cb[q] = cB[(size_t)J * dc + K];
+                la[q] = treeA[(size_t)i * m + j];
+                lb[q] = treeB[(size_t)j * m + k];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (32 * q >= m) break;
+            const int j = 32 * q + lane;
+            const bool keep = j < m && keep_pair(ca[q], cb[q], thr, et) && keep_pair(la[q], lb[q], thr, et);
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            if (keep) out[cnt + __popc(bal & ((1u << lane) - 1u))] = j;
+            cnt += __popc(bal);
+        }
+        return cnt;
+    }
+    for (int j0 = 0; j0 < m; j0 += 32) {
+        const int j = j0 + lane;
+        bool coarse = false;
+        if (j < m) {
+            const int J = j >> td.shift;
+            coarse = keep_pair(cA[(size_t)I * dc + J], cB[(size_t)J * dc + K], thr, et);
+        }
+        if (!__any_sync(0xffffffffu, coarse)) continue;
+        const bool keep = coarse && keep_pair(treeA[(size_t)i * m + j], treeB[(size_t)j * m + k], thr, et);
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (keep) out[cnt + __popc(bal & ((1u << lane) - 1u))] = j;
+        cnt += __popc(bal);
+    }
+    return cnt;
+}
+
+// One warp per output tile (i, k), the task list by cull_tile.
 __global__ void __launch_bounds__(256) k_cull(TreeDev td, const double* __restrict__ treeA,
                                               const double* __restrict__ treeB, double tau, CullOut co,
                                               unsigned long long* __restrict__ total, double* __restrict__ thr_out,
@@ -694,24 +765,7 @@ __global__ void __launch_bounds__(256) k_cull(TreeDev td, const double* __restri
     bool listed = false;
     if (wid < m * m) {
         const int i = wid / m, k = wid - (wid / m) * m;
-        const int dc = td.dim[td.coarse];
-        const double* cA = treeA + td.off[td.coarse];
-        const double* cB = treeB + td.off[td.coarse];
-        const int I = i >> td.shift, K = k >> td.shift;
-        int* out = co.jlist + (size_t)wid * m;
-        for (int j0 = 0; j0 < m; j0 += 32) {
-            const int j = j0 + lane;
-            bool coarse = false;
-            if (j < m) {
-                const int J = j >> td.shift;
-                coarse = !(cA[(size_t)I * dc + J] * cB[(size_t)J * dc + K] < thr);
-            }
-            if (!__any_sync(0xffffffffu, coarse)) continue;
-            const bool keep = coarse && !(treeA[(size_t)i * m + j] * treeB[(size_t)j * m + k] < thr);
-            const unsigned bal = __ballot_sync(0xffffffffu, keep);
-            if (keep) out[cnt + __popc(bal & ((1u << lane) - 1u))] = j;
-            cnt += __popc(bal);
-        }
+        cnt = cull_tile(td, treeA, treeB, thr, i, k, lane, co.jlist + (size_t)wid * m);
         if (lane == 0) {
             co.counts[wid] = cnt;
             if (co.tile_list) {
@@ -792,24 +846,7 @@ __global__ void __launch_bounds__(256) k_cull_batched(const ProdDesc* __restrict
     bool listed = false;
     if (wid < m * m) {
         const int i = wid / m, k = wid - (wid / m) * m;
-        const int dc = td.dim[td.coarse];
-        const double* cA = treeA + td.off[td.coarse];
-        const double* cB = treeB + td.off[td.coarse];
-        const int I = i >> td.shift, K = k >> td.shift;
-        int* out = d.jlist + (size_t)wid * m;
-        for (int j0 = 0; j0 < m; j0 += 32) {
-            const int j = j0 + lane;
-            bool coarse = false;
-            if (j < m) {
-                const int J = j >> td.shift;
-                coarse = !(cA[(size_t)I * dc + J] * cB[(size_t)J * dc + K] < thr);
-            }
-            if (!__any_sync(0xffffffffu, coarse)) continue;
-            const bool keep = coarse && !(treeA[(size_t)i * m + j] * treeB[(size_t)j * m + k] < thr);
-            const unsigned bal = __ballot_sync(0xffffffffu, keep);
-            if (keep) out[cnt + __popc(bal & ((1u << lane) - 1u))] = j;
-            cnt += __popc(bal);
-        }
+        cnt = cull_tile(td, treeA, treeB, thr, i, k, lane, d.jlist + (size_t)wid * m);
         if (lane == 0) {
             d.counts[wid] = cnt;
             listed = cnt > 0 || (d.mode != EPI_PLAIN && i == k);
