@@ -644,6 +644,66 @@ __device__ __forceinline__ void tree_levels(const TreeDev& td, double* __restric
     }
 }
 
+// The same levels for trees of at most 64 x 64 leaves (L <= 6), by 1024 threads with one block barrier.
+// The leaf grid is taken as 64 x 64 with zeros beyond m (adding a zero child is exact), so real level l is
+// level l + 6 - L of the padded tree.  Thread t holds the level-5 node whose Morton code is t (even bits:
+// column, odd bits: row) and sums its four leaves as child_sum does; the next two levels are groups of 4
+// and 16 consecutive lanes, combined with shuffles in child_sum's order (the two top-row children first,
+// then the two bottom-row ones, then the two sums).  The 64 level-3 nodes go through shared memory to one
+// warp, which finishes levels 2, 1 and 0 the same way.  Every node is written to its level of the tree.
+__device__ __forceinline__ int compact_bits(int x) {  // bits 0, 2, 4, 6, 8 of x to bits 0..4
+    x &= 0x155;
+    x = (x | (x >> 1)) & 0x133;
+    x = (x | (x >> 2)) & 0x10F;
+    x = (x | (x >> 4)) & 0x01F;
+    return x;
+}
+__device__ __forceinline__ void put_node(const TreeDev& td, double* __restrict__ tree, int vlevel, int I, int J,
+                                         double v) {
+    const int l = vlevel - (6 - td.L);
+    if (l >= 0 && l < td.L && I < td.dim[l] && J < td.dim[l]) tree[td.off[l] + (long)I * td.dim[l] + J] = v;
+}
+__device__ __forceinline__ void tree_levels_small(const TreeDev& td, double* __restrict__ tree, double* lvl3) {
+    const int t = threadIdx.x, lane = t & 31;
+    const int J = compact_bits(t), I = compact_bits(t >> 1);  // level-5 node (I, J)
+    const int m = td.m;
+    const double* leaf = tree + td.off[td.L];
+    const int r0 = 2 * I, c0 = 2 * J;
+    const double a00 = (r0 < m && c0 < m) ? leaf[r0 * m + c0] : 0.0;
+    const double a01 = (r0 < m && c0 + 1 < m) ? leaf[r0 * m + c0 + 1] : 0.0;
+    const double a10 = (r0 + 1 < m && c0 < m) ? leaf[(r0 + 1) * m + c0] : 0.0;
+    const double a11 = (r0 + 1 < m && c0 + 1 < m) ? leaf[(r0 + 1) * m + c0 + 1] : 0.0;
+    double v = (a00 + a01) + (a10 + a11);
+    put_node(td, tree, 5, I, J, v);
+    // level 4: lanes 4q .. 4q+3 hold (top-left, top-right, bottom-left, bottom-right)
+    double h = v + __shfl_xor_sync(0xffffffffu, v, 1);
+    v = h + __shfl_xor_sync(0xffffffffu, h, 2);
+    if ((t & 3) == 0) put_node(td, tree, 4, I >> 1, J >> 1, v);
+    // level 3: the level-4 nodes sit on lanes 16q + 4p
+    h = v + __shfl_xor_sync(0xffffffffu, v, 4);
+    v = h + __shfl_xor_sync(0xffffffffu, h, 8);
+    if ((t & 15) == 0) {
+        put_node(td, tree, 3, I >> 2, J >> 2, v);
+        lvl3[t >> 4] = v;
+    }
+    __syncthreads();
+    if (t < 32) {
+        // level 2: lane q pairs level-3 nodes 2q, 2q+1 (Morton-consecutive), then combines with lane q ^ 1
+        h = lvl3[2 * lane] + lvl3[2 * lane + 1];
+        v = h + __shfl_xor_sync(0xffffffffu, h, 1);
+        const int q2 = lane >> 1;  // Morton code of the level-2 node
+        if ((lane & 1) == 0) put_node(td, tree, 2, compact_bits(q2 >> 1), compact_bits(q2), v);
+        h = v + __shfl_xor_sync(0xffffffffu, v, 2);
+        v = h + __shfl_xor_sync(0xffffffffu, h, 4);
+        const int q1 = lane >> 3;
+        if ((lane & 7) == 0) put_node(td, tree, 1, q1 >> 1, q1 & 1, v);
+        h = v + __shfl_xor_sync(0xffffffffu, v, 8);
+        v = h + __shfl_xor_sync(0xffffffffu, h, 16);
+        if (lane == 0) put_node(td, tree, 0, 0, 0, v);
+    }
+    __syncthreads();
+}
+
 // kLoop: the instance in a graph's conditional loop body, the only one that calls the device runtime
 // (profilers skip kernels that do, so every other launch uses the plain instance).
 template <bool kLoop>
@@ -653,7 +713,8 @@ __global__ void __launch_bounds__(1024) k_tree(TreeDev td, double* __restrict__ 
     if (done && *done) return;
     __shared__ double bufA[64 * 64];
     __shared__ double bufB[32 * 32];
-    tree_levels<1024>(td, tree, bufA, bufB);
+    if (td.L <= 6) tree_levels_small(td, tree, bufB);
+    else tree_levels<1024>(td, tree, bufA, bufB);
     if (ex.zero_int && threadIdx.x < ex.zero_n) ex.zero_int[threadIdx.x] = 0;
     if (ex.trace_part && threadIdx.x < 32)
         trace_error<kLoop>(ex.trace_part, ex.n, td.m, ex);
