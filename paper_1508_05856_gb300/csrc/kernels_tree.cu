@@ -750,11 +750,10 @@ __device__ __forceinline__ bool keep_pair(double a, double b, double thr, int et
 }
 
 // Task list of output tile (i, k) by one warp: lanes test 32 consecutive j at a time and the survivors are
-// compacted with a ballot in ascending j.  For m <= 128 every candidate's coarse and leaf norms are loaded
-// at once (one round trip); for larger m a chunk of 32 j is skipped when no coarse block J under it passes
+// compacted with a ballot in ascending j.  A chunk of 32 j is skipped when no coarse block J under it passes
 // the coarse test (parents hold sums of non-negative children, so a coarse pair below the threshold has no
-// surviving leaf pair under it).  Either way the surviving set is exactly the leaf test nuA(i,j) * nuB(j,k)
-// >= thr, i.e. the recursion of Eq. (newspamm).  Returns the count (in every lane).
+// surviving leaf pair under it).  The surviving set is exactly the leaf test nuA(i,j) * nuB(j,k) >= thr,
+// i.e. the recursion of Eq. (newspamm).  Returns the count (in every lane).
 __device__ __forceinline__ int cull_tile(const TreeDev& td, const double* __restrict__ treeA,
                                          const double* __restrict__ treeB, double thr, int i, int k, int lane,
                                          int* __restrict__ out) {
@@ -765,31 +764,6 @@ __device__ __forceinline__ int cull_tile(const TreeDev& td, const double* __rest
     const double* cB = treeB + td.off[td.coarse];
     const int I = i >> td.shift, K = k >> td.shift;
     int cnt = 0;
-    if (m <= 128) {
-        double ca[4], cb[4], la[4], lb[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int j = 32 * q + lane;
-            ca[q] = cb[q] = la[q] = lb[q] = 0.0;
-            if (j < m) {
-                const int J = j >> td.shift;
-                ca[q] = cA[(size_t)I * dc + J];
-                cb[q] = cB[(size_t)J * dc + K];
-                la[q] = treeA[(size_t)i * m + j];
-                lb[q] = treeB[(size_t)j * m + k];
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (32 * q >= m) break;
-            const int j = 32 * q + lane;
-            const bool keep = j < m && keep_pair(ca[q], cb[q], thr, et) && keep_pair(la[q], lb[q], thr, et);
-            const unsigned bal = __ballot_sync(0xffffffffu, keep);
-            if (keep) out[cnt + __popc(bal & ((1u << lane) - 1u))] = j;
-            cnt += __popc(bal);
-        }
-        return cnt;
-    }
     for (int j0 = 0; j0 < m; j0 += 32) {
         const int j = j0 + lane;
         bool coarse = false;
