@@ -366,7 +366,8 @@ int capture(Batch* b, double mu_rel) {
         np.conditional.size = 1;
         ce = cudaGraphAddNode(&node, graph, deps, edata, ndeps, &np);
     }
-    if (ce == cudaSuccess) ce = cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (ce == cudaSuccess)
+        ce = cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
     long long lb0 = 0, lb1 = 0;
     if (ce == cudaSuccess) {
         ce = cudaStreamBeginCaptureToGraph(b->bst, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
