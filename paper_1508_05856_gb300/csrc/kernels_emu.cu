@@ -260,35 +260,17 @@ __global__ void __launch_bounds__(256, 5) k_slice(const double* __restrict__ X0,
     }
 }
 
-// Double-word FP32 accumulation (hi + lo, about 2^-44 relative) of the
-// squares of FP64 values: FP64 arithmetic is slow on this part, so the
-// per-tile sums of squares use FP32 pairs.
-struct DFloat {
-    float hi, lo;
-};
-__device__ __forceinline__ DFloat df_add(DFloat x, DFloat y) {
-    const float s = x.hi + y.hi;
-    const float bb = s - x.hi;
-    const float e = ((x.hi - (s - bb)) + (y.hi - bb)) + (x.lo + y.lo);
-    const float h = s + e;
-    return DFloat{h, e - (h - s)};
-}
-// v * v as a double-word: v split into its leading 24 mantissa bits and the rest.
-__device__ __forceinline__ DFloat df_square(double v) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
-    const int E = (int)(b >> 52);
-    const int fe = E - 1023 + 127;
-    if (E == 0 || fe <= 0 || fe >= 255) return DFloat{0.f, 0.f};  // zero, or below FP32 range (negligible)
-    const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
-    const float hi = __uint_as_float(((unsigned)fe << 23) | (unsigned)(mant >> 29));
-    const int le = E - 1023 - 52 + 127;  // exponent of the low 29 bits' unit
-    const float lo = le > 0 ? (float)(unsigned)(mant & 0x1FFFFFFFull) * __uint_as_float((unsigned)le << 23) : 0.f;
-    const float p = hi * hi;
-    const float pe = fmaf(hi, hi, -p);
-    return DFloat{p, fmaf(2.0f * hi, lo, pe)};
-}
-__device__ __forceinline__ DFloat df_shfl_xor(DFloat x, int o) {
-    return DFloat{__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o)};
+// |v| as FP32 from the IEEE bits b of |v|, its mantissa cut to 23 bits (relative error below 2^-23); 0 for
+// zero and for magnitudes outside FP32's normal range.  The per-tile sums of squares are taken in FP32:
+// they only steer the cull, and a relative error near 1e-6 in a tile norm moves a keep decision only for
+// pairs that sit that close to the threshold.  Their squares overflow for |v| >= 2^64, far above the
+// magnitudes of the scaled iteration.
+__device__ __forceinline__ float f32_of_bits(unsigned long long b) {
+    const unsigned hw = (unsigned)(b >> 32);
+    const int E = (int)(hw >> 20);
+    // the low 9 exponent bits and the leading 23 mantissa bits, the bias moved from 1023 to 127 (mod 2^32)
+    const unsigned f = __funnelshift_r((unsigned)b, hw, 29) - (896u << 23);
+    return (E > 896 && E < 1151) ? __uint_as_float(f) : 0.f;
 }
 
 // Row and column magnitude maxima of a packed FP64 matrix, kept as the upper 32 bits of the IEEE pattern
@@ -342,7 +324,7 @@ struct EmuArgs {
     const unsigned long long* cmaxB;    // column maxima of the right operand
     unsigned long long* units;          // (stack, slice) units issued, summed over the launch (may be null)
     double* C;                          // FP64 output tiles
-    double* leafC;                      // output leaf norms (squared Frobenius, double-word FP32 sums)
+    double* leafC;                      // output leaf norms (squared Frobenius, FP32 sums)
     int* slice_list;                    // copy of the drawn tiles ([m*m] ids, count at [m*m]) for slicing
     unsigned long long* rmaxC;          // output row / column maxima (pre-zeroed)
     unsigned long long* cmaxC;
@@ -428,6 +410,21 @@ __device__ __forceinline__ double fixed_to_double(long long tot, int s) {
     // a rounding carry out of the 52 mantissa bits moves into the exponent field
     const unsigned long long bits = ((unsigned long long)ef << 52) + keep + up;
     return __longlong_as_double((long long)(bits | sign));
+}
+
+// IEEE bits of |fixed_to_double(tot, s)|, branch-free (0 for tot = 0 and for a flushed result); the
+// caller supplies the sign.
+__device__ __forceinline__ unsigned long long fixed_mag_bits(long long tot, int s) {
+    const unsigned long long u = tot < 0 ? 0ull - (unsigned long long)tot : (unsigned long long)tot;
+    const unsigned hw = (unsigned)(u >> 32), lw = (unsigned)u;
+    const int lz = hw ? __clz(hw) : 32 + __clz(lw);
+    const unsigned long long mnorm = u << (lz & 63);
+    const unsigned long long keep = mnorm >> 11;
+    const unsigned rem = (unsigned)mnorm & 0x7FFu;
+    const unsigned up = (rem + 0x3FFu + ((unsigned)keep & 1u)) >> 11;
+    const int ef = 62 - lz + s + 1023;
+    const unsigned long long bits = ((unsigned long long)(unsigned)ef << 52) + keep + up;
+    return (u == 0 || ef < 0) ? 0ull : bits;
 }
 
 // Move one chunk's accumulator groups from TMEM into the 64-bit fixed-point
@@ -535,7 +532,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
     __shared__ int prod_sh[2];
     __shared__ int eA_sh[2][NB], eB_sh[2][NB];
     __shared__ double tr_sh[kEpiWarps];
-    __shared__ DFloat nu_sh[kEpiWarps];
+    __shared__ float nu_sh[kEpiWarps];
     __shared__ int abort_sh;
 
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dyn_smem) + 1023) & ~uintptr_t(1023));
@@ -820,44 +817,53 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
             const int r0 = et >> 6;  // 0..7
             const int gj = k * NB + c;
             const int eBc = eB_sh[slot][c];
-            double* outt = ev.C + (size_t)tile * NB * NB;
             const bool nsx = ev.mode == EPI_NS_X;
             const bool with_tr = ev.mode != EPI_PLAIN;
             // T = 1.5 I - 0.5 X: off the diagonal -x/2 is the conversion of -t64 one binade lower; the one
             // thread per column that owns the diagonal entry computes it up front (and its trace share)
             const int rd = (with_tr && i == k && (c & 7) == r0 && gj < ev.n) ? c : -1;
-            double xd = 0.0, vd = 0.0;
+            double xd = 0.0;
+            unsigned long long vdb = 0;  // bits of the diagonal entry of x or T
             if (rd >= 0) {
                 xd = fixed_to_double(sTop[c * 65 + c] + sBot[c * 65 + c], eA_sh[slot][c] + eBc - 48);
-                vd = nsx ? 1.5 - 0.5 * xd : xd;
+                vdb = (unsigned long long)__double_as_longlong(nsx ? 1.5 - 0.5 * xd : xd);
             }
             const int sc = eBc - 48 - (nsx ? 1 : 0);
-            unsigned long long cmx = 0;
-            DFloat nup = {0.f, 0.f};
+            // the sign of x, or of -x/2 for T: the sign bit of the sum, flipped for T
+            const unsigned long long flip = nsx ? 0x8000000000000000ull : 0ull;
+            unsigned long long* outb = reinterpret_cast<unsigned long long*>(ev.C) + (size_t)tile * NB * NB;
+            unsigned cmx = 0;  // upper words of the column's magnitudes
+            float nf = 0.f;
             unsigned rowm = 0;  // lane q: upper magnitude bits of row r0 + 8q over this warp's 32 columns
-            for (int q0 = 0; q0 < 8; q0 += 8) {
+            long long t64[8];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int r = r0 + 8 * (q0 + u);
-                    const long long t64 = sTop[c * 65 + r] + sBot[c * 65 + r];
-                    double v = fixed_to_double(nsx ? -t64 : t64, eA_sh[slot][r] + sc);
-                    v = r == rd ? vd : v;
-                    outt[r * NB + c] = v;  // consecutive lanes: consecutive columns
-                    nup = df_add(nup, df_square(v));
-                    const unsigned long long vb = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
-                    cmx = max(cmx, vb);
-                    // the maxima only feed the slicing exponents: the upper 32 bits carry the exponent exactly
-                    const unsigned rm = __reduce_max_sync(0xffffffffu, (unsigned)(vb >> 32));
-                    if (lane == q0 + u) rowm = rm;
+            for (int u = 0; u < 8; ++u) t64[u] = sTop[c * 65 + r0 + 8 * u] + sBot[c * 65 + r0 + 8 * u];
+            // the entries are moved as IEEE bit patterns only: no FP64 instruction in the loop
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int r = r0 + 8 * u;
+                unsigned long long vb = fixed_mag_bits(t64[u], eA_sh[slot][r] + sc);
+                unsigned long long sb = vb | (vb ? ((unsigned long long)t64[u] ^ flip) & 0x8000000000000000ull : 0ull);
+                if (r == rd) {
+                    sb = vdb;
+                    vb = vdb & 0x7FFFFFFFFFFFFFFFull;
                 }
+                outb[r * NB + c] = sb;  // consecutive lanes: consecutive columns
+                const float f = f32_of_bits(vb);
+                nf = fmaf(f, f, nf);
+                // the maxima only feed the slicing exponents: the upper 32 bits carry the exponent exactly
+                const unsigned hw = (unsigned)(vb >> 32);
+                cmx = max(cmx, hw);
+                const unsigned rm = __reduce_max_sync(0xffffffffu, hw);
+                if (lane == u) rowm = rm;
             }
             // X itself (EPI_X) is not sliced: the maxima are those of the map's output, taken by k_map
             if (ev.mode != EPI_X) {
-                if (cmx) atomicMax(ev.cmaxC + gj, cmx);
+                if (cmx) atomicMax(ev.cmaxC + gj, (unsigned long long)cmx << 32);
                 if (lane < 8 && rowm) atomicMax(ev.rmaxC + i * NB + r0 + 8 * lane, (unsigned long long)rowm << 32);
             }
-            for (int o = 16; o > 0; o >>= 1) nup = df_add(nup, df_shfl_xor(nup, o));
-            if (lane == 0) nu_sh[ew] = nup;
+            for (int o = 16; o > 0; o >>= 1) nf += __shfl_xor_sync(0xffffffffu, nf, o);
+            if (lane == 0) nu_sh[ew] = nf;
             const bool diag_tile = with_tr && i == k;
             if (diag_tile) {
                 double tr = rd >= 0 ? xd : 0.0;
@@ -866,14 +872,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
             }
             // every epilogue warp is done with the staging buffer (and tr_sh holds the trace partials)
             ptx::named_sync(1, 32 * kEpiWarps);
-            if (et == 0) {
-                DFloat t = nu_sh[0];
-                for (int w = 1; w < kEpiWarps; ++w) t = df_add(t, nu_sh[w]);
-                ev.leafC[tile] = (double)t.hi + (double)t.lo;
-                if (diag_tile) {
-                    double s8 = 0.0;
-                    for (int w = 0; w < kEpiWarps; ++w) s8 += tr_sh[w];
-                    ev.trace_part[i] = s8;
+            if (ew == 0) {
+                float t = lane < kEpiWarps ? nu_sh[lane] : 0.f;
+                for (int o = kEpiWarps / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+                if (lane == 0) {
+                    ev.leafC[tile] = (double)t;
+                    if (diag_tile) {
+                        double s8 = 0.0;
+                        for (int w = 0; w < kEpiWarps; ++w) s8 += tr_sh[w];
+                        ev.trace_part[i] = s8;
+                    }
                 }
             }
             if (lane == 0) ptx::mbar_arrive(&bar_tfree[slot]);

@@ -349,7 +349,7 @@ void launch_slice(const double* X, const double* leaf, double* leaf_out, const u
                   const unsigned long long* cmax, uint8_t* sA, uint8_t* sB, const Geometry& g, const int* tile_list,
                   const int* tile_count, const int* done, cudaStream_t st);
 // Leaf products on the tensor cores; writes C's FP64 tiles, leaf norms
-// (double-word FP32 sums, about 2^-44 relative), row/column maxima
+// (FP32 sums of squares, about 1e-6 relative), row/column maxima
 // (pre-zeroed), trace partials for EPI_NS_X, and C.slice_list; *err set on a
 // timed-out internal wait.  units (may be null) gets += the (stack, slice)
 // units issued: twelve 128 x 64 x 64 FP16 products per task.  stall_polls > 0
