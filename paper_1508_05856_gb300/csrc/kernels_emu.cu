@@ -66,7 +66,9 @@ constexpr uint32_t EPI_BYTES = 2 * 64 * 65 * 8;          // epilogue staging of 
 constexpr uint32_t SMEM_DYN = NSTAGE * STAGE_BYTES + EPI_BYTES + 1024;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int kEpiWarps = 16;                // four per TMEM lane quarter (16 output columns each)
-constexpr int kThreads = 32 * (2 + kEpiWarps);
+constexpr int kSchedWarp = 2 + kEpiWarps;   // prepares the tiles' task lists and scales
+constexpr int kThreads = 32 * (3 + kEpiWarps);
+constexpr int NSLOT = 3;                     // tiles in flight: streamed, prepared, being prepared
 constexpr int kGroups = 6;                   // accumulator groups (64 TMEM columns each)
 constexpr int kChunk = 7;                    // tasks accumulated in TMEM between flushes (exactness bound)
 // tasks of one output tile: at most m, and the API limits SPAMM_EMU64 to m <= 512
@@ -512,25 +514,29 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, vo
 
 // Persistent: one CTA per SM takes output tiles from the compacted list with
 // an atomic ticket (a CTA that draws cheap tiles draws more of them).  The
-// three roles run decoupled: the producer warp draws and prepares tile t+1
-// (task list, scales) and streams its half-tasks while the MMA warp is still
-// on tile t and the epilogue warps finish tile t-1; the tile id travels in
-// the slot, and mbarriers order the roles.  The last CTA to finish resets
-// the ticket counters for the next launch.
+// four roles run decoupled through NSLOT tile slots: the scheduler warp draws
+// tiles and writes their task lists and scales up to two tiles ahead, so the
+// producer warp streams half-tasks from one tile straight into the next while
+// the MMA warp multiplies and the epilogue warps finish the tile before; the
+// tile id travels in the slot, and mbarriers order the roles.  The last CTA
+// to finish resets the ticket counters for the next launch.
 template <bool kBatched>
 __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
     grid_dependency_wait();
     if (a.done && *a.done) return;
     extern __shared__ uint8_t dyn_smem[];
     __shared__ __align__(8) uint64_t bar_full[NSTAGE], bar_empty[NSTAGE], bar_accf, bar_acce;
-    __shared__ __align__(8) uint64_t bar_tready[2], bar_tfree[2];
+    __shared__ __align__(8) uint64_t bar_tready[NSLOT], bar_tfree[NSLOT];
     __shared__ __align__(8) uint64_t bar_stall, bar_drain;
     __shared__ uint32_t tmem_base_sh;
-    __shared__ int tasks_sh[2][kMaxTasks];
-    __shared__ int ntask_sh[2];
-    __shared__ int tile_sh[2];
-    __shared__ int prod_sh[2];
-    __shared__ int eA_sh[2][NB], eB_sh[2][NB];
+    __shared__ int tasks_sh[NSLOT][kMaxTasks];
+    __shared__ int ntask_sh[NSLOT];
+    __shared__ int tile_sh[NSLOT];
+    __shared__ int prod_sh[NSLOT];
+    __shared__ int eA_sh[NSLOT][NB], eB_sh[NSLOT][NB];
+    __shared__ const uint8_t* srcA_sh[NSLOT];  // slices of A_i0 and B_0k; strideB_sh: bytes from B_jk to B_j+1,k
+    __shared__ const uint8_t* srcB_sh[NSLOT];
+    __shared__ size_t strideB_sh[NSLOT];
     __shared__ double tr_sh[kEpiWarps];
     __shared__ float nu_sh[kEpiWarps];
     __shared__ int abort_sh;
@@ -563,7 +569,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
         ptx::mbar_init(&bar_acce, kEpiWarps);
         ptx::mbar_init(&bar_stall, 1);
         ptx::mbar_init(&bar_drain, 1);
-        for (int q = 0; q < 2; ++q) {
+        for (int q = 0; q < NSLOT; ++q) {
             ptx::mbar_init(&bar_tready[q], 1);
             ptx::mbar_init(&bar_tfree[q], kEpiWarps);
         }
@@ -587,55 +593,73 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
     }
 
     if (warp == 0) {
-        // ---------------- producer: per tile the task list and scales, then the half-task stream
+        // ---------------- producer: streams the half-tasks of the tiles the scheduler prepared
         long long H = 0;
-        int tau = 0;
-        int idx = lane == 0 ? atomicAdd(a.sched, 1) : 0;
-        idx = __shfl_sync(0xffffffffu, idx, 0);
-        for (;; ++tau) {
-            const int slot = tau & 1;
-            const bool end = idx >= ntiles || *abort_flag;
-            // the following ticket is in flight while this tile is prepared
-            int nxt = 0;
-            if (!end && lane == 0) nxt = atomicAdd(a.sched, 1);
-            int item = 0;
-            if (!end) {
-                int t = idx, b = 0;
-#pragma unroll
-                for (int q = 0; q < kTileBuckets - 1; ++q)
-                    if (b == q && t >= bcount[q]) {
-                        t -= bcount[q];
-                        b = q + 1;
+        if (lane == 0) {
+            for (int tau = 0;; ++tau) {
+                const int slot = tau % NSLOT;
+                if (!wait_or_abort(&bar_tready[slot], (uint32_t)((tau / NSLOT) & 1), abort_flag, a.poll_limit)) {
+                    atomicExch(a.err, 1);
+                    break;
+                }
+                if (tile_sh[slot] < 0) break;
+                const int T = ntask_sh[slot];
+                const uint8_t* const baseA = srcA_sh[slot];
+                const uint8_t* const baseB = srcB_sh[slot];
+                const size_t strideB = strideB_sh[slot];
+                for (int t = 0; t < T; ++t) {
+                    const int j = tasks_sh[slot][t];
+                    const uint8_t* srcA = baseA + (size_t)j * A_TILE_BYTES;
+                    const uint8_t* srcB = baseB + (size_t)j * strideB;
+                    for (int h = 0; h < 2; ++h, ++H) {
+                        const int s = (int)(H % NSTAGE);
+                        if (H >= NSTAGE &&
+                            !wait_or_abort(&bar_empty[s], (uint32_t)(((H / NSTAGE) - 1) & 1), abort_flag, a.poll_limit)) {
+                            atomicExch(a.err, 1);
+                            break;
+                        }
+                        uint8_t* dst = smem + (size_t)s * STAGE_BYTES;
+                        ptx::mbar_arrive_expect_tx(&bar_full[s], STAGE_BYTES);
+                        ptx::bulk_g2s(dst, srcA + h * A_HALF_BYTES, A_HALF_BYTES, &bar_full[s]);
+                        ptx::bulk_g2s(dst + A_HALF_BYTES, srcB + h * B_HALF_BYTES, B_HALF_BYTES, &bar_full[s]);
                     }
-                item = a.tile_list[(size_t)b * lstride + t];
+                    if (*abort_flag) break;
+                }
+                if (*abort_flag) break;
             }
-            const int prod = kBatched ? item_prod(item) : 0;
-            const int tile = kBatched ? item_tile(item) : item;
-            const ProducerView v = producer_view<kBatched>(a, prod);
-            const int m = v.m;
-            const int i = tile / m, k = tile - (tile / m) * m;
-            // this tile's metadata, fetched before waiting for its slot
-            const int cnt = end ? 0 : v.counts[tile];
-            const int* js = v.jlist + (size_t)tile * m;
-            const int jpre0 = lane < cnt ? js[lane] : 0;
-            const int jpre1 = lane + 32 < cnt ? js[lane + 32] : 0;
-            unsigned long long ra0 = 0, ra1 = 0, cb0 = 0, cb1 = 0;
-            if (!end) {
-                ra0 = v.rmaxA[i * NB + lane];
-                ra1 = v.rmaxA[i * NB + 32 + lane];
-                cb0 = v.cmaxB[k * NB + lane];
-                cb1 = v.cmaxB[k * NB + 32 + lane];
-            }
-            if (tau >= 2) {
+            // an aborted CTA leaves no copy in flight: wait (bounded) for the last copy issued on every stage
+            if (*abort_flag)
+                for (int s = 0; s < NSTAGE; ++s)
+                    if (H > s) {
+                        const long long hl = s + ((H - 1 - s) / NSTAGE) * NSTAGE;
+                        ptx::mbar_wait_bounded(&bar_full[s], (uint32_t)((hl / NSTAGE) & 1), kDrainPolls);
+                    }
+        }
+        __syncwarp();
+    } else if (warp == kSchedWarp) {
+        // ---------------- scheduler: draws tiles and writes each one's task list and scales into a slot, up
+        // to two tiles ahead of the one being streamed
+        for (int tau = 0;; ++tau) {
+            const int slot = tau % NSLOT;
+            if (tau >= NSLOT) {
                 bool ok = true;
-                if (lane == 0) ok = wait_or_abort(&bar_tfree[slot], (uint32_t)(((tau >> 1) & 1) ^ 1), abort_flag, a.poll_limit);
+                if (lane == 0)
+                    ok = wait_or_abort(&bar_tfree[slot], (uint32_t)(((tau / NSLOT) & 1) ^ 1), abort_flag, a.poll_limit);
                 ok = __shfl_sync(0xffffffffu, ok, 0);
                 if (!ok) {
                     if (lane == 0) atomicExch(a.err, 1);
                     break;
                 }
             }
-            if (end) {
+            // a CTA's first ticket is its block index; later ones come from the counter, after the grid's
+            int idx = (int)blockIdx.x;
+            if (tau > 0) {
+                idx = lane == 0 ? (int)gridDim.x + atomicAdd(a.sched, 1) : 0;
+                idx = __shfl_sync(0xffffffffu, idx, 0);
+            }
+            // lane 0 decides for the warp: the abort flag may change between the lanes' reads
+            const int stop = __shfl_sync(0xffffffffu, lane == 0 ? (int)(idx >= ntiles || *abort_flag) : 0, 0);
+            if (stop) {
                 // no more tiles: the other roles see tile -1 in this slot and stop
                 if (lane == 0) {
                     tile_sh[slot] = -1;
@@ -643,12 +667,31 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
                 }
                 break;
             }
+            // the first tickets take the cheapest tiles, so every CTA's epilogue starts early; the others take
+            // the rest most expensive first (tiles cost the epilogue about the same, the products do not)
+            const int g0 = min((int)gridDim.x, ntiles);
+            int t = idx < g0 ? ntiles - 1 - idx : idx - g0, b = 0;
+#pragma unroll
+            for (int q = 0; q < kTileBuckets - 1; ++q)
+                if (b == q && t >= bcount[q]) {
+                    t -= bcount[q];
+                    b = q + 1;
+                }
+            const int item = a.tile_list[(size_t)b * lstride + t];
+            const int prod = kBatched ? item_prod(item) : 0;
+            const int tile = kBatched ? item_tile(item) : item;
+            const ProducerView v = producer_view<kBatched>(a, prod);
+            const int m = v.m;
+            const int i = tile / m, k = tile - (tile / m) * m;
+            const int cnt = v.counts[tile];
+            const int* js = v.jlist + (size_t)tile * m;
+            const unsigned long long ra0 = v.rmaxA[i * NB + lane], ra1 = v.rmaxA[i * NB + 32 + lane];
+            const unsigned long long cb0 = v.cmaxB[k * NB + lane], cb1 = v.cmaxB[k * NB + 32 + lane];
             int T = 0;
             for (int base = 0; base < cnt; base += 32) {
-                const int t = base + lane;
-                int j = base == 0 ? jpre0 : (base == 32 ? jpre1 : 0);
-                bool keep = t < cnt;
-                if (keep && base >= 64) j = js[t];
+                const int tt = base + lane;
+                bool keep = tt < cnt;
+                const int j = keep ? js[tt] : 0;
                 // with thr > 0 every listed task has two nonzero operand tiles; with thr = 0 the
                 // tasks with an exactly zero operand contribute nothing and are skipped
                 if (keep && v.zero_filter) keep = v.leafA[(size_t)i * m + j] != 0.0 && v.leafB[(size_t)j * m + k] != 0.0;
@@ -664,52 +707,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
                 ntask_sh[slot] = T;
                 tile_sh[slot] = tile;
                 prod_sh[slot] = prod;
+                srcA_sh[slot] = v.sliceA + (size_t)i * m * A_TILE_BYTES;
+                srcB_sh[slot] = v.sliceB + (size_t)k * B_TILE_BYTES;
+                strideB_sh[slot] = (size_t)m * B_TILE_BYTES;
                 drawn[idx] = item;
             }
             __syncwarp();
-            if (lane == 0) {
-                ptx::mbar_arrive(&bar_tready[slot]);  // release: the task list and scales are visible
-                for (int t = 0; t < T; ++t) {
-                    const int j = tasks_sh[slot][t];
-                    const uint8_t* srcA = v.sliceA + ((size_t)i * m + j) * A_TILE_BYTES;
-                    const uint8_t* srcB = v.sliceB + ((size_t)j * m + k) * B_TILE_BYTES;
-                    for (int h = 0; h < 2; ++h, ++H) {
-                        const int s = (int)(H % NSTAGE);
-                        if (H >= NSTAGE &&
-                            !wait_or_abort(&bar_empty[s], (uint32_t)(((H / NSTAGE) - 1) & 1), abort_flag, a.poll_limit)) {
-                            atomicExch(a.err, 1);
-                            break;
-                        }
-                        uint8_t* dst = smem + (size_t)s * STAGE_BYTES;
-                        ptx::mbar_arrive_expect_tx(&bar_full[s], STAGE_BYTES);
-                        ptx::bulk_g2s(dst, srcA + h * A_HALF_BYTES, A_HALF_BYTES, &bar_full[s]);
-                        ptx::bulk_g2s(dst + A_HALF_BYTES, srcB + h * B_HALF_BYTES, B_HALF_BYTES, &bar_full[s]);
-                    }
-                    if (*abort_flag) break;
-                }
-            }
-            __syncwarp();
-            idx = __shfl_sync(0xffffffffu, nxt, 0);
+            if (lane == 0) ptx::mbar_arrive(&bar_tready[slot]);  // release: the task list and scales are visible
         }
-        // an aborted CTA leaves no copy in flight: wait (bounded) for the last copy issued on every stage
-        if (lane == 0 && *abort_flag)
-            for (int s = 0; s < NSTAGE; ++s)
-                if (H > s) {
-                    const long long hl = s + ((H - 1 - s) / NSTAGE) * NSTAGE;
-                    ptx::mbar_wait_bounded(&bar_full[s], (uint32_t)((hl / NSTAGE) & 1), kDrainPolls);
-                }
     } else if (warp == 1) {
         // ---------------- MMA issuer: tasks accumulate in TMEM in chunks of kChunk
         if (lane == 0) {
             constexpr uint32_t idesc256 = ptx::idesc_f16_f32(128, 256);
             constexpr uint32_t idesc128 = ptx::idesc_f16_f32(128, 128);
+            // descriptors of the other stages and K steps differ from stage 0's by a constant in the address
+            // field (shared addresses stay below 2^18, so the 14-bit field never carries)
+            const uint64_t dA0 = ptx::smem_desc(stage_addr(sbase, 0), 128, 512);
+            const uint64_t dB0 = ptx::smem_desc(stage_addr(sbase, 0) + A_HALF_BYTES, 128, 512);
+            constexpr uint64_t kDStage = STAGE_BYTES >> 4, kDK = 256 >> 4, kDStack = A_HALF_STACK >> 4;
+            constexpr uint64_t kDSl4 = (4 * B_HALF_SLICE) >> 4;
             long long H = 0, C = 0;
             unsigned long long units = 0;
             int tau = 0;
             bool ok = true;
             for (; ok; ++tau) {
-                const int slot = tau & 1;
-                if (!wait_or_abort(&bar_tready[slot], (uint32_t)((tau >> 1) & 1), abort_flag, a.poll_limit)) {
+                const int slot = tau % NSLOT;
+                if (!wait_or_abort(&bar_tready[slot], (uint32_t)((tau / NSLOT) & 1), abort_flag, a.poll_limit)) {
                     atomicExch(a.err, 2);
                     break;
                 }
@@ -733,21 +756,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
                             break;
                         }
                         ptx::tc_fence_after();
-                        const uint32_t sA = stage_addr(sbase, s), sB = sA + A_HALF_BYTES;
+                        const uint64_t dA = dA0 + (uint64_t)s * kDStage, dB = dB0 + (uint64_t)s * kDStage;
                         // the chunk's first K step overwrites groups 0-5 (stack 0 covers them all);
                         // stacks 1 and 2 always accumulate onto it
                         const uint32_t fresh = chunk_start && h == 0;
+#pragma unroll
                         for (int ks = 0; ks < 2; ++ks) {
                             const uint32_t acc = fresh && ks == 0 ? 0u : 1u;
-                            const uint32_t b0 = sB + ks * 256;
-                            ptx::mma_f16(tmem, ptx::smem_desc(sA + ks * 256, 128, 512),
-                                          ptx::smem_desc(b0, 128, 512), idesc256, acc);
-                            ptx::mma_f16(tmem + 256u, ptx::smem_desc(sA + ks * 256, 128, 512),
-                                          ptx::smem_desc(b0 + 4 * B_HALF_SLICE, 128, 512), idesc128, acc);
-                            ptx::mma_f16(tmem + 128u, ptx::smem_desc(sA + A_HALF_STACK + ks * 256, 128, 512),
-                                          ptx::smem_desc(b0, 128, 512), idesc256, 1u);
-                            ptx::mma_f16(tmem + 256u, ptx::smem_desc(sA + 2 * A_HALF_STACK + ks * 256, 128, 512),
-                                          ptx::smem_desc(b0, 128, 512), idesc128, 1u);
+                            const uint64_t a = dA + ks * kDK, b = dB + ks * kDK;
+                            ptx::mma_f16(tmem, a, b, idesc256, acc);
+                            ptx::mma_f16(tmem + 256u, a, b + kDSl4, idesc128, acc);
+                            ptx::mma_f16(tmem + 128u, a + kDStack, b, idesc256, 1u);
+                            ptx::mma_f16(tmem + 256u, a + 2 * kDStack, b, idesc128, 1u);
                         }
                         ptx::mma_commit(&bar_empty[s]);
                     }
@@ -778,8 +798,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
         long long C = 0;
         int tau = 0;
         for (;; ++tau) {
-            const int slot = tau & 1;
-            if (!wait_or_abort(&bar_tready[slot], (uint32_t)((tau >> 1) & 1), abort_flag, a.poll_limit)) {
+            const int slot = tau % NSLOT;
+            if (!wait_or_abort(&bar_tready[slot], (uint32_t)((tau / NSLOT) & 1), abort_flag, a.poll_limit)) {
                 atomicExch(a.err, 4);
                 break;
             }
