@@ -922,7 +922,7 @@ void launch_cull_batched(const ProdDesc* prods, const int4* blocks, int nblocks,
 // k_tree does for one solve; the last block to finish ends the batch once every matrix has stopped (and,
 // in a graph's loop body, clears the loop's condition).
 template <bool kLoop>
-__global__ void __launch_bounds__(256) k_tree_batched(const ProdDesc* __restrict__ prods, int nprod,
+__global__ void __launch_bounds__(1024) k_tree_batched(const ProdDesc* __restrict__ prods, int nprod,
                                                       int* __restrict__ tile_count, int* __restrict__ stage_ctr,
                                                       int* __restrict__ ndone, int count, int* __restrict__ all_done,
                                                       cudaGraphConditionalHandle cond, int x_stage) {
@@ -932,7 +932,10 @@ __global__ void __launch_bounds__(256) k_tree_batched(const ProdDesc* __restrict
     __shared__ double bufB[32 * 32];
     const ProdDesc& d = prods[blockIdx.x];
     const bool live = d.mflags[0] == 0;
-    if (live) tree_levels<256>(d.td, d.Ctree, bufA, bufB);
+    if (live) {
+        if (d.td.L <= 6) tree_levels_small(d.td, d.Ctree, bufB);
+        else tree_levels<1024>(d.td, d.Ctree, bufA, bufB);
+    }
     if (blockIdx.x == 0 && threadIdx.x < kTileBuckets) tile_count[threadIdx.x] = 0;
     if (!x_stage) return;
     if (live && threadIdx.x < 32) {
@@ -963,10 +966,10 @@ __global__ void __launch_bounds__(256) k_tree_batched(const ProdDesc* __restrict
 void launch_tree_batched(const ProdDesc* prods, int nprod, int* tile_count, int* stage_ctr, int* ndone, int count,
                          int* all_done, const cudaGraphConditionalHandle* cond, bool x_stage, cudaStream_t st) {
     if (cond)
-        launch_dependent(k_tree_batched<true>, dim3(nprod), dim3(256), 0, st, prods, nprod, tile_count, stage_ctr,
+        launch_dependent(k_tree_batched<true>, dim3(nprod), dim3(1024), 0, st, prods, nprod, tile_count, stage_ctr,
                          ndone, count, all_done, *cond, x_stage ? 1 : 0);
     else
-        launch_dependent(k_tree_batched<false>, dim3(nprod), dim3(256), 0, st, prods, nprod, tile_count, stage_ctr,
+        launch_dependent(k_tree_batched<false>, dim3(nprod), dim3(1024), 0, st, prods, nprod, tile_count, stage_ctr,
                          ndone, count, all_done, (cudaGraphConditionalHandle)0, x_stage ? 1 : 0);
     note_launch();
 }
