@@ -161,6 +161,9 @@ struct Plan {
     // tensor-core path: the slicing of a product output runs on its own stream per branch, beside the
     // tree and the next culls; ev_norm orders it after the output's norm pass
     cudaStream_t slice_st[2] = {nullptr, nullptr};
+    // the prologue's side passes (Z0, X0's slices): streams of their own, never used inside a loop body,
+    // which is captured separately from the solve around it
+    cudaStream_t pro_st[2] = {nullptr, nullptr};
     cudaEvent_t ev_norm[2] = {nullptr, nullptr};
     unsigned sliced_mask = 0;  // buffers whose `sliced` event this call recorded
     unsigned long long* task_ctr = nullptr;  // [3 * maxit_cap + 4]
@@ -212,6 +215,7 @@ static void free_plan(Plan* p) {
     }
     for (int q = 0; q < 2; ++q) {
         if (p->slice_st[q]) cudaStreamDestroy(p->slice_st[q]);
+        if (p->pro_st[q]) cudaStreamDestroy(p->pro_st[q]);
         if (p->ev_norm[q]) cudaEventDestroy(p->ev_norm[q]);
     }
     cudaFree(p->counts);
@@ -323,6 +327,7 @@ static int ensure_emu(Plan* p) {
     }
     for (int q = 0; q < 2; ++q) {
         CKA(cudaStreamCreateWithFlags(&p->slice_st[q], cudaStreamNonBlocking));
+        CKA(cudaStreamCreateWithFlags(&p->pro_st[q], cudaStreamNonBlocking));
         CKA(cudaEventCreateWithFlags(&p->ev_norm[q], cudaEventDisableTiming));
     }
     p->emu_ready = true;
@@ -881,6 +886,24 @@ static int enqueue_prologue(Plan* p, const double* dS, int n, const spamm_opts& 
     double* sqc = p->scal + 3;
     double* rc = p->scal + 6;
     double* rsqc = p->scal + 7;
+    // Z0 = I does not depend on S: on the tensor-core path its pass (identity, quadtree, maxima, slices) runs
+    // on a side stream beside the scaling and packing of S, and X0's maxima and slices run on another one
+    // beside the map.  A profiled call keeps everything on one stream.
+    const bool side = p->emu && !p->profile;
+    cudaStream_t zs = side ? p->pro_st[1] : st;
+    cudaStream_t xs = side ? p->pro_st[0] : st;
+    if (o.channel == SPAMM_CHANNEL_SINGLE)
+        *sb = SolveBufs{p->buf[3], p->buf[1], p->buf[2], p->buf[3], p->buf[4], p->buf[0], p->buf[5]};
+    else
+        *sb = SolveBufs{p->buf[0], p->buf[1], p->buf[2], p->buf[3], p->buf[4], TileMat(), TileMat()};
+    if (side) {
+        cudaEventRecord(p->ev_norm[1], st);
+        cudaStreamWaitEvent(zs, p->ev_norm[1], 0);
+    }
+    launch_identity(g, sb->Zb, zs);
+    launch_tree(g, sb->Zb.tree, nullptr, zs);
+    if (p->emu) prepare_emu(p, sb->Zb, zs);
+
     const double* mu_ptr = nullptr;
     if (o.mu_rel > 0.0) {
         launch_gershgorin(dS, n, nullptr, p->rowsum, c0, st);
@@ -892,22 +915,19 @@ static int enqueue_prologue(Plan* p, const double* dS, int n, const spamm_opts& 
 
     // X0 = s in buf 0: Y0 of the dual channel, the constant s of the single channel
     const TileMat X0 = p->buf[0];
-    if (o.channel == SPAMM_CHANNEL_SINGLE)
-        *sb = SolveBufs{p->buf[3], p->buf[1], p->buf[2], p->buf[3], p->buf[4], X0, p->buf[5]};
-    else
-        *sb = SolveBufs{X0, p->buf[1], p->buf[2], p->buf[3], p->buf[4], TileMat(), TileMat()};
     launch_pack(dS, n, g, mu_ptr, rc, X0, st);
     launch_tree(g, X0.tree, nullptr, st);
+    if (side) {
+        cudaEventRecord(p->ev_norm[0], st);
+        cudaStreamWaitEvent(xs, p->ev_norm[0], 0);
+    }
+    if (p->emu) prepare_emu(p, X0, xs);
     if (o.map == SPAMM_MAP_SCALED) launch_trace_parts(X0.t, g, p->trace_part, st);
     launch_map(X0.t, X0.tree, sb->Tb, g, o.map, p->trace_part, false, nullptr, st);
     launch_tree(g, sb->Tb.tree, nullptr, st);
-    launch_identity(g, sb->Zb, st);
-    launch_tree(g, sb->Zb.tree, nullptr, st);
-    if (p->emu) {
-        prepare_emu(p, X0, st);
-        prepare_emu(p, sb->Tb, st);
-        prepare_emu(p, sb->Zb, st);
-    }
+    if (p->emu) prepare_emu(p, sb->Tb, st);
+    // the first culls read Z0's quadtree (its slicing event follows the tree on the same stream)
+    if (side) cudaStreamWaitEvent(st, sb->Zb.sliced, 0);
     if (o.channel == SPAMM_CHANNEL_SINGLE) {
         // W = s Z0 = s: the Y output of a solve with no iteration
         CK(cudaMemcpyAsync(sb->Yb.t, X0.t, g.elems() * sizeof(double), cudaMemcpyDeviceToDevice, st));
