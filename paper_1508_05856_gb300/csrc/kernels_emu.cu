@@ -128,6 +128,57 @@ __device__ __forceinline__ uint32_t digit_pair_f16(const Digits& a, const Digits
     return *reinterpret_cast<const uint32_t*>(&r);
 }
 
+// The 512 items of one operand role of a staged tile, two per thread: item `it` covers row (A role) or
+// column (B role) r and k-group g, 8 entries, i.e. 16 bytes of every slice.  8 consecutive items fill one
+// 128-byte core matrix, 32 consecutive items 512 contiguous bytes.  The role is a template parameter, so
+// the entries are read and moved as bit patterns with no per-entry selects.
+template <bool kA>
+__device__ __forceinline__ void slice_role(const double (*xs)[NB + 1], const int* e, uint8_t* dst) {
+#pragma unroll 1
+    for (int it = threadIdx.x; it < 512; it += 256) {
+        const int kgi = (it >> 3) & 3, kh = (it >> 5) & 1;
+        const int r = (it >> 6) * 8 + (it & 7), g = kh * 4 + kgi;  // A: row r, k-group g; B: column r, k-group g
+        // digits of |F| with F = round(|x| 2^(48-e)); the sign goes onto the FP16 digits afterwards
+        Digits D[8];
+        unsigned neg = 0;
+        const int se = e[r] + 1027;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const unsigned long long bq =
+                (unsigned long long)__double_as_longlong(kA ? xs[r][8 * g + q] : xs[8 * g + q][r]);
+            neg |= (unsigned)(bq >> 63) << q;
+            D[q] = balanced_digits(fixed48_mag(bq, se));
+        }
+        uint8_t* const base = dst + (uint32_t)kh * (kA ? A_HALF_BYTES : B_HALF_BYTES) +
+                              (uint32_t)(((r >> 3) * 4 + kgi) * 128 + (r & 7) * 16);
+        // FP16 sign bits of element pairs (2h, 2h+1): bit 15 and bit 31 of word h
+        const uint32_t m0 = ((neg & 1u) << 15) | ((neg & 2u) << 30);
+        const uint32_t m1 = ((neg & 4u) << 13) | ((neg & 8u) << 28);
+        const uint32_t m2 = ((neg & 16u) << 11) | ((neg & 32u) << 26);
+        const uint32_t m3 = ((neg & 64u) << 9) | ((neg & 128u) << 24);
+        // A role: slice p sits in stack p/2, rows 64 (p%2) + r (the odd rows 8 row groups, 4 KB, further on);
+        // B role: slice p is the p-th 64-column block
+#define SPAMM_STORE_SLICE(P)                                                                                 \
+        {                                                                                                    \
+            uint4 w;                                                                                         \
+            w.x = digit_pair_f16<P>(D[0], D[1], m0);                                                         \
+            w.y = digit_pair_f16<P>(D[2], D[3], m1);                                                         \
+            w.z = digit_pair_f16<P>(D[4], D[5], m2);                                                         \
+            w.w = digit_pair_f16<P>(D[6], D[7], m3);                                                         \
+            constexpr uint32_t off = kA ? (uint32_t)(P >> 1) * A_HALF_STACK + (uint32_t)(P & 1) * 4096u       \
+                                        : (uint32_t)P * B_HALF_SLICE;                                        \
+            *reinterpret_cast<uint4*>(base + off) = w;                                                       \
+        }
+        SPAMM_STORE_SLICE(0)
+        SPAMM_STORE_SLICE(1)
+        SPAMM_STORE_SLICE(2)
+        SPAMM_STORE_SLICE(3)
+        SPAMM_STORE_SLICE(4)
+        SPAMM_STORE_SLICE(5)
+#undef SPAMM_STORE_SLICE
+    }
+}
+
 // ------------------------------------------------------------------ slicing
 // Grid-stride over the listed tiles (tile_list / tile_count), or over all
 // m*m tiles when tile_list is null.  With leaf_out null, leaf tiles with
@@ -204,61 +255,8 @@ __global__ void __launch_bounds__(256, 5) k_slice(const double* __restrict__ X0,
         const double s45 = nu_sh[4] + nu_sh[5], s67 = nu_sh[6] + nu_sh[7];
         leaf_out[tile] = (s01 + s23) + (s45 + s67);
     }
-    uint8_t* a = sA + (size_t)tile * A_TILE_BYTES;
-    uint8_t* b = sB + (size_t)tile * B_TILE_BYTES;
-    for (int item = threadIdx.x; item < 2 * 512; item += 256) {
-        const bool arole = item < 512;
-        const int it = arole ? item : item - 512;
-        // 8 consecutive items fill one 128-byte core matrix, 32 consecutive items 512 contiguous bytes
-        const int kgi = (it >> 3) & 3, kh = (it >> 5) & 1;
-        const int r = (it >> 6) * 8 + (it & 7), g = kh * 4 + kgi;  // A: row r, k-group g; B: column r, k-group g
-        // digits of |F| with F = round(|x| 2^(48-e)); the sign goes onto the FP16 digits afterwards
-        Digits D[8];
-        unsigned neg = 0;
-        const int se = (arole ? eR[r] : eC[r]) + 1027;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const double v = arole ? xs[r][8 * g + q] : xs[8 * g + q][r];
-            const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-            neg |= (unsigned)(b >> 63) << q;
-            D[q] = balanced_digits(fixed48_mag(b, se));
-        }
-        uint8_t* base;
-        uint32_t pstride;
-        if (arole) {
-            // slice p sits in stack p/2, rows 64 (p%2) + r
-            base = a + (uint32_t)kh * A_HALF_BYTES + (uint32_t)(((r >> 3) * 4 + kgi) * 128 + (r & 7) * 16);
-            pstride = A_HALF_STACK;
-        } else {
-            base = b + (uint32_t)kh * B_HALF_BYTES + (uint32_t)(((r >> 3) * 4 + kgi) * 128 + (r & 7) * 16);
-            pstride = B_HALF_SLICE;
-        }
-        // odd slices of the A role: rows 64..127 of the stack, 8 row groups (4 KB) further on
-        const uint32_t aodd = arole ? 8u * 4u * 128u : 0u;
-        // FP16 sign bits of element pairs (2h, 2h+1): bit 15 and bit 31 of word h
-        const uint32_t m0 = ((neg & 1u) << 15) | ((neg & 2u) << 30);
-        const uint32_t m1 = ((neg & 4u) << 13) | ((neg & 8u) << 28);
-        const uint32_t m2 = ((neg & 16u) << 11) | ((neg & 32u) << 26);
-        const uint32_t m3 = ((neg & 64u) << 9) | ((neg & 128u) << 24);
-#define SPAMM_STORE_SLICE(P)                                                                                 \
-        {                                                                                                    \
-            uint4 w;                                                                                         \
-            w.x = digit_pair_f16<P>(D[0], D[1], m0);                                                         \
-            w.y = digit_pair_f16<P>(D[2], D[3], m1);                                                         \
-            w.z = digit_pair_f16<P>(D[4], D[5], m2);                                                         \
-            w.w = digit_pair_f16<P>(D[6], D[7], m3);                                                         \
-            const uint32_t off = arole ? (uint32_t)(P >> 1) * pstride + (uint32_t)(P & 1) * aodd             \
-                                       : (uint32_t)P * pstride;                                              \
-            *reinterpret_cast<uint4*>(base + off) = w;                                                       \
-        }
-        SPAMM_STORE_SLICE(0)
-        SPAMM_STORE_SLICE(1)
-        SPAMM_STORE_SLICE(2)
-        SPAMM_STORE_SLICE(3)
-        SPAMM_STORE_SLICE(4)
-        SPAMM_STORE_SLICE(5)
-#undef SPAMM_STORE_SLICE
-    }
+    slice_role<true>(xs, eR, sA + (size_t)tile * A_TILE_BYTES);
+    slice_role<false>(xs, eC, sB + (size_t)tile * B_TILE_BYTES);
     }
 }
 
