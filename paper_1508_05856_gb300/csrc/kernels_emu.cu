@@ -196,9 +196,11 @@ __global__ void __launch_bounds__(256, 5) k_slice(const double* __restrict__ X0,
                                                const unsigned long long* __restrict__ cmax0,
                                                uint8_t* __restrict__ sA0, uint8_t* __restrict__ sB0, int m0,
                                                const int* __restrict__ tile_list, const int* __restrict__ tile_count,
-                                               const int* __restrict__ done, const ProdDesc* __restrict__ prods) {
+                                               const int* __restrict__ done, const ProdDesc* __restrict__ prods,
+                                               const double* __restrict__ skip_root, double skip_factor) {
     grid_dependency_wait();
     if (done && *done) return;
+    const double skip_below = skip_root ? skip_factor * *skip_root : 0.0;
     __shared__ double xs[NB][NB + 1];
     __shared__ int eR[NB], eC[NB];
     __shared__ double nu_sh[8];
@@ -223,7 +225,10 @@ __global__ void __launch_bounds__(256, 5) k_slice(const double* __restrict__ X0,
         sA = d.CsliceA;
         sB = d.CsliceB;
     }
-    if (!leaf_out && leaf[tile] == 0.0) continue;
+    if (!leaf_out) {
+        const double nu = leaf[tile];
+        if (nu == 0.0 || nu < skip_below) continue;
+    }
     __syncthreads();
     const int i = tile / m, j = tile - (tile / m) * m;
     const double* x = X + (size_t)tile * NB * NB;
@@ -939,12 +944,13 @@ void launch_rowcol_max(const double* X, const Geometry& g, unsigned long long* r
 
 void launch_slice(const double* X, const double* leaf, double* leaf_out, const unsigned long long* rmax,
                   const unsigned long long* cmax, uint8_t* sA, uint8_t* sB, const Geometry& g, const int* tile_list,
-                  const int* tile_count, const int* done, cudaStream_t st) {
+                  const int* tile_count, const int* done, cudaStream_t st, const double* skip_root,
+                  double skip_factor) {
     // five blocks (34 KB shared memory, 48 registers) are resident per SM: one wave, so a dependent launched
     // early never holds slots the grid still needs
     const int grid = std::min(device_sm_count() * 5, g.m * g.m);
     launch_dependent(emu::k_slice<false>, dim3(grid), dim3(256), 0, st, X, leaf, leaf_out, rmax, cmax, sA, sB, g.m,
-                     tile_list, tile_count, done, (const ProdDesc*)nullptr);
+                     tile_list, tile_count, done, (const ProdDesc*)nullptr, skip_root, skip_factor);
     note_launch();
 }
 
@@ -954,7 +960,7 @@ void launch_slice_batched(const ProdDesc* prods, const int* slice_items, int cap
     launch_dependent(emu::k_slice<true>, dim3(grid), dim3(256), 0, st, (const double*)nullptr,
                      (const double*)nullptr, (double*)nullptr, (const unsigned long long*)nullptr,
                      (const unsigned long long*)nullptr, (uint8_t*)nullptr, (uint8_t*)nullptr, 0, slice_items,
-                     slice_items + cap, all_done, prods);
+                     slice_items + cap, all_done, prods, (const double*)nullptr, 0.0);
     note_launch();
 }
 

@@ -695,11 +695,15 @@ static void product(Plan* p, const TileMat& A, const TileMat& B, TileMat& C, dou
 }
 
 // Row/column maxima and slices of a freshly packed matrix (tensor-core path).
-static void prepare_emu(Plan* p, const TileMat& M, cudaStream_t st) {
+// tau_min > 0: every product that reads M culls at tau >= tau_min, so the tiles below 0.999 tau_min^2 of M's
+// squared norm are never read (a kept pair has nu_a nu_b >= tau^2 nu_A nu_B with nu_b <= nu_B; the factor
+// leaves a margin far above the rounding of that test) and are not sliced.  M's quadtree must be complete.
+static void prepare_emu(Plan* p, const TileMat& M, cudaStream_t st, double tau_min = 0.0) {
     const Geometry& g = p->g;
     cudaMemsetAsync(M.rmax, 0, 2 * (size_t)g.m * g.nb * sizeof(unsigned long long), st);
     launch_rowcol_max(M.t, g, M.rmax, M.cmax, st);
-    launch_slice(M.t, M.tree, nullptr, M.rmax, M.cmax, M.sliceA, M.sliceB, g, nullptr, nullptr, nullptr, st);
+    launch_slice(M.t, M.tree, nullptr, M.rmax, M.cmax, M.sliceA, M.sliceB, g, nullptr, nullptr, nullptr, st,
+                 tau_min > 0.0 ? M.tree + g.off[0] : nullptr, 0.999 * tau_min * tau_min);
     mark_sliced(p, M, st);
 }
 
@@ -872,7 +876,10 @@ struct SolveBufs {
 
 // a1-a2: flags and histories cleared, Gershgorin bound (plus the Tikhonov shift of Sec. 6) and scaling,
 // X0 = Y0 = S / c packed with leaf norms, T0 = h[X0], Z0 = I (and their slices on the tensor-core path).
-static int enqueue_prologue(Plan* p, const double* dS, int n, const spamm_opts& o, cudaStream_t st, SolveBufs* sb) {
+// tau_min is the smallest threshold of the products that read them (tau_s or tau): their slices are cut
+// only for tiles those products can keep.
+static int enqueue_prologue(Plan* p, const double* dS, int n, const spamm_opts& o, cudaStream_t st, SolveBufs* sb,
+                            double tau_min) {
     const Geometry& g = p->g;
     CK(cudaMemsetAsync(p->flags, 0, kFlagInts * sizeof(int), st));
     CK(cudaMemsetAsync(p->task_ctr, 0, (3 * (size_t)p->maxit_cap + 4) * sizeof(unsigned long long), st));
@@ -902,7 +909,7 @@ static int enqueue_prologue(Plan* p, const double* dS, int n, const spamm_opts& 
     }
     launch_identity(g, sb->Zb, zs);
     launch_tree(g, sb->Zb.tree, nullptr, zs);
-    if (p->emu) prepare_emu(p, sb->Zb, zs);
+    if (p->emu) prepare_emu(p, sb->Zb, zs, tau_min);
 
     const double* mu_ptr = nullptr;
     if (o.mu_rel > 0.0) {
@@ -921,11 +928,11 @@ static int enqueue_prologue(Plan* p, const double* dS, int n, const spamm_opts& 
         cudaEventRecord(p->ev_norm[0], st);
         cudaStreamWaitEvent(xs, p->ev_norm[0], 0);
     }
-    if (p->emu) prepare_emu(p, X0, xs);
+    if (p->emu) prepare_emu(p, X0, xs, tau_min);
     if (o.map == SPAMM_MAP_SCALED) launch_trace_parts(X0.t, g, p->trace_part, st);
     launch_map(X0.t, X0.tree, sb->Tb, g, o.map, p->trace_part, false, nullptr, st);
     launch_tree(g, sb->Tb.tree, nullptr, st);
-    if (p->emu) prepare_emu(p, sb->Tb, st);
+    if (p->emu) prepare_emu(p, sb->Tb, st, tau_min);
     // the first culls read Z0's quadtree (its slicing event follows the tree on the same stream)
     if (side) cudaStreamWaitEvent(st, sb->Zb.sliced, 0);
     if (o.channel == SPAMM_CHANNEL_SINGLE) {
@@ -1035,7 +1042,7 @@ static int enqueue_epilogue(Plan* p, const SolveBufs& sb, double* dY, double* dZ
 static int enqueue_solve(Plan* p, const double* dS, double* dY, double* dZ, int n, double tau, double tau_s,
                          int maxit, const spamm_opts& o, cudaStream_t st, bool host_poll) {
     SolveBufs sb;
-    int e = enqueue_prologue(p, dS, n, o, st, &sb);
+    int e = enqueue_prologue(p, dS, n, o, st, &sb, std::min(tau, tau_s));
     if (e) return e;
     int swaps = 0;
     for (int k = 0; k < maxit; ++k) {
@@ -1057,7 +1064,7 @@ static int enqueue_solve(Plan* p, const double* dS, double* dY, double* dZ, int 
 static int enqueue_solve_loop(Plan* p, const double* dS, double* dY, double* dZ, int n, double tau, double tau_s,
                               int maxit, const spamm_opts& o, cudaStream_t st) {
     SolveBufs sb;
-    int e = enqueue_prologue(p, dS, n, o, st, &sb);
+    int e = enqueue_prologue(p, dS, n, o, st, &sb, std::min(tau, tau_s));
     if (e) return e;
     join_slicing(p, st);  // the body waits on nothing recorded outside it
     cudaStreamCaptureStatus cs;

@@ -343,11 +343,15 @@ void launch_rowcol_max(const double* X, const Geometry& g, unsigned long long* r
                        cudaStream_t st);
 // FP16 digit slices of both operand roles from FP64 tiles and row/column maxima,
 // for the listed tiles (or all tiles when tile_list is null).  With leaf_out
-// null, tiles whose leaf[] norm is zero are skipped; with leaf_out set, every
-// listed tile is sliced and its squared Frobenius norm written to leaf_out.
+// null, tiles whose leaf[] norm is zero are skipped, and so are those below
+// skip_factor * (*skip_root) when skip_root is set (a matrix whose products all
+// cull at tau >= tau_min never reads a tile with nu < tau_min^2 * nu_root: see
+// the prologue); with leaf_out set, every listed tile is sliced and its squared
+// Frobenius norm written to leaf_out.
 void launch_slice(const double* X, const double* leaf, double* leaf_out, const unsigned long long* rmax,
                   const unsigned long long* cmax, uint8_t* sA, uint8_t* sB, const Geometry& g, const int* tile_list,
-                  const int* tile_count, const int* done, cudaStream_t st);
+                  const int* tile_count, const int* done, cudaStream_t st, const double* skip_root = nullptr,
+                  double skip_factor = 0.0);
 // Leaf products on the tensor cores; writes C's FP64 tiles, leaf norms
 // (FP32 sums of squares, about 1e-6 relative), row/column maxima
 // (pre-zeroed), trace partials for EPI_NS_X, and C.slice_list; *err set on a
