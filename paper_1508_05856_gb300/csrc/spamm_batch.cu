@@ -280,12 +280,14 @@ void enqueue_setup(Batch* b, BatchMat& M, double mu_rel, cudaStream_t st) {
     launch_tree(g, T0.tree, nullptr, st);
     launch_identity(g, Z0, st);
     launch_tree(g, Z0.tree, nullptr, st);
+    // the first y and z products read these at tau_s and tau: tiles neither can keep are not sliced
+    const double tau_min = std::min(M.tau, M.tau_s);
     if (b->emu)
         for (const TileMat* P : {&X0, &T0, &Z0}) {
             cudaMemsetAsync(P->rmax, 0, 2 * (size_t)g.m * g.nb * sizeof(unsigned long long), st);
             launch_rowcol_max(P->t, g, P->rmax, P->cmax, st);
             launch_slice(P->t, P->tree, nullptr, P->rmax, P->cmax, P->sliceA, P->sliceB, g, nullptr, nullptr,
-                         nullptr, st);
+                         nullptr, st, tau_min > 0.0 ? P->tree + g.off[0] : nullptr, 0.999 * tau_min * tau_min);
         }
 }
 
