@@ -356,6 +356,18 @@ void launch_trace_parts(const double* X, const Geometry& g, double* trace_part, 
 // both exact).  Grid-stride over tiles; a tile whose X is exactly zero (leaf
 // norm 0, data unwritten) off the diagonal stays zero.  Writes T's leaf
 // norms and, when rmax is set (64 x 64 tiles), T's row/column magnitude maxima.
+// -x/2 as the multiply gives it, from the bits where that is exact: for a normal x whose half is normal the
+// exponent field drops by one and the sign flips; +-0 flips its sign; anything else (a half below the
+// normal range, inf, nan) takes the FP64 multiply, which this part runs at a small fraction of its integer
+// rate.
+__device__ __forceinline__ double neg_half(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned E = (unsigned)(b >> 52) & 0x7FFu;
+    if (E > 1u && E < 0x7FFu) return __longlong_as_double((long long)((b - (1ull << 52)) ^ 0x8000000000000000ull));
+    if ((b << 1) == 0ull) return __longlong_as_double((long long)(b ^ 0x8000000000000000ull));
+    return -0.5 * x;
+}
+
 template <int NB>
 __global__ void __launch_bounds__(256, 4) k_map(const double* X, double* T, const double* leafX, double* leafT,
                                                 int n, int m, int map, const double* __restrict__ trace_part,
@@ -381,6 +393,8 @@ __global__ void __launch_bounds__(256, 4) k_map(const double* X, double* T, cons
     }
     __syncthreads();
     const double c0 = coef[0], c1 = coef[1];
+    // alpha = 1: c1 = -1/2 exactly, so the entries off the diagonal are -x/2 from their bits
+    const bool half_neg = map != SPAMM_MAP_SCALED;
     using TS = TileSplit<NB, 8>;
     constexpr int ne = NB * NB;
     const int lane = threadIdx.x & 31;
@@ -410,8 +424,8 @@ __global__ void __launch_bounds__(256, 4) k_map(const double* X, double* T, cons
             const int r = idx / NB, cc = idx % NB;
             const int gi = i * NB + r, gj = j * NB + cc;
             const double xv = xb[u];
-            // off the diagonal tiles no entry takes c0: one multiply
-            const double v = (i == j && gi == gj && gi < n) ? fma(c1, xv, c0) : c1 * xv;
+            // off the diagonal no entry takes c0: one multiply, or its exact bit form for alpha = 1
+            const double v = (i == j && gi == gj && gi < n) ? fma(c1, xv, c0) : (half_neg ? neg_half(xv) : c1 * xv);
             t[idx] = v;
             acc = fma(v, v, acc);
             if (NB == 64 && rmax) {
