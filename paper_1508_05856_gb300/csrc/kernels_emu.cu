@@ -265,19 +265,6 @@ __global__ void __launch_bounds__(256, 5) k_slice(const double* __restrict__ X0,
     }
 }
 
-// |v| as FP32 from the IEEE bits b of |v|, its mantissa cut to 23 bits (relative error below 2^-23); 0 for
-// zero and for magnitudes outside FP32's normal range.  The per-tile sums of squares are taken in FP32:
-// they only steer the cull, and a relative error near 1e-6 in a tile norm moves a keep decision only for
-// pairs that sit that close to the threshold.  Their squares overflow for |v| >= 2^64, far above the
-// magnitudes of the scaled iteration.
-__device__ __forceinline__ float f32_of_bits(unsigned long long b) {
-    const unsigned hw = (unsigned)(b >> 32);
-    const int E = (int)(hw >> 20);
-    // the low 9 exponent bits and the leading 23 mantissa bits, the bias moved from 1023 to 127 (mod 2^32)
-    const unsigned f = __funnelshift_r((unsigned)b, hw, 29) - (896u << 23);
-    return (E > 896 && E < 1151) ? __uint_as_float(f) : 0.f;
-}
-
 // Row and column magnitude maxima of a packed FP64 matrix, kept as the upper 32 bits of the IEEE pattern
 // (sign cleared), which carry the exponent exactly: the maxima feed only the slicing exponents.  Warp w
 // takes rows 8w .. 8w+7 of a 64 x 64 tile and lane l the columns l and l + 32, sixteen independent loads

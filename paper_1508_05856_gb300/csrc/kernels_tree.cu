@@ -243,7 +243,9 @@ __device__ __forceinline__ double pack_tile(const double* __restrict__ src, int 
 // t of the band in every row, so a row of the band is read as one 2 KB run (the eight warps side by side)
 // and each thread touches a single tile (t / 64); sixteen independent loads at a time.  The leaf norm of a
 // tile is the sum over its two warps of the per-thread sums of squares (rows in order), fixed order.
-template <bool kScale>
+// kF32 (the tensor-core path): the sums of squares in FP32 from the entries' bits, so the FP64 pipe does one
+// multiply per entry instead of two operations.
+template <bool kScale, bool kF32>
 __device__ __forceinline__ void pack_band64(const double* __restrict__ src, int n, int m, int i, int jb, double mu,
                                             double rc, double* __restrict__ dst, double* __restrict__ leaf,
                                             double* red) {
@@ -254,6 +256,7 @@ __device__ __forceinline__ void pack_band64(const double* __restrict__ src, int 
     const bool colok = j < m && gj < n;
     double* d = dst + ((size_t)i * m + j) * 4096;
     double acc = 0.0;
+    float accf = 0.f;
 #pragma unroll 1
     for (int r0 = 0; r0 < 64; r0 += 16) {
         double v[16];
@@ -271,9 +274,15 @@ __device__ __forceinline__ void pack_band64(const double* __restrict__ src, int 
                 x = x * rc;
             }
             if (j < m) d[(r0 + u) * 64 + c] = x;
-            acc = fma(x, x, acc);
+            if (kF32) {
+                const float f = f32_of_bits((unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull);
+                accf = fmaf(f, f, accf);
+            } else {
+                acc = fma(x, x, acc);
+            }
         }
     }
+    if (kF32) acc = (double)accf;
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if ((t & 31) == 0) red[t >> 5] = acc;
     __syncthreads();
@@ -283,11 +292,15 @@ __device__ __forceinline__ void pack_band64(const double* __restrict__ src, int 
 __global__ void __launch_bounds__(256) k_pack_band64(const double* __restrict__ src, int n, int m, int bands,
                                                      const double* __restrict__ mu_dev,
                                                      const double* __restrict__ rc_dev, double* __restrict__ dst,
-                                                     double* __restrict__ leaf) {
+                                                     double* __restrict__ leaf, int f32_norms) {
     __shared__ double red[8];
     const int i = blockIdx.x / bands, jb = blockIdx.x - (blockIdx.x / bands) * bands;
-    if (rc_dev) pack_band64<true>(src, n, m, i, jb, mu_dev ? *mu_dev : 0.0, *rc_dev, dst, leaf, red);
-    else pack_band64<false>(src, n, m, i, jb, 0.0, 1.0, dst, leaf, red);
+    if (rc_dev) {
+        if (f32_norms) pack_band64<true, true>(src, n, m, i, jb, mu_dev ? *mu_dev : 0.0, *rc_dev, dst, leaf, red);
+        else pack_band64<true, false>(src, n, m, i, jb, mu_dev ? *mu_dev : 0.0, *rc_dev, dst, leaf, red);
+    } else {
+        pack_band64<false, false>(src, n, m, i, jb, 0.0, 1.0, dst, leaf, red);
+    }
 }
 
 template <int NB>
@@ -308,13 +321,14 @@ __global__ void __launch_bounds__(256) k_pack(const double* __restrict__ src, in
 }
 
 void launch_pack(const double* src, int n, const Geometry& g, const double* mu, const double* recip_c,
-                 TileMat dst, cudaStream_t st) {
+                 TileMat dst, cudaStream_t st, bool f32_norms) {
     const dim3 grid(g.m * g.m), block(256);
     if (g.nb == 32) {
         k_pack<32><<<grid, block, 0, st>>>(src, n, g.m, mu, recip_c, dst.t, dst.tree);
     } else if (g.nb == 64) {
         const int bands = (g.m + 3) / 4;
-        k_pack_band64<<<dim3(g.m * bands), block, 0, st>>>(src, n, g.m, bands, mu, recip_c, dst.t, dst.tree);
+        k_pack_band64<<<dim3(g.m * bands), block, 0, st>>>(src, n, g.m, bands, mu, recip_c, dst.t, dst.tree,
+                                                           f32_norms ? 1 : 0);
     } else {
         k_pack<128><<<grid, block, 0, st>>>(src, n, g.m, mu, recip_c, dst.t, dst.tree);
     }
@@ -372,7 +386,8 @@ template <int NB>
 __global__ void __launch_bounds__(256, 4) k_map(const double* X, double* T, const double* leafX, double* leafT,
                                                 int n, int m, int map, const double* __restrict__ trace_part,
                                                 unsigned long long* __restrict__ rmax,
-                                                unsigned long long* __restrict__ cmax, const int* __restrict__ done) {
+                                                unsigned long long* __restrict__ cmax, const int* __restrict__ done,
+                                                int f32_norms) {
     grid_dependency_wait();
     if (done && *done) return;
     __shared__ double red[8];
@@ -411,6 +426,7 @@ __global__ void __launch_bounds__(256, 4) k_map(const double* X, double* T, cons
             continue;
         }
         double acc = 0.0;
+        float accf = 0.f;
         unsigned long long cmx = 0;
 #pragma unroll 1
         for (int q0 = 0; q0 < TS::kPer; q0 += TS::kBatch) {
@@ -427,7 +443,12 @@ __global__ void __launch_bounds__(256, 4) k_map(const double* X, double* T, cons
             // off the diagonal no entry takes c0: one multiply, or its exact bit form for alpha = 1
             const double v = (i == j && gi == gj && gi < n) ? fma(c1, xv, c0) : (half_neg ? neg_half(xv) : c1 * xv);
             t[idx] = v;
-            acc = fma(v, v, acc);
+            if (f32_norms) {
+                const float f = f32_of_bits((unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull);
+                accf = fmaf(f, f, accf);
+            } else {
+                acc = fma(v, v, acc);
+            }
             if (NB == 64 && rmax) {
                 // 64-wide tiles: this thread keeps column threadIdx.x & 63, and the row's 64 entries sit in
                 // two consecutive warps; the maxima feed only the slicing exponents, so the upper 32 bits
@@ -448,26 +469,26 @@ __global__ void __launch_bounds__(256, 4) k_map(const double* X, double* T, cons
                 if (mx) atomicMax(cmax + (size_t)j * NB + threadIdx.x, mx);
             }
         }
-        const double s = block_sum_256(acc, red);
+        const double s = block_sum_256(f32_norms ? (double)accf : acc, red);
         if (threadIdx.x == 0) leafT[tile] = s;
     }
 }
 
 void launch_map(const double* X, const double* leafX, TileMat T, const Geometry& g, int map, const double* trace_part,
-                bool maxima, const int* done, cudaStream_t st) {
+                bool maxima, const int* done, cudaStream_t st, bool f32_norms) {
     // one resident wave (four 256-thread blocks per SM), so a dependent launch never waits on a later wave
     const int grid = std::min(device_sm_count() * 4, g.m * g.m);
     unsigned long long* rmax = maxima ? T.rmax : nullptr;
     unsigned long long* cmax = maxima ? T.cmax : nullptr;
     if (g.nb == 32)
         launch_dependent(k_map<32>, dim3(grid), dim3(256), 0, st, X, T.t, leafX, T.tree, g.n, g.m, map, trace_part,
-                         rmax, cmax, done);
+                         rmax, cmax, done, f32_norms ? 1 : 0);
     else if (g.nb == 64)
         launch_dependent(k_map<64>, dim3(grid), dim3(256), 0, st, X, T.t, leafX, T.tree, g.n, g.m, map, trace_part,
-                         rmax, cmax, done);
+                         rmax, cmax, done, f32_norms ? 1 : 0);
     else
         launch_dependent(k_map<128>, dim3(grid), dim3(256), 0, st, X, T.t, leafX, T.tree, g.n, g.m, map, trace_part,
-                         rmax, cmax, done);
+                         rmax, cmax, done, f32_norms ? 1 : 0);
     note_launch();
 }
 

@@ -922,7 +922,8 @@ static int enqueue_prologue(Plan* p, const double* dS, int n, const spamm_opts& 
 
     // X0 = s in buf 0: Y0 of the dual channel, the constant s of the single channel
     const TileMat X0 = p->buf[0];
-    launch_pack(dS, n, g, mu_ptr, rc, X0, st);
+    // the tensor-core path's tile norms are FP32 sums (they only steer its culls)
+    launch_pack(dS, n, g, mu_ptr, rc, X0, st, p->emu);
     launch_tree(g, X0.tree, nullptr, st);
     if (side) {
         cudaEventRecord(p->ev_norm[0], st);
@@ -930,7 +931,7 @@ static int enqueue_prologue(Plan* p, const double* dS, int n, const spamm_opts& 
     }
     if (p->emu) prepare_emu(p, X0, xs, tau_min);
     if (o.map == SPAMM_MAP_SCALED) launch_trace_parts(X0.t, g, p->trace_part, st);
-    launch_map(X0.t, X0.tree, sb->Tb, g, o.map, p->trace_part, false, nullptr, st);
+    launch_map(X0.t, X0.tree, sb->Tb, g, o.map, p->trace_part, false, nullptr, st, p->emu);
     launch_tree(g, sb->Tb.tree, nullptr, st);
     if (p->emu) prepare_emu(p, sb->Tb, st, tau_min);
     // the first culls read Z0's quadtree (its slicing event follows the tree on the same stream)

@@ -274,9 +274,9 @@ void enqueue_setup(Batch* b, BatchMat& M, double mu_rel, cudaStream_t st) {
     launch_gershgorin(M.S, g.n, mu_ptr, M.rowsum, c, st);
     launch_scale_consts(c, sqc, rc, rsqc, st);
     const TileMat &X0 = M.buf[0], &Z0 = M.buf[1], &T0 = M.buf[2];
-    launch_pack(M.S, g.n, g, mu_ptr, rc, X0, st);
+    launch_pack(M.S, g.n, g, mu_ptr, rc, X0, st, b->emu);  // FP32 tile norms on the tensor-core path, as one solve
     launch_tree(g, X0.tree, nullptr, st);
-    launch_map(X0.t, X0.tree, T0, g, SPAMM_MAP_NS, M.trace_part, false, nullptr, st);
+    launch_map(X0.t, X0.tree, T0, g, SPAMM_MAP_NS, M.trace_part, false, nullptr, st, b->emu);
     launch_tree(g, T0.tree, nullptr, st);
     launch_identity(g, Z0, st);
     launch_tree(g, Z0.tree, nullptr, st);

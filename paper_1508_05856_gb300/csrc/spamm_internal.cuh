@@ -117,8 +117,9 @@ void launch_transpose_rm(const double* A, double* T, int n, cudaStream_t st);
 void launch_scale_mu(const double* c0, double mu_rel, double* mu_out, cudaStream_t st);
 // Row-major src -> tile-major dst with leaf norms.  When recip_c != null:
 // dst = (src + mu delta) * (*recip_c), the scaling by the once-rounded 1/c.  Edge padding is zero.
+// f32_norms (scaled 64 x 64 packs): the leaf norms are FP32 sums of squares (f32_of_bits).
 void launch_pack(const double* src, int n, const Geometry& g, const double* mu, const double* recip_c,
-                 TileMat dst, cudaStream_t st);
+                 TileMat dst, cudaStream_t st, bool f32_norms = false);
 // trace_part[i] = logical trace of diagonal tile (i, i) of a packed matrix.
 void launch_trace_parts(const double* X, const Geometry& g, double* trace_part, cudaStream_t st);
 // T = h_alpha[eps I + (1 - 2 eps) X] elementwise on tiles (logical identity):
@@ -126,8 +127,9 @@ void launch_trace_parts(const double* X, const Geometry& g, double* trace_part, 
 // t = (n - sum trace_part)/n).  X may be T.t (in place; leafX then T.tree).
 // Writes T's leaf norms and, with `maxima`, accumulates T's row/column
 // maxima into T.rmax/T.cmax (which must be zero).  Skipped once *done is set.
+// f32_norms: T's leaf norms are FP32 sums of squares (f32_of_bits).
 void launch_map(const double* X, const double* leafX, TileMat T, const Geometry& g, int map, const double* trace_part,
-                bool maxima, const int* done, cudaStream_t st);
+                bool maxima, const int* done, cudaStream_t st, bool f32_norms = false);
 // Plane-diagonal profile of one product's task lists (counts, jlist): adds
 // to lens[(*iter * 3 + which) * 3 * bins + q * bins + d] the triples (i,j,k)
 // at distance d from plane q (|i-j|, |j-k|, |i-k|; d clamped to bins-1).
@@ -192,6 +194,18 @@ __host__ __device__ inline int tile_bucket(int cnt) {
     return cnt >= 16 ? 0 : cnt >= 8 ? 1 : cnt >= 4 ? 2 : cnt >= 2 ? 3 : 4;
 }
 #ifdef __CUDACC__
+// |v| as FP32 from the IEEE bits b of |v|, its mantissa cut to 23 bits (relative error below 2^-23); 0 for
+// zero and for magnitudes outside FP32's normal range.  On the tensor-core path the per-tile sums of
+// squares are taken in FP32: they only steer the cull, and a relative error near 1e-6 in a tile norm moves
+// a keep decision only for pairs that sit that close to the threshold.  Their squares overflow for
+// |v| >= 2^64, far above the magnitudes of the scaled iteration.
+__device__ __forceinline__ float f32_of_bits(unsigned long long b) {
+    const unsigned hw = (unsigned)(b >> 32);
+    const int E = (int)(hw >> 20);
+    // the low 9 exponent bits and the leading 23 mantissa bits, the bias moved from 1023 to 127 (mod 2^32)
+    const unsigned f = __funnelshift_r((unsigned)b, hw, 29) - (896u << 23);
+    return (E > 896 && E < 1151) ? __uint_as_float(f) : 0.f;
+}
 // Number of listed tiles, and the id of the t-th one (buckets in order).
 __device__ __forceinline__ int listed_total(const int* tile_count, int buckets) {
     int n = 0;
