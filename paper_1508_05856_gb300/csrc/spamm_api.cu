@@ -698,13 +698,17 @@ static void product(Plan* p, const TileMat& A, const TileMat& B, TileMat& C, dou
 // tau_min > 0: every product that reads M culls at tau >= tau_min, so the tiles below 0.999 tau_min^2 of M's
 // squared norm are never read (a kept pair has nu_a nu_b >= tau^2 nu_A nu_B with nu_b <= nu_B; the factor
 // leaves a margin far above the rounding of that test) and are not sliced.  M's quadtree must be complete.
+static void slice_emu(Plan* p, const TileMat& M, cudaStream_t st, double tau_min) {
+    const Geometry& g = p->g;
+    launch_slice(M.t, M.tree, nullptr, M.rmax, M.cmax, M.sliceA, M.sliceB, g, nullptr, nullptr, nullptr, st,
+                 tau_min > 0.0 ? M.tree + g.off[0] : nullptr, 0.999 * tau_min * tau_min);
+    mark_sliced(p, M, st);
+}
 static void prepare_emu(Plan* p, const TileMat& M, cudaStream_t st, double tau_min = 0.0) {
     const Geometry& g = p->g;
     cudaMemsetAsync(M.rmax, 0, 2 * (size_t)g.m * g.nb * sizeof(unsigned long long), st);
     launch_rowcol_max(M.t, g, M.rmax, M.cmax, st);
-    launch_slice(M.t, M.tree, nullptr, M.rmax, M.cmax, M.sliceA, M.sliceB, g, nullptr, nullptr, nullptr, st,
-                 tau_min > 0.0 ? M.tree + g.off[0] : nullptr, 0.999 * tau_min * tau_min);
-    mark_sliced(p, M, st);
+    slice_emu(p, M, st, tau_min);
 }
 
 // Every slicing stream of this call joins the call's stream (before the outputs are read, and before a
@@ -931,9 +935,11 @@ static int enqueue_prologue(Plan* p, const double* dS, int n, const spamm_opts& 
     }
     if (p->emu) prepare_emu(p, X0, xs, tau_min);
     if (o.map == SPAMM_MAP_SCALED) launch_trace_parts(X0.t, g, p->trace_part, st);
-    launch_map(X0.t, X0.tree, sb->Tb, g, o.map, p->trace_part, false, nullptr, st, p->emu);
+    // on the tensor-core path the map also takes T0's row and column maxima
+    if (p->emu) cudaMemsetAsync(sb->Tb.rmax, 0, 2 * (size_t)g.m * g.nb * sizeof(unsigned long long), st);
+    launch_map(X0.t, X0.tree, sb->Tb, g, o.map, p->trace_part, p->emu, nullptr, st, p->emu);
     launch_tree(g, sb->Tb.tree, nullptr, st);
-    if (p->emu) prepare_emu(p, sb->Tb, st, tau_min);
+    if (p->emu) slice_emu(p, sb->Tb, st, tau_min);
     // the first culls read Z0's quadtree (its slicing event follows the tree on the same stream)
     if (side) cudaStreamWaitEvent(st, sb->Zb.sliced, 0);
     if (o.channel == SPAMM_CHANNEL_SINGLE) {
