@@ -276,7 +276,9 @@ void enqueue_setup(Batch* b, BatchMat& M, double mu_rel, cudaStream_t st) {
     const TileMat &X0 = M.buf[0], &Z0 = M.buf[1], &T0 = M.buf[2];
     launch_pack(M.S, g.n, g, mu_ptr, rc, X0, st, b->emu);  // FP32 tile norms on the tensor-core path, as one solve
     launch_tree(g, X0.tree, nullptr, st);
-    launch_map(X0.t, X0.tree, T0, g, SPAMM_MAP_NS, M.trace_part, false, nullptr, st, b->emu);
+    // the tensor-core path takes T0's row and column maxima in the map
+    if (b->emu) cudaMemsetAsync(T0.rmax, 0, 2 * (size_t)g.m * g.nb * sizeof(unsigned long long), st);
+    launch_map(X0.t, X0.tree, T0, g, SPAMM_MAP_NS, M.trace_part, b->emu, nullptr, st, b->emu);
     launch_tree(g, T0.tree, nullptr, st);
     launch_identity(g, Z0, st);
     launch_tree(g, Z0.tree, nullptr, st);
@@ -284,8 +286,10 @@ void enqueue_setup(Batch* b, BatchMat& M, double mu_rel, cudaStream_t st) {
     const double tau_min = std::min(M.tau, M.tau_s);
     if (b->emu)
         for (const TileMat* P : {&X0, &T0, &Z0}) {
-            cudaMemsetAsync(P->rmax, 0, 2 * (size_t)g.m * g.nb * sizeof(unsigned long long), st);
-            launch_rowcol_max(P->t, g, P->rmax, P->cmax, st);
+            if (P != &T0) {
+                cudaMemsetAsync(P->rmax, 0, 2 * (size_t)g.m * g.nb * sizeof(unsigned long long), st);
+                launch_rowcol_max(P->t, g, P->rmax, P->cmax, st);
+            }
             launch_slice(P->t, P->tree, nullptr, P->rmax, P->cmax, P->sliceA, P->sliceB, g, nullptr, nullptr,
                          nullptr, st, tau_min > 0.0 ? P->tree + g.off[0] : nullptr, 0.999 * tau_min * tau_min);
         }
