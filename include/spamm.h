@@ -105,8 +105,9 @@ extern "C" {
                                    no residual and no profile; otherwise as
                                    SPAMM_SCHED_BRANCHES)                       */
 #define SPAMM_SCHED_AUTO 2      /* chosen per device, n, arithmetic, leaf and
-                                   decade of tau by timing one solve of the
-                                   call's own input with each (cached)         */
+                                   decade of tau by timing the call's own
+                                   input: three solves with each, alternating,
+                                   the faster minimum kept (cached)            */
 
 /* ---- order of the two channel products --------------------------------- */
 #define SPAMM_ORDER_PAPER 0       /* Y <- T Y, Z <- Z T, X <- Y Z (as printed)  */
