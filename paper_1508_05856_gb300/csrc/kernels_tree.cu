@@ -244,8 +244,9 @@ __device__ __forceinline__ double pack_tile(const double* __restrict__ src, int 
 // and each thread touches a single tile (t / 64); sixteen independent loads at a time.  The leaf norm of a
 // tile is the sum over its two warps of the per-thread sums of squares (rows in order), fixed order.
 // kF32 (the tensor-core path): the sums of squares in FP32 from the entries' bits, so the FP64 pipe does one
-// multiply per entry instead of two operations.
-template <bool kScale, bool kF32>
+// multiply per entry instead of two operations.  kShift: add mu on the diagonal (a compile-time switch, so
+// that without a shift no entry carries a predicated add).
+template <bool kScale, bool kF32, bool kShift>
 __device__ __forceinline__ void pack_band64(const double* __restrict__ src, int n, int m, int i, int jb, double mu,
                                             double rc, double* __restrict__ dst, double* __restrict__ leaf,
                                             double* red) {
@@ -270,7 +271,7 @@ __device__ __forceinline__ void pack_band64(const double* __restrict__ src, int 
             const int gi = i * 64 + r0 + u;
             double x = v[u];
             if (kScale && colok && gi < n) {
-                if (gi == gj) x += mu;
+                if (kShift && gi == gj) x += mu;
                 x = x * rc;
             }
             if (j < m) d[(r0 + u) * 64 + c] = x;
@@ -296,10 +297,16 @@ __global__ void __launch_bounds__(256) k_pack_band64(const double* __restrict__ 
     __shared__ double red[8];
     const int i = blockIdx.x / bands, jb = blockIdx.x - (blockIdx.x / bands) * bands;
     if (rc_dev) {
-        if (f32_norms) pack_band64<true, true>(src, n, m, i, jb, mu_dev ? *mu_dev : 0.0, *rc_dev, dst, leaf, red);
-        else pack_band64<true, false>(src, n, m, i, jb, mu_dev ? *mu_dev : 0.0, *rc_dev, dst, leaf, red);
+        const double rc = *rc_dev;
+        if (mu_dev) {
+            if (f32_norms) pack_band64<true, true, true>(src, n, m, i, jb, *mu_dev, rc, dst, leaf, red);
+            else pack_band64<true, false, true>(src, n, m, i, jb, *mu_dev, rc, dst, leaf, red);
+        } else {
+            if (f32_norms) pack_band64<true, true, false>(src, n, m, i, jb, 0.0, rc, dst, leaf, red);
+            else pack_band64<true, false, false>(src, n, m, i, jb, 0.0, rc, dst, leaf, red);
+        }
     } else {
-        pack_band64<false, false>(src, n, m, i, jb, 0.0, 1.0, dst, leaf, red);
+        pack_band64<false, false, false>(src, n, m, i, jb, 0.0, 1.0, dst, leaf, red);
     }
 }
 
@@ -382,6 +389,53 @@ __device__ __forceinline__ double neg_half(double x) {
     return -0.5 * x;
 }
 
+// The entries of one tile of the map, thread t taking t + 256 q: T = c1 X + c0 I (kHalf: c1 = -1/2, the
+// entries off the diagonal from their bits), the thread's sum of squares (FP32 from the bits when f32 is
+// set, then widened) and, with rmax, the row maxima by warp reductions and the thread's column maximum.
+template <int NB, bool kHalf, bool kDiag>
+__device__ __forceinline__ double map_entries(const double* x, double* t, int i, int j, int n, double c0, double c1,
+                                              bool f32, unsigned long long* __restrict__ rmax, int lane,
+                                              unsigned long long& cmx) {
+    using TS = TileSplit<NB, 8>;
+    double acc = 0.0;
+    float accf = 0.f;
+#pragma unroll 1
+    for (int q0 = 0; q0 < TS::kPer; q0 += TS::kBatch) {
+        // a batch of independent loads first (in place, each thread reads its entries before writing them)
+        double xb[TS::kBatch];
+#pragma unroll
+        for (int u = 0; u < TS::kBatch; ++u) xb[u] = x[threadIdx.x + 256 * (q0 + u)];
+#pragma unroll
+        for (int u = 0; u < TS::kBatch; ++u) {
+            const int idx = threadIdx.x + 256 * (q0 + u);
+            const int r = idx / NB, cc = idx % NB;
+            const double xv = xb[u];
+            double v = kHalf ? neg_half(xv) : c1 * xv;
+            if (kDiag) {
+                const int gi = i * NB + r, gj = j * NB + cc;
+                if (gi == gj && gi < n) v = fma(c1, xv, c0);
+            }
+            t[idx] = v;
+            if (f32) {
+                const float f = f32_of_bits((unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull);
+                accf = fmaf(f, f, accf);
+            } else {
+                acc = fma(v, v, acc);
+            }
+            if (NB == 64 && rmax) {
+                // 64-wide tiles: this thread keeps column threadIdx.x & 63, and the row's 64 entries sit in
+                // two consecutive warps; the maxima feed only the slicing exponents, so the upper 32 bits
+                // (sign cleared) carry what is needed
+                const unsigned long long vb = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+                cmx = max(cmx, vb);
+                const unsigned rm = __reduce_max_sync(0xffffffffu, (unsigned)(vb >> 32));
+                if (lane == 0 && rm) atomicMax(rmax + (size_t)i * NB + r, (unsigned long long)rm << 32);
+            }
+        }
+    }
+    return f32 ? (double)accf : acc;
+}
+
 template <int NB>
 __global__ void __launch_bounds__(256, 4) k_map(const double* X, double* T, const double* leafX, double* leafT,
                                                 int n, int m, int map, const double* __restrict__ trace_part,
@@ -410,7 +464,6 @@ __global__ void __launch_bounds__(256, 4) k_map(const double* X, double* T, cons
     const double c0 = coef[0], c1 = coef[1];
     // alpha = 1: c1 = -1/2 exactly, so the entries off the diagonal are -x/2 from their bits
     const bool half_neg = map != SPAMM_MAP_SCALED;
-    using TS = TileSplit<NB, 8>;
     constexpr int ne = NB * NB;
     const int lane = threadIdx.x & 31;
     for (int tile = blockIdx.x; tile < m * m; tile += gridDim.x) {
@@ -426,39 +479,15 @@ __global__ void __launch_bounds__(256, 4) k_map(const double* X, double* T, cons
             continue;
         }
         double acc = 0.0;
-        float accf = 0.f;
         unsigned long long cmx = 0;
-#pragma unroll 1
-        for (int q0 = 0; q0 < TS::kPer; q0 += TS::kBatch) {
-          // a batch of independent loads first (in place, each thread reads its entries before writing them)
-          double xb[TS::kBatch];
-#pragma unroll
-          for (int u = 0; u < TS::kBatch; ++u) xb[u] = x[threadIdx.x + 256 * (q0 + u)];
-#pragma unroll
-          for (int u = 0; u < TS::kBatch; ++u) {
-            const int idx = threadIdx.x + 256 * (q0 + u);
-            const int r = idx / NB, cc = idx % NB;
-            const int gi = i * NB + r, gj = j * NB + cc;
-            const double xv = xb[u];
-            // off the diagonal no entry takes c0: one multiply, or its exact bit form for alpha = 1
-            const double v = (i == j && gi == gj && gi < n) ? fma(c1, xv, c0) : (half_neg ? neg_half(xv) : c1 * xv);
-            t[idx] = v;
-            if (f32_norms) {
-                const float f = f32_of_bits((unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull);
-                accf = fmaf(f, f, accf);
-            } else {
-                acc = fma(v, v, acc);
-            }
-            if (NB == 64 && rmax) {
-                // 64-wide tiles: this thread keeps column threadIdx.x & 63, and the row's 64 entries sit in
-                // two consecutive warps; the maxima feed only the slicing exponents, so the upper 32 bits
-                // (sign cleared) carry what is needed
-                const unsigned long long vb = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
-                cmx = max(cmx, vb);
-                const unsigned rm = __reduce_max_sync(0xffffffffu, (unsigned)(vb >> 32));
-                if (lane == 0 && rm) atomicMax(rmax + (size_t)i * NB + r, (unsigned long long)rm << 32);
-            }
-          }
+        // every switch of the entry loop is uniform over the tile, so each case is its own loop: no entry of
+        // an off-diagonal tile carries a predicated fused multiply-add, and alpha = 1 no multiply
+        if (i == j) {
+            if (half_neg) acc = map_entries<NB, true, true>(x, t, i, j, n, c0, c1, f32_norms, rmax, lane, cmx);
+            else acc = map_entries<NB, false, true>(x, t, i, j, n, c0, c1, f32_norms, rmax, lane, cmx);
+        } else {
+            if (half_neg) acc = map_entries<NB, true, false>(x, t, i, j, n, c0, c1, f32_norms, rmax, lane, cmx);
+            else acc = map_entries<NB, false, false>(x, t, i, j, n, c0, c1, f32_norms, rmax, lane, cmx);
         }
         if (NB == 64 && rmax) {
             cm_sh[threadIdx.x >> 6][threadIdx.x & 63] = cmx;
@@ -469,7 +498,7 @@ __global__ void __launch_bounds__(256, 4) k_map(const double* X, double* T, cons
                 if (mx) atomicMax(cmax + (size_t)j * NB + threadIdx.x, mx);
             }
         }
-        const double s = block_sum_256(f32_norms ? (double)accf : acc, red);
+        const double s = block_sum_256(acc, red);
         if (threadIdx.x == 0) leafT[tile] = s;
     }
 }
