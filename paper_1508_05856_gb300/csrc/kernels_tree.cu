@@ -1045,11 +1045,19 @@ template <int NB, bool kScale>
 __device__ __forceinline__ void unpack_tile(const double* __restrict__ s, bool zero, int n, int i, int j, double f,
                                             double* __restrict__ dst) {
     using TS = TileSplit<NB, 16>;
+    if (zero) {
+        // an all-zero tile (its scale factor is positive, so +0 either way) costs stores only
+        for (int idx = threadIdx.x; idx < NB * NB; idx += 256) {
+            const int gi = i * NB + idx / NB, gj = j * NB + idx % NB;
+            if (gi < n && gj < n) dst[(size_t)gi * n + gj] = 0.0;
+        }
+        return;
+    }
 #pragma unroll 1
     for (int q0 = 0; q0 < TS::kPer; q0 += TS::kBatch) {
         double v[TS::kBatch];
 #pragma unroll
-        for (int u = 0; u < TS::kBatch; ++u) v[u] = zero ? 0.0 : s[threadIdx.x + 256 * (q0 + u)];
+        for (int u = 0; u < TS::kBatch; ++u) v[u] = s[threadIdx.x + 256 * (q0 + u)];
 #pragma unroll
         for (int u = 0; u < TS::kBatch; ++u) {
             const int idx = threadIdx.x + 256 * (q0 + u);
