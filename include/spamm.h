@@ -366,6 +366,19 @@ int spamm_server_destroy(spamm_server* server);
  */
 int spamm_test_expire_next_wait(long long polls);
 
+/*
+ * Layout check of the tensor-core leaf product (SPAMM_EMU64).  A product
+ * whose output tile holds more than one accumulator chunk of tasks can run with
+ * the chunks at alternating tensor-memory columns, so that the next chunk's
+ * products start while part of this chunk's accumulator is still being read
+ * out.  Both layouts give the same result bits.  mode = -1: the library's
+ * choice (alternating from 128 tiles per side, single products only);
+ * 0: never; 1: always.  Process-wide; affects products enqueued (or graphs
+ * captured) after the call, so release cached plans (spamm_release) before
+ * comparing.  SPAMM_ERR_ARG for mode outside -1..1.
+ */
+int spamm_test_emu_alternate(int mode);
+
 /* Message for the calling thread's last failure ("" if none). */
 const char* spamm_last_error(void);
 

@@ -48,6 +48,7 @@ HEADER_SYMBOLS = ["spamm_opts_init", "spamm_autotune_leaf", "spamm_multiply", "s
                   "spamm_sqrt_invsqrt_batched", "spamm_norm_tree", "spamm_cull", "spamm_last_error", "spamm_strerror",
                   "spamm_release",
                   "spamm_kernel_launches", "spamm_version", "spamm_multiply_noalloc", "spamm_test_expire_next_wait",
+                  "spamm_test_emu_alternate",
                   "spamm_server_create",
                   "spamm_server_submit", "spamm_server_poll", "spamm_server_wait", "spamm_server_destroy"]
 
@@ -144,6 +145,8 @@ def lib(build_if_missing: bool = True):
         L.spamm_server_destroy.restype = ip
         L.spamm_test_expire_next_wait.argtypes = [ctypes.c_longlong]
         L.spamm_test_expire_next_wait.restype = ip
+        L.spamm_test_emu_alternate.argtypes = [ip]
+        L.spamm_test_emu_alternate.restype = ip
         L.spamm_kernel_launches.argtypes = []
         L.spamm_kernel_launches.restype = ctypes.c_longlong
         L.spamm_version.argtypes = []

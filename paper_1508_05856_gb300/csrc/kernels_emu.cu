@@ -42,6 +42,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "spamm_internal.cuh"
 #include "tc_ptx.cuh"
@@ -488,6 +489,94 @@ __device__ __forceinline__ void flush_groups(uint32_t lane_col_base, int half, l
     }
 }
 
+// The alternating layout (kernel instances with kAlt): the chunks of a tile of more than one chunk sit at
+// TMEM columns 0-383 and 128-511 in turn, so the next chunk overwrites only four of this chunk's six
+// groups.  The epilogue reads those four first and releases the accumulator (release()), then reads the
+// other two while the next chunk's products already run: with many tasks per tile the MMA warp then waits
+// for two thirds of a flush instead of all of it.  kNextHigh: this chunk sits at 0-383 and the next at
+// 128-511 (groups 2-5 are shared); otherwise this chunk sits at 128-511 and the next at 0-383 (groups 0-3
+// are shared).  The integer sums are the same in any order; the groups of diagonal >= 4 are combined in
+// FP32 exactly as flush_groups does, so both layouts give the same bits.
+// Each load completes before the next is issued: overlapping them as flush_groups does spills registers in
+// this instance and was slower.
+__device__ __forceinline__ void tmem_ld16_now(uint32_t taddr, uint32_t (&r)[16]) {
+    ptx::tmem_ld16(taddr, r);
+    ptx::tmem_ld_wait(r);
+}
+template <bool kNextHigh, typename Release>
+__device__ __forceinline__ void flush_groups_split(uint32_t b, int half, long long (&acc)[16], Release release) {
+    uint32_t ra[16], rb[16];
+    if (kNextHigh) {
+        if (half == 0) {
+            tmem_ld16_now(col16(b, 2, 0), ra);
+            flush_exact<16>(ra, 0, acc);
+            tmem_ld16_now(col16(b, 3, 0), ra);
+            flush_exact<8>(ra, 0, acc);
+            tmem_ld16_now(col16(b, 4, 0), ra);
+            tmem_ld16_now(col16(b, 5, 0), rb);
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+                acc[c] += (long long)__float2int_rn(fmaf(__uint_as_float(rb[c]), 0x1p-8f, __uint_as_float(ra[c])));
+            release();
+            tmem_ld16_now(col16(b, 0, 0), ra);
+            flush_exact<32>(ra, 0, acc);
+            tmem_ld16_now(col16(b, 1, 0), ra);
+            flush_exact<24>(ra, 0, acc);
+        } else {
+            tmem_ld16_now(col16(b, 2, 0), ra);
+            flush_exact<8>(ra, 0, acc);
+            tmem_ld16_now(col16(b, 3, 0), rb);
+            tmem_ld16_now(col16(b, 4, 0), ra);
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+                rb[c] = __float_as_uint(fmaf(__uint_as_float(ra[c]), 0x1p-8f, __uint_as_float(rb[c])));
+            tmem_ld16_now(col16(b, 5, 0), ra);
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+                acc[c] += (long long)__float2int_rn(fmaf(__uint_as_float(ra[c]), 0x1p-16f, __uint_as_float(rb[c])));
+            release();
+            tmem_ld16_now(col16(b, 0, 0), ra);
+            flush_exact<24>(ra, 0, acc);
+            tmem_ld16_now(col16(b, 1, 0), ra);
+            flush_exact<16>(ra, 0, acc);
+        }
+    } else {
+        if (half == 0) {
+            tmem_ld16_now(col16(b, 0, 0), ra);
+            flush_exact<32>(ra, 0, acc);
+            tmem_ld16_now(col16(b, 1, 0), ra);
+            flush_exact<24>(ra, 0, acc);
+            tmem_ld16_now(col16(b, 2, 0), ra);
+            flush_exact<16>(ra, 0, acc);
+            tmem_ld16_now(col16(b, 3, 0), ra);
+            flush_exact<8>(ra, 0, acc);
+            release();
+            tmem_ld16_now(col16(b, 4, 0), ra);
+            tmem_ld16_now(col16(b, 5, 0), rb);
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+                acc[c] += (long long)__float2int_rn(fmaf(__uint_as_float(rb[c]), 0x1p-8f, __uint_as_float(ra[c])));
+        } else {
+            tmem_ld16_now(col16(b, 0, 0), ra);
+            flush_exact<24>(ra, 0, acc);
+            tmem_ld16_now(col16(b, 1, 0), ra);
+            flush_exact<16>(ra, 0, acc);
+            tmem_ld16_now(col16(b, 2, 0), ra);
+            flush_exact<8>(ra, 0, acc);
+            tmem_ld16_now(col16(b, 3, 0), rb);  // diagonal 4 of the odd rows: kept for the FP32 combination
+            release();
+            tmem_ld16_now(col16(b, 4, 0), ra);
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+                rb[c] = __float_as_uint(fmaf(__uint_as_float(ra[c]), 0x1p-8f, __uint_as_float(rb[c])));
+            tmem_ld16_now(col16(b, 5, 0), ra);
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+                acc[c] += (long long)__float2int_rn(fmaf(__uint_as_float(ra[c]), 0x1p-16f, __uint_as_float(rb[c])));
+        }
+    }
+}
+
 // Polls of the waits that drain an aborted CTA's copies and products before it exits.
 constexpr long long kDrainPolls = 1ll << 22;
 
@@ -510,7 +599,7 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, vo
 // the MMA warp multiplies and the epilogue warps finish the tile before; the
 // tile id travels in the slot, and mbarriers order the roles.  The last CTA
 // to finish resets the ticket counters for the next launch.
-template <bool kBatched>
+template <bool kBatched, bool kAlt>
 __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
     grid_dependency_wait();
     if (a.done && *a.done) return;
@@ -728,8 +817,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
                 }
                 if (tile_sh[slot] < 0) break;
                 const int T = ntask_sh[slot];
+                uint32_t acc0 = tmem;  // kAlt: odd chunks of a tile sit 128 columns on
                 for (int t = 0; t < T && ok; ++t) {
                     const bool chunk_start = (t % kChunk) == 0;
+                    if (kAlt && chunk_start) acc0 = ((t / kChunk) & 1) ? tmem + 128u : tmem;
                     units += 12;  // twelve stacked (stack, slice) products per task
                     for (int h = 0; h < 2; ++h, ++H) {
                         const int s = (int)(H % NSTAGE);
@@ -754,10 +845,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
                         for (int ks = 0; ks < 2; ++ks) {
                             const uint32_t acc = fresh && ks == 0 ? 0u : 1u;
                             const uint64_t a = dA + ks * kDK, b = dB + ks * kDK;
-                            ptx::mma_f16(tmem, a, b, idesc256, acc);
-                            ptx::mma_f16(tmem + 256u, a, b + kDSl4, idesc128, acc);
-                            ptx::mma_f16(tmem + 128u, a + kDStack, b, idesc256, 1u);
-                            ptx::mma_f16(tmem + 256u, a + 2 * kDStack, b, idesc128, 1u);
+                            ptx::mma_f16(acc0, a, b, idesc256, acc);
+                            ptx::mma_f16(acc0 + 256u, a, b + kDSl4, idesc128, acc);
+                            ptx::mma_f16(acc0 + 128u, a + kDStack, b, idesc256, 1u);
+                            ptx::mma_f16(acc0 + 256u, a + 2 * kDStack, b, idesc128, 1u);
                         }
                         ptx::mma_commit(&bar_empty[s]);
                     }
@@ -811,10 +902,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
                     break;
                 }
                 ptx::tc_fence_after();
-                flush_groups(lane_col_base, half, acc);
-                ptx::tc_fence_before();
-                __syncwarp();
-                if (lane == 0) ptx::mbar_arrive(&bar_acce);
+                auto release = [&] {
+                    ptx::tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) ptx::mbar_arrive(&bar_acce);
+                };
+                // kAlt: chunk ck of the tile sits at columns 128 (ck & 1) onwards; the tile's next chunk (or the
+                // next tile's first, at 0) decides which groups it shares with this one
+                const int sel = kAlt ? ck & 1 : 0, next_sel = kAlt && ck + 1 < nchunks ? (ck + 1) & 1 : 0;
+                if (!kAlt || sel == next_sel) {
+                    flush_groups(lane_col_base, half, acc);
+                    release();
+                } else if (sel == 0) {
+                    flush_groups_split<true>(lane_col_base, half, acc, release);
+                } else {
+                    flush_groups_split<false>(lane_col_base + 128u, half, acc, release);
+                }
             }
             if (!ok) break;
             // stage both halves' 64-bit sums, then finish the tile element-parallel:
@@ -919,8 +1022,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_emu(const EmuArgs a) {
 size_t emu_slice_bytes_per_tile() { return emu::A_TILE_BYTES; }
 
 void emu_kernel_attributes() {
-    cudaFuncSetAttribute(emu::k_gemm_emu<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)emu::SMEM_DYN);
-    cudaFuncSetAttribute(emu::k_gemm_emu<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)emu::SMEM_DYN);
+    cudaFuncSetAttribute(emu::k_gemm_emu<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)emu::SMEM_DYN);
+    cudaFuncSetAttribute(emu::k_gemm_emu<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)emu::SMEM_DYN);
+    cudaFuncSetAttribute(emu::k_gemm_emu<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)emu::SMEM_DYN);
 }
 
 void launch_rowcol_max(const double* X, const Geometry& g, unsigned long long* rmax, unsigned long long* cmax,
@@ -949,6 +1053,16 @@ void launch_slice_batched(const ProdDesc* prods, const int* slice_items, int cap
                      (const unsigned long long*)nullptr, (uint8_t*)nullptr, (uint8_t*)nullptr, 0, slice_items,
                      slice_items + cap, all_done, prods, (const double*)nullptr, 0.0);
     note_launch();
+}
+
+// Which leaf-product layout a single product uses: the alternating one from 128 tiles per side (where this
+// library's product-heavy cases live: about 22 tasks per tile on the 3D Gaussian, against 3.4 on the KMS
+// headline, whose kernel stays the plain one); spamm_test_emu_alternate forces either.
+static std::atomic<int> g_emu_alt_mode{-1};
+void set_emu_alternate(int mode) { g_emu_alt_mode.store(mode < 0 ? -1 : (mode ? 1 : 0)); }
+bool emu_alternate(int m) {
+    const int mode = g_emu_alt_mode.load();
+    return mode < 0 ? m >= 128 : mode == 1;
 }
 
 void launch_gemm_emu(const Geometry& g, const TileMat& A, const TileMat& B, const TileMat& C, const int* counts,
@@ -989,7 +1103,10 @@ void launch_gemm_emu(const Geometry& g, const TileMat& A, const TileMat& B, cons
     a.poll_limit = 1ll << 22;
     a.stall_polls = stall_polls;
     const int grid = std::min(device_sm_count(), g.m * g.m);
-    launch_dependent(emu::k_gemm_emu<false>, dim3(grid), dim3(emu::kThreads), emu::SMEM_DYN, st, a);
+    if (emu_alternate(g.m))
+        launch_dependent(emu::k_gemm_emu<false, true>, dim3(grid), dim3(emu::kThreads), emu::SMEM_DYN, st, a);
+    else
+        launch_dependent(emu::k_gemm_emu<false, false>, dim3(grid), dim3(emu::kThreads), emu::SMEM_DYN, st, a);
     note_launch();
 }
 
@@ -1010,7 +1127,7 @@ void launch_gemm_emu_batched(const ProdDesc* prods, const int* tile_list, const 
     a.poll_limit = 1ll << 22;
     a.stall_polls = 0;
     const int grid = std::min(device_sm_count(), cap);
-    launch_dependent(emu::k_gemm_emu<true>, dim3(grid), dim3(emu::kThreads), emu::SMEM_DYN, st, a);
+    launch_dependent(emu::k_gemm_emu<true, false>, dim3(grid), dim3(emu::kThreads), emu::SMEM_DYN, st, a);
     note_launch();
 }
 

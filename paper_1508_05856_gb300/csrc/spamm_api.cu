@@ -1602,6 +1602,15 @@ int spamm_test_expire_next_wait(long long polls) {
     return SPAMM_OK;
 }
 
+int spamm_test_emu_alternate(int mode) {
+    if (mode < -1 || mode > 1) {
+        g_last_error = "mode must be -1, 0 or 1";
+        return SPAMM_ERR_ARG;
+    }
+    set_emu_alternate(mode);
+    return SPAMM_OK;
+}
+
 int spamm_multiply(const double* A, const double* B, double* C, int n, double tau, const spamm_opts* opts,
                    spamm_stats* stats) {
     try {

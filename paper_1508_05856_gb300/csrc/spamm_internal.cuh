@@ -375,6 +375,10 @@ void launch_slice(const double* X, const double* leaf, double* leaf_out, const u
 // the expired-wait path (error 5 in *err, no copy or product issued, tensor
 // memory freed, no tile handed to the slicing pass).
 // sched: two ints, zero before the first launch; the kernel leaves them zero.
+// Leaf-product layout of single products: alternating accumulator columns (true) or one fixed block.
+// mode -1 = by size, 0 = never, 1 = always.
+void set_emu_alternate(int mode);
+bool emu_alternate(int m);
 void launch_gemm_emu(const Geometry& g, const TileMat& A, const TileMat& B, const TileMat& C, const int* counts,
                      const int* jlist, const int* tile_list, const int* tile_count, EpiMode mode, double* trace_part,
                      int* sched, const int* done, int* err, double tau, cudaStream_t st, int buckets = 1,

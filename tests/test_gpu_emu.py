@@ -230,3 +230,30 @@ def test_expired_device_wait_returns_timeout_and_the_next_call_succeeds():
     x = torch.arange(1, 1025, device="cuda", dtype=torch.float64).sum()
     torch.cuda.synchronize()
     assert float(x) == 1024 * 1025 / 2
+
+
+@pytest.mark.parametrize("n,length", [(1000, 400.0), (2048, 900.0)])
+def test_alternating_accumulator_layout_gives_the_same_bits(n, length):
+    """The leaf kernel can place the accumulator chunks of one output tile at alternating tensor-memory
+    columns (the next chunk's products overlap the read-out of this one).  Tiles of one, two, three and more
+    chunks (7 tasks each) exercise every hand-over between the two positions; products and solves must come
+    out bit for bit as with the fixed position."""
+    A = dev(synth.decay_matrix(n, seed=31, length=length))
+    B = dev(synth.decay_matrix(n, seed=32, length=length))
+    S = dev(synth.gaussian_lattice(n, 0.7, seed=3))
+    out = {}
+    try:
+        for mode in (0, 1):
+            assert sp.lib().spamm_test_emu_alternate(mode) == 0
+            sp.release()
+            C, st = sp.multiply(A, B, 1e-10, leaf=64, precision=sp.EMU64)
+            Y, Z, s2 = sp.sqrt_invsqrt(S, 1e-10, 8, leaf=64, precision=sp.EMU64, raise_on=False)
+            out[mode] = (C, st["tasks_total"], Y, Z, s2["tasks_total"])
+    finally:
+        sp.lib().spamm_test_emu_alternate(-1)
+        sp.release()
+    assert sp.lib().spamm_test_emu_alternate(2) == -1
+    (C0, t0, Y0, Z0, k0), (C1, t1, Y1, Z1, k1) = out[0], out[1]
+    m = (n + 63) // 64
+    assert t0 == t1 and t0 > 7 * m * m, (t0, m)   # more than one chunk per tile on average
+    assert torch.equal(C0, C1) and torch.equal(Y0, Y1) and torch.equal(Z0, Z1) and k0 == k1
