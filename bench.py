@@ -1036,6 +1036,9 @@ def main():
     ap.add_argument("--no-oracle-error", action="store_true",
                     help="skip the oracle solves that give every result's error against the oracle")
     ap.add_argument("--c3", action="store_true", help="large 3D Gaussian configuration instead of the headline solve")
+    ap.add_argument("--emu-layout", choices=["auto", "fixed", "alternating"], default="auto",
+                    help="accumulator layout of the tensor-core leaf products (auto: alternating from 128 tiles "
+                         "per side); both give the same bits")
     ap.add_argument("--no-extra", action="store_true",
                     help="headline only: leave out the large, batched and served configurations")
     ap.add_argument("--c3-tau-default", type=float, default=1e-15,
@@ -1092,6 +1095,9 @@ def main():
     ws, rank, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, ws, rank)
+    if args.emu_layout != "auto" and args.impl != "reference":
+        import paper_1508_05856_gb300 as sp
+        sp.lib().spamm_test_emu_alternate(1 if args.emu_layout == "alternating" else 0)
     if args.c3:
         return run_c3(args, local)
     if args.product_rep:
