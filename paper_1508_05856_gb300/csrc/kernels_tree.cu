@@ -844,6 +844,42 @@ __device__ __forceinline__ int cull_tile(const TreeDev& td, const double* __rest
     return cnt;
 }
 
+// Up to 64 candidates (m <= 64), the list of cull_tile without its coarse pre-filter: every candidate's two
+// leaf norms are loaded at once, before the threshold's roots have arrived, so the test waits for one round
+// trip instead of one per chunk and level.  The list is the same: a coarse node is the rounded sum of its
+// non-negative children, so it is at least each of them, and the rounded product is monotone; a pair the
+// pre-filter would have skipped fails the leaf test too.
+struct LeafPre {
+    double a0, b0, a1, b1;
+};
+__device__ __forceinline__ LeafPre cull_preload(const double* __restrict__ treeA, const double* __restrict__ treeB,
+                                                int m, int i, int k, int lane) {
+    LeafPre p{0.0, 0.0, 0.0, 0.0};
+    if (lane < m) {
+        p.a0 = treeA[(size_t)i * m + lane];
+        p.b0 = treeB[(size_t)lane * m + k];
+    }
+    if (lane + 32 < m) {
+        p.a1 = treeA[(size_t)i * m + lane + 32];
+        p.b1 = treeB[(size_t)(lane + 32) * m + k];
+    }
+    return p;
+}
+__device__ __forceinline__ int cull_tile_small(const LeafPre& p, double thr, int m, int lane, int* __restrict__ out) {
+    const int et = biased_exponent(thr);
+    const bool k0 = lane < m && keep_pair(p.a0, p.b0, thr, et);
+    const unsigned b0 = __ballot_sync(0xffffffffu, k0);
+    if (k0) out[__popc(b0 & ((1u << lane) - 1u))] = lane;
+    int cnt = __popc(b0);
+    if (m > 32) {
+        const bool k1 = lane + 32 < m && keep_pair(p.a1, p.b1, thr, et);
+        const unsigned b1 = __ballot_sync(0xffffffffu, k1);
+        if (k1) out[cnt + __popc(b1 & ((1u << lane) - 1u))] = lane + 32;
+        cnt += __popc(b1);
+    }
+    return cnt;
+}
+
 // One warp per output tile (i, k), the task list by cull_tile.
 __global__ void __launch_bounds__(256) k_cull(TreeDev td, const double* __restrict__ treeA,
                                               const double* __restrict__ treeB, double tau, CullOut co,
@@ -859,12 +895,15 @@ __global__ void __launch_bounds__(256) k_cull(TreeDev td, const double* __restri
     const int m = td.m;
     const int wid = blockIdx.x * 8 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
+    const bool small = m <= 64;
+    const LeafPre pre = small && wid < m * m ? cull_preload(treeA, treeB, m, wid / m, wid % m, lane) : LeafPre{};
     const double thr = ((tau * tau) * treeA[td.off[0]]) * treeB[td.off[0]];
     int cnt = 0;
     bool listed = false;
     if (wid < m * m) {
         const int i = wid / m, k = wid - (wid / m) * m;
-        cnt = cull_tile(td, treeA, treeB, thr, i, k, lane, co.jlist + (size_t)wid * m);
+        int* const out = co.jlist + (size_t)wid * m;
+        cnt = small ? cull_tile_small(pre, thr, m, lane, out) : cull_tile(td, treeA, treeB, thr, i, k, lane, out);
         if (lane == 0) {
             co.counts[wid] = cnt;
             if (co.tile_list) {
@@ -940,12 +979,15 @@ __global__ void __launch_bounds__(256) k_cull_batched(const ProdDesc* __restrict
     const int wid = bt.y + warp;
     const double* treeA = d.Atree;
     const double* treeB = d.Btree;
+    const bool small = m <= 64;
+    const LeafPre pre = small && wid < m * m ? cull_preload(treeA, treeB, m, wid / m, wid % m, lane) : LeafPre{};
     const double thr = ((d.tau * d.tau) * treeA[td.off[0]]) * treeB[td.off[0]];
     int cnt = 0;
     bool listed = false;
     if (wid < m * m) {
         const int i = wid / m, k = wid - (wid / m) * m;
-        cnt = cull_tile(td, treeA, treeB, thr, i, k, lane, d.jlist + (size_t)wid * m);
+        int* const out = d.jlist + (size_t)wid * m;
+        cnt = small ? cull_tile_small(pre, thr, m, lane, out) : cull_tile(td, treeA, treeB, thr, i, k, lane, out);
         if (lane == 0) {
             d.counts[wid] = cnt;
             listed = cnt > 0 || (d.mode != EPI_PLAIN && i == k);
