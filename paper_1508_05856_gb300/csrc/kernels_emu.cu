@@ -25,6 +25,15 @@
 // the digit truncation leave an error of a few 2^{-48} per product term
 // relative to 2^{e_row + e_col}: a normwise FP64-class product.
 //
+// Method: this is an instance of the Ozaki scheme (Ozaki, Ogita, Oishi and
+// Rump, 2012: split each FP64 operand into slices that a low-precision unit
+// multiplies exactly, and sum the slice products at higher precision), in the
+// integer-slice form that shares one power of two per row of A and per
+// column of B (Ootomo, Ozaki and Yokota, 2024).  The digit width, the
+// balanced digits, the pair set, the stacking into M = 128 and the flush
+// schedule above are this library's own, fitted to FP16 inputs, FP32 TMEM
+// accumulators and 64 x 64 leaf tiles; so is the error model.
+//
 // Layout (no swizzle, K-major canonical core matrices of 8 rows x 16 bytes;
 // per K-half of 32, core (row_group, k_group) at ((row_group * 4 + k_group) *
 // 128) bytes, so the descriptors use LBO = 128 and SBO = 512):
