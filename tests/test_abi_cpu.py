@@ -122,3 +122,15 @@ def test_product_representation_rejects_bad_arguments_without_device():
     bad = (ctypes.c_double * 2)(0.1, float("nan"))
     assert L.spamm_invsqrt_product(buf, 4, 2, bad, 1e-3, 1e-5, 10, buf, its, ctypes.byref(o)) == -1
     assert L.spamm_invsqrt_product(None, 4, 2, mu, 1e-3, 1e-5, 10, buf, its, ctypes.byref(o)) == -1
+
+
+def test_test_hooks_reject_bad_arguments_without_device():
+    """The two check hooks validate their argument on the host; a valid call only records the request."""
+    L = sp.lib()
+    assert L.spamm_test_expire_next_wait(-1) == -1
+    assert L.spamm_test_expire_next_wait(0) == 0
+    for bad in (-2, 2, 7):
+        assert L.spamm_test_emu_alternate(bad) == -1
+        assert "mode" in sp.lib().spamm_last_error().decode()
+    for ok in (1, 0, -1):   # -1 last: the library's own choice again
+        assert L.spamm_test_emu_alternate(ok) == 0
